@@ -1,0 +1,348 @@
+"""Benchmark: sigma = H c throughput (determinants/s) on CAS(14e,14o), Ms=0.
+
+One step = one full sigma build (sigma_1 + sigma_2 + sigma_3 of Eq. 8) over
+the 11,778,624-determinant CI vector, with the tables and integrals resident
+on the device.  The reported value is whole-job throughput in Gdet/s.
+
+Timing: W untimed warm-up steps, then K steps bracketed by a barrier and
+cuda synchronize, timed with CUDA events on the launching stream, max over
+ranks.  The inputs rotate through a ring of vectors whose total size exceeds
+the 129 MB L2, so no step reads its input from L2.
+
+Extra keys: per-kernel roofline of the dominant kernel, the oracle on the host
+cores (cpu_baseline), end-to-end throughput with host buffers (e2e), the FP32
+sigma rate, and Davidson time-to-1e-8 Eh (FP64 and mixed).
+
+``--impl reference`` times the CPU oracle instead (the only reference this
+work has: a plain FP64 CPU implementation written from the paper).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import fci_inputs as fi  # noqa: E402
+
+WORKLOADS = {"cas14": (14, 7, 7, 100), "cas16": (16, 8, 8, 100), "cas12": (12, 6, 6, 100), "cas8": (8, 4, 4, 40)}
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), nominal
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "_fallback": True}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "100"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def dist_setup(n_gpus):
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(norb, na, nb, h1, eri, c, target_s=15.0, seed=0):
+    """The oracle as it stands, on a bounded random sample of sigma rows."""
+    import oracle
+
+    N = c.size
+    rng = np.random.default_rng(seed)
+    pilot = rng.integers(0, N, 256)
+    t = time.perf_counter()
+    oracle.sigma_rows(norb, na, nb, h1, eri, c, pilot)
+    dt = max(time.perf_counter() - t, 1e-3)
+    nrows = int(min(N, max(256, 256 * target_s / dt)))
+    rows = rng.integers(0, N, nrows)
+    t = time.perf_counter()
+    oracle.sigma_rows(norb, na, nb, h1, eri, c, rows)
+    dt = time.perf_counter() - t
+    return {"value": nrows / dt / 1e9, "unit": "Gdet/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{nrows} random sigma rows of CAS({na + nb}e,{norb}o), direct Slater-Condon sum, FP64, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    norb, na, nb, rank_eri = WORKLOADS[args.workload]
+    h1, eri = fi.make_integrals(norb, rank_eri)
+    import oracle
+
+    N = oracle.ndet(norb, na, nb)
+    c = fi.make_vector(N)
+    rng = np.random.default_rng(1)
+    rows_per_step = 2000
+    for _ in range(args.warmup):
+        oracle.sigma_rows(norb, na, nb, h1, eri, c, rng.integers(0, N, 256))
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.sigma_rows(norb, na, nb, h1, eri, c, rng.integers(0, N, rows_per_step))
+    dt = time.perf_counter() - t
+    value = rows_per_step * args.steps / dt / 1e9
+    out = {"impl": "reference", "metric": "sigma=Hc throughput", "value": value, "unit": "Gdet/s",
+           "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"CAS({na + nb}e,{norb}o) Ms=0 sigma, {N} determinants, Cholesky rank {rank_eri}",
+                      "step": f"{rows_per_step} sigma rows per step (bounded sample)"},
+           "cpu_baseline": {"value": value, "unit": "Gdet/s", "cores": oracle.num_threads(), "kind": "oracle",
+                            "sample": f"{rows_per_step} random rows per step, {args.steps} steps"},
+           "e2e": {"value": value, "unit": "Gdet/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def time_sigma_ring(pkg, ctx, vecs, outs, steps, warmup, stream, world):
+    import torch
+
+    for i in range(warmup):
+        pkg.fci_sigma(ctx, vecs[i % len(vecs)], outs[i % len(outs)], stream=stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        pkg.fci_sigma(ctx, vecs[i % len(vecs)], outs[i % len(outs)], stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    return e0.elapsed_time(e1) / 1e3
+
+
+def time_to_tol(log, e_ref, tol=1e-8):
+    for row in log:
+        if abs(row[3] - e_ref) <= tol:
+            return float(row[2])
+    return None
+
+
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_1707_04346_gb300 as pkg
+
+    norb, na, nb, rank_eri = WORKLOADS[args.workload]
+    h1, eri = fi.make_integrals(norb, rank_eri)
+    ctx = pkg.fci_init(norb, na, nb, h1, eri)
+    N = ctx.ndet
+    nsa, nsb = ctx.nstr
+    c_host = fi.make_vector(N)
+    stream = torch.cuda.current_stream(dev)
+    # ring of inputs/outputs larger than L2
+    ring = max(2, int(np.ceil(4 * 129e6 / (N * 8))))
+    c0 = torch.from_numpy(c_host).to(dev)
+    vecs = [c0 * (1.0 + 0.01 * k) for k in range(ring)]
+    outs = [torch.empty_like(c0) for _ in range(ring)]
+
+    # FP64 sigma: the headline
+    pkg.fci_profile_enable(ctx, True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    t = time_sigma_ring(pkg, ctx, vecs, outs, args.steps, args.warmup, stream, world)
+    clk = clocks.stop()
+    names, prof = pkg.fci_profile_read(ctx)
+    pkg.fci_profile_enable(ctx, False)
+    prof = prof[-args.steps:]
+    t = max_over_ranks(t, world)
+    value = world * N * args.steps / t / 1e9
+    kmean = prof.mean(axis=0) / 1e3  # seconds per launch
+    kshare = prof.sum(axis=0) / prof.sum()
+    top = int(np.argmax(kmean))
+    sa = pkg.fci_query(ctx, 4)
+    sb = pkg.fci_query(ctx, 5)
+    from paper_1707_04346_gb300 import fci as F
+
+    # algorithmic work per launch
+    nsame = 1 + na * (norb - na) + (na * (na - 1) // 2) * ((norb - na) * (norb - na - 1) // 2)
+    work = {
+        "sigma3_exact": ("alu", 2.0 * sa * sb * N, "TFLOP/s"),
+        "sigma2_rows": ("alu", 2.0 * nsame * N, "TFLOP/s"),
+        "sigma1_cols": ("alu", 2.0 * nsame * N, "TFLOP/s"),
+    }
+    bound, flops, unit = work[names[top]]
+    achieved = flops / kmean[top] / 1e12
+    peaks = load_peaks()
+    roof = {"kernel": names[top], "bound": bound, "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": unit,
+            "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
+            "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s (no FP64 entry in MEASURED_PEAKS.json)",
+            "work_per_launch": f"{flops:.4g} FLOP (2 x {sa} x {sb} alpha-beta replacement pairs x {N} dets)",
+            "kernels": {n: {"ms": float(kmean[i] * 1e3), "share": float(kshare[i])} for i, n in enumerate(names)}}
+
+    # FP32 sigma
+    v32 = [v.float() for v in vecs]
+    o32 = [torch.empty_like(v) for v in v32]
+    t32 = time_sigma_ring(pkg, ctx, v32, o32, args.steps, args.warmup, stream, world)
+    t32 = max_over_ranks(t32, world)
+    fp32_value = world * N * args.steps / t32 / 1e9
+    del v32, o32
+
+    # end to end through the C ABI with host buffers
+    hc = torch.from_numpy(c_host).pin_memory()
+    hs = torch.empty(N, dtype=torch.float64).pin_memory()
+    dc = torch.empty(N, dtype=torch.float64, device=dev)
+    ds = torch.empty_like(dc)
+    for _ in range(args.warmup):
+        dc.copy_(hc, non_blocking=True)
+        pkg.fci_sigma(ctx, dc, ds, stream=stream)
+        hs.copy_(ds, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        dc.copy_(hc, non_blocking=True)
+        pkg.fci_sigma(ctx, dc, ds, stream=stream)
+        hs.copy_(ds, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    te = max_over_ranks(e0.elapsed_time(e1) / 1e3, world)
+    e2e = {"value": world * N * args.steps / te / 1e9, "unit": "Gdet/s", "h2d_bytes_per_step": N * 8,
+           "d2h_bytes_per_step": N * 8}
+    del vecs, outs
+
+    result = None
+    if rank == 0:
+        result = {
+            "metric": "sigma=Hc throughput (FP64)", "value": value, "unit": "Gdet/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"CAS({na + nb}e,{norb}o) Ms=0 sigma, {N} determinants ({nsa}x{nsb}), "
+                                   f"Cholesky-factored integrals rank {rank_eri}, seeds 1707/4346",
+                       "l2": f"input/output ring of {ring} vectors x {N * 8 / 1e6:.0f} MB > 129 MB L2",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roof, "clocks": clk, "gpu_launches": len(names) * args.steps, "e2e": e2e,
+            "fp32_sigma": {"value": fp32_value, "unit": "Gdet/s"},
+        }
+    if args.davidson and rank == 0:
+        import torch as _t
+
+        e_ref = pkg.fci_davidson(ctx, 1, 1e-10)[0]
+        log64 = pkg.fci_davidson_log(ctx, 1)
+        ctxm = pkg.fci_init(norb, na, nb, h1, eri, pkg.default_options(precision=pkg.FCI_PREC_MIXED))
+        em = pkg.fci_davidson(ctxm, 1, 1e-10)[0]
+        logm = pkg.fci_davidson_log(ctxm, 1)
+        result["davidson"] = {
+            "roots": 1, "E_fp64": e_ref, "E_mixed": em, "abs_diff": abs(em - e_ref),
+            "fp64_time_to_1e-8_s": time_to_tol(log64, e_ref), "mixed_time_to_1e-8_s": time_to_tol(logm, e_ref),
+            "fp64_iterations": int(len(log64)), "mixed_iterations": int(len(logm)),
+            "mixed_fp32_iterations": int((logm[:, 1] == 1).sum()),
+        }
+        pkg.fci_free(ctxm)
+    if args.cpu_baseline and rank == 0 and world == 1:
+        result["cpu_baseline"] = cpu_baseline(norb, na, nb, h1, eri, c_host, target_s=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(result))
+    pkg.fci_free(ctx)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cas14", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-davidson", dest="davidson", action="store_false")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,188 @@
+/*
+ * fci.h -- C ABI of the GB300 determinant-CI sigma library.
+ *
+ * The library computes, on one CUDA device, the sigma vector of direct
+ * determinant CI, sigma = H c (arXiv 1707.04346, Section 2.1, Eq. 4-5), with
+ * the spin-free Hamiltonian of Eq. 6 over Slater determinants factorised into
+ * alpha and beta strings (Eq. 2), and the Davidson eigensolver around it
+ * (Section 3.3).  All compute runs in the library's own CUDA kernels; there is
+ * no CPU fallback.  Every call returns an int status (FCI_OK on success).  On
+ * failure fci_last_error() returns a message for the calling thread.
+ *
+ * Conventions shared by every call:
+ *  - Orbitals are real; h1 is norb x norb row-major, symmetric; eri is the
+ *    chemist-notation tensor (ij|kl) as norb^4 row-major doubles with the
+ *    8-fold permutational symmetry.  Eq. 6 has no core energy and neither do
+ *    the energies returned here.
+ *  - Strings of one spin are listed in ascending bitmask order (bit p =
+ *    orbital p); the address of a string p0 < p1 < ... is sum_m C(p_m, m+1).
+ *  - A determinant is alpha(Ia) beta(Ib)|vac> with alpha creators to the left
+ *    (Eq. 2); CI vectors are row-major N_alpha x N_beta matrices (Eq. 4):
+ *    element Ia * N_beta + Ib.
+ *  - Vectors passed as `const void*` / `void*` are DEVICE pointers owned by
+ *    the caller, unless the parameter says "host".
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Stream-ordered calls return before the work has finished.
+ */
+#ifndef FCI_GB300_H
+#define FCI_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define FCI_OK 0
+#define FCI_ERR_ARG 1     /* invalid argument (sizes, symmetry, null pointer) */
+#define FCI_ERR_OOM 2     /* device allocation failed */
+#define FCI_ERR_CUDA 3    /* a CUDA call or kernel launch failed */
+#define FCI_ERR_NOCONV 4  /* Davidson reached max_iter; best energies filled */
+#define FCI_ERR_TIMEOUT 5 /* a bounded device wait gave up */
+#define FCI_ERR_STATE 6   /* call not valid in the context's current state */
+#define FCI_ERR_NAN 7     /* non-finite value detected in an input or result */
+
+/* ---- element types of CI vectors --------------------------------------- */
+#define FCI_F64 0
+#define FCI_F32 1
+
+/* ---- precision modes for the Davidson driver --------------------------- */
+#define FCI_PREC_FP64 0  /* every sigma in FP64 */
+#define FCI_PREC_MIXED 1 /* FP32 sigma until converged at the loose level, then FP64 refinement */
+
+/* ---- fci_query selectors ------------------------------------------------ */
+#define FCI_Q_NDET 1          /* N_alpha * N_beta */
+#define FCI_Q_NSTR_ALPHA 2
+#define FCI_Q_NSTR_BETA 3
+#define FCI_Q_NSINGLE_ALPHA 4 /* replacement-list entries per alpha string */
+#define FCI_Q_NSINGLE_BETA 5
+#define FCI_Q_NPAIR 6         /* norb (norb + 1) / 2 */
+#define FCI_Q_DEVICE_BYTES 7  /* device memory held by the context */
+#define FCI_Q_ITERATIONS 8    /* iterations of the last fci_davidson call */
+#define FCI_Q_SIGMA_CALLS 9   /* sigma builds done inside the last fci_davidson */
+
+typedef struct fci_ctx fci_ctx;
+
+typedef struct fci_options {
+    int struct_size;     /* set to sizeof(fci_options) */
+    int device;          /* CUDA device ordinal; -1 = the current device */
+    int max_subspace;    /* Davidson subspace limit in vectors (default 24) */
+    int max_iter;        /* Davidson iteration limit (default 100) */
+    int precision;       /* FCI_PREC_FP64 (default) or FCI_PREC_MIXED */
+    double mixed_switch; /* MIXED: residual norm at which FP64 refinement starts (default 1e-4) */
+    double symmetry_tol; /* tolerance of the h1/eri symmetry check (default 1e-10) */
+} fci_options;
+
+/* Fill *opt with the defaults listed above. */
+void fci_default_options(fci_options *opt);
+
+/*
+ * Create a context for CAS(n_alpha + n_beta electrons, norb orbitals).
+ *
+ * Builds on the device, once: the alpha and beta string lists (Eq. 2), the
+ * single-replacement lists E_kl with signs (Eq. 7), the same-spin string
+ * Hamiltonians used by sigma_1 / sigma_2 (Eq. 8), the packed pair matrix of
+ * two-electron integrals used by sigma_3, and the determinant diagonal.
+ *
+ *  ctx      out: new context (free with fci_free)
+ *  norb     1..30
+ *  nalpha,nbeta  0..norb; the string counts must stay below 2^21
+ *  h1, eri  HOST pointers, copied in; the caller keeps ownership
+ *  opt      may be NULL (defaults)
+ * Errors: FCI_ERR_ARG (sizes, NULL pointers, or h1/eri not symmetric within
+ * opt->symmetry_tol, or non-finite values), FCI_ERR_OOM, FCI_ERR_CUDA.
+ * Blocking.
+ */
+int fci_init(fci_ctx **ctx, int norb, int nalpha, int nbeta, const double *h1, const double *eri,
+             const fci_options *opt);
+
+/* Release every device buffer of the context.  NULL is accepted. */
+int fci_free(fci_ctx *ctx);
+
+/*
+ * sigma = H c (Eq. 4-5), computed as sigma_1 + sigma_2 + sigma_3 (Eq. 8):
+ * beta-beta, alpha-alpha and alpha-beta parts.
+ *
+ *  c, sigma  device vectors of N = N_alpha * N_beta elements of type dtype
+ *            (FCI_F64 or FCI_F32); must not overlap.  sigma is overwritten.
+ *  dtype     FCI_F64: FP64 arithmetic throughout.  FCI_F32: FP32 vectors and
+ *            arithmetic (the low-precision phase of the mixed Davidson).
+ *  stream    cudaStream_t or NULL.  Asynchronous.
+ * Errors: FCI_ERR_ARG, FCI_ERR_CUDA (launch failure).
+ */
+int fci_sigma(fci_ctx *ctx, const void *c, void *sigma, int dtype, void *stream);
+
+/* Copy the FP64 determinant diagonal H_II (N elements) to device memory `out`. */
+int fci_hdiag(fci_ctx *ctx, double *out, void *stream);
+
+/*
+ * Davidson eigensolver (Section 3.3) for the lowest nroots eigenpairs.
+ *
+ *  nroots    1..8
+ *  tol       energy convergence threshold (Eh); also ||r|| < sqrt(tol)
+ *  energies  HOST array [nroots], ascending, filled on return (also on
+ *            FCI_ERR_NOCONV, with the last Ritz values)
+ *  vecs      NULL, or DEVICE FP64 [nroots][N]: normalised eigenvectors
+ *  guess     NULL (unit vectors on the lowest diagonal elements), or DEVICE
+ *            FP64 [nroots][N] starting vectors
+ * Uses the options given at fci_init (max_subspace, max_iter, precision).
+ * Blocking; runs on the context's internal stream.
+ * Errors: FCI_ERR_ARG, FCI_ERR_OOM, FCI_ERR_CUDA, FCI_ERR_NOCONV.
+ */
+int fci_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *vecs, const void *guess);
+
+/*
+ * Per-iteration log of the last fci_davidson call.  Writes up to `cap`
+ * records of (nroots + 3) doubles each into HOST `out`: iteration, precision
+ * (0 FP64, 1 FP32), elapsed seconds since the call started, then the nroots
+ * Ritz values.  Returns the number of records available via *count.
+ */
+int fci_davidson_log(fci_ctx *ctx, double *out, int cap, int *count);
+
+/*
+ * Spin-summed one-particle density gamma_pq = <c|E_pq|c> (Eq. 7 operator),
+ * the density built after the Davidson iterations (Section 4).
+ *
+ *  c      device vector (dtype FCI_F64 or FCI_F32) of N elements
+ *  gamma  HOST array norb x norb, row-major, filled on return (blocking)
+ */
+int fci_rdm1(fci_ctx *ctx, const void *c, int dtype, double *gamma);
+
+/*
+ * Copy tables to the host (for checking): the string list of one spin
+ * (spin 0 = alpha, 1 = beta) as uint32 bitmasks [N_spin], and its
+ * single-replacement lists [N_spin][n_single]: for string X and each
+ * (k, l) with l occupied and k empty or k == l, in the order l ascending
+ * then k ascending, a+_k a_l |X> = sign |target>.  Any of tgt/k/l/sign may
+ * be NULL.  Blocking.
+ */
+int fci_get_strings(fci_ctx *ctx, int spin, uint32_t *out);
+int fci_get_single_table(fci_ctx *ctx, int spin, int32_t *tgt, int8_t *k, int8_t *l, int8_t *sign);
+
+/*
+ * Per-kernel timing (tracing).  While enabled, every fci_sigma call records
+ * CUDA events on the caller's stream around each kernel it launches (no
+ * synchronisation; the events go into a ring of 1024 records).
+ * fci_profile_read waits for the recorded events and returns, per record,
+ * the elapsed milliseconds of each kernel, row-major [nrecords][nkernels],
+ * oldest first (at most cap_records), then empties the ring.
+ * fci_profile_kernel_name names kernel slot i of the current sigma pipeline
+ * (NULL if out of range).  Enabling allocates the events (FCI_ERR_CUDA on
+ * failure); disabling keeps them for reuse.
+ */
+int fci_profile_enable(fci_ctx *ctx, int on);
+int fci_profile_read(fci_ctx *ctx, double *ms, int cap_records, int *nrecords, int *nkernels);
+const char *fci_profile_kernel_name(fci_ctx *ctx, int i);
+
+/* Sizes and counters (FCI_Q_*); returns -1 for an unknown selector. */
+int64_t fci_query(fci_ctx *ctx, int what);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *fci_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FCI_GB300_H */

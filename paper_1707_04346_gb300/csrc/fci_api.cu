@@ -1,0 +1,296 @@
+// C ABI entry points (include/fci.h): context lifetime, argument checks,
+// error reporting, and dispatch to the kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "internal.cuh"
+
+namespace fci {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+int fail(int code, const std::string &msg) {
+    set_error(msg);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    char buf[512];
+    snprintf(buf, sizeof(buf), "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+    set_error(buf);
+    return e == cudaErrorMemoryAllocation ? FCI_ERR_OOM : FCI_ERR_CUDA;
+}
+
+void *dalloc(fci_ctx *ctx, size_t bytes, int *rc) {
+    if (*rc != FCI_OK || bytes == 0) return nullptr;
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        char buf[160];
+        snprintf(buf, sizeof(buf), "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        set_error(buf);
+        *rc = FCI_ERR_OOM;
+        return nullptr;
+    }
+    ctx->bytes += bytes;
+    return p;
+}
+
+void dfree(fci_ctx *ctx, void *p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    ctx->bytes -= bytes;
+}
+
+int unpack_table(fci_ctx *ctx, int spin, int32_t *tgt, int8_t *k, int8_t *l, int8_t *sg);
+
+int prof_begin(fci_ctx *ctx, cudaStream_t s, int nkernels, const char *const *names) {
+    if (!ctx->prof || ctx->prof_ev.empty()) return -1;
+    if (ctx->prof_count > 0 && ctx->prof_nk != nkernels) {
+        ctx->prof_count = 0;  // pipeline changed: drop old records
+        ctx->prof_head = 0;
+    }
+    ctx->prof_nk = nkernels;
+    ctx->prof_names.assign(names, names + nkernels);
+    int slot = ctx->prof_head;
+    ctx->prof_head = (ctx->prof_head + 1) % kProfRing;
+    if (ctx->prof_count < kProfRing) ctx->prof_count++;
+    int base = slot * (kProfMaxKernels + 1);
+    cudaEventRecord(ctx->prof_ev[base], s);
+    return base;
+}
+
+void prof_mark(fci_ctx *ctx, int rec, int i, cudaStream_t s) {
+    if (rec < 0) return;
+    cudaEventRecord(ctx->prof_ev[rec + 1 + i], s);
+}
+
+static int check_integrals(int n, const double *h1, const double *eri, double tol) {
+    for (int i = 0; i < n * n; ++i)
+        if (!std::isfinite(h1[i])) return fail(FCI_ERR_ARG, "h1 has a non-finite element");
+    for (int p = 0; p < n; ++p)
+        for (int q = 0; q < p; ++q)
+            if (std::fabs(h1[p * n + q] - h1[q * n + p]) > tol) return fail(FCI_ERR_ARG, "h1 is not symmetric");
+    const int64_t n2 = (int64_t)n * n;
+    auto at = [&](int i, int j, int k, int l) { return eri[(i * n2 * n) + (int64_t)j * n2 + (int64_t)k * n + l]; };
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            for (int k = 0; k < n; ++k)
+                for (int l = 0; l < n; ++l) {
+                    double v = at(i, j, k, l);
+                    if (!std::isfinite(v)) return fail(FCI_ERR_ARG, "eri has a non-finite element");
+                    if (std::fabs(v - at(j, i, k, l)) > tol || std::fabs(v - at(i, j, l, k)) > tol ||
+                        std::fabs(v - at(k, l, i, j)) > tol)
+                        return fail(FCI_ERR_ARG, "eri lacks the 8-fold permutational symmetry of real orbitals");
+                }
+    return FCI_OK;
+}
+
+static int64_t binom64(int n, int k) {
+    if (k < 0 || k > n) return 0;
+    int64_t r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
+}
+
+}  // namespace fci
+
+using namespace fci;
+
+extern "C" {
+
+void fci_default_options(fci_options *opt) {
+    if (!opt) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->struct_size = (int)sizeof(fci_options);
+    opt->device = -1;
+    opt->max_subspace = 24;
+    opt->max_iter = 100;
+    opt->precision = FCI_PREC_FP64;
+    opt->mixed_switch = 1e-4;
+    opt->symmetry_tol = 1e-10;
+}
+
+const char *fci_last_error(void) { return g_last_error.c_str(); }
+
+int fci_init(fci_ctx **out, int norb, int nalpha, int nbeta, const double *h1, const double *eri,
+             const fci_options *opt) {
+    set_error("");
+    if (!out) return fail(FCI_ERR_ARG, "ctx pointer is NULL");
+    *out = nullptr;
+    if (!h1 || !eri) return fail(FCI_ERR_ARG, "h1 or eri is NULL");
+    if (norb < 1 || norb > 30) return fail(FCI_ERR_ARG, "norb must be in 1..30");
+    if (nalpha < 0 || nbeta < 0 || nalpha > norb || nbeta > norb)
+        return fail(FCI_ERR_ARG, "electron counts must be in 0..norb");
+    if (binom64(norb, nalpha) > kMaxStrings || binom64(norb, nbeta) > kMaxStrings)
+        return fail(FCI_ERR_ARG, "too many strings of one spin (limit 2^21 - 1)");
+    fci_options o;
+    fci_default_options(&o);
+    if (opt) {
+        if (opt->struct_size != (int)sizeof(fci_options)) return fail(FCI_ERR_ARG, "fci_options.struct_size mismatch");
+        o = *opt;
+    }
+    if (o.max_subspace < 2 || o.max_iter < 1) return fail(FCI_ERR_ARG, "max_subspace >= 2 and max_iter >= 1 required");
+    if (o.precision != FCI_PREC_FP64 && o.precision != FCI_PREC_MIXED) return fail(FCI_ERR_ARG, "unknown precision");
+    if (int rc = check_integrals(norb, h1, eri, o.symmetry_tol)) return rc;
+
+    fci_ctx *ctx = new (std::nothrow) fci_ctx();
+    if (!ctx) return fail(FCI_ERR_OOM, "host allocation failed");
+    ctx->opt = o;
+    ctx->norb = norb;
+    ctx->A.ne = nalpha;
+    ctx->B.ne = nbeta;
+    int dev = o.device;
+    if (dev < 0) {
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) { delete ctx; return cuda_fail(e, "cudaGetDevice"); }
+    }
+    ctx->device = dev;
+    cudaError_t e = cudaSetDevice(dev);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { delete ctx; return cuda_fail(e, "device setup"); }
+    int rc = build_tables(ctx, h1, eri);
+    if (rc) {
+        std::string msg = g_last_error;
+        fci_free(ctx);
+        set_error(msg);
+        return rc;
+    }
+    *out = ctx;
+    return FCI_OK;
+}
+
+int fci_free(fci_ctx *ctx) {
+    if (!ctx) return FCI_OK;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    free_tables(ctx);
+    for (auto &e : ctx->prof_ev) cudaEventDestroy(e);
+    if (ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return FCI_OK;
+}
+
+int fci_sigma(fci_ctx *ctx, const void *c, void *sigma, int dtype, void *stream) {
+    if (!ctx) return fail(FCI_ERR_ARG, "ctx is NULL");
+    if (!c || !sigma) return fail(FCI_ERR_ARG, "c or sigma is NULL");
+    if (c == sigma) return fail(FCI_ERR_ARG, "c and sigma must not overlap");
+    FCI_CUDA(cudaSetDevice(ctx->device));
+    return launch_sigma(ctx, c, sigma, dtype, (cudaStream_t)stream);
+}
+
+int fci_hdiag(fci_ctx *ctx, double *out, void *stream) {
+    if (!ctx || !out) return fail(FCI_ERR_ARG, "NULL argument");
+    FCI_CUDA(cudaSetDevice(ctx->device));
+    FCI_CUDA(cudaMemcpyAsync(out, ctx->hdiag, sizeof(double) * ctx->ndet, cudaMemcpyDeviceToDevice,
+                             (cudaStream_t)stream));
+    return FCI_OK;
+}
+
+int fci_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *vecs, const void *guess) {
+    if (!ctx || !energies) return fail(FCI_ERR_ARG, "NULL argument");
+    if (nroots < 1 || nroots > 8 || nroots > ctx->ndet) return fail(FCI_ERR_ARG, "nroots must be in 1..min(8, N)");
+    if (!(tol > 0)) return fail(FCI_ERR_ARG, "tol must be positive");
+    FCI_CUDA(cudaSetDevice(ctx->device));
+    return run_davidson(ctx, nroots, tol, energies, vecs, guess);
+}
+
+int fci_davidson_log(fci_ctx *ctx, double *out, int cap, int *count) {
+    if (!ctx) return fail(FCI_ERR_ARG, "ctx is NULL");
+    int w = ctx->log_width;
+    int nrec = w ? (int)(ctx->log.size() / w) : 0;
+    if (count) *count = nrec;
+    if (out && cap > 0 && w) {
+        int m = nrec < cap ? nrec : cap;
+        memcpy(out, ctx->log.data(), sizeof(double) * (size_t)m * w);
+    }
+    return FCI_OK;
+}
+
+int fci_rdm1(fci_ctx *ctx, const void *c, int dtype, double *gamma) {
+    if (!ctx || !c || !gamma) return fail(FCI_ERR_ARG, "NULL argument");
+    if (dtype != FCI_F64 && dtype != FCI_F32) return fail(FCI_ERR_ARG, "dtype must be FCI_F64 or FCI_F32");
+    FCI_CUDA(cudaSetDevice(ctx->device));
+    return run_rdm1(ctx, c, dtype, gamma);
+}
+
+int fci_get_strings(fci_ctx *ctx, int spin, uint32_t *out) {
+    if (!ctx || !out || (spin != 0 && spin != 1)) return fail(FCI_ERR_ARG, "bad argument");
+    FCI_CUDA(cudaSetDevice(ctx->device));
+    const SpinTables &T = spin ? ctx->B : ctx->A;
+    FCI_CUDA(cudaMemcpyAsync(out, T.str, sizeof(uint32_t) * T.ns, cudaMemcpyDeviceToHost, ctx->stream));
+    FCI_CUDA(cudaStreamSynchronize(ctx->stream));
+    return FCI_OK;
+}
+
+int fci_get_single_table(fci_ctx *ctx, int spin, int32_t *tgt, int8_t *k, int8_t *l, int8_t *sign) {
+    if (!ctx || (spin != 0 && spin != 1)) return fail(FCI_ERR_ARG, "bad argument");
+    FCI_CUDA(cudaSetDevice(ctx->device));
+    return unpack_table(ctx, spin, tgt, k, l, sign);
+}
+
+int fci_profile_enable(fci_ctx *ctx, int on) {
+    if (!ctx) return fail(FCI_ERR_ARG, "ctx is NULL");
+    FCI_CUDA(cudaSetDevice(ctx->device));
+    if (on && ctx->prof_ev.empty()) {
+        ctx->prof_ev.resize((size_t)kProfRing * (kProfMaxKernels + 1));
+        for (auto &e : ctx->prof_ev) FCI_CUDA(cudaEventCreate(&e));
+    }
+    ctx->prof = on != 0;
+    ctx->prof_count = 0;
+    ctx->prof_head = 0;
+    return FCI_OK;
+}
+
+int fci_profile_read(fci_ctx *ctx, double *ms, int cap_records, int *nrecords, int *nkernels) {
+    if (!ctx) return fail(FCI_ERR_ARG, "ctx is NULL");
+    FCI_CUDA(cudaSetDevice(ctx->device));
+    const int nk = ctx->prof_nk, cnt = ctx->prof_count;
+    if (nkernels) *nkernels = nk;
+    int m = cnt < cap_records ? cnt : cap_records;
+    if (!ms) m = 0;
+    const int first = (ctx->prof_head - cnt + kProfRing) % kProfRing;
+    for (int r = 0; r < m; ++r) {
+        int base = ((first + r) % kProfRing) * (kProfMaxKernels + 1);
+        for (int i = 0; i < nk; ++i) {
+            FCI_CUDA(cudaEventSynchronize(ctx->prof_ev[base + 1 + i]));
+            float t = 0.f;
+            FCI_CUDA(cudaEventElapsedTime(&t, ctx->prof_ev[base + i], ctx->prof_ev[base + 1 + i]));
+            ms[(size_t)r * nk + i] = t;
+        }
+    }
+    if (nrecords) *nrecords = ms ? m : cnt;
+    if (ms) {
+        ctx->prof_count = 0;
+        ctx->prof_head = 0;
+    }
+    return FCI_OK;
+}
+
+const char *fci_profile_kernel_name(fci_ctx *ctx, int i) {
+    if (!ctx || i < 0 || i >= (int)ctx->prof_names.size()) return nullptr;
+    return ctx->prof_names[i];
+}
+
+int64_t fci_query(fci_ctx *ctx, int what) {
+    if (!ctx) return -1;
+    switch (what) {
+        case FCI_Q_NDET: return ctx->ndet;
+        case FCI_Q_NSTR_ALPHA: return ctx->A.ns;
+        case FCI_Q_NSTR_BETA: return ctx->B.ns;
+        case FCI_Q_NSINGLE_ALPHA: return ctx->A.nsingle;
+        case FCI_Q_NSINGLE_BETA: return ctx->B.nsingle;
+        case FCI_Q_NPAIR: return ctx->npair;
+        case FCI_Q_DEVICE_BYTES: return (int64_t)ctx->bytes;
+        case FCI_Q_ITERATIONS: return ctx->iterations;
+        case FCI_Q_SIGMA_CALLS: return ctx->sigma_calls;
+        default: return -1;
+    }
+}
+
+}  // extern "C"

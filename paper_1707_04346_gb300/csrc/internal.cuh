@@ -1,0 +1,115 @@
+// Internal declarations shared by the library's translation units.
+// Not part of the public ABI (see include/fci.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "fci.h"
+
+namespace fci {
+
+// ---- error plumbing -------------------------------------------------------
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define FCI_CUDA(call)                                          \
+    do {                                                        \
+        cudaError_t _e = (call);                                \
+        if (_e != cudaSuccess) return ::fci::cuda_fail(_e, #call); \
+    } while (0)
+
+// ---- packed single-replacement entry -------------------------------------
+// bits 0..20  target string address (< 2^21)
+// bits 21..30 packed orbital-pair index (k,l) -> max*(max+1)/2 + min (< 1024)
+// bit  31     1 if the sign is negative
+constexpr int kTargetBits = 21;
+constexpr uint32_t kTargetMask = (1u << kTargetBits) - 1u;
+constexpr int kPairShift = 21;
+constexpr uint32_t kPairMask = 0x3FFu;
+constexpr int kMaxStrings = (1 << kTargetBits) - 1;
+
+__host__ __device__ inline uint32_t ent_target(uint32_t e) { return e & kTargetMask; }
+__host__ __device__ inline uint32_t ent_pair(uint32_t e) { return (e >> kPairShift) & kPairMask; }
+__host__ __device__ inline bool ent_negative(uint32_t e) { return (e >> 31) != 0u; }
+__host__ __device__ inline int pair_index(int k, int l) {
+    int hi = k > l ? k : l, lo = k > l ? l : k;
+    return hi * (hi + 1) / 2 + lo;
+}
+
+// ---- per-spin string data on the device ------------------------------------
+struct SpinTables {
+    int ne = 0;
+    int64_t ns = 0;        // number of strings
+    int nsingle = 0;       // ne*(norb-ne)+ne entries per string
+    int nsame = 0;         // same-spin Hamiltonian row width: 1 + singles + doubles
+    uint32_t *str = nullptr;   // [ns] bitmasks, ascending
+    uint32_t *tab = nullptr;   // [nsingle][ns] packed entries (entry-major)
+    int32_t *gcol = nullptr;   // [nsame][ns] same-spin Hamiltonian columns (ELL)
+    double *gval = nullptr;    // [nsame][ns]
+    float *gvalf = nullptr;    // [nsame][ns] FP32 copy
+    bool owner = true;         // false when aliasing the alpha tables
+};
+
+}  // namespace fci
+
+struct fci_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;  // internal stream (blocking calls, Davidson)
+    fci_options opt{};
+    int norb = 0;
+    int npair = 0;
+    int64_t ndet = 0;
+    fci::SpinTables A, B;           // alpha, beta
+    double *h1 = nullptr;           // [n][n]
+    double *eri = nullptr;          // [n^4]
+    double *W = nullptr;            // [npair][npair] packed (ij|kl)
+    float *Wf = nullptr;
+    double *hdiag = nullptr;        // [ndet]
+    size_t bytes = 0;
+    // Davidson bookkeeping
+    std::vector<double> log;        // records of (nroots + 3) doubles
+    int log_width = 0;
+    int iterations = 0;
+    int sigma_calls = 0;
+    // per-kernel timing ring (fci_profile_*)
+    bool prof = false;
+    std::vector<cudaEvent_t> prof_ev;    // kProfRing * (kProfMaxKernels + 1)
+    int prof_head = 0, prof_count = 0, prof_nk = 0;
+    std::vector<const char *> prof_names;
+};
+
+namespace fci {
+
+constexpr int kProfRing = 1024;
+constexpr int kProfMaxKernels = 8;
+
+// Start a profiling record for one sigma call (no-op unless enabled); returns
+// the record's first event index or -1.  prof_mark(ctx, rec, i, s) records
+// the event that closes kernel slot i.
+int prof_begin(fci_ctx *ctx, cudaStream_t s, int nkernels, const char *const *names);
+void prof_mark(fci_ctx *ctx, int rec, int i, cudaStream_t s);
+
+void *dalloc(fci_ctx *ctx, size_t bytes, int *rc);
+void dfree(fci_ctx *ctx, void *p, size_t bytes);
+
+// tables.cu
+int build_tables(fci_ctx *ctx, const double *h1_host, const double *eri_host);
+void free_tables(fci_ctx *ctx);
+
+// sigma.cu
+int launch_sigma(fci_ctx *ctx, const void *c, void *sigma, int dtype, cudaStream_t s);
+
+// davidson.cu
+int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *vecs, const void *guess);
+
+// rdm.cu
+int run_rdm1(fci_ctx *ctx, const void *c, int dtype, double *gamma);
+
+inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+}  // namespace fci

@@ -1,0 +1,215 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances:
+* string lists and replacement tables: bit-exact;
+* FP64 sigma: max_I |sigma_gpu - sigma_ref| <= 1e-12 * max_I |sigma_ref|
+  (normwise), and on small spaces per element
+  |d sigma_I| <= 1e-12 * sum_J |H_IJ||c_J|;
+* FP32 sigma: FP32 arithmetic with at most ~n_terms roundings of 2^-24 per
+  element; checked normwise at 2e-5 * max_I sum_J |H_IJ c_J| (the realistic
+  error is ~1e-7 relative);
+* Davidson energies (FP64): 1e-9 Eh of LAPACK on explicit H for tol 1e-11.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import fci_inputs as fi
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1707_04346_gb300 as p
+
+    return p
+
+
+def make_ctx(pkg, norb, na, nb, rank=40, seed=1707, **opt):
+    h1, eri = fi.make_integrals(norb, rank, seed)
+    o = pkg.default_options(**opt) if opt else None
+    return pkg.fci_init(norb, na, nb, h1, eri, o), h1, eri
+
+
+def gpu_sigma(pkg, ctx, c, dtype=torch.float64):
+    c_d = torch.as_tensor(c).to(DEV, dtype)
+    s_d = torch.empty_like(c_d)
+    pkg.fci_sigma(ctx, c_d, s_d)
+    torch.cuda.synchronize()
+    return s_d.double().cpu().numpy()
+
+
+SPACES = [(1, 1, 0), (2, 1, 1), (3, 1, 2), (4, 2, 2), (5, 2, 3), (6, 3, 3), (6, 4, 2), (7, 3, 4), (8, 4, 4),
+          (8, 5, 3), (9, 4, 5), (5, 5, 5), (6, 0, 3), (6, 6, 0)]
+
+
+@pytest.mark.parametrize("norb,na,nb", SPACES + [(10, 5, 5), (12, 6, 6), (14, 7, 7)])
+def test_tables_bit_exact(pkg, oracle_mod, norb, na, nb):
+    ctx, _, _ = make_ctx(pkg, norb, na, nb)
+    for spin, ne in ((0, na), (1, nb)):
+        assert np.array_equal(pkg.fci_get_strings(ctx, spin), oracle_mod.strings(norb, ne))
+        got = pkg.fci_get_single_table(ctx, spin)
+        ref = oracle_mod.single_table(norb, ne)
+        for g, r in zip(got, ref):
+            assert np.array_equal(g, r)
+
+
+@pytest.mark.parametrize("norb,na,nb", SPACES)
+def test_sigma_fp64_small_elementwise(pkg, oracle_mod, norb, na, nb):
+    ctx, h1, eri = make_ctx(pkg, norb, na, nb)
+    H = oracle_mod.hamiltonian(norb, na, nb, h1, eri)
+    for kind in ("random", "uniform"):
+        c = fi.make_vector(H.shape[0], kind=kind)
+        got = gpu_sigma(pkg, ctx, c)
+        ref = H @ c
+        bound = 1e-12 * (np.abs(H) @ np.abs(c)) + 1e-300
+        assert np.all(np.abs(got - ref) <= bound), float(np.max(np.abs(got - ref) / bound))
+    d = torch.empty(H.shape[0], dtype=torch.float64, device=DEV)
+    pkg.fci_hdiag(ctx, d)
+    torch.cuda.synchronize()
+    assert np.allclose(d.cpu().numpy(), np.diag(H), rtol=0, atol=1e-13 * max(1, np.abs(np.diag(H)).max()))
+
+
+def test_sigma_fp64_random_non_cholesky_integrals(pkg, oracle_mod):
+    rng = np.random.default_rng(5)
+    n = 6
+    g = rng.standard_normal((n,) * 4)
+    g = g + g.transpose(1, 0, 2, 3)
+    g = g + g.transpose(0, 1, 3, 2)
+    g = (g + g.transpose(2, 3, 0, 1)) / 8
+    a = rng.standard_normal((n, n))
+    h = 0.5 * (a + a.T)
+    ctx = pkg.fci_init(n, 4, 2, h, g)
+    H = oracle_mod.hamiltonian(n, 4, 2, h, g, "operator")
+    c = rng.standard_normal(H.shape[0])
+    got = gpu_sigma(pkg, ctx, c)
+    assert np.abs(got - H @ c).max() <= 1e-12 * np.abs(H @ c).max()
+
+
+@pytest.mark.parametrize("norb,na,nb", [(10, 5, 5), (11, 6, 5), (10, 4, 6)])
+def test_sigma_fp64_medium_full(pkg, oracle_mod, norb, na, nb):
+    ctx, h1, eri = make_ctx(pkg, norb, na, nb, rank=100)
+    c = fi.make_vector(ctx.ndet)
+    got = gpu_sigma(pkg, ctx, c)
+    ref = oracle_mod.sigma(norb, na, nb, h1, eri, c)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("norb,ne,nrows", [(12, 6, 3000), (14, 7, 2000)])
+def test_sigma_fp64_large_sampled(pkg, oracle_mod, norb, ne, nrows):
+    """Full-size CAS(12,12) and CAS(14,14) (the benchmark workload) sigma,
+    checked on sampled rows that the oracle computes one by one, including
+    the first and last determinants and a ragged spread in between."""
+    ctx, h1, eri = make_ctx(pkg, norb, ne, ne, rank=100)
+    N = ctx.ndet
+    c = fi.make_vector(N)
+    got = gpu_sigma(pkg, ctx, c)
+    rng = np.random.default_rng(norb)
+    rows = np.unique(np.concatenate([[0, 1, N // 2, N - 2, N - 1], rng.integers(0, N, nrows)]))
+    ref = oracle_mod.sigma_rows(norb, ne, ne, h1, eri, c, rows)
+    scale = np.abs(ref).max()
+    assert np.abs(got[rows] - ref).max() <= 1e-12 * scale
+    # property that holds at any size: c^T sigma is the Rayleigh quotient
+    # and sigma is linear; check linearity on the GPU alone
+    got2 = gpu_sigma(pkg, ctx, 2.0 * c)
+    assert np.abs(got2 - 2.0 * got).max() <= 1e-13 * np.abs(got).max()
+
+
+@pytest.mark.parametrize("norb,na,nb", [(8, 4, 4), (7, 4, 3)])
+def test_sigma_fp32_elementwise(pkg, oracle_mod, norb, na, nb):
+    ctx, h1, eri = make_ctx(pkg, norb, na, nb)
+    H = oracle_mod.hamiltonian(norb, na, nb, h1, eri)
+    c = fi.make_vector(ctx.ndet)
+    got = gpu_sigma(pkg, ctx, c, torch.float32)
+    c32 = c.astype(np.float32).astype(np.float64)
+    bound = 2e-5 * np.abs(H) @ np.abs(c32)
+    assert np.all(np.abs(got - H @ c32) <= bound)
+
+
+@pytest.mark.parametrize("norb,na,nb", [(10, 5, 5), (9, 5, 4)])
+def test_sigma_fp32_normwise(pkg, oracle_mod, norb, na, nb):
+    ctx, h1, eri = make_ctx(pkg, norb, na, nb)
+    c = fi.make_vector(ctx.ndet)
+    got = gpu_sigma(pkg, ctx, c, torch.float32)
+    ref = oracle_mod.sigma(norb, na, nb, h1, eri, c.astype(np.float32).astype(np.float64))
+    assert np.abs(got - ref).max() <= 2e-5 * np.abs(ref).max()
+
+
+def test_sigma_transpose_symmetry(pkg):
+    ctx, _, _ = make_ctx(pkg, 10, 5, 5)
+    ns = ctx.nstr[0]
+    c = fi.make_vector(ns * ns)
+    s1 = gpu_sigma(pkg, ctx, c).reshape(ns, ns)
+    s2 = gpu_sigma(pkg, ctx, c.reshape(ns, ns).T.reshape(-1)).reshape(ns, ns)
+    assert np.abs(s1.T - s2).max() <= 1e-12 * np.abs(s1).max()
+
+
+@pytest.mark.parametrize("norb,na,nb,nroots", [(6, 3, 3, 1), (8, 4, 4, 1), (8, 4, 4, 3), (7, 4, 3, 2)])
+def test_davidson_fp64_matches_lapack(pkg, oracle_mod, norb, na, nb, nroots):
+    ctx, h1, eri = make_ctx(pkg, norb, na, nb, max_subspace=16)
+    H = oracle_mod.hamiltonian(norb, na, nb, h1, eri)
+    w, v = np.linalg.eigh(H)
+    vecs = torch.empty((nroots, ctx.ndet), dtype=torch.float64, device=DEV)
+    e = pkg.fci_davidson(ctx, nroots, 1e-11, vecs=vecs)
+    assert np.abs(e - w[:nroots]).max() < 1e-9
+    X = vecs.cpu().numpy()
+    for k in range(nroots):
+        assert abs(np.linalg.norm(X[k]) - 1) < 1e-10
+        assert np.linalg.norm(H @ X[k] - w[k] * X[k]) < 1e-4
+        assert X[k][np.argmax(np.abs(X[k]))] > 0
+
+
+def test_davidson_mixed_matches_fp64(pkg, oracle_mod):
+    norb, ne = 8, 4
+    ctx, h1, eri = make_ctx(pkg, norb, ne, ne, precision=pkg.FCI_PREC_MIXED)
+    H = oracle_mod.hamiltonian(norb, ne, ne, h1, eri)
+    e = pkg.fci_davidson(ctx, 2, 1e-10)
+    assert np.abs(e - np.linalg.eigvalsh(H)[:2]).max() < 1e-8
+    log = pkg.fci_davidson_log(ctx, 2)
+    assert log[:, 1].max() == 1.0 and log[-1, 1] == 0.0  # FP32 phase, then FP64
+
+
+def test_davidson_cas14_vs_oracle_davidson(pkg, oracle_mod):
+    """CAS(14,14) lowest root: GPU FP64 vs GPU mixed; the FP64 Ritz vector's
+    Rayleigh quotient is checked with oracle sigma rows."""
+    ctx, h1, eri = make_ctx(pkg, 14, 7, 7, rank=100)
+    vec = torch.empty((1, ctx.ndet), dtype=torch.float64, device=DEV)
+    e64 = pkg.fci_davidson(ctx, 1, 1e-10, vecs=vec)
+    ctxm, _, _ = make_ctx(pkg, 14, 7, 7, rank=100, precision=pkg.FCI_PREC_MIXED)
+    em = pkg.fci_davidson(ctxm, 1, 1e-10)
+    assert abs(em[0] - e64[0]) < 1e-8
+    x = vec[0].cpu().numpy()
+    # residual on sampled rows: (H x)_I = E x_I
+    rows = np.argsort(-np.abs(x))[:200]
+    hx = oracle_mod.sigma_rows(14, 7, 7, h1, eri, x, rows)
+    assert np.abs(hx - e64[0] * x[rows]).max() < 1e-4
+
+
+@pytest.mark.parametrize("norb,na,nb", [(6, 3, 3), (7, 4, 3), (8, 4, 4), (5, 0, 2)])
+def test_rdm1(pkg, oracle_mod, norb, na, nb):
+    ctx, _, _ = make_ctx(pkg, norb, na, nb)
+    c = fi.make_vector(ctx.ndet)
+    g = pkg.fci_rdm1(ctx, torch.from_numpy(c).to(DEV))
+    ref = oracle_mod.rdm1(norb, na, nb, c)
+    assert np.abs(g - ref).max() < 1e-13
+    g32 = pkg.fci_rdm1(ctx, torch.from_numpy(c).to(DEV, torch.float32))
+    assert np.abs(g32 - ref).max() < 1e-5
+
+
+def test_errors_on_device(pkg):
+    ctx, _, _ = make_ctx(pkg, 4, 2, 2)
+    c = torch.zeros(ctx.ndet, dtype=torch.float64, device=DEV)
+    with pytest.raises(pkg.FciError):
+        pkg.fci_sigma(ctx, c, c)  # aliasing
+    with pytest.raises(pkg.FciError):
+        pkg.fci_davidson(ctx, 0, 1e-8)
