@@ -145,7 +145,8 @@ int fci_davidson_log(fci_ctx *ctx, double *out, int cap, int *count);
  * Spin-summed one-particle density gamma_pq = <c|E_pq|c> (Eq. 7 operator),
  * the density built after the Davidson iterations (Section 4).
  *
- *  c      device vector (dtype FCI_F64 or FCI_F32) of N elements
+ *  c      device vector (dtype FCI_F64 or FCI_F32) of N elements; the call
+ *         first waits for all work on the device, so c may come from any stream
  *  gamma  HOST array norb x norb, row-major, filled on return (blocking)
  */
 int fci_rdm1(fci_ctx *ctx, const void *c, int dtype, double *gamma);

@@ -216,6 +216,7 @@ int fci_rdm1(fci_ctx *ctx, const void *c, int dtype, double *gamma) {
     if (!ctx || !c || !gamma) return fail(FCI_ERR_ARG, "NULL argument");
     if (dtype != FCI_F64 && dtype != FCI_F32) return fail(FCI_ERR_ARG, "dtype must be FCI_F64 or FCI_F32");
     FCI_CUDA(cudaSetDevice(ctx->device));
+    FCI_CUDA(cudaDeviceSynchronize());  // c may still be in flight on the caller's streams
     return run_rdm1(ctx, c, dtype, gamma);
 }
 
