@@ -152,6 +152,37 @@ int fci_davidson_log(fci_ctx *ctx, double *out, int cap, int *count);
 int fci_rdm1(fci_ctx *ctx, const void *c, int dtype, double *gamma);
 
 /*
+ * fci_rdm1_noalloc -- the density of fci_rdm1, computed without allocating
+ * any device memory.  The paper has no counterpart: this is an interface
+ * convenience.
+ *
+ * fci_rdm1 allocates its scratch (one partial sum per replacement-list entry)
+ * with cudaMalloc and releases it with cudaFree on every call.  Some callers
+ * cannot do that: an application whose device memory is handed out entirely
+ * by its own pool or by a framework's caching allocator, or one that keeps
+ * other streams busy and cannot accept the device-wide synchronisation that
+ * cudaFree implies.  This entry point serves them: it uses a fixed array in
+ * the library's device memory and runs on the caller's stream.
+ *
+ *  c       device vector (dtype FCI_F64 or FCI_F32), ordered on `stream`
+ *  gamma   HOST array norb x norb, row-major, filled on return
+ *  stream  cudaStream_t or NULL; the call waits for this stream only
+ *
+ * Limit: N_alpha * n_single_alpha + N_beta * n_single_beta + norb^2 must not
+ * exceed FCI_RDM1_NOALLOC_MAX_DOUBLES (2^21 doubles, 16 MiB: enough for
+ * CAS(16,16)); larger spaces get FCI_ERR_ARG and must use fci_rdm1.
+ * The array lives in every GPU that loads the library until the process
+ * exits.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array, which keeps the
+ * last call's contents: calls whose GPU work overlaps (other streams,
+ * threads or contexts on the same device) race on it and corrupt each
+ * other's results, so serialise them.
+ */
+#define FCI_RDM1_NOALLOC_MAX_DOUBLES (1 << 21)
+int fci_rdm1_noalloc(fci_ctx *ctx, const void *c, int dtype, double *gamma, void *stream);
+
+/*
  * Copy tables to the host (for checking): the string list of one spin
  * (spin 0 = alpha, 1 = beta) as uint32 bitmasks [N_spin], and its
  * single-replacement lists [N_spin][n_single]: for string X and each

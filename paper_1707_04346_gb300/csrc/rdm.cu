@@ -123,3 +123,81 @@ int run_rdm1(fci_ctx *ctx, const void *c, int dtype, double *gamma) {
 }
 
 }  // namespace fci
+
+// ---------------------------------------------------------------------------
+// fci_rdm1_noalloc: the same density as fci_rdm1, with its scratch in a
+// file-scope device array instead of per-call cudaMalloc/cudaFree.
+//
+// The array below is a host-side stand-in in host code: its device address
+// is looked up with cudaGetSymbolAddress once per device (with that device
+// current) and cached; kernels receive that address.  Every call shares the
+// one array, so calls whose GPU work overlaps race on it.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+static __device__ __align__(256) double g_rdm1_scratch[FCI_RDM1_NOALLOC_MAX_DOUBLES];
+
+namespace fci {
+namespace {
+std::mutex g_scratch_mu;
+constexpr int kMaxDevices = 64;
+double *g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_rdm1_scratch on the current device `dev`.
+int scratch_address(int dev, double **out) {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (dev < 0 || dev >= kMaxDevices) return fail(FCI_ERR_ARG, "device ordinal out of range for the scratch cache");
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_rdm1_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(rdm1 scratch)");
+        g_scratch_addr[dev] = (double *)p;
+    }
+    *out = g_scratch_addr[dev];
+    return FCI_OK;
+}
+
+template <typename T>
+int rdm_noalloc_impl(fci_ctx *ctx, const T *C, double *gamma_host, cudaStream_t s) {
+    const SpinTables &A = ctx->A, &B = ctx->B;
+    const int n = ctx->norb;
+    const size_t na = (size_t)A.ns * A.nsingle, nb = (size_t)B.ns * B.nsingle, ng = (size_t)n * n;
+    if (na + nb + ng > (size_t)FCI_RDM1_NOALLOC_MAX_DOUBLES) {
+        char buf[200];
+        snprintf(buf, sizeof(buf),
+                 "fci_rdm1_noalloc needs %zu scratch doubles, above its fixed limit of %d "
+                 "(FCI_RDM1_NOALLOC_MAX_DOUBLES); use fci_rdm1",
+                 na + nb + ng, FCI_RDM1_NOALLOC_MAX_DOUBLES);
+        return fail(FCI_ERR_ARG, buf);
+    }
+    double *base = nullptr;
+    if (int rc = scratch_address(ctx->device, &base)) return rc;
+    double *pa = base, *pb = base + na, *g = base + na + nb;
+    // the density bins must start at zero; the partials are fully overwritten
+    FCI_CUDA(cudaMemsetAsync(g, 0, sizeof(double) * ng, s));
+    if (na) {
+        k_rdm_alpha<T><<<dim3((unsigned)A.ns, A.nsingle), 256, 0, s>>>(C, A, B.ns, pa);
+        FCI_CUDA(cudaGetLastError());
+    }
+    if (nb) {
+        k_rdm_beta<T><<<dim3(ceil_div(B.ns, 256), B.nsingle), 256, 0, s>>>(C, B, A.ns, pb);
+        FCI_CUDA(cudaGetLastError());
+    }
+    k_rdm_bins<<<ctx->npair, 256, 0, s>>>(A, B, pa, pb, n, g);
+    FCI_CUDA(cudaGetLastError());
+    FCI_CUDA(cudaMemcpyAsync(gamma_host, g, sizeof(double) * ng, cudaMemcpyDeviceToHost, s));
+    FCI_CUDA(cudaStreamSynchronize(s));
+    return FCI_OK;
+}
+}  // namespace
+}  // namespace fci
+
+extern "C" int fci_rdm1_noalloc(fci_ctx *ctx, const void *c, int dtype, double *gamma, void *stream) {
+    using namespace fci;
+    if (!ctx || !c || !gamma) return fail(FCI_ERR_ARG, "NULL argument");
+    if (dtype != FCI_F64 && dtype != FCI_F32) return fail(FCI_ERR_ARG, "dtype must be FCI_F64 or FCI_F32");
+    FCI_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == FCI_F64) return rdm_noalloc_impl<double>(ctx, (const double *)c, gamma, s);
+    return rdm_noalloc_impl<float>(ctx, (const float *)c, gamma, s);
+}

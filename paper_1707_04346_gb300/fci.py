@@ -27,6 +27,7 @@ EXPORTED = [
     "fci_default_options", "fci_init", "fci_free", "fci_sigma", "fci_hdiag", "fci_davidson",
     "fci_davidson_log", "fci_rdm1", "fci_get_strings", "fci_get_single_table", "fci_query",
     "fci_last_error", "fci_profile_enable", "fci_profile_read", "fci_profile_kernel_name",
+    "fci_rdm1_noalloc",
 ]
 
 
@@ -90,6 +91,8 @@ def load(path: str = LIB_PATH):
         lib.fci_profile_enable.argtypes = [vp, i32]
         lib.fci_profile_read.restype = i32
         lib.fci_profile_read.argtypes = [vp, vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        lib.fci_rdm1_noalloc.restype = i32
+        lib.fci_rdm1_noalloc.argtypes = [vp, vp, i32, vp, vp]
         lib.fci_profile_kernel_name.restype = ctypes.c_char_p
         lib.fci_profile_kernel_name.argtypes = [vp, i32]
         _lib = lib
@@ -224,6 +227,14 @@ def fci_rdm1(ctx: FciContext, c) -> np.ndarray:
     g = np.zeros((ctx.norb, ctx.norb))
     code = _dtype_code(c)
     _check(load().fci_rdm1(ctx.handle, _dev_ptr(c, code), code, _np_ptr(g)))
+    return g
+
+
+def fci_rdm1_noalloc(ctx: FciContext, c, stream=None) -> np.ndarray:
+    """1-RDM without device allocation (fixed library scratch; see include/fci.h)."""
+    g = np.zeros((ctx.norb, ctx.norb))
+    code = _dtype_code(c)
+    _check(load().fci_rdm1_noalloc(ctx.handle, _dev_ptr(c, code), code, _np_ptr(g), _stream_ptr(stream)))
     return g
 
 
