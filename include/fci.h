@@ -50,7 +50,7 @@ extern "C" {
 
 /* ---- precision modes for the Davidson driver --------------------------- */
 #define FCI_PREC_FP64 0  /* every sigma in FP64 */
-#define FCI_PREC_MIXED 1 /* FP32 sigma until converged at the loose level, then FP64 refinement */
+#define FCI_PREC_MIXED 1 /* FP32 sigma for new vectors, FP64 sigma only at refinement points */
 
 /* ---- fci_query selectors ------------------------------------------------ */
 #define FCI_Q_NDET 1          /* N_alpha * N_beta */
@@ -62,6 +62,8 @@ extern "C" {
 #define FCI_Q_DEVICE_BYTES 7  /* device memory held by the context */
 #define FCI_Q_ITERATIONS 8    /* iterations of the last fci_davidson call */
 #define FCI_Q_SIGMA_CALLS 9   /* sigma builds done inside the last fci_davidson */
+#define FCI_Q_DEVICE_ERROR 10 /* device error word: nonzero if a bounded wait inside a kernel
+                                 gave up (blocking read; the word is then cleared) */
 
 typedef struct fci_ctx fci_ctx;
 
@@ -69,10 +71,13 @@ typedef struct fci_options {
     int struct_size;     /* set to sizeof(fci_options) */
     int device;          /* CUDA device ordinal; -1 = the current device */
     int max_subspace;    /* Davidson subspace limit in vectors (default 24) */
-    int max_iter;        /* Davidson iteration limit (default 100) */
+    int max_iter;        /* Davidson iteration limit (default 300) */
     int precision;       /* FCI_PREC_FP64 (default) or FCI_PREC_MIXED */
-    double mixed_switch; /* MIXED: residual norm at which FP64 refinement starts (default 1e-4) */
+    double mixed_switch; /* MIXED: residual reduction between FP64 refinements (default 1e-2) */
     double symmetry_tol; /* tolerance of the h1/eri symmetry check (default 1e-10) */
+    int f32_splits;      /* FCI_F32 sigma_3 on the tensor cores: FP32 operands split into 2
+                            (split-BF16x3, ~1e-5 relative) or 3 (split-BF16x6, ~FP32) bf16
+                            slices; default 3 */
 } fci_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -107,8 +112,11 @@ int fci_free(fci_ctx *ctx);
  *
  *  c, sigma  device vectors of N = N_alpha * N_beta elements of type dtype
  *            (FCI_F64 or FCI_F32); must not overlap.  sigma is overwritten.
- *  dtype     FCI_F64: FP64 arithmetic throughout.  FCI_F32: FP32 vectors and
- *            arithmetic (the low-precision phase of the mixed Davidson).
+ *  dtype     FCI_F64: FP64 arithmetic throughout.  FCI_F32: FP32 vectors;
+ *            sigma_1/sigma_2 in FP32, sigma_3 on the tensor cores with bf16
+ *            slices of the FP32 operands and FP32 accumulation (see
+ *            fci_options.f32_splits); the low-precision phase of the mixed
+ *            Davidson.
  *  stream    cudaStream_t or NULL.  Asynchronous.
  * Errors: FCI_ERR_ARG, FCI_ERR_CUDA (launch failure).
  */

@@ -18,11 +18,17 @@
 // Jacobi in one CTA, FP64) and the residual norms stay on the device.  The
 // host reads back 2*nroots doubles per iteration for the convergence test.
 //
-// Mixed precision: while the largest residual norm is above opt.mixed_switch
-// sigma is built in FP32 (the basis, the projected matrix, orthogonalisation
-// and residuals stay FP64).  Then the subspace collapses to the Ritz vectors,
-// their sigma is rebuilt in FP64, and the iterations continue in FP64 to the
-// requested tolerance.
+// Mixed precision: every new correction gets an FP32 sigma (sigma_3 on the
+// tensor cores); the basis, the projected matrix, orthogonalisation and the
+// residuals stay FP64.  Refinement points: when the residual has fallen by
+// opt.mixed_switch (default 1e-2) since the last one, after 12 corrections,
+// or when it is below sqrt(tol), the FP64 sigma of each Ritz vector x = B v is
+// built and the subspace sigma vectors are corrected along v,
+// S <- S + (sigma64(x) - S v) v^T, together with the projected matrix.  The
+// Ritz values there are exact Rayleigh quotients and the residuals exact; the
+// FP32 error left in the other directions shrinks with the size of the
+// corrections.  Convergence is tested only at those points, which the
+// iteration log marks with precision 0.
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -122,6 +128,31 @@ __global__ void __launch_bounds__(256) k_residual_precond(const double *__restri
         for (int w = 0; w < 8; ++w) v += red[w];
         partial[blockIdx.x] = v;
     }
+}
+
+// S_j += V[j][k] * delta for j < m (rank-1 correction of the subspace sigma vectors)
+__global__ void k_rank1_sigma(double *__restrict__ S, int m, const double *__restrict__ V, int k,
+                              const double *__restrict__ delta, int64_t n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride) {
+        const double d = delta[r];
+        for (int j = 0; j < m; ++j) S[(int64_t)j * n + r] += V[j * m + k] * d;
+    }
+}
+
+// A[i][j] += g[i] * V[j][k]  (projected matrix after the rank-1 correction)
+__global__ void k_rank1_proj(double *__restrict__ A, int lda, int m, const double *__restrict__ g,
+                             const double *__restrict__ V, int k) {
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+        const int i = t / m, j = t % m;
+        A[i * lda + j] += g[i] * V[j * m + k];
+    }
+}
+
+// delta = a - b
+__global__ void k_sub(const double *__restrict__ a, const double *__restrict__ b, double *__restrict__ out, int64_t n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride) out[r] = a[r] - b[r];
 }
 
 __global__ void k_scale(double *__restrict__ y, const double *__restrict__ nrm2, double floor_norm,
@@ -444,21 +475,27 @@ int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *v
         if (kept) ++m;
     }
     if (m == 0) return fail(FCI_ERR_ARG, "initial guess vectors are linearly dependent");
-    bool fp32 = mixed;
     for (int i = 0; i < m; ++i)
-        if (int rc = sigma_of(W, fp32, W.Bv + (size_t)i * n, W.Sv + (size_t)i * n)) return rc;
+        if (int rc = sigma_of(W, mixed, W.Bv + (size_t)i * n, W.Sv + (size_t)i * n)) return rc;
     for (int j = 0; j < m; ++j)
         if (int rc = dots(W, W.Bv, m, W.Sv + (size_t)j * n, W.A + j, kMaxSub)) return rc;
 
+    // exact: the subspace sigma vectors are FP64-exact along the current Ritz
+    // vectors, so Ritz values and residuals are exact; convergence is only
+    // tested there.  Always true in FP64 mode.
+    bool exact = !mixed;
     std::vector<double> e_prev(nroots, INFINITY), ev(kMaxSub), rn(nroots);
     bool converged = false;
-    int it = 0, fp32_iters = 0;
+    int it = 0, inner = 0;
+    double r_ref = INFINITY;
+    const double drop = ctx->opt.mixed_switch > 0 && ctx->opt.mixed_switch < 1 ? ctx->opt.mixed_switch : 1e-2;
+
     for (it = 1; it <= ctx->opt.max_iter; ++it) {
-        // diagonalise the projected matrix
+        // (4) diagonalise the projected matrix
         k_jacobi<<<1, 64, 0, s>>>(W.A, kMaxSub, m, W.w, W.V);
         FCI_CUDA(cudaGetLastError());
         const int nr = nroots < m ? nroots : m;
-        // Ritz vectors, sigma of Ritz vectors, residuals, corrections
+        // Ritz vectors, their sigma, residuals and (2)-(3) preconditioned corrections
         for (int k = 0; k < nr; ++k) {
             k_lincomb<<<grid_for(n), 256, 0, s>>>(W.Bv, m, W.V + k, m, 0.0, W.X + (size_t)k * n, n);
             k_lincomb<<<grid_for(n), 256, 0, s>>>(W.Sv, m, W.V + k, m, 0.0, W.HX + (size_t)k * n, n);
@@ -469,7 +506,10 @@ int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *v
         }
         FCI_CUDA(cudaMemcpyAsync(ev.data(), W.w, sizeof(double) * nr, cudaMemcpyDeviceToHost, s));
         FCI_CUDA(cudaMemcpyAsync(rn.data(), W.rn2, sizeof(double) * nr, cudaMemcpyDeviceToHost, s));
+        int derr = 0;
+        FCI_CUDA(cudaMemcpyAsync(&derr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
         FCI_CUDA(cudaStreamSynchronize(s));
+        if (derr) return fail(FCI_ERR_TIMEOUT, "a bounded device wait gave up inside sigma");
         double rmax = 0.0, demax = 0.0;
         for (int k = 0; k < nr; ++k) {
             rn[k] = std::sqrt(rn[k]);
@@ -479,36 +519,43 @@ int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *v
         {
             const double el = std::chrono::duration<double>(clk::now() - t0).count();
             ctx->log.push_back((double)it);
-            ctx->log.push_back(fp32 ? 1.0 : 0.0);
+            ctx->log.push_back(exact ? 0.0 : 1.0);
             ctx->log.push_back(el);
             for (int k = 0; k < nroots; ++k) ctx->log.push_back(k < nr ? ev[k] : NAN);
         }
-        if (!fp32 && nr == nroots && demax < tol && rmax < std::sqrt(tol)) {
-            converged = true;
-            break;
-        }
-        for (int k = 0; k < nr; ++k) e_prev[k] = ev[k];
-        // switch from FP32 to FP64 sigma: collapse to the Ritz vectors, rebuild their sigma in FP64
-        ++fp32_iters;
-        const bool do_switch = fp32 && (rmax < ctx->opt.mixed_switch || fp32_iters >= ctx->opt.max_iter / 2);
-        if (do_switch || m + nr > maxsub) {
-            // the Ritz vectors are orthonormal to rounding; keep them as the new basis
-            FCI_CUDA(cudaMemcpyAsync(W.Bv, W.X, sizeof(double) * nr * n, cudaMemcpyDeviceToDevice, s));
-            if (do_switch) {
-                fp32 = false;
-                for (int k = 0; k < nr; ++k)
-                    if (int rc = sigma_of(W, false, W.Bv + (size_t)k * n, W.Sv + (size_t)k * n)) return rc;
-                for (int k = 0; k < nroots; ++k) e_prev[k] = INFINITY;
-            } else {
-                FCI_CUDA(cudaMemcpyAsync(W.Sv, W.HX, sizeof(double) * nr * n, cudaMemcpyDeviceToDevice, s));
+        if (exact) {
+            if (nr == nroots && demax < tol && rmax < std::sqrt(tol)) {
+                converged = true;
+                break;
             }
+            for (int k = 0; k < nr; ++k) e_prev[k] = ev[k];
+            r_ref = rmax;
+            inner = 0;
+        } else if (++inner >= 12 || rmax < drop * r_ref || rmax < std::sqrt(tol)) {
+            // refinement: exact FP64 sigma of each Ritz vector; the difference to
+            // the subspace estimate corrects every sigma vector along that Ritz
+            // direction (S += delta v^T) and the projected matrix with it
+            for (int k = 0; k < nr; ++k) {
+                double *d = W.T + (size_t)k * n;
+                if (int rc = sigma_of(W, false, W.X + (size_t)k * n, d)) return rc;
+                k_sub<<<grid_for(n), 256, 0, s>>>(d, W.HX + (size_t)k * n, d, n);
+                if (int rc = dots(W, W.Bv, m, d, W.scal, 1)) return rc;
+                k_rank1_sigma<<<grid_for(n), 256, 0, s>>>(W.Sv, m, W.V, k, d, n);
+                k_rank1_proj<<<1, 256, 0, s>>>(W.A, kMaxSub, m, W.scal, W.V, k);
+                FCI_CUDA(cudaGetLastError());
+            }
+            exact = true;
+            continue;
+        }
+        if (m + nr > maxsub) {
+            // collapse onto the Ritz vectors (orthonormal to rounding) and their sigma
+            FCI_CUDA(cudaMemcpyAsync(W.Bv, W.X, sizeof(double) * nr * n, cudaMemcpyDeviceToDevice, s));
+            FCI_CUDA(cudaMemcpyAsync(W.Sv, W.HX, sizeof(double) * nr * n, cudaMemcpyDeviceToDevice, s));
             m = nr;
             FCI_CUDA(cudaMemsetAsync(W.A, 0, sizeof(double) * kMaxSub * kMaxSub, s));
             for (int j = 0; j < m; ++j)
                 if (int rc = dots(W, W.Bv, m, W.Sv + (size_t)j * n, W.A + j, kMaxSub)) return rc;
-            if (do_switch) continue;  // fresh FP64 projected matrix: re-diagonalise before adding vectors
         }
-        // (2)-(3): preconditioned corrections, orthogonalised against the basis
         int added = 0;
         for (int k = 0; k < nr && m < maxsub; ++k) {
             double *b = W.Bv + (size_t)m * n;
@@ -516,21 +563,22 @@ int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *v
             int kept = 0;
             if (int rc = orthonormalise(W, W.Bv, m, b, &kept)) return rc;
             if (!kept) continue;
-            // (4) new sigma, new row/column of the projected matrix
-            if (int rc = sigma_of(W, fp32, b, W.Sv + (size_t)m * n)) return rc;
+            // (4) new sigma (FP32 in mixed mode), new row/column of the projected matrix
+            if (int rc = sigma_of(W, mixed, b, W.Sv + (size_t)m * n)) return rc;
             ++m;
             if (int rc = dots(W, W.Bv, m, W.Sv + (size_t)(m - 1) * n, W.A + (m - 1), kMaxSub)) return rc;
             if (int rc = dots(W, W.Sv, m, W.Bv + (size_t)(m - 1) * n, W.A + (size_t)(m - 1) * kMaxSub, 1)) return rc;
             ++added;
         }
         if (added == 0) {
-            if (fp32) {
-                fp32 = false;  // nothing left to gain in FP32: move on to FP64
+            if (!exact) {
+                inner = 1 << 20;  // force a refinement on the next pass
                 continue;
             }
             converged = rmax < std::sqrt(tol);
             break;
         }
+        if (mixed) exact = false;
     }
     ctx->iterations = it > ctx->opt.max_iter ? ctx->opt.max_iter : it;
     for (int k = 0; k < nroots; ++k) energies[k] = ev[k];

@@ -110,10 +110,11 @@ void fci_default_options(fci_options *opt) {
     opt->struct_size = (int)sizeof(fci_options);
     opt->device = -1;
     opt->max_subspace = 24;
-    opt->max_iter = 100;
+    opt->max_iter = 300;
     opt->precision = FCI_PREC_FP64;
-    opt->mixed_switch = 1e-4;
+    opt->mixed_switch = 1e-2;
     opt->symmetry_tol = 1e-10;
+    opt->f32_splits = 3;
 }
 
 const char *fci_last_error(void) { return g_last_error.c_str(); }
@@ -137,6 +138,7 @@ int fci_init(fci_ctx **out, int norb, int nalpha, int nbeta, const double *h1, c
     }
     if (o.max_subspace < 2 || o.max_iter < 1) return fail(FCI_ERR_ARG, "max_subspace >= 2 and max_iter >= 1 required");
     if (o.precision != FCI_PREC_FP64 && o.precision != FCI_PREC_MIXED) return fail(FCI_ERR_ARG, "unknown precision");
+    if (o.f32_splits != 2 && o.f32_splits != 3) return fail(FCI_ERR_ARG, "f32_splits must be 2 or 3");
     if (int rc = check_integrals(norb, h1, eri, o.symmetry_tol)) return rc;
 
     fci_ctx *ctx = new (std::nothrow) fci_ctx();
@@ -290,6 +292,14 @@ int64_t fci_query(fci_ctx *ctx, int what) {
         case FCI_Q_DEVICE_BYTES: return (int64_t)ctx->bytes;
         case FCI_Q_ITERATIONS: return ctx->iterations;
         case FCI_Q_SIGMA_CALLS: return ctx->sigma_calls;
+        case FCI_Q_DEVICE_ERROR: {
+            int h = 0;
+            if (cudaSetDevice(ctx->device) != cudaSuccess) return -1;
+            if (cudaDeviceSynchronize() != cudaSuccess) return -1;
+            if (cudaMemcpy(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+            if (h && cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess) return -1;
+            return h;
+        }
         default: return -1;
     }
 }

@@ -49,6 +49,7 @@ struct SpinTables {
     int nsame = 0;         // same-spin Hamiltonian row width: 1 + singles + doubles
     uint32_t *str = nullptr;   // [ns] bitmasks, ascending
     uint32_t *tab = nullptr;   // [nsingle][ns] packed entries (entry-major)
+    uint32_t *tabq = nullptr;  // [ns][nsingle] the same entries, string-major, sorted by pair index
     int32_t *gcol = nullptr;   // [nsame][ns] same-spin Hamiltonian columns (ELL)
     double *gval = nullptr;    // [nsame][ns]
     float *gvalf = nullptr;    // [nsame][ns] FP32 copy
@@ -70,6 +71,7 @@ struct fci_ctx {
     double *W = nullptr;            // [npair][npair] packed (ij|kl)
     float *Wf = nullptr;
     double *hdiag = nullptr;        // [ndet]
+    int *d_err = nullptr;           // device error word (bounded waits that gave up)
     size_t bytes = 0;
     // Davidson bookkeeping
     std::vector<double> log;        // records of (nroots + 3) doubles
@@ -103,6 +105,10 @@ void free_tables(fci_ctx *ctx);
 
 // sigma.cu
 int launch_sigma(fci_ctx *ctx, const void *c, void *sigma, int dtype, cudaStream_t s);
+
+// sigma_tc.cu (tensor-core sigma_3 for FP32 vectors; nsplit = 2 or 3 bf16 slices)
+int launch_sigma3_tc(fci_ctx *ctx, const float *C, float *sig, int nsplit, cudaStream_t s);
+size_t sigma3_tc_smem(const fci_ctx *ctx, int nsplit);
 
 // davidson.cu
 int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *vecs, const void *guess);

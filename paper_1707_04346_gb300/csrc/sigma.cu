@@ -80,6 +80,13 @@ __device__ __forceinline__ float w_of<float>(const double *, const float *Wf, in
     return Wf[i];
 }
 
+__device__ __forceinline__ double flip_sign(double x, uint32_t signbit) {
+    return __longlong_as_double(__double_as_longlong(x) ^ ((long long)signbit << 32));
+}
+__device__ __forceinline__ float flip_sign(float x, uint32_t signbit) {
+    return __int_as_float(__float_as_int(x) ^ (int)signbit);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(512) k_sigma3_exact(const T *__restrict__ C, T *__restrict__ sig, SpinTables A,
                                                       SpinTables B, const double *__restrict__ W,
@@ -106,8 +113,9 @@ __global__ void __launch_bounds__(512) k_sigma3_exact(const T *__restrict__ C, T
             T v = 0;
             for (int b = 0; b < B.nsingle; ++b) {
                 const uint32_t entb = B.tab[(int64_t)b * nsb + ib];
-                T t = wrow[ent_pair(entb)] * crow[ent_target(entb)];
-                v += ent_negative(entb) ? -t : t;
+                // the beta sign goes in by flipping the sign bit (integer pipe), so
+                // each replacement pair costs one fused multiply-add
+                v = fma(flip_sign(wrow[ent_pair(entb)], entb & 0x80000000u), crow[ent_target(entb)], v);
             }
             acc[ib] += sa * v;
         }
@@ -131,7 +139,7 @@ static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s) {
     const SpinTables &A = ctx->A, &B = ctx->B;
     const int64_t nsa = A.ns, nsb = B.ns;
     const size_t lim = smem_limit();
-    static const char *const names[3] = {"sigma2_rows", "sigma1_cols", "sigma3_exact"};
+    static const char *const names[3] = {"sigma2_rows", "sigma1_cols", sizeof(T) == 4 ? "sigma3_tc" : "sigma3_exact"};
     const int rec = prof_begin(ctx, s, 3, names);
     // sigma_2
     {
@@ -153,7 +161,9 @@ static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s) {
         prof_mark(ctx, rec, 1, s);
     }
     // sigma_3
-    if (A.nsingle > 0 && B.nsingle > 0) {
+    if (A.nsingle > 0 && B.nsingle > 0 && sizeof(T) == 4) {
+        if (int rc = launch_sigma3_tc(ctx, (const float *)C, (float *)sig, ctx->opt.f32_splits, s)) return rc;
+    } else if (A.nsingle > 0 && B.nsingle > 0) {
         size_t sm = sizeof(T) * (2 * nsb + ctx->npair) + sizeof(uint32_t) * A.nsingle;
         if (sm > lim) return fail(FCI_ERR_ARG, "beta string count too large for the sigma_3 row kernel");
         if (sm > 48 * 1024) FCI_CUDA(cudaFuncSetAttribute(k_sigma3_exact<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));

@@ -100,6 +100,23 @@ __global__ void k_unpack_table(const uint32_t *tab, const uint32_t *str, int64_t
     if (sg) sg[t] = ent_negative(ent) ? (int8_t)-1 : (int8_t)1;
 }
 
+// String-major copy of the replacement list of each string, sorted by pair
+// index (the order in which the tensor-core sigma_3 epilogue walks the pairs).
+__global__ void k_sort_by_pair(const uint32_t *tab, int64_t ns, int nsingle, uint32_t *tabq) {
+    int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (x >= ns) return;
+    uint32_t *out = tabq + x * nsingle;
+    for (int e = 0; e < nsingle; ++e) {
+        uint32_t v = tab[(int64_t)e * ns + x];
+        int i = e - 1;
+        while (i >= 0 && ent_pair(out[i]) > ent_pair(v)) {
+            out[i + 1] = out[i];
+            --i;
+        }
+        out[i + 1] = v;
+    }
+}
+
 __device__ __forceinline__ double eri4(const double *eri, int n, int p, int q, int r, int s) {
     return eri[((p * n + q) * n + r) * n + s];
 }
@@ -224,6 +241,7 @@ static int build_spin(fci_ctx *ctx, SpinTables &T, int ne) {
     const int64_t ns = T.ns;
     T.str = (uint32_t *)dalloc(ctx, sizeof(uint32_t) * ns, &rc);
     T.tab = (uint32_t *)dalloc(ctx, sizeof(uint32_t) * ns * T.nsingle, &rc);
+    T.tabq = (uint32_t *)dalloc(ctx, sizeof(uint32_t) * ns * T.nsingle, &rc);
     T.gcol = (int32_t *)dalloc(ctx, sizeof(int32_t) * ns * T.nsame, &rc);
     T.gval = (double *)dalloc(ctx, sizeof(double) * ns * T.nsame, &rc);
     T.gvalf = (float *)dalloc(ctx, sizeof(float) * ns * T.nsame, &rc);
@@ -233,6 +251,8 @@ static int build_spin(fci_ctx *ctx, SpinTables &T, int ne) {
     FCI_CUDA(cudaGetLastError());
     if (T.nsingle > 0) {
         k_single_table<<<ceil_div(ns * T.nsingle, 256), 256, 0, s>>>(T.str, ns, n, ne, T.nsingle, T.tab);
+        FCI_CUDA(cudaGetLastError());
+        k_sort_by_pair<<<ceil_div(ns, 128), 128, 0, s>>>(T.tab, ns, T.nsingle, T.tabq);
         FCI_CUDA(cudaGetLastError());
     }
     k_same_spin_rows<<<ceil_div(ns, 64), 64, 0, s>>>(T.str, ns, n, ne, T.nsame, ctx->h1, ctx->eri, T.gcol, T.gval);
@@ -272,7 +292,9 @@ int build_tables(fci_ctx *ctx, const double *h1_host, const double *eri_host) {
     }
     ctx->ndet = ctx->A.ns * ctx->B.ns;
     ctx->hdiag = (double *)dalloc(ctx, sizeof(double) * ctx->ndet, &rc);
+    ctx->d_err = (int *)dalloc(ctx, sizeof(int), &rc);
     if (rc) return rc;
+    FCI_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
     // the diagonal same-spin entries sit in ELL slot 0
     k_hdiag<<<ceil_div(ctx->ndet, 256), 256, 0, ctx->stream>>>(ctx->A.gval, ctx->B.gval, ctx->A.str, ctx->B.str,
                                                               ctx->A.ns, ctx->B.ns, n, ctx->eri, ctx->hdiag);
@@ -285,6 +307,7 @@ static void free_spin(fci_ctx *ctx, SpinTables &T) {
     if (!T.owner) return;
     dfree(ctx, T.str, sizeof(uint32_t) * T.ns);
     dfree(ctx, T.tab, sizeof(uint32_t) * T.ns * T.nsingle);
+    dfree(ctx, T.tabq, sizeof(uint32_t) * T.ns * T.nsingle);
     dfree(ctx, T.gcol, sizeof(int32_t) * T.ns * T.nsame);
     dfree(ctx, T.gval, sizeof(double) * T.ns * T.nsame);
     dfree(ctx, T.gvalf, sizeof(float) * T.ns * T.nsame);
@@ -300,6 +323,8 @@ void free_tables(fci_ctx *ctx) {
     dfree(ctx, ctx->W, sizeof(double) * ctx->npair * ctx->npair);
     dfree(ctx, ctx->Wf, sizeof(float) * ctx->npair * ctx->npair);
     dfree(ctx, ctx->hdiag, sizeof(double) * ctx->ndet);
+    dfree(ctx, ctx->d_err, sizeof(int));
+    ctx->d_err = nullptr;
     ctx->h1 = ctx->eri = ctx->W = ctx->hdiag = nullptr;
     ctx->Wf = nullptr;
 }

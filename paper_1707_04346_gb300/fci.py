@@ -21,7 +21,7 @@ FCI_F64, FCI_F32 = 0, 1
 FCI_PREC_FP64, FCI_PREC_MIXED = 0, 1
 FCI_Q_NDET, FCI_Q_NSTR_ALPHA, FCI_Q_NSTR_BETA = 1, 2, 3
 FCI_Q_NSINGLE_ALPHA, FCI_Q_NSINGLE_BETA, FCI_Q_NPAIR = 4, 5, 6
-FCI_Q_DEVICE_BYTES, FCI_Q_ITERATIONS, FCI_Q_SIGMA_CALLS = 7, 8, 9
+FCI_Q_DEVICE_BYTES, FCI_Q_ITERATIONS, FCI_Q_SIGMA_CALLS, FCI_Q_DEVICE_ERROR = 7, 8, 9, 10
 
 EXPORTED = [
     "fci_default_options", "fci_init", "fci_free", "fci_sigma", "fci_hdiag", "fci_davidson",
@@ -46,6 +46,7 @@ class fci_options(ctypes.Structure):
         ("precision", ctypes.c_int),
         ("mixed_switch", ctypes.c_double),
         ("symmetry_tol", ctypes.c_double),
+        ("f32_splits", ctypes.c_int),
     ]
 
 

@@ -51,8 +51,8 @@ def test_default_options(lib):
 
     o = fci.default_options()
     assert o.struct_size == ctypes.sizeof(fci.fci_options)
-    assert o.max_subspace == 24 and o.max_iter == 100 and o.precision == fci.FCI_PREC_FP64
-    assert o.device == -1 and o.symmetry_tol == 1e-10
+    assert o.max_subspace == 24 and o.max_iter == 300 and o.precision == fci.FCI_PREC_FP64
+    assert o.device == -1 and o.symmetry_tol == 1e-10 and o.f32_splits == 3
 
 
 def _init(lib, norb, na, nb, h1, eri, opt=None):

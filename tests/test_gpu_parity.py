@@ -145,6 +145,45 @@ def test_sigma_fp32_normwise(pkg, oracle_mod, norb, na, nb):
     assert np.abs(got - ref).max() <= 2e-5 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("norb,na,nb", [(9, 5, 4), (10, 5, 5), (12, 6, 6), (13, 7, 6), (11, 3, 8)])
+@pytest.mark.parametrize("splits,rtol", [(3, 2e-6), (2, 1e-4)])
+def test_sigma_fp32_tensor_core_splits(pkg, oracle_mod, norb, na, nb, splits, rtol):
+    """sigma_3 on tcgen05 with 3 (split-BF16x6) and 2 (split-BF16x3) bf16 slices;
+    ragged last beta tile, K and N padding, n_alpha != n_beta."""
+    ctx, h1, eri = make_ctx(pkg, norb, na, nb, rank=60, f32_splits=splits)
+    N = ctx.ndet
+    c = fi.make_vector(N)
+    got = gpu_sigma(pkg, ctx, c, torch.float32)
+    c32 = c.astype(np.float32).astype(np.float64)
+    if N <= 100000:
+        ref = oracle_mod.sigma(norb, na, nb, h1, eri, c32)
+        assert np.abs(got - ref).max() <= rtol * np.abs(ref).max()
+    else:
+        rows = np.unique(np.concatenate([[0, N - 1], np.random.default_rng(3).integers(0, N, 1500)]))
+        ref = oracle_mod.sigma_rows(norb, na, nb, h1, eri, c32, rows)
+        assert np.abs(got[rows] - ref).max() <= rtol * np.abs(ref).max()
+
+
+def test_sigma_fp32_cas14_sampled(pkg, oracle_mod):
+    """The benchmark workload in the FP32 launch configuration (split-BF16x6)."""
+    ctx, h1, eri = make_ctx(pkg, 14, 7, 7, rank=100)
+    N = ctx.ndet
+    c = fi.make_vector(N)
+    got = gpu_sigma(pkg, ctx, c, torch.float32)
+    rows = np.unique(np.concatenate([[0, 1, N // 2, N - 1], np.random.default_rng(14).integers(0, N, 1500)]))
+    ref = oracle_mod.sigma_rows(14, 7, 7, h1, eri, c.astype(np.float32).astype(np.float64), rows)
+    assert np.abs(got[rows] - ref).max() <= 2e-6 * np.abs(ref).max()
+
+
+def test_device_error_word_clear(pkg):
+    ctx, _, _ = make_ctx(pkg, 10, 5, 5)
+    c = torch.from_numpy(fi.make_vector(ctx.ndet)).to(DEV, torch.float32)
+    s = torch.empty_like(c)
+    pkg.fci_sigma(ctx, c, s)
+    torch.cuda.synchronize()
+    assert pkg.fci_query(ctx, 10) == 0  # no bounded wait gave up
+
+
 def test_sigma_transpose_symmetry(pkg):
     ctx, _, _ = make_ctx(pkg, 10, 5, 5)
     ns = ctx.nstr[0]
