@@ -216,6 +216,65 @@ int fci_profile_enable(fci_ctx *ctx, int on);
 int fci_profile_read(fci_ctx *ctx, double *ms, int cap_records, int *nrecords, int *nkernels);
 const char *fci_profile_kernel_name(fci_ctx *ctx, int i);
 
+/* ---- batched CASCI ------------------------------------------------------
+ *
+ * Many independent CASCI problems solved together, the single-GPU analogue
+ * of the paper's many TTSS batches distributed over processors (Section 3.1):
+ * all instances advance through the Davidson iterations of Section 3.3 in
+ * lock-step, every vector operation is one launch over all instances, and the
+ * sigma vectors of all instances come from one persistent kernel that pulls
+ * (instance, alpha-row group) work items, largest instances first, from a
+ * device queue.  The per-iteration kernel sequences are captured in CUDA
+ * graphs.  Threads per alpha row are chosen per (norb, precision) by timing
+ * the candidates {32, 64, 128, 256} on the first instance of each size at
+ * fci_batch_init (the tuning table is readable with fci_batch_tuning).
+ */
+typedef struct fci_instance {
+    int norb, nalpha, nbeta;  /* as in fci_init (norb <= 16 here) */
+    const double *h1;         /* HOST, norb x norb */
+    const double *eri;        /* HOST, norb^4 */
+} fci_instance;
+
+typedef struct fci_batch fci_batch;
+
+/*
+ * Build the tables of every instance and tune the sigma kernel.
+ *  opt: precision FCI_PREC_FP64 (FP64 sigma) or FCI_PREC_MIXED (FP32 sigma for
+ *       new vectors, FP64 refinement as in fci_davidson); max_subspace,
+ *       max_iter and mixed_switch as for fci_davidson.
+ * Errors: FCI_ERR_ARG (ninst < 1, a bad instance, norb > 16), FCI_ERR_OOM,
+ * FCI_ERR_CUDA.  Blocking.
+ */
+int fci_batch_init(fci_batch **batch, int ninst, const fci_instance *inst, const fci_options *opt);
+
+/*
+ * Lowest nroots eigenvalues of every instance; energies is HOST
+ * [ninst][nroots].  Returns FCI_ERR_NOCONV if any instance did not converge
+ * within max_iter (all energies are still filled).  Blocking.
+ */
+int fci_batch_davidson(fci_batch *batch, int nroots, double tol, double *energies);
+
+/*
+ * sigma for every instance at once: c and sigma are DEVICE vectors holding
+ * the instances' CI vectors back to back (instance i at offset
+ * fci_batch_offset(batch, i)), dtype FCI_F64 or FCI_F32.  Stream-ordered.
+ */
+int fci_batch_sigma(fci_batch *batch, const void *c, void *sigma, int dtype, void *stream);
+
+/* Offset of instance i in a batch vector; i == ninst gives the total length. */
+int64_t fci_batch_offset(fci_batch *batch, int i);
+
+/* Tuning table: for each distinct (norb, dtype) writes norb, dtype and the
+ * chosen threads per row into HOST `out` (3 ints per entry, up to cap
+ * entries); *count receives the number of entries. */
+int fci_batch_tuning(fci_batch *batch, int *out, int cap, int *count);
+
+/* Iterations and sigma launches of the last fci_batch_davidson: what = 0
+ * iterations, 1 batched sigma launches, 2 graph launches. */
+int64_t fci_batch_stats(fci_batch *batch, int what);
+
+int fci_batch_free(fci_batch *batch);
+
 /* Sizes and counters (FCI_Q_*); returns -1 for an unknown selector. */
 int64_t fci_query(fci_ctx *ctx, int what);
 

@@ -1,0 +1,1080 @@
+// Batched CASCI: many independent determinant-CI problems (different active
+// spaces and integrals) solved together on one GPU.
+//
+// The paper reaches parallelism by cutting one CI vector into many TTSS
+// batches and handing them to processors (Section 3.1); here the independent
+// units are whole CASCI instances.  All instances run the Davidson scheme of
+// Section 3.3 in lock-step (same subspace size m), so every step is one launch
+// over all instances:
+//  * vectors of all instances are stored back to back ("batch vectors"); the
+//    element-wise and reduction kernels walk a list of <=256-element chunks,
+//    each inside one instance, and reduce per instance in a fixed order;
+//  * sigma of every instance comes from one persistent launch whose CTAs pull
+//    (instance, alpha-row group) items, largest instances first, from a device
+//    work counter; a row group of `tpr` threads builds sigma_1 + sigma_2 +
+//    sigma_3 (Eq. 8) of one output alpha row with the same string-driven
+//    formulas as the single-instance kernels;
+//  * `tpr` is tuned per (norb, precision) at init by timing 32/64/128/256 on
+//    the first instance of that size;
+//  * the per-iteration kernel sequences are captured in CUDA graphs (one per
+//    subspace size), with every per-instance parameter in device memory.
+// An instance that converged is masked off; a slot an instance does not fill
+// in an iteration (dropped correction, refinement step, or converged) is a
+// zero vector whose projected-matrix diagonal is set to 1e30, so it never
+// mixes into the lowest Ritz pairs.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace fci {
+namespace bt {
+
+constexpr int kBlock = 256;
+constexpr int kMaxSub = 32;
+constexpr int kMaxRoots = 8;
+constexpr int kChunk = 256;
+constexpr double kPad = 1e30;
+
+struct InstDev {
+    SpinTables A, B;
+    const double *W;
+    const float *Wf;
+    const double *hdiag;
+    int64_t ndet, off;
+    int npair, tpr;
+};
+
+struct Chunk {
+    int inst, len;
+    int64_t start;
+};
+
+struct Item {
+    int inst, row0;
+};
+
+__device__ __forceinline__ double flipb(double x, uint32_t sb) {
+    return __longlong_as_double(__double_as_longlong(x) ^ ((long long)sb << 32));
+}
+__device__ __forceinline__ float flipb(float x, uint32_t sb) { return __int_as_float(__float_as_int(x) ^ (int)sb); }
+
+template <typename T>
+__device__ __forceinline__ T gv(const SpinTables &S, int64_t i);
+template <>
+__device__ __forceinline__ double gv<double>(const SpinTables &S, int64_t i) { return S.gval[i]; }
+template <>
+__device__ __forceinline__ float gv<float>(const SpinTables &S, int64_t i) { return S.gvalf[i]; }
+
+template <typename T>
+__device__ __forceinline__ T wv(const InstDev &d, int64_t i);
+template <>
+__device__ __forceinline__ double wv<double>(const InstDev &d, int64_t i) { return d.W[i]; }
+template <>
+__device__ __forceinline__ float wv<float>(const InstDev &d, int64_t i) { return d.Wf[i]; }
+
+__device__ __forceinline__ void group_sync(int g, int tpr) {
+    if (tpr == 32) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(tpr) : "memory");
+    }
+}
+
+// Persistent batched sigma.  cin/cout: per-instance vector pointers; on:
+// per-instance enable flags; row_elems: shared-memory elements per row group.
+template <typename T>
+__global__ void __launch_bounds__(kBlock, 1) k_bsigma(const InstDev *__restrict__ D, const Item *__restrict__ items,
+                                                       int nitems, int *__restrict__ counter, const T *const *cin,
+                                                       T *const *cout, const int *__restrict__ on, int row_elems) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *base = reinterpret_cast<T *>(smem_raw);
+    __shared__ int s_item;
+    const int tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= nitems) break;
+        const Item I = items[it];
+        if (!on[I.inst]) continue;
+        const InstDev d = D[I.inst];
+        const int tpr = d.tpr, g = tid / tpr, lt = tid % tpr;
+        const int64_t row = (int64_t)I.row0 + g;
+        if (row >= d.A.ns) continue;  // whole group idle; its barrier is private
+        const int64_t nsb = d.B.ns;
+        const int64_t nsa = d.A.ns;
+        const T *C = cin[I.inst];
+        T *S = cout[I.inst];
+        T *cself = base + (int64_t)g * row_elems;
+        T *ca = cself + nsb;
+        T *acc = ca + nsb;
+        T *wrow = acc + nsb;
+        for (int64_t j = lt; j < nsb; j += tpr) cself[j] = C[row * nsb + j];
+        group_sync(g, tpr);
+        // sigma_2 (alpha-alpha rows of C) and sigma_1 (inside the row)
+        for (int64_t j = lt; j < nsb; j += tpr) {
+            T a = 0;
+            for (int e = 0; e < d.A.nsame; ++e) {
+                const int64_t ix = (int64_t)e * nsa + row;
+                a = fma(gv<T>(d.A, ix), C[(int64_t)d.A.gcol[ix] * nsb + j], a);
+            }
+            for (int e = 0; e < d.B.nsame; ++e) {
+                const int64_t ix = (int64_t)e * nsb + j;
+                a = fma(gv<T>(d.B, ix), cself[d.B.gcol[ix]], a);
+            }
+            acc[j] = a;
+        }
+        // sigma_3: one staged alpha-replacement row at a time
+        for (int a = 0; a < d.A.nsingle; ++a) {
+            const uint32_t ea = d.A.tab[(int64_t)a * nsa + row];
+            const int64_t ja = ent_target(ea);
+            const int pa = ent_pair(ea);
+            group_sync(g, tpr);
+            for (int64_t j = lt; j < nsb; j += tpr) ca[j] = C[ja * nsb + j];
+            for (int q = lt; q < d.npair; q += tpr) wrow[q] = wv<T>(d, (int64_t)pa * d.npair + q);
+            group_sync(g, tpr);
+            for (int64_t j = lt; j < nsb; j += tpr) {
+                T v = 0;
+                for (int b = 0; b < d.B.nsingle; ++b) {
+                    const uint32_t eb = d.B.tab[(int64_t)b * nsb + j];
+                    v = fma(flipb(wrow[ent_pair(eb)], eb & 0x80000000u), ca[ent_target(eb)], v);
+                }
+                acc[j] += ent_negative(ea) ? -v : v;
+            }
+        }
+        for (int64_t j = lt; j < nsb; j += tpr) S[row * nsb + j] = acc[j];
+        group_sync(g, tpr);
+    }
+}
+
+// ---- flat batch-vector kernels (one CTA per chunk) ---------------------------
+
+// partial[c][j] = sum over chunk c of X_j . y   (j < m)
+template <int MAXM>
+__global__ void __launch_bounds__(kBlock) k_bdots(const Chunk *__restrict__ ch, const int *__restrict__ on,
+                                                  const double *__restrict__ X, int64_t ntot, int m,
+                                                  const double *__restrict__ y, double *__restrict__ partial) {
+    const Chunk c = ch[blockIdx.x];
+    double acc[MAXM];
+#pragma unroll
+    for (int j = 0; j < MAXM; ++j) acc[j] = 0.0;
+    if (on[c.inst] && threadIdx.x < c.len) {
+        const int64_t idx = c.start + threadIdx.x;
+        const double yv = y[idx];
+#pragma unroll
+        for (int j = 0; j < MAXM; ++j)
+            if (j < m) acc[j] = X[(int64_t)j * ntot + idx] * yv;
+    }
+    __shared__ double red[MAXM][kBlock / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < MAXM; ++j) {
+        double v = acc[j];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[j][warp] = v;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        double v = 0.0;
+        for (int w = 0; w < kBlock / 32; ++w) v += red[j][w];
+        partial[(int64_t)blockIdx.x * MAXM + j] = v;
+    }
+}
+
+// out[i*os + j*js] = sum of partial[c][j] over instance i's chunks (fixed order)
+template <int MAXM>
+__global__ void k_breduce(const int *__restrict__ cfirst, const int *__restrict__ on,
+                          const double *__restrict__ partial, int m, double *__restrict__ out, int64_t os, int64_t js) {
+    const int i = blockIdx.x;
+    if (!on[i]) return;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        double v = 0.0;
+        for (int c = cfirst[i]; c < cfirst[i + 1]; ++c) v += partial[(int64_t)c * MAXM + j];
+        out[i * os + j * js] = v;
+    }
+}
+
+// y = beta*y + alpha * sum_j coef[i*cs + j*cj] X_j     (masked by on)
+__global__ void __launch_bounds__(kBlock) k_blincomb(const Chunk *__restrict__ ch, const int *__restrict__ on,
+                                                     const double *__restrict__ X, int64_t ntot, int m,
+                                                     const double *__restrict__ coef, int64_t cs, int64_t cj,
+                                                     double alpha, double beta, double *__restrict__ y) {
+    const Chunk c = ch[blockIdx.x];
+    if (!on[c.inst] || threadIdx.x >= c.len) return;
+    const int64_t idx = c.start + threadIdx.x;
+    const double *cf = coef + c.inst * cs;
+    double v = 0.0;
+    for (int j = 0; j < m; ++j) v += cf[j * cj] * X[(int64_t)j * ntot + idx];
+    y[idx] = (beta == 0.0 ? 0.0 : beta * y[idx]) + alpha * v;
+}
+
+// r = hx - w x ; t = -r/(diag - w) with the 1e-8 floor; partial[c] = |r|^2 over the chunk
+__global__ void __launch_bounds__(kBlock) k_bresid(const Chunk *__restrict__ ch, const int *__restrict__ on,
+                                                   const InstDev *__restrict__ D, const double *__restrict__ x,
+                                                   const double *__restrict__ hx, const double *__restrict__ w,
+                                                   int wstride, double *__restrict__ t, double *__restrict__ partial) {
+    const Chunk c = ch[blockIdx.x];
+    double a = 0.0;
+    if (on[c.inst] && threadIdx.x < c.len) {
+        const int64_t idx = c.start + threadIdx.x;
+        const double e = w[(int64_t)c.inst * wstride];
+        const double r = hx[idx] - e * x[idx];
+        double dd = D[c.inst].hdiag[idx - D[c.inst].off] - e;
+        if (fabs(dd) < 1e-8) dd = dd < 0 ? -1e-8 : 1e-8;
+        t[idx] = -r / dd;
+        a = r * r;
+    }
+    __shared__ double red[kBlock / 32];
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int k = 0; k < kBlock / 32; ++k) v += red[k];
+        partial[(int64_t)blockIdx.x * 8] = v;
+    }
+}
+
+// y *= 1/sqrt(nrm2[i]) if the norm is at least 1e-10, else y = 0 (keep[i] = 0)
+__global__ void __launch_bounds__(kBlock) k_bnormalise(const Chunk *__restrict__ ch, const int *__restrict__ on,
+                                                       const double *__restrict__ nrm2, double *__restrict__ y) {
+    const Chunk c = ch[blockIdx.x];
+    if (!on[c.inst] || threadIdx.x >= c.len) return;
+    const int64_t idx = c.start + threadIdx.x;
+    const double nn = sqrt(nrm2[c.inst]);
+    y[idx] = nn >= 1e-10 ? y[idx] / nn : 0.0;
+}
+
+__global__ void __launch_bounds__(kBlock) k_bcopy(const Chunk *__restrict__ ch, const int *__restrict__ on,
+                                                  const double *__restrict__ a, double *__restrict__ b,
+                                                  int zero_when_off) {
+    const Chunk c = ch[blockIdx.x];
+    if (threadIdx.x >= c.len) return;
+    const int64_t idx = c.start + threadIdx.x;
+    if (on[c.inst]) b[idx] = a[idx];
+    else if (zero_when_off) b[idx] = 0.0;
+}
+
+__global__ void k_d2f(const double *__restrict__ a, float *__restrict__ b, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+__global__ void k_f2d(const float *__restrict__ a, double *__restrict__ b, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (double)a[i];
+}
+
+// S_j += V_i[j][k] * delta for j < m (rank-1 refinement), masked
+__global__ void __launch_bounds__(kBlock) k_brank1(const Chunk *__restrict__ ch, const int *__restrict__ on,
+                                                   double *__restrict__ S, int64_t ntot, int m,
+                                                   const double *__restrict__ V, int k,
+                                                   const double *__restrict__ delta) {
+    const Chunk c = ch[blockIdx.x];
+    if (!on[c.inst] || threadIdx.x >= c.len) return;
+    const int64_t idx = c.start + threadIdx.x;
+    const double dl = delta[idx];
+    const double *Vi = V + (int64_t)c.inst * kMaxSub * kMaxSub;
+    for (int j = 0; j < m; ++j) S[(int64_t)j * ntot + idx] += Vi[j * m + k] * dl;
+}
+
+// A_i[r][c] += g_i[r] * V_i[c][k]
+__global__ void k_brank1_proj(const int *__restrict__ on, double *__restrict__ A, const double *__restrict__ g,
+                              const double *__restrict__ V, int m, int k) {
+    const int i = blockIdx.x;
+    if (!on[i]) return;
+    double *Ai = A + (int64_t)i * kMaxSub * kMaxSub;
+    const double *gi = g + (int64_t)i * kMaxSub;
+    const double *Vi = V + (int64_t)i * kMaxSub * kMaxSub;
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+        const int r = t / m, cc = t % m;
+        Ai[r * kMaxSub + cc] += gi[r] * Vi[cc * m + k];
+    }
+}
+
+// slot j of instance i: if the new vector was dropped (norm below 1e-10) or the
+// instance is masked, make it a padding slot: A[j][*] = A[*][j] = 0, A[j][j] = kPad
+__global__ void k_bpad(const int *__restrict__ on, const double *__restrict__ nrm2, double *__restrict__ A, int j,
+                       int ninst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ninst) return;
+    const bool pad = !on[i] || !(sqrt(nrm2[i]) >= 1e-10);
+    if (!pad) return;
+    double *Ai = A + (int64_t)i * kMaxSub * kMaxSub;
+    for (int t = 0; t < kMaxSub; ++t) {
+        Ai[j * kMaxSub + t] = 0.0;
+        Ai[t * kMaxSub + j] = 0.0;
+    }
+    Ai[j * kMaxSub + j] = kPad;
+}
+
+// Cyclic Jacobi per instance (textbook; ascending order, stable).
+__global__ void k_bjacobi(const int *__restrict__ on, const double *__restrict__ Aall, int m,
+                          double *__restrict__ wall, double *__restrict__ Vall) {
+    const int i = blockIdx.x;
+    if (!on[i]) return;
+    const double *A = Aall + (int64_t)i * kMaxSub * kMaxSub;
+    double *w = wall + (int64_t)i * kMaxSub;
+    double *V = Vall + (int64_t)i * kMaxSub * kMaxSub;
+    __shared__ double a[kMaxSub][kMaxSub + 1];
+    __shared__ double v[kMaxSub][kMaxSub + 1];
+    __shared__ double cs[2];
+    __shared__ int order[kMaxSub];
+    const int tid = threadIdx.x;
+    for (int t = tid; t < m * m; t += blockDim.x) {
+        const int r = t / m, c = t % m;
+        a[r][c] = 0.5 * (A[r * kMaxSub + c] + A[c * kMaxSub + r]);
+        v[r][c] = (r == c) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int r = 0; r < m; ++r)
+            for (int c = 0; c < m; ++c) {
+                const double x = a[r][c] * a[r][c];
+                const bool pad_diag = r == c && a[r][r] >= 0.5 * kPad;  // padding slots stay out of the norm
+                if (!pad_diag) tot += x;
+                if (r != c) off += x;
+            }
+        if (off <= 1e-30 * tot || off == 0.0) break;
+        for (int p = 0; p < m - 1; ++p)
+            for (int q = p + 1; q < m; ++q) {
+                if (tid == 0) {
+                    const double apq = a[p][q];
+                    double c = 1.0, s = 0.0;
+                    if (apq != 0.0) {
+                        const double theta = (a[q][q] - a[p][p]) / (2.0 * apq);
+                        const double tt = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                        c = 1.0 / sqrt(tt * tt + 1.0);
+                        s = tt * c;
+                    }
+                    cs[0] = c;
+                    cs[1] = s;
+                }
+                __syncthreads();
+                const double c = cs[0], s = cs[1];
+                if (s != 0.0) {
+                    for (int k = tid; k < m; k += blockDim.x) {
+                        const double akp = a[k][p], akq = a[k][q];
+                        a[k][p] = c * akp - s * akq;
+                        a[k][q] = s * akp + c * akq;
+                    }
+                    __syncthreads();
+                    for (int k = tid; k < m; k += blockDim.x) {
+                        const double apk = a[p][k], aqk = a[q][k];
+                        a[p][k] = c * apk - s * aqk;
+                        a[q][k] = s * apk + c * aqk;
+                        const double vkp = v[k][p], vkq = v[k][q];
+                        v[k][p] = c * vkp - s * vkq;
+                        v[k][q] = s * vkp + c * vkq;
+                    }
+                }
+                __syncthreads();
+            }
+    }
+    if (tid == 0) {
+        for (int r = 0; r < m; ++r) order[r] = r;
+        for (int r = 1; r < m; ++r) {
+            const int o = order[r];
+            int j = r - 1;
+            while (j >= 0 && a[order[j]][order[j]] > a[o][o]) {
+                order[j + 1] = order[j];
+                --j;
+            }
+            order[j + 1] = o;
+        }
+    }
+    __syncthreads();
+    for (int t = tid; t < m; t += blockDim.x) w[t] = a[order[t]][order[t]];
+    for (int t = tid; t < m * m; t += blockDim.x) {
+        const int r = t / m, k = t % m;
+        V[r * m + k] = v[r][order[k]];
+    }
+}
+
+// nroots smallest diagonal entries per instance (ties: lower index) -> unit vectors in B_k
+__global__ void k_bguess(const InstDev *__restrict__ D, int nroots, double *__restrict__ Bv, int64_t ntot) {
+    const int i = blockIdx.x;
+    const InstDev d = D[i];
+    __shared__ double sb[256];
+    __shared__ int64_t si[256];
+    __shared__ int64_t chosen[kMaxRoots];
+    for (int k = 0; k < nroots; ++k) {
+        double best = INFINITY;
+        int64_t bi = INT64_MAX;
+        for (int64_t r = threadIdx.x; r < d.ndet; r += blockDim.x) {
+            bool skip = false;
+            for (int c = 0; c < k; ++c) skip |= chosen[c] == r;
+            const double v = d.hdiag[r];
+            if (!skip && (v < best || (v == best && r < bi))) {
+                best = v;
+                bi = r;
+            }
+        }
+        sb[threadIdx.x] = best;
+        si[threadIdx.x] = bi;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) {
+                const double v = sb[threadIdx.x + s];
+                const int64_t j = si[threadIdx.x + s];
+                if (v < sb[threadIdx.x] || (v == sb[threadIdx.x] && j < si[threadIdx.x])) {
+                    sb[threadIdx.x] = v;
+                    si[threadIdx.x] = j;
+                }
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) chosen[k] = si[0];
+        __syncthreads();
+        double *b = Bv + (int64_t)k * ntot + d.off;
+        for (int64_t r = threadIdx.x; r < d.ndet; r += blockDim.x) b[r] = (r == chosen[k]) ? 1.0 : 0.0;
+        __syncthreads();
+    }
+}
+
+}  // namespace bt
+}  // namespace fci
+
+using namespace fci;
+using namespace fci::bt;
+
+struct fci_batch {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    fci_options opt{};
+    std::vector<fci_ctx *> ctx;
+    std::vector<int64_t> off;  // ninst + 1
+    int64_t ntot = 0;
+    int ninst = 0, nsm = 0;
+    InstDev *d_inst = nullptr;
+    std::vector<InstDev> h_inst;
+    Chunk *d_chunks = nullptr;
+    int nchunks = 0;
+    int *d_cfirst = nullptr;
+    Item *d_items = nullptr;
+    int nitems = 0;
+    int *d_counter = nullptr;
+    int row_elems64 = 0, row_elems32 = 0;
+    size_t smem64 = 0, smem32 = 0;
+    std::vector<int> tune;  // triples (norb, dtype, tpr)
+    // sigma call plumbing
+    void **d_cin = nullptr, **d_cout = nullptr;
+    int *d_on_all = nullptr;
+    int64_t stats[3] = {0, 0, 0};
+    std::vector<std::pair<void *, size_t>> allocs;
+};
+
+namespace {
+
+template <typename P>
+P *balloc(fci_batch *b, size_t count, int *rc) {
+    if (*rc || count == 0) return nullptr;
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, sizeof(P) * count);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *rc = fail(FCI_ERR_OOM, "batched CASCI: device allocation failed");
+        return nullptr;
+    }
+    b->allocs.push_back({p, sizeof(P) * count});
+    return (P *)p;
+}
+
+unsigned grid_flat(int64_t n) {
+    int64_t g = (n + 255) / 256;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 4 * 152));
+}
+
+// Work items with the instances' current tpr, largest instances first.
+int build_items(fci_batch *b, int *rc) {
+    std::vector<int> order(b->ninst);
+    for (int i = 0; i < b->ninst; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->h_inst[x].ndet > b->h_inst[y].ndet; });
+    std::vector<Item> items;
+    for (int i : order) {
+        const int R = kBlock / b->h_inst[i].tpr;
+        for (int64_t r = 0; r < b->h_inst[i].A.ns; r += R) items.push_back({i, (int)r});
+    }
+    b->nitems = (int)items.size();
+    if (!b->d_items) b->d_items = balloc<Item>(b, items.size(), rc);
+    if (*rc) return *rc;
+    FCI_CUDA(cudaMemcpy(b->d_items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice));
+    FCI_CUDA(cudaMemcpy(b->d_inst, b->h_inst.data(), sizeof(InstDev) * b->ninst, cudaMemcpyHostToDevice));
+    return FCI_OK;
+}
+
+template <typename T>
+int launch_bsigma(fci_batch *b, const int *d_on, const T *const *d_in, T *const *d_out, cudaStream_t s,
+                  const Item *items, int nitems) {
+    FCI_CUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(int), s));
+    const size_t smem = sizeof(T) == 8 ? b->smem64 : b->smem32;
+    const int re = sizeof(T) == 8 ? b->row_elems64 : b->row_elems32;
+    k_bsigma<T><<<b->nsm, kBlock, smem, s>>>(b->d_inst, items, nitems, b->d_counter, d_in, d_out, d_on, re);
+    FCI_CUDA(cudaGetLastError());
+    return FCI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fci_batch_free(fci_batch *b) {
+    if (!b) return FCI_OK;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (auto &a : b->allocs) cudaFree(a.first);
+    for (auto *c : b->ctx) fci_free(c);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return FCI_OK;
+}
+
+int64_t fci_batch_offset(fci_batch *b, int i) {
+    if (!b || i < 0 || i > b->ninst) return -1;
+    return b->off[i];
+}
+
+int fci_batch_tuning(fci_batch *b, int *out, int cap, int *count) {
+    if (!b) return fail(FCI_ERR_ARG, "batch is NULL");
+    const int n = (int)b->tune.size() / 3;
+    if (count) *count = n;
+    if (out)
+        for (int i = 0; i < n && i < cap; ++i)
+            for (int k = 0; k < 3; ++k) out[3 * i + k] = b->tune[3 * i + k];
+    return FCI_OK;
+}
+
+int64_t fci_batch_stats(fci_batch *b, int what) {
+    if (!b || what < 0 || what > 2) return -1;
+    return b->stats[what];
+}
+
+int fci_batch_init(fci_batch **out, int ninst, const fci_instance *inst, const fci_options *opt) {
+    if (!out || !inst || ninst < 1) return fail(FCI_ERR_ARG, "batched CASCI: bad arguments");
+    *out = nullptr;
+    fci_options o;
+    fci_default_options(&o);
+    if (opt) {
+        if (opt->struct_size != (int)sizeof(fci_options)) return fail(FCI_ERR_ARG, "fci_options.struct_size mismatch");
+        o = *opt;
+    }
+    for (int i = 0; i < ninst; ++i)
+        if (inst[i].norb < 1 || inst[i].norb > 16) return fail(FCI_ERR_ARG, "batched CASCI: norb must be in 1..16");
+    fci_batch *b = new (std::nothrow) fci_batch();
+    if (!b) return fail(FCI_ERR_OOM, "host allocation failed");
+    b->opt = o;
+    b->ninst = ninst;
+    int rc = FCI_OK;
+    {
+        int dev = o.device;
+        if (dev < 0) cudaGetDevice(&dev);
+        b->device = dev;
+        cudaSetDevice(dev);
+        cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    }
+    fci_options oi = o;
+    oi.device = b->device;
+    b->off.assign(ninst + 1, 0);
+    int maxnsb = 0, maxnpair = 0;
+    for (int i = 0; i < ninst && rc == FCI_OK; ++i) {
+        fci_ctx *c = nullptr;
+        rc = fci_init(&c, inst[i].norb, inst[i].nalpha, inst[i].nbeta, inst[i].h1, inst[i].eri, &oi);
+        if (rc) break;
+        b->ctx.push_back(c);
+        InstDev d;
+        d.A = c->A;
+        d.B = c->B;
+        d.W = c->W;
+        d.Wf = c->Wf;
+        d.hdiag = c->hdiag;
+        d.ndet = c->ndet;
+        d.off = b->off[i];
+        d.npair = c->npair;
+        d.tpr = 128;
+        b->h_inst.push_back(d);
+        b->off[i + 1] = b->off[i] + c->ndet;
+        maxnsb = std::max<int>(maxnsb, (int)c->B.ns);
+        maxnpair = std::max(maxnpair, c->npair);
+    }
+    if (rc) {
+        std::string msg = fci_last_error();
+        fci_batch_free(b);
+        set_error(msg);
+        return rc;
+    }
+    b->ntot = b->off[ninst];
+    // chunks of <= 256 elements inside one instance
+    std::vector<Chunk> ch;
+    std::vector<int> cfirst(ninst + 1, 0);
+    for (int i = 0; i < ninst; ++i) {
+        cfirst[i] = (int)ch.size();
+        for (int64_t s0 = 0; s0 < b->h_inst[i].ndet; s0 += kChunk)
+            ch.push_back({i, (int)std::min<int64_t>(kChunk, b->h_inst[i].ndet - s0), b->off[i] + s0});
+    }
+    cfirst[ninst] = (int)ch.size();
+    b->nchunks = (int)ch.size();
+    b->d_chunks = balloc<Chunk>(b, ch.size(), &rc);
+    b->d_cfirst = balloc<int>(b, ninst + 1, &rc);
+    b->d_inst = balloc<InstDev>(b, ninst, &rc);
+    b->d_counter = balloc<int>(b, 1, &rc);
+    b->d_cin = balloc<void *>(b, ninst, &rc);
+    b->d_cout = balloc<void *>(b, ninst, &rc);
+    b->d_on_all = balloc<int>(b, ninst, &rc);
+    if (rc) {
+        fci_batch_free(b);
+        return rc;
+    }
+    cudaMemcpy(b->d_chunks, ch.data(), sizeof(Chunk) * ch.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(b->d_cfirst, cfirst.data(), sizeof(int) * (ninst + 1), cudaMemcpyHostToDevice);
+    std::vector<int> ones(ninst, 1);
+    cudaMemcpy(b->d_on_all, ones.data(), sizeof(int) * ninst, cudaMemcpyHostToDevice);
+    // shared memory: up to 8 row groups (tpr = 32) of 3 rows + one integral row
+    b->row_elems64 = (3 * maxnsb + maxnpair + 1) & ~1;
+    b->row_elems32 = (3 * maxnsb + maxnpair + 3) & ~3;
+    b->smem64 = sizeof(double) * 8 * b->row_elems64;
+    b->smem32 = sizeof(float) * 8 * b->row_elems32;
+    cudaFuncSetAttribute(k_bsigma<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem64);
+    cudaFuncSetAttribute(k_bsigma<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem32);
+    if (b->smem64 > 227 * 1024) {
+        fci_batch_free(b);
+        return fail(FCI_ERR_ARG, "batched CASCI: an instance is too large for the batched sigma kernel");
+    }
+
+    // ---- autotuner: threads per alpha row for each (norb, dtype) ----
+    {
+        const int cands[4] = {32, 64, 128, 256};
+        std::map<int, int> first_of;  // norb -> first instance index
+        for (int i = 0; i < ninst; ++i)
+            if (!first_of.count(inst[i].norb)) first_of[inst[i].norb] = i;
+        // scratch vectors for the largest tuning instance
+        int64_t maxn = 0;
+        for (auto &kv : first_of) maxn = std::max<int64_t>(maxn, b->h_inst[kv.second].ndet);
+        double *x64 = balloc<double>(b, maxn, &rc), *y64 = balloc<double>(b, maxn, &rc);
+        float *x32 = balloc<float>(b, maxn, &rc), *y32 = balloc<float>(b, maxn, &rc);
+        Item *titems = balloc<Item>(b, 1 << 16, &rc);
+        int *ton = balloc<int>(b, ninst, &rc);
+        if (rc) {
+            fci_batch_free(b);
+            return rc;
+        }
+        cudaMemsetAsync(x64, 0, sizeof(double) * maxn, b->stream);
+        cudaMemsetAsync(x32, 0, sizeof(float) * maxn, b->stream);
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        std::map<int, int> best64, best32;
+        for (auto &kv : first_of) {
+            const int i = kv.second;
+            std::vector<int> onv(ninst, 0);
+            onv[i] = 1;
+            cudaMemcpy(ton, onv.data(), sizeof(int) * ninst, cudaMemcpyHostToDevice);
+            std::vector<void *> pin(ninst, nullptr), pout(ninst, nullptr);
+            for (int dt = 0; dt < 2; ++dt) {
+                pin[i] = dt == 0 ? (void *)x64 : (void *)x32;
+                pout[i] = dt == 0 ? (void *)y64 : (void *)y32;
+                cudaMemcpy(b->d_cin, pin.data(), sizeof(void *) * ninst, cudaMemcpyHostToDevice);
+                cudaMemcpy(b->d_cout, pout.data(), sizeof(void *) * ninst, cudaMemcpyHostToDevice);
+                float best_ms = 1e30f;
+                int best = 128;
+                for (int tpr : cands) {
+                    b->h_inst[i].tpr = tpr;
+                    cudaMemcpy(b->d_inst + i, &b->h_inst[i], sizeof(InstDev), cudaMemcpyHostToDevice);
+                    std::vector<Item> it;
+                    const int R = kBlock / tpr;
+                    for (int64_t r = 0; r < b->h_inst[i].A.ns && it.size() < (1u << 16); r += R) it.push_back({i, (int)r});
+                    cudaMemcpy(titems, it.data(), sizeof(Item) * it.size(), cudaMemcpyHostToDevice);
+                    float tmin = 1e30f;
+                    for (int rep = 0; rep < 3; ++rep) {
+                        cudaEventRecord(e0, b->stream);
+                        if (dt == 0)
+                            launch_bsigma<double>(b, ton, (const double *const *)b->d_cin, (double *const *)b->d_cout,
+                                                  b->stream, titems, (int)it.size());
+                        else
+                            launch_bsigma<float>(b, ton, (const float *const *)b->d_cin, (float *const *)b->d_cout,
+                                                 b->stream, titems, (int)it.size());
+                        cudaEventRecord(e1, b->stream);
+                        cudaEventSynchronize(e1);
+                        float ms = 0.f;
+                        cudaEventElapsedTime(&ms, e0, e1);
+                        tmin = std::min(tmin, ms);
+                    }
+                    if (tmin < best_ms) {
+                        best_ms = tmin;
+                        best = tpr;
+                    }
+                }
+                (dt == 0 ? best64 : best32)[kv.first] = best;
+                b->tune.push_back(kv.first);
+                b->tune.push_back(dt == 0 ? FCI_F64 : FCI_F32);
+                b->tune.push_back(best);
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        b->stats[1] = 0;
+        // the FP32 choice is used in mixed mode (most sigma calls), else FP64
+        for (int i = 0; i < ninst; ++i)
+            b->h_inst[i].tpr = (o.precision == FCI_PREC_MIXED ? best32 : best64)[inst[i].norb];
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            fci_batch_free(b);
+            return cuda_fail(e, "batched CASCI tuning");
+        }
+    }
+    if ((rc = build_items(b, &rc))) {
+        fci_batch_free(b);
+        return rc;
+    }
+    *out = b;
+    return FCI_OK;
+}
+
+int fci_batch_sigma(fci_batch *b, const void *c, void *sigma, int dtype, void *stream) {
+    if (!b || !c || !sigma) return fail(FCI_ERR_ARG, "NULL argument");
+    if (dtype != FCI_F64 && dtype != FCI_F32) return fail(FCI_ERR_ARG, "dtype must be FCI_F64 or FCI_F32");
+    FCI_CUDA(cudaSetDevice(b->device));
+    const size_t es = dtype == FCI_F64 ? 8 : 4;
+    std::vector<void *> pin(b->ninst), pout(b->ninst);
+    for (int i = 0; i < b->ninst; ++i) {
+        pin[i] = (char *)c + es * b->off[i];
+        pout[i] = (char *)sigma + es * b->off[i];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    FCI_CUDA(cudaMemcpyAsync(b->d_cin, pin.data(), sizeof(void *) * b->ninst, cudaMemcpyHostToDevice, s));
+    FCI_CUDA(cudaMemcpyAsync(b->d_cout, pout.data(), sizeof(void *) * b->ninst, cudaMemcpyHostToDevice, s));
+    int rc;
+    if (dtype == FCI_F64)
+        rc = launch_bsigma<double>(b, b->d_on_all, (const double *const *)b->d_cin, (double *const *)b->d_cout, s,
+                                   b->d_items, b->nitems);
+    else
+        rc = launch_bsigma<float>(b, b->d_on_all, (const float *const *)b->d_cin, (float *const *)b->d_cout, s,
+                                  b->d_items, b->nitems);
+    if (rc) return rc;
+    FCI_CUDA(cudaStreamSynchronize(s));  // the pointer tables are reused by the next call
+    return FCI_OK;
+}
+
+}  // extern "C"
+
+// ---- batched Davidson ----------------------------------------------------------
+
+namespace fci {
+namespace bt {
+
+// d = d - h (masked)
+__global__ void __launch_bounds__(kBlock) k_bsub(const Chunk *__restrict__ ch, const int *__restrict__ on,
+                                                 double *__restrict__ d, const double *__restrict__ h) {
+    const Chunk c = ch[blockIdx.x];
+    if (!on[c.inst] || threadIdx.x >= c.len) return;
+    const int64_t idx = c.start + threadIdx.x;
+    d[idx] -= h[idx];
+}
+// h = h + d (masked)
+__global__ void __launch_bounds__(kBlock) k_badd(const Chunk *__restrict__ ch, const int *__restrict__ on,
+                                                 double *__restrict__ h, const double *__restrict__ d) {
+    const Chunk c = ch[blockIdx.x];
+    if (!on[c.inst] || threadIdx.x >= c.len) return;
+    const int64_t idx = c.start + threadIdx.x;
+    h[idx] += d[idx];
+}
+
+struct BWork {
+    fci_batch *b;
+    cudaStream_t s;
+    int nroots, maxsub;
+    bool mixed;
+    double *Bv, *Sv, *X, *HX, *T;   // batch vectors: [maxsub|nroots][ntot]
+    float *c32, *s32;               // [ntot]
+    double *A, *w, *V, *g, *nrm2, *rn2, *partial;
+    int *on, *on_exp, *on_ref;      // masks: active, expanding, refining
+    void **ptr32;                   // [2][ninst]: c32 / s32 per instance
+    void **ptrBS;                   // [maxsub][2][ninst]: B_j -> S_j per instance
+    void **ptrXT;                   // [nroots][2][ninst]: X_k -> T_k per instance
+    void **ptrD2;                   // [2][ninst]: scratch for the initial guesses
+    std::map<int, cudaGraphExec_t> g_ritz, g_expand;
+};
+
+// out[i*os + j*js] = X_j . y for j < m, per instance (masked by on)
+static void bdots(BWork &W, const int *on, const double *X, int m, const double *y, double *out, int64_t os,
+                  int64_t js) {
+    fci_batch *b = W.b;
+    if (m <= 8) {
+        k_bdots<8><<<b->nchunks, kBlock, 0, W.s>>>(b->d_chunks, on, X, b->ntot, m, y, W.partial);
+        k_breduce<8><<<b->ninst, 32, 0, W.s>>>(b->d_cfirst, on, W.partial, m, out, os, js);
+    } else {
+        k_bdots<32><<<b->nchunks, kBlock, 0, W.s>>>(b->d_chunks, on, X, b->ntot, m, y, W.partial);
+        k_breduce<32><<<b->ninst, 32, 0, W.s>>>(b->d_cfirst, on, W.partial, m, out, os, js);
+    }
+}
+
+// hx = H x for the batch vector x (instances masked by on); FP32 arithmetic when low.
+// tab: [2][ninst] FP64 in/out pointers of x and hx.
+static int bsigma(BWork &W, const int *on, const double *x, double *hx, void **tab, bool low) {
+    fci_batch *b = W.b;
+    const int n = b->ninst;
+    if (low) {
+        k_d2f<<<grid_flat(b->ntot), 256, 0, W.s>>>(x, W.c32, b->ntot);
+        if (int rc = launch_bsigma<float>(b, on, (const float *const *)W.ptr32, (float *const *)(W.ptr32 + n), W.s,
+                                          b->d_items, b->nitems))
+            return rc;
+        k_f2d<<<grid_flat(b->ntot), 256, 0, W.s>>>(W.s32, hx, b->ntot);
+        return FCI_OK;
+    }
+    return launch_bsigma<double>(b, on, (const double *const *)tab, (double *const *)(tab + n), W.s, b->d_items,
+                                 b->nitems);
+}
+
+}  // namespace bt
+}  // namespace fci
+
+extern "C" int fci_batch_davidson(fci_batch *b, int nroots, double tol, double *energies) {
+    using namespace fci::bt;
+    if (!b || !energies) return fail(FCI_ERR_ARG, "NULL argument");
+    if (nroots < 1 || nroots > kMaxRoots) return fail(FCI_ERR_ARG, "nroots must be in 1..8");
+    for (int i = 0; i < b->ninst; ++i)
+        if (b->h_inst[i].ndet < 2 * nroots) return fail(FCI_ERR_ARG, "an instance has fewer than 2*nroots determinants");
+    if (!(tol > 0)) return fail(FCI_ERR_ARG, "tol must be positive");
+    FCI_CUDA(cudaSetDevice(b->device));
+    FCI_CUDA(cudaDeviceSynchronize());
+    const int ninst = b->ninst;
+    const int64_t ntot = b->ntot;
+    int rc = FCI_OK;
+    BWork W{};
+    W.b = b;
+    W.s = b->stream;
+    W.nroots = nroots;
+    W.mixed = b->opt.precision == FCI_PREC_MIXED;
+    const int maxsub = std::min(kMaxSub, std::max(b->opt.max_subspace, 2 * nroots));
+    W.maxsub = maxsub;
+    std::vector<std::pair<void *, size_t>> mine;
+    auto get = [&](size_t bytes) -> void * {
+        if (rc) return nullptr;
+        void *p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            rc = fail(FCI_ERR_OOM, "batched Davidson: device allocation failed");
+            return nullptr;
+        }
+        mine.push_back({p, bytes});
+        return p;
+    };
+    W.Bv = (double *)get(sizeof(double) * maxsub * ntot);
+    W.Sv = (double *)get(sizeof(double) * maxsub * ntot);
+    W.X = (double *)get(sizeof(double) * nroots * ntot);
+    W.HX = (double *)get(sizeof(double) * nroots * ntot);
+    W.T = (double *)get(sizeof(double) * nroots * ntot);
+    W.c32 = (float *)get(sizeof(float) * ntot);
+    W.s32 = (float *)get(sizeof(float) * ntot);
+    W.A = (double *)get(sizeof(double) * ninst * kMaxSub * kMaxSub);
+    W.V = (double *)get(sizeof(double) * ninst * kMaxSub * kMaxSub);
+    W.w = (double *)get(sizeof(double) * ninst * kMaxSub);
+    W.g = (double *)get(sizeof(double) * ninst * kMaxSub);
+    W.nrm2 = (double *)get(sizeof(double) * ninst);
+    W.rn2 = (double *)get(sizeof(double) * ninst * kMaxRoots);
+    W.partial = (double *)get(sizeof(double) * (size_t)b->nchunks * 32);
+    W.on = (int *)get(sizeof(int) * ninst);
+    W.on_exp = (int *)get(sizeof(int) * ninst);
+    W.on_ref = (int *)get(sizeof(int) * ninst);
+    W.ptr32 = (void **)get(sizeof(void *) * 2 * ninst);
+    W.ptrBS = (void **)get(sizeof(void *) * 2 * ninst * maxsub);
+    W.ptrXT = (void **)get(sizeof(void *) * 2 * ninst * nroots);
+    auto cleanup = [&]() {
+        for (auto &kv : W.g_ritz) cudaGraphExecDestroy(kv.second);
+        for (auto &kv : W.g_expand) cudaGraphExecDestroy(kv.second);
+        for (auto &a : mine) cudaFree(a.first);
+    };
+    if (rc) {
+        cleanup();
+        return rc;
+    }
+    cudaStream_t s = W.s;
+    {
+        std::vector<void *> t(2 * ninst);
+        for (int i = 0; i < ninst; ++i) {
+            t[i] = W.c32 + b->off[i];
+            t[ninst + i] = W.s32 + b->off[i];
+        }
+        cudaMemcpy(W.ptr32, t.data(), sizeof(void *) * 2 * ninst, cudaMemcpyHostToDevice);
+        std::vector<void *> u(2 * ninst * maxsub);
+        for (int j = 0; j < maxsub; ++j)
+            for (int i = 0; i < ninst; ++i) {
+                u[(size_t)j * 2 * ninst + i] = W.Bv + (size_t)j * ntot + b->off[i];
+                u[(size_t)j * 2 * ninst + ninst + i] = W.Sv + (size_t)j * ntot + b->off[i];
+            }
+        cudaMemcpy(W.ptrBS, u.data(), sizeof(void *) * u.size(), cudaMemcpyHostToDevice);
+        std::vector<void *> v(2 * ninst * nroots);
+        for (int k = 0; k < nroots; ++k)
+            for (int i = 0; i < ninst; ++i) {
+                v[(size_t)k * 2 * ninst + i] = W.X + (size_t)k * ntot + b->off[i];
+                v[(size_t)k * 2 * ninst + ninst + i] = W.T + (size_t)k * ntot + b->off[i];
+            }
+        cudaMemcpy(W.ptrXT, v.data(), sizeof(void *) * v.size(), cudaMemcpyHostToDevice);
+    }
+    std::vector<int> active(ninst, 1), exact(ninst, W.mixed ? 0 : 1), inner(ninst, 0), refine(ninst, 0), expand(ninst);
+    std::vector<double> e_prev((size_t)ninst * nroots, INFINITY), r_ref(ninst, INFINITY);
+    std::vector<double> hw((size_t)ninst * kMaxSub), hrn((size_t)ninst * kMaxRoots);
+    const double drop = b->opt.mixed_switch > 0 && b->opt.mixed_switch < 1 ? b->opt.mixed_switch : 1e-2;
+    auto upload = [&](int *dst, const std::vector<int> &vv) {
+        return cudaMemcpyAsync(dst, vv.data(), sizeof(int) * ninst, cudaMemcpyHostToDevice, s);
+    };
+    b->stats[0] = b->stats[1] = b->stats[2] = 0;
+
+    // (1) initial subspace: unit vectors on the lowest diagonal elements, their sigma
+    FCI_CUDA(upload(W.on, active));
+    FCI_CUDA(cudaMemsetAsync(W.A, 0, sizeof(double) * ninst * kMaxSub * kMaxSub, s));
+    k_bguess<<<ninst, 256, 0, s>>>(b->d_inst, nroots, W.Bv, ntot);
+    for (int k = 0; k < nroots && !rc; ++k)
+        rc = bsigma(W, W.on, W.Bv + (size_t)k * ntot, W.Sv + (size_t)k * ntot, W.ptrBS + (size_t)k * 2 * ninst,
+                    W.mixed);
+    b->stats[1] += nroots;
+    int m = nroots;
+    for (int j = 0; j < m && !rc; ++j)
+        bdots(W, W.on, W.Bv, m, W.Sv + (size_t)j * ntot, W.A + j, kMaxSub * kMaxSub, kMaxSub);
+    if (rc) {
+        cleanup();
+        return rc;
+    }
+
+    int it = 0;
+    bool all_done = false;
+    for (it = 1; it <= b->opt.max_iter && !rc; ++it) {
+        // (4) diagonalise; Ritz vectors, residuals and (2)-(3) corrections: one graph per m
+        FCI_CUDA(upload(W.on, active));
+        auto gr = W.g_ritz.find(m);
+        if (gr == W.g_ritz.end()) {
+            cudaGraph_t graph;
+            FCI_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            k_bjacobi<<<ninst, 64, 0, s>>>(W.on, W.A, m, W.w, W.V);
+            for (int k = 0; k < nroots; ++k) {
+                k_blincomb<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on, W.Bv, ntot, m, W.V + k,
+                                                          kMaxSub * kMaxSub, m, 1.0, 0.0, W.X + (size_t)k * ntot);
+                k_blincomb<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on, W.Sv, ntot, m, W.V + k,
+                                                          kMaxSub * kMaxSub, m, 1.0, 0.0, W.HX + (size_t)k * ntot);
+                k_bresid<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on, b->d_inst, W.X + (size_t)k * ntot,
+                                                        W.HX + (size_t)k * ntot, W.w + k, kMaxSub,
+                                                        W.T + (size_t)k * ntot, W.partial);
+                k_breduce<8><<<ninst, 32, 0, s>>>(b->d_cfirst, W.on, W.partial, 1, W.rn2 + k, kMaxRoots, 1);
+            }
+            FCI_CUDA(cudaStreamEndCapture(s, &graph));
+            cudaGraphExec_t ex;
+            FCI_CUDA(cudaGraphInstantiate(&ex, graph, 0));
+            cudaGraphDestroy(graph);
+            gr = W.g_ritz.emplace(m, ex).first;
+        }
+        FCI_CUDA(cudaGraphLaunch(gr->second, s));
+        b->stats[2]++;
+        FCI_CUDA(cudaMemcpyAsync(hw.data(), W.w, sizeof(double) * ninst * kMaxSub, cudaMemcpyDeviceToHost, s));
+        FCI_CUDA(cudaMemcpyAsync(hrn.data(), W.rn2, sizeof(double) * ninst * kMaxRoots, cudaMemcpyDeviceToHost, s));
+        FCI_CUDA(cudaStreamSynchronize(s));
+        // per-instance decisions (convergence only where the Ritz data are exact)
+        bool any_ref = false;
+        for (int i = 0; i < ninst; ++i) {
+            refine[i] = 0;
+            if (!active[i]) continue;
+            double rmax = 0.0, demax = 0.0;
+            for (int k = 0; k < nroots; ++k) {
+                rmax = std::max(rmax, std::sqrt(hrn[(size_t)i * kMaxRoots + k]));
+                demax = std::max(demax, std::fabs(hw[(size_t)i * kMaxSub + k] - e_prev[(size_t)i * nroots + k]));
+            }
+            for (int k = 0; k < nroots; ++k) energies[(size_t)i * nroots + k] = hw[(size_t)i * kMaxSub + k];
+            if (exact[i]) {
+                if (demax < tol && rmax < std::sqrt(tol)) {
+                    active[i] = 0;
+                    continue;
+                }
+                for (int k = 0; k < nroots; ++k) e_prev[(size_t)i * nroots + k] = hw[(size_t)i * kMaxSub + k];
+                r_ref[i] = rmax;
+                inner[i] = 0;
+            } else if (++inner[i] >= 12 || rmax < drop * r_ref[i] || rmax < std::sqrt(tol)) {
+                refine[i] = 1;
+                any_ref = true;
+            }
+        }
+        all_done = std::none_of(active.begin(), active.end(), [](int a) { return a != 0; });
+        if (all_done) break;
+        for (int i = 0; i < ninst; ++i) expand[i] = active[i] && !refine[i];
+        FCI_CUDA(upload(W.on, active));
+        FCI_CUDA(upload(W.on_ref, refine));
+        FCI_CUDA(upload(W.on_exp, expand));
+        if (any_ref) {
+            // refinement: delta = sigma64(x_k) - HX_k corrects S along v_k (rank 1)
+            for (int k = 0; k < nroots && !rc; ++k) {
+                double *d = W.T + (size_t)k * ntot;  // refining instances add no correction this round
+                rc = bsigma(W, W.on_ref, W.X + (size_t)k * ntot, d, W.ptrXT + (size_t)k * 2 * ninst, false);
+                if (rc) break;
+                k_bsub<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on_ref, d, W.HX + (size_t)k * ntot);
+                k_badd<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on_ref, W.HX + (size_t)k * ntot, d);
+                bdots(W, W.on_ref, W.Bv, m, d, W.g, kMaxSub, 1);
+                k_brank1<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on_ref, W.Sv, ntot, m, W.V, k, d);
+                k_brank1_proj<<<ninst, 256, 0, s>>>(W.on_ref, W.A, W.g, W.V, m, k);
+            }
+            if (rc) break;
+            FCI_CUDA(cudaGetLastError());
+            b->stats[1] += nroots;
+            for (int i = 0; i < ninst; ++i)
+                if (refine[i]) exact[i] = 1;
+        }
+        if (m + nroots > maxsub) {
+            // collapse every active instance onto its Ritz vectors and their sigma
+            for (int k = 0; k < nroots; ++k) {
+                k_bcopy<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on, W.X + (size_t)k * ntot,
+                                                       W.Bv + (size_t)k * ntot, 0);
+                k_bcopy<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on, W.HX + (size_t)k * ntot,
+                                                       W.Sv + (size_t)k * ntot, 0);
+            }
+            m = nroots;
+            FCI_CUDA(cudaMemsetAsync(W.A, 0, sizeof(double) * ninst * kMaxSub * kMaxSub, s));
+            for (int j = 0; j < m; ++j)
+                bdots(W, W.on, W.Bv, m, W.Sv + (size_t)j * ntot, W.A + j, kMaxSub * kMaxSub, kMaxSub);
+        }
+        // expansion: one new vector per root and instance (padding where not expanding)
+        auto ge = W.g_expand.find(m);
+        if (ge == W.g_expand.end()) {
+            cudaGraph_t graph;
+            FCI_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            for (int k = 0, mm = m; k < nroots; ++k, ++mm) {
+                double *bv = W.Bv + (size_t)mm * ntot, *sv = W.Sv + (size_t)mm * ntot;
+                k_bcopy<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on_exp, W.T + (size_t)k * ntot, bv, 1);
+                for (int pass = 0; pass < 2; ++pass) {
+                    bdots(W, W.on_exp, W.Bv, mm, bv, W.g, kMaxSub, 1);
+                    k_blincomb<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on_exp, W.Bv, ntot, mm, W.g, kMaxSub, 1,
+                                                              -1.0, 1.0, bv);
+                }
+                bdots(W, W.on_exp, bv, 1, bv, W.nrm2, 1, 1);
+                k_bnormalise<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on_exp, W.nrm2, bv);
+                cudaMemsetAsync(sv, 0, sizeof(double) * ntot, s);
+                bsigma(W, W.on_exp, bv, sv, W.ptrBS + (size_t)mm * 2 * ninst, W.mixed);
+                bdots(W, W.on_exp, W.Bv, mm + 1, sv, W.A + mm, kMaxSub * kMaxSub, kMaxSub);
+                bdots(W, W.on_exp, W.Sv, mm + 1, bv, W.A + (size_t)mm * kMaxSub, kMaxSub * kMaxSub, 1);
+                k_bpad<<<(ninst + 127) / 128, 128, 0, s>>>(W.on_exp, W.nrm2, W.A, mm, ninst);
+            }
+            FCI_CUDA(cudaStreamEndCapture(s, &graph));
+            cudaGraphExec_t ex;
+            FCI_CUDA(cudaGraphInstantiate(&ex, graph, 0));
+            cudaGraphDestroy(graph);
+            ge = W.g_expand.emplace(m, ex).first;
+        }
+        FCI_CUDA(cudaGraphLaunch(ge->second, s));
+        b->stats[2]++;
+        b->stats[1] += nroots;
+        m += nroots;
+        if (W.mixed)
+            for (int i = 0; i < ninst; ++i)
+                if (expand[i]) exact[i] = 0;
+    }
+    b->stats[0] = it > b->opt.max_iter ? b->opt.max_iter : it;
+    cudaError_t e = cudaStreamSynchronize(s);
+    cleanup();
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "batched Davidson");
+    if (!all_done) return fail(FCI_ERR_NOCONV, "batched Davidson: some instances did not converge within max_iter");
+    return FCI_OK;
+}

@@ -27,7 +27,8 @@ EXPORTED = [
     "fci_default_options", "fci_init", "fci_free", "fci_sigma", "fci_hdiag", "fci_davidson",
     "fci_davidson_log", "fci_rdm1", "fci_get_strings", "fci_get_single_table", "fci_query",
     "fci_last_error", "fci_profile_enable", "fci_profile_read", "fci_profile_kernel_name",
-    "fci_rdm1_noalloc",
+    "fci_rdm1_noalloc", "fci_batch_init", "fci_batch_davidson", "fci_batch_sigma", "fci_batch_offset",
+    "fci_batch_tuning", "fci_batch_stats", "fci_batch_free",
 ]
 
 
@@ -35,6 +36,16 @@ class FciError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"fci error {code}: {msg}")
         self.code = code
+
+
+class fci_instance(ctypes.Structure):
+    _fields_ = [
+        ("norb", ctypes.c_int),
+        ("nalpha", ctypes.c_int),
+        ("nbeta", ctypes.c_int),
+        ("h1", ctypes.c_void_p),
+        ("eri", ctypes.c_void_p),
+    ]
 
 
 class fci_options(ctypes.Structure):
@@ -92,6 +103,20 @@ def load(path: str = LIB_PATH):
         lib.fci_profile_enable.argtypes = [vp, i32]
         lib.fci_profile_read.restype = i32
         lib.fci_profile_read.argtypes = [vp, vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        lib.fci_batch_init.restype = i32
+        lib.fci_batch_init.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(fci_instance), ctypes.POINTER(fci_options)]
+        lib.fci_batch_davidson.restype = i32
+        lib.fci_batch_davidson.argtypes = [vp, i32, dbl, vp]
+        lib.fci_batch_sigma.restype = i32
+        lib.fci_batch_sigma.argtypes = [vp, vp, vp, i32, vp]
+        lib.fci_batch_offset.restype = i64
+        lib.fci_batch_offset.argtypes = [vp, i32]
+        lib.fci_batch_tuning.restype = i32
+        lib.fci_batch_tuning.argtypes = [vp, vp, i32, ctypes.POINTER(i32)]
+        lib.fci_batch_stats.restype = i64
+        lib.fci_batch_stats.argtypes = [vp, i32]
+        lib.fci_batch_free.restype = i32
+        lib.fci_batch_free.argtypes = [vp]
         lib.fci_rdm1_noalloc.restype = i32
         lib.fci_rdm1_noalloc.argtypes = [vp, vp, i32, vp, vp]
         lib.fci_profile_kernel_name.restype = ctypes.c_char_p
@@ -273,3 +298,74 @@ def fci_profile_read(ctx: FciContext):
     _check(load().fci_profile_read(ctx.handle, _np_ptr(out), nrec.value, ctypes.byref(nrec), ctypes.byref(nk)))
     names = [load().fci_profile_kernel_name(ctx.handle, i).decode() for i in range(nk.value)]
     return names, out[: nrec.value, : nk.value]
+
+
+class FciBatch:
+    """Owns a ``fci_batch*`` (many independent CASCI instances)."""
+
+    def __init__(self, handle, insts, keep):
+        self.handle = handle
+        self.insts = insts
+        self._keep = keep  # host integral buffers referenced during init
+
+    @property
+    def ninst(self) -> int:
+        return len(self.insts)
+
+    def offset(self, i: int) -> int:
+        return int(load().fci_batch_offset(self.handle, i))
+
+    def __del__(self):
+        try:
+            fci_batch_free(self)
+        except Exception:
+            pass
+
+
+def fci_batch_init(instances, options: fci_options | None = None) -> FciBatch:
+    """instances: sequence of (norb, nalpha, nbeta, h1, eri)."""
+    lib = load()
+    arr = (fci_instance * len(instances))()
+    keep = []
+    for i, (norb, na, nb, h1, eri) in enumerate(instances):
+        h1 = np.ascontiguousarray(h1, dtype=np.float64)
+        eri = np.ascontiguousarray(eri, dtype=np.float64)
+        keep += [h1, eri]
+        arr[i] = fci_instance(norb, na, nb, h1.ctypes.data, eri.ctypes.data)
+    handle = ctypes.c_void_p()
+    opt = options if options is not None else default_options()
+    _check(lib.fci_batch_init(ctypes.byref(handle), len(instances), arr, ctypes.byref(opt)))
+    return FciBatch(handle, [tuple(x[:3]) for x in instances], keep)
+
+
+def fci_batch_davidson(batch: FciBatch, nroots: int, tol: float) -> np.ndarray:
+    e = np.zeros((batch.ninst, nroots))
+    _check(load().fci_batch_davidson(batch.handle, nroots, float(tol), _np_ptr(e)))
+    return e
+
+
+def fci_batch_sigma(batch: FciBatch, c, sigma, stream=None):
+    code = _dtype_code(c)
+    _check(load().fci_batch_sigma(batch.handle, _dev_ptr(c, code), _dev_ptr(sigma, code), code, _stream_ptr(stream)))
+    return sigma
+
+
+def fci_batch_tuning(batch: FciBatch):
+    cnt = ctypes.c_int(0)
+    load().fci_batch_tuning(batch.handle, None, 0, ctypes.byref(cnt))
+    out = np.zeros(3 * max(cnt.value, 1), dtype=np.int32)
+    _check(load().fci_batch_tuning(batch.handle, _np_ptr(out), cnt.value, ctypes.byref(cnt)))
+    return [tuple(int(v) for v in out[3 * i:3 * i + 3]) for i in range(cnt.value)]
+
+
+def fci_batch_stats(batch: FciBatch) -> dict:
+    lib = load()
+    return {"iterations": int(lib.fci_batch_stats(batch.handle, 0)),
+            "sigma_launches": int(lib.fci_batch_stats(batch.handle, 1)),
+            "graph_launches": int(lib.fci_batch_stats(batch.handle, 2))}
+
+
+def fci_batch_free(batch: FciBatch):
+    if batch.handle:
+        load().fci_batch_free(batch.handle)
+        batch.handle = None

@@ -1,0 +1,88 @@
+"""Batched CASCI (many independent instances in lock-step) against the
+single-instance path and the oracle."""
+import numpy as np
+import pytest
+
+import fci_inputs as fi
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1707_04346_gb300 as p
+
+    return p
+
+
+def instances(spec, base_seed=1707):
+    out = []
+    for i, (n, na, nb) in enumerate(spec):
+        rank = min(40, n * (n + 1) // 2)
+        h1, eri = fi.make_integrals(n, rank, seed=base_seed + i)
+        out.append((n, na, nb, h1, eri))
+    return out
+
+
+SPEC = [(6, 3, 3), (8, 4, 4), (10, 5, 5), (7, 4, 3), (6, 3, 3), (9, 4, 5), (4, 2, 2)]
+
+
+@pytest.mark.parametrize("dtype,rtol", [(torch.float64, 1e-12), (torch.float32, 2e-5)])
+def test_batch_sigma_matches_single_instance(pkg, dtype, rtol):
+    insts = instances(SPEC)
+    batch = pkg.fci_batch_init(insts)
+    total = batch.offset(batch.ninst)
+    c = torch.from_numpy(fi.make_vector(total, seed=9)).to(DEV, dtype)
+    s = torch.empty_like(c)
+    pkg.fci_batch_sigma(batch, c, s)
+    torch.cuda.synchronize()
+    for i, (n, na, nb, h1, eri) in enumerate(insts):
+        ctx = pkg.fci_init(n, na, nb, h1, eri)
+        lo, hi = batch.offset(i), batch.offset(i + 1)
+        ci = c[lo:hi].contiguous().double()
+        si = torch.empty_like(ci)
+        pkg.fci_sigma(ctx, ci, si)
+        torch.cuda.synchronize()
+        ref = si.cpu().numpy()
+        got = s[lo:hi].double().cpu().numpy()
+        assert np.abs(got - ref).max() <= rtol * np.abs(ref).max(), i
+        pkg.fci_free(ctx)
+
+
+def test_batch_davidson_fp64_matches_lapack(pkg, oracle_mod):
+    spec = [(6, 3, 3), (8, 4, 4), (7, 4, 3), (6, 3, 3), (5, 3, 2), (8, 4, 4)]
+    insts = instances(spec, base_seed=11)
+    batch = pkg.fci_batch_init(insts, pkg.default_options(max_subspace=16))
+    e = pkg.fci_batch_davidson(batch, 2, 1e-11)
+    for i, (n, na, nb, h1, eri) in enumerate(insts):
+        ref = np.linalg.eigvalsh(oracle_mod.hamiltonian(n, na, nb, h1, eri))[:2]
+        assert np.abs(e[i] - ref).max() < 1e-9, (i, e[i], ref)
+    st = pkg.fci_batch_stats(batch)
+    assert st["iterations"] > 0 and st["graph_launches"] > 0 and st["sigma_launches"] > 0
+
+
+def test_batch_davidson_mixed_matches_single_fp64(pkg):
+    spec = [(10, 5, 5), (8, 4, 4), (6, 3, 3), (10, 5, 5), (9, 5, 4), (12, 6, 6)]
+    insts = instances(spec, base_seed=31)
+    batch = pkg.fci_batch_init(insts, pkg.default_options(precision=pkg.FCI_PREC_MIXED))
+    e = pkg.fci_batch_davidson(batch, 2, 1e-10)
+    for i, (n, na, nb, h1, eri) in enumerate(insts):
+        ctx = pkg.fci_init(n, na, nb, h1, eri)
+        ref = pkg.fci_davidson(ctx, 2, 1e-10)
+        assert np.abs(e[i] - ref).max() < 1e-8, (i, e[i], ref)
+        pkg.fci_free(ctx)
+
+
+def test_batch_tuning_table(pkg):
+    insts = instances([(6, 3, 3), (8, 4, 4), (6, 3, 3)])
+    batch = pkg.fci_batch_init(insts)
+    table = pkg.fci_batch_tuning(batch)
+    assert sorted((n, d) for n, d, _ in table) == [(6, 0), (6, 1), (8, 0), (8, 1)]
+    assert all(t in (32, 64, 128, 256) for _, _, t in table)
