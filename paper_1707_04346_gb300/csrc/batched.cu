@@ -868,8 +868,9 @@ extern "C" int fci_batch_davidson(fci_batch *b, int nroots, double tol, double *
     };
     W.Bv = (double *)get(sizeof(double) * maxsub * ntot);
     W.Sv = (double *)get(sizeof(double) * maxsub * ntot);
-    W.X = (double *)get(sizeof(double) * nroots * ntot);
-    W.HX = (double *)get(sizeof(double) * nroots * ntot);
+    const int keepn = std::max(nroots, std::min(8, maxsub / 2));  // thick restart
+    W.X = (double *)get(sizeof(double) * keepn * ntot);
+    W.HX = (double *)get(sizeof(double) * keepn * ntot);
     W.T = (double *)get(sizeof(double) * nroots * ntot);
     W.c32 = (float *)get(sizeof(float) * ntot);
     W.s32 = (float *)get(sizeof(float) * ntot);
@@ -1023,14 +1024,24 @@ extern "C" int fci_batch_davidson(fci_batch *b, int nroots, double tol, double *
                 if (refine[i]) exact[i] = 1;
         }
         if (m + nroots > maxsub) {
-            // collapse every active instance onto its Ritz vectors and their sigma
-            for (int k = 0; k < nroots; ++k) {
+            // thick restart: every active instance collapses onto its lowest `keep`
+            // Ritz vectors and their sigma
+            const int keep = std::min(keepn, m);
+            for (int k = nroots; k < keep; ++k) {
+                k_blincomb<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on, W.Bv, ntot, m, W.V + k,
+                                                          kMaxSub * kMaxSub, m, 1.0, 0.0, W.X + (size_t)k * ntot);
+                k_blincomb<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on, W.Sv, ntot, m, W.V + k,
+                                                          kMaxSub * kMaxSub, m, 1.0, 0.0, W.HX + (size_t)k * ntot);
+            }
+            for (int k = 0; k < keep; ++k) {
                 k_bcopy<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on, W.X + (size_t)k * ntot,
                                                        W.Bv + (size_t)k * ntot, 0);
                 k_bcopy<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on, W.HX + (size_t)k * ntot,
                                                        W.Sv + (size_t)k * ntot, 0);
             }
-            m = nroots;
+            m = keep;
+            if (W.mixed && keep > nroots)
+                for (int i = 0; i < ninst; ++i) exact[i] = 0;  // the extra vectors carry FP32 sigma
             FCI_CUDA(cudaMemsetAsync(W.A, 0, sizeof(double) * ninst * kMaxSub * kMaxSub, s));
             for (int j = 0; j < m; ++j)
                 bdots(W, W.on, W.Bv, m, W.Sv + (size_t)j * ntot, W.A + j, kMaxSub * kMaxSub, kMaxSub);

@@ -12,7 +12,8 @@
 // Gram-Schmidt applied twice, corrections with norm < 1e-10 dropped,
 // convergence when every root has |dE| < tol and ||r|| < sqrt(tol), unit
 // vectors on the lowest diagonal elements as the guess (ties: lower index),
-// and collapse to the Ritz vectors when the subspace is full.
+// and a thick restart when the subspace is full: collapse onto the lowest
+// min(8, max_subspace/2) Ritz vectors (at least nroots).
 //
 // Every vector operation, the projected matrix, its diagonalisation (cyclic
 // Jacobi in one CTA, FP64) and the residual norms stay on the device.  The
@@ -434,8 +435,10 @@ int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *v
     const bool mixed = ctx->opt.precision == FCI_PREC_MIXED;
     W.Bv = W.get<double>((size_t)maxsub * W.n);
     W.Sv = W.get<double>((size_t)maxsub * W.n);
-    W.X = W.get<double>((size_t)nroots * W.n);
-    W.HX = W.get<double>((size_t)nroots * W.n);
+    // thick restart: a collapse keeps up to `keepn` Ritz vectors (at least nroots)
+    const int keepn = std::max(nroots, std::min(8, maxsub / 2));
+    W.X = W.get<double>((size_t)keepn * W.n);
+    W.HX = W.get<double>((size_t)keepn * W.n);
     W.T = W.get<double>((size_t)nroots * W.n);
     if (mixed) {
         W.c32 = W.get<float>(W.n);
@@ -548,10 +551,18 @@ int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *v
             continue;
         }
         if (m + nr > maxsub) {
-            // collapse onto the Ritz vectors (orthonormal to rounding) and their sigma
-            FCI_CUDA(cudaMemcpyAsync(W.Bv, W.X, sizeof(double) * nr * n, cudaMemcpyDeviceToDevice, s));
-            FCI_CUDA(cudaMemcpyAsync(W.Sv, W.HX, sizeof(double) * nr * n, cudaMemcpyDeviceToDevice, s));
-            m = nr;
+            // thick restart: collapse onto the lowest `keep` Ritz vectors (orthonormal
+            // to rounding) and their sigma
+            const int keep = std::min(keepn, m);
+            for (int k = nr; k < keep; ++k) {
+                k_lincomb<<<grid_for(n), 256, 0, s>>>(W.Bv, m, W.V + k, m, 0.0, W.X + (size_t)k * n, n);
+                k_lincomb<<<grid_for(n), 256, 0, s>>>(W.Sv, m, W.V + k, m, 0.0, W.HX + (size_t)k * n, n);
+            }
+            FCI_CUDA(cudaGetLastError());
+            FCI_CUDA(cudaMemcpyAsync(W.Bv, W.X, sizeof(double) * keep * n, cudaMemcpyDeviceToDevice, s));
+            FCI_CUDA(cudaMemcpyAsync(W.Sv, W.HX, sizeof(double) * keep * n, cudaMemcpyDeviceToDevice, s));
+            if (mixed && keep > nr) exact = false;  // the extra vectors carry FP32 sigma
+            m = keep;
             FCI_CUDA(cudaMemsetAsync(W.A, 0, sizeof(double) * kMaxSub * kMaxSub, s));
             for (int j = 0; j < m; ++j)
                 if (int rc = dots(W, W.Bv, m, W.Sv + (size_t)j * n, W.A + j, kMaxSub)) return rc;

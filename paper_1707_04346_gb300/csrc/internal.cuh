@@ -50,6 +50,8 @@ struct SpinTables {
     uint32_t *str = nullptr;   // [ns] bitmasks, ascending
     uint32_t *tab = nullptr;   // [nsingle][ns] packed entries (entry-major)
     uint32_t *tabq = nullptr;  // [ns][nsingle] the same entries, string-major, sorted by pair index
+    uint32_t *tabo = nullptr;  // [ne*(norb-ne)][ns] off-diagonal entries only (k != l), entry-major
+    double *wdiag = nullptr;   // [npair][ns]: sum over occupied l of (p | ll)
     int32_t *gcol = nullptr;   // [nsame][ns] same-spin Hamiltonian columns (ELL)
     double *gval = nullptr;    // [nsame][ns]
     float *gvalf = nullptr;    // [nsame][ns] FP32 copy

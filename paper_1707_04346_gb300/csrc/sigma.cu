@@ -1,20 +1,22 @@
 // sigma = H c as sigma_1 + sigma_2 + sigma_3 (Eq. 8), string driven (Section 3.3).
 //
 // Layout: C and sigma are row-major [N_alpha][N_beta] (Eq. 4).
-//  sigma_2 (alpha-alpha, I_beta = J_beta): row gather
-//      sigma(Ia, :) = sum_J G_a(Ia, J) C(J, :)
-//    over the ELL row of the alpha same-spin Hamiltonian; every load of a C
-//    row is coalesced along beta.
-//  sigma_1 (beta-beta, I_alpha = J_alpha): gather inside one C row
-//      sigma(Ia, Ib) += sum_J G_b(Ib, J) C(Ia, J)
-//    with the C row staged in shared memory.
+//  sigma_1 (beta-beta, I_alpha = J_alpha): gather inside C rows
+//      sigma(Ia, Ib) = sum_J G_b(Ib, J) C(Ia, J)
+//    with R rows of C staged in shared memory, so each entry of the beta
+//    same-spin Hamiltonian (ELL) is read once per R rows.
+//  sigma_2 (alpha-alpha, I_beta = J_beta): the same gather along columns
+//      sigma(Ia, Ib) += sum_J G_a(Ia, J) C(J, Ib)
+//    with R beta columns of C staged in shared memory (read and written as
+//    runs of R consecutive elements of each row).
 //  sigma_3 (alpha-beta): with W[(ij),(kl)] = (ij|kl) and the replacement
 //    lists of both strings,
 //      sigma(Ia, Ib) += sum_{a in E(Ia)} s_a sum_{b in E(Ib)} s_b W[p_a][p_b] C(J_a, J_b)
 //    (the alpha-beta part of 1/2 sum (ij|kl) E_ij E_kl, where the alpha-beta
-//    and beta-alpha halves coincide).  One CTA owns an output row; for each
-//    alpha replacement a it stages C(J_a, :) and W[p_a, :] in shared memory
-//    and accumulates the row of sigma in shared memory.
+//    and beta-alpha halves coincide).  FP64: one CTA owns an output row; for
+//    each alpha replacement a it stages C(J_a, :) and W[p_a, :] in shared
+//    memory and accumulates the row of sigma in shared memory (diagonal
+//    replacements merged, see k_sigma3_exact).  FP32: sigma_tc.cu.
 #include "internal.cuh"
 
 namespace fci {
@@ -30,94 +32,130 @@ __device__ __forceinline__ float gval_of<float>(const SpinTables &S, int64_t idx
     return S.gvalf[idx];
 }
 
-// sigma(Ia, Ib) = sum_e G_a[e][Ia] * C(col_e, Ib)   (overwrites sigma)
-template <typename T>
-__global__ void __launch_bounds__(256) k_sigma2_rows(const T *__restrict__ C, T *__restrict__ sig, SpinTables A,
-                                                     int64_t nsb) {
+// sigma_1 (beta-beta, I_alpha = J_alpha): R rows of C in shared memory,
+//   sigma(Ia, Ib) = sum_e G_b[e][Ib] * C(Ia, col_e)        (overwrites sigma)
+// Each ELL entry of a beta string is read once per block of R rows.
+template <typename T, int R>
+__global__ void __launch_bounds__(512) k_sigma1_rows(const T *__restrict__ C, T *__restrict__ sig, SpinTables B,
+                                                     int64_t nsa) {
     extern __shared__ unsigned char smem_raw[];
-    int32_t *col = reinterpret_cast<int32_t *>(smem_raw);
-    T *val = reinterpret_cast<T *>(smem_raw + ((sizeof(int32_t) * A.nsame + 15) & ~size_t(15)));
-    const int64_t ia = blockIdx.y;
-    for (int e = threadIdx.x; e < A.nsame; e += blockDim.x) {
-        col[e] = A.gcol[(int64_t)e * A.ns + ia];
-        val[e] = gval_of<T>(A, (int64_t)e * A.ns + ia);
-    }
-    __syncthreads();
-    const int64_t ib = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (ib >= nsb) return;
-    T acc = 0;
-    for (int e = 0; e < A.nsame; ++e) acc += val[e] * C[(int64_t)col[e] * nsb + ib];
-    sig[ia * nsb + ib] = acc;
-}
-
-// sigma(Ia, Ib) += sum_e G_b[e][Ib] * C(Ia, col_e)
-template <typename T>
-__global__ void __launch_bounds__(512) k_sigma1_cols(const T *__restrict__ C, T *__restrict__ sig, SpinTables B) {
-    extern __shared__ unsigned char smem_raw[];
-    T *row = reinterpret_cast<T *>(smem_raw);
+    T *rows = reinterpret_cast<T *>(smem_raw);
     const int64_t nsb = B.ns;
-    const int64_t ia = blockIdx.x;
-    for (int64_t j = threadIdx.x; j < nsb; j += blockDim.x) row[j] = C[ia * nsb + j];
+    const int64_t r0 = (int64_t)blockIdx.x * R;
+    for (int64_t t = threadIdx.x; t < (int64_t)R * nsb; t += blockDim.x) {
+        const int64_t r = t / nsb, j = t % nsb;
+        rows[t] = (r0 + r < nsa) ? C[(r0 + r) * nsb + j] : T(0);
+    }
     __syncthreads();
     for (int64_t ib = threadIdx.x; ib < nsb; ib += blockDim.x) {
-        T acc = 0;
+        T acc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = 0;
         for (int e = 0; e < B.nsame; ++e) {
-            int64_t idx = (int64_t)e * nsb + ib;
-            acc += gval_of<T>(B, idx) * row[B.gcol[idx]];
+            const int64_t idx = (int64_t)e * nsb + ib;
+            const int32_t col = B.gcol[idx];
+            const T v = gval_of<T>(B, idx);
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] = fma(v, rows[(int64_t)r * nsb + col], acc[r]);
         }
-        sig[ia * nsb + ib] += acc;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (r0 + r < nsa) sig[(r0 + r) * nsb + ib] = acc[r];
     }
 }
 
-template <typename T>
-__device__ __forceinline__ T w_of(const double *W, const float *Wf, int64_t i);
-template <>
-__device__ __forceinline__ double w_of<double>(const double *W, const float *, int64_t i) {
-    return W[i];
-}
-template <>
-__device__ __forceinline__ float w_of<float>(const double *, const float *Wf, int64_t i) {
-    return Wf[i];
+// sigma_2 (alpha-alpha, I_beta = J_beta): R beta columns of C in shared memory,
+//   sigma(Ia, Ib) += sum_e G_a[e][Ia] * C(col_e, Ib)
+// Columns are loaded and written as runs of R consecutive elements of a row.
+template <typename T, int R>
+__global__ void __launch_bounds__(512) k_sigma2_cols(const T *__restrict__ C, T *__restrict__ sig, SpinTables A,
+                                                     int64_t nsb) {
+    extern __shared__ unsigned char smem_raw[];
+    T *cols = reinterpret_cast<T *>(smem_raw);  // [R][nsa]
+    const int64_t nsa = A.ns;
+    const int64_t c0 = (int64_t)blockIdx.x * R;
+    for (int64_t ia = threadIdx.x; ia < nsa; ia += blockDim.x) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) cols[(int64_t)r * nsa + ia] = (c0 + r < nsb) ? C[ia * nsb + c0 + r] : T(0);
+    }
+    __syncthreads();
+    for (int64_t ia = threadIdx.x; ia < nsa; ia += blockDim.x) {
+        T acc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = 0;
+        for (int e = 0; e < A.nsame; ++e) {
+            const int64_t idx = (int64_t)e * nsa + ia;
+            const int32_t col = A.gcol[idx];
+            const T v = gval_of<T>(A, idx);
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] = fma(v, cols[(int64_t)r * nsa + col], acc[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (c0 + r < nsb) sig[ia * nsb + c0 + r] += acc[r];
+    }
 }
 
 __device__ __forceinline__ double flip_sign(double x, uint32_t signbit) {
     return __longlong_as_double(__double_as_longlong(x) ^ ((long long)signbit << 32));
 }
-__device__ __forceinline__ float flip_sign(float x, uint32_t signbit) {
-    return __int_as_float(__float_as_int(x) ^ (int)signbit);
-}
 
-template <typename T>
-__global__ void __launch_bounds__(512) k_sigma3_exact(const T *__restrict__ C, T *__restrict__ sig, SpinTables A,
-                                                      SpinTables B, const double *__restrict__ W,
-                                                      const float *__restrict__ Wf, int npair) {
+// FP64 sigma_3, exact sparse, with the diagonal replacements merged:
+//  * the n_alpha entries E_kk (k in I_a) all map I_a onto itself with sign +1;
+//    they form one pass over C(I_a, :) with the integral row sum_k (kk|q);
+//  * for every other alpha entry, the n_beta entries E_ll (l in I_b) of the
+//    beta list contribute sum_l (p_a|ll) C(J_a, I_b) = wdiag_b[p_a][I_b] C(J_a, I_b).
+// Each remaining (alpha, beta) replacement pair is one DFMA, the beta sign
+// applied by flipping the sign bit:
+//   2 * (s_b + (s_a - n_a)(s_b - n_b + 1)) FLOP per determinant.
+__global__ void __launch_bounds__(512) k_sigma3_exact(const double *__restrict__ C, double *__restrict__ sig,
+                                                      SpinTables A, SpinTables B, const double *__restrict__ W,
+                                                      int npair) {
     extern __shared__ unsigned char smem_raw[];
     const int64_t nsb = B.ns;
-    T *crow = reinterpret_cast<T *>(smem_raw);
-    T *acc = crow + nsb;
-    T *wrow = acc + nsb;
+    double *crow = reinterpret_cast<double *>(smem_raw);
+    double *acc = crow + nsb;
+    double *wrow = acc + nsb;
     uint32_t *ea = reinterpret_cast<uint32_t *>(wrow + npair);
     const int64_t ia = blockIdx.x;
+    const int noff_b = B.ne * (int)(B.nsingle / (B.ne > 0 ? B.ne : 1) - 1);  // n_b (norb - n_b)
     for (int e = threadIdx.x; e < A.nsingle; e += blockDim.x) ea[e] = A.tab[(int64_t)e * A.ns + ia];
-    for (int64_t j = threadIdx.x; j < nsb; j += blockDim.x) acc[j] = 0;
+    for (int64_t j = threadIdx.x; j < nsb; j += blockDim.x) crow[j] = C[ia * nsb + j];
+    __syncthreads();
+    // merged alpha-diagonal pass
+    for (int q = threadIdx.x; q < npair; q += blockDim.x) {
+        double w = 0.0;
+        for (int a = 0; a < A.nsingle; ++a)
+            if ((int64_t)ent_target(ea[a]) == ia) w += W[(int64_t)ent_pair(ea[a]) * npair + q];
+        wrow[q] = w;
+    }
+    __syncthreads();
+    for (int64_t ib = threadIdx.x; ib < nsb; ib += blockDim.x) {
+        double v = 0.0;
+        for (int b = 0; b < B.nsingle; ++b) {
+            const uint32_t entb = B.tab[(int64_t)b * nsb + ib];
+            v = fma(flip_sign(wrow[ent_pair(entb)], entb & 0x80000000u), crow[ent_target(entb)], v);
+        }
+        acc[ib] = v;
+    }
+    // off-diagonal alpha entries
     for (int a = 0; a < A.nsingle; ++a) {
-        __syncthreads();  // previous a finished with crow / wrow; ea visible
         const uint32_t enta = ea[a];
         const int64_t ja = ent_target(enta);
+        if (ja == ia) continue;
         const int pa = ent_pair(enta);
+        __syncthreads();  // previous pass finished with crow / wrow
         for (int64_t j = threadIdx.x; j < nsb; j += blockDim.x) crow[j] = C[ja * nsb + j];
-        for (int q = threadIdx.x; q < npair; q += blockDim.x) wrow[q] = w_of<T>(W, Wf, (int64_t)pa * npair + q);
+        for (int q = threadIdx.x; q < npair; q += blockDim.x) wrow[q] = W[(int64_t)pa * npair + q];
         __syncthreads();
-        const T sa = ent_negative(enta) ? T(-1) : T(1);
+        const double *wd = B.wdiag + (int64_t)pa * nsb;
         for (int64_t ib = threadIdx.x; ib < nsb; ib += blockDim.x) {
-            T v = 0;
-            for (int b = 0; b < B.nsingle; ++b) {
-                const uint32_t entb = B.tab[(int64_t)b * nsb + ib];
-                // the beta sign goes in by flipping the sign bit (integer pipe), so
-                // each replacement pair costs one fused multiply-add
+            double v = wd[ib] * crow[ib];
+            for (int b = 0; b < noff_b; ++b) {
+                const uint32_t entb = B.tabo[(int64_t)b * nsb + ib];
                 v = fma(flip_sign(wrow[ent_pair(entb)], entb & 0x80000000u), crow[ent_target(entb)], v);
             }
-            acc[ib] += sa * v;
+            acc[ib] += ent_negative(enta) ? -v : v;
         }
     }
     __syncthreads();
@@ -139,36 +177,52 @@ static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s) {
     const SpinTables &A = ctx->A, &B = ctx->B;
     const int64_t nsa = A.ns, nsb = B.ns;
     const size_t lim = smem_limit();
-    static const char *const names[3] = {"sigma2_rows", "sigma1_cols", sizeof(T) == 4 ? "sigma3_tc" : "sigma3_exact"};
+    static const char *const names[3] = {"sigma1_rows", "sigma2_cols", sizeof(T) == 4 ? "sigma3_tc" : "sigma3_exact"};
     const int rec = prof_begin(ctx, s, 3, names);
-    // sigma_2
+    // sigma_1 then sigma_2: R rows / columns per block, the largest R whose block fits
+    auto pick_r = [&](int64_t len) -> int {
+        for (int r = 8; r >= 1; r >>= 1)
+            if ((size_t)r * len * sizeof(T) <= lim) return r;
+        return 0;
+    };
     {
-        size_t sm = ((sizeof(int32_t) * A.nsame + 15) & ~size_t(15)) + sizeof(T) * A.nsame;
-        if (sm > lim) return fail(FCI_ERR_ARG, "same-spin row too wide for shared memory");
-        if (sm > 48 * 1024) FCI_CUDA(cudaFuncSetAttribute(k_sigma2_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        dim3 grid(ceil_div(nsb, 256), (unsigned)nsa);
-        k_sigma2_rows<T><<<grid, 256, sm, s>>>(C, sig, A, nsb);
-        FCI_CUDA(cudaGetLastError());
+        const int R = pick_r(nsb);
+        if (!R) return fail(FCI_ERR_ARG, "beta string count too large for the sigma_1 kernel");
+        const size_t sm = (size_t)R * nsb * sizeof(T);
+        void *k = R == 8 ? (void *)k_sigma1_rows<T, 8> : R == 4 ? (void *)k_sigma1_rows<T, 4>
+                : R == 2 ? (void *)k_sigma1_rows<T, 2> : (void *)k_sigma1_rows<T, 1>;
+        FCI_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        int64_t nsa_ = nsa;
+        SpinTables Bt = B;
+        void *args[] = {(void *)&C, (void *)&sig, (void *)&Bt, (void *)&nsa_};
+        FCI_CUDA(cudaLaunchKernel(k, dim3(ceil_div(nsa, R)), dim3(512), args, sm, s));
         prof_mark(ctx, rec, 0, s);
     }
-    // sigma_1
     {
-        size_t sm = sizeof(T) * nsb;
-        if (sm > lim) return fail(FCI_ERR_ARG, "beta string count too large for the sigma_1 row kernel");
-        if (sm > 48 * 1024) FCI_CUDA(cudaFuncSetAttribute(k_sigma1_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_sigma1_cols<T><<<(unsigned)nsa, 512, sm, s>>>(C, sig, B);
-        FCI_CUDA(cudaGetLastError());
+        const int R = pick_r(nsa);
+        if (!R) return fail(FCI_ERR_ARG, "alpha string count too large for the sigma_2 kernel");
+        const size_t sm = (size_t)R * nsa * sizeof(T);
+        void *k = R == 8 ? (void *)k_sigma2_cols<T, 8> : R == 4 ? (void *)k_sigma2_cols<T, 4>
+                : R == 2 ? (void *)k_sigma2_cols<T, 2> : (void *)k_sigma2_cols<T, 1>;
+        FCI_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        int64_t nsb_ = nsb;
+        SpinTables At = A;
+        void *args[] = {(void *)&C, (void *)&sig, (void *)&At, (void *)&nsb_};
+        FCI_CUDA(cudaLaunchKernel(k, dim3(ceil_div(nsb, R)), dim3(512), args, sm, s));
         prof_mark(ctx, rec, 1, s);
     }
     // sigma_3
     if (A.nsingle > 0 && B.nsingle > 0 && sizeof(T) == 4) {
         if (int rc = launch_sigma3_tc(ctx, (const float *)C, (float *)sig, ctx->opt.f32_splits, s)) return rc;
     } else if (A.nsingle > 0 && B.nsingle > 0) {
-        size_t sm = sizeof(T) * (2 * nsb + ctx->npair) + sizeof(uint32_t) * A.nsingle;
-        if (sm > lim) return fail(FCI_ERR_ARG, "beta string count too large for the sigma_3 row kernel");
-        if (sm > 48 * 1024) FCI_CUDA(cudaFuncSetAttribute(k_sigma3_exact<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_sigma3_exact<T><<<(unsigned)nsa, 512, sm, s>>>(C, sig, A, B, ctx->W, ctx->Wf, ctx->npair);
-        FCI_CUDA(cudaGetLastError());
+        if constexpr (sizeof(T) == 8) {
+            size_t sm = sizeof(double) * (2 * nsb + ctx->npair) + sizeof(uint32_t) * A.nsingle;
+            if (sm > lim) return fail(FCI_ERR_ARG, "beta string count too large for the FP64 sigma_3 row kernel");
+            if (sm > 48 * 1024)
+                FCI_CUDA(cudaFuncSetAttribute(k_sigma3_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            k_sigma3_exact<<<(unsigned)nsa, 512, sm, s>>>(C, sig, A, B, ctx->W, ctx->npair);
+            FCI_CUDA(cudaGetLastError());
+        }
     }
     prof_mark(ctx, rec, 2, s);
     return FCI_OK;

@@ -16,18 +16,24 @@
 // tensor memory: NS = 2 is split-BF16x3, NS = 3 is split-BF16x6 (about FP32
 // accuracy).
 //
-// CTA: 8 warps, one CTA per SM, persistent over output alpha rows.  Each beta
-// string of a 128-row tile has two threads, each gathering half of its K
-// values.  Per tile: the gathered values (already in registers) are split and
-// stored K-major (no swizzle) into shared memory; one thread issues the
-// NS(NS+1)/2 x K/16 MMAs and commits to an mbarrier; while the tensor cores
-// run, every thread already loads the next tile's values; after the (bounded)
-// wait the accumulator is staged from tensor memory into shared memory
-// (tcgen05.ld, warp w reads lanes 32*(w%4).., the two warp groups split the
-// columns), and each thread pair scatters its string's replacement-list
-// entries into the sigma row held in shared memory with FP32 atomics (for a
-// fixed pair the map J_b -> I_b is one-to-one).  If the staged accumulator
-// would not fit, the columns are staged in several passes.
+// CTA: 9 warps, one CTA per SM, persistent over output alpha rows, with
+// three roles that run concurrently on consecutive 128-string tiles:
+//  * warps 0-3 (producers): each thread gathers the K values of one beta
+//    string (the next tile's loads are in flight while the current one is
+//    split into bf16 slices and stored K-major, no swizzle, into one of two A
+//    buffers) and arrives on full[stage];
+//  * warp 8 (one thread) waits for full[stage] and for a free accumulator,
+//    issues the NS(NS+1)/2 x K/16 MMAs into one of two TMEM accumulators and
+//    commits to done[acc];
+//  * warps 4-7 (epilogue): wait for done[acc], copy their 32 accumulator lanes
+//    (tcgen05.ld) into a private shared-memory row, release the accumulator
+//    (empty[acc]) and scatter the string's replacement-list entries into the
+//    sigma row held in shared memory (FP32 atomics; for a fixed pair the map
+//    J_b -> I_b is one-to-one).
+// All waits are bounded; a wait that gives up sets the device error word and
+// the CTA drains and frees its tensor memory.  The pipeline drains at the end
+// of each alpha row, where the sigma row is added to the output and the B
+// operand of the next row is built.
 #include <cuda_bf16.h>
 
 #include "internal.cuh"
@@ -36,7 +42,7 @@ namespace fci {
 namespace tc {
 
 constexpr int kM = 128;
-constexpr long kSpinLimit = 1L << 24;  // mbarrier polls before giving up
+constexpr long kSpinLimit = 1L << 22;  // mbarrier polls before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -133,64 +139,89 @@ __device__ __forceinline__ void store_split8(const float (&v)[8], unsigned char 
     }
 }
 
+// Packed-conversion split: 8 floats -> NS bf16 slices (round to nearest), the
+// remainder carried to the next slice.
+template <int NS>
+__device__ __forceinline__ void store_split8p(const float *v, unsigned char *base, uint32_t slice_bytes,
+                                              uint32_t off) {
+    float rem[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) rem[i] = v[i];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(rem[2 * i], rem[2 * i + 1]);
+            w[i] = *reinterpret_cast<const uint32_t *>(&h);
+            if (s + 1 < NS) {
+                rem[2 * i] -= __uint_as_float(w[i] << 16);
+                rem[2 * i + 1] -= __uint_as_float(w[i] & 0xFFFF0000u);
+            }
+        }
+        *reinterpret_cast<uint4 *>(base + s * slice_bytes + off) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
 struct Layout {
     uint32_t bytesB, bytesA, offA, offG, offSig, offEa, offBar, total;
-    int gcols;   // accumulator columns staged per epilogue pass
-    int passes;  // epilogue passes over the columns
+    int gcols;   // accumulator columns staged per epilogue chunk
+    int stages;  // A tile buffers (1 or 2)
 };
 
-// gcols: columns of the accumulator staged in shared memory at once (npad when
-// everything fits, else a multiple of 16 below it).
-__host__ __device__ inline Layout make_layout(int ns_split, int kpad, int npad, int64_t nsb, int nsingle_a, int gcols) {
+__host__ __device__ inline Layout make_layout(int ns_split, int kpad, int npad, int64_t nsb, int nsingle_a, int gcols,
+                                              int stages) {
     Layout L;
     L.bytesB = (uint32_t)(npad * kpad * 2);
     L.bytesA = (uint32_t)(kM * kpad * 2);
     L.gcols = gcols;
-    L.passes = (npad + gcols - 1) / gcols;
+    L.stages = stages;
     L.offA = ns_split * L.bytesB;
-    L.offG = L.offA + ns_split * L.bytesA;
+    L.offG = L.offA + stages * ns_split * L.bytesA;
     L.offSig = L.offG + (uint32_t)(kM * (gcols + 1) * 4);
     L.offSig = (L.offSig + 15u) & ~15u;
     L.offEa = L.offSig + (uint32_t)(((nsb + 3) / 4) * 16);
     L.offBar = L.offEa + (uint32_t)(((nsingle_a + 3) / 4) * 16);
-    L.total = L.offBar + 16;
+    L.total = L.offBar + 8 * 8 + 16;  // full[2], done[2], empty[2], fail word, tmem slot
     return L;
 }
 
-constexpr int kThreads2 = 256;      // two threads per beta string of the tile
-constexpr int kColBatch = 48;       // accumulator columns loaded per tcgen05.wait
-constexpr int kEntBatch = 24;       // replacement-list entries prefetched per batch
+// roles: warps 0-3 producers, 4-7 epilogue (TMEM lane quarter = warp % 4), 8 issues the MMAs
+constexpr int kThreads2 = 288;
+constexpr int kColBatch = 48;  // accumulator columns loaded per tcgen05.wait
+constexpr int kEntBatch = 24;  // replacement-list entries prefetched per batch
 
-// Gather this thread's half of the K values of tile row `jb` into registers.
-template <int KH>
-__device__ __forceinline__ void gather_half(float (&pre)[KH], const float *__restrict__ C, const uint32_t *sEa,
-                                            int sa_n, int half, int64_t jb, int64_t nsb) {
-#pragma unroll
-    for (int i = 0; i < KH; ++i) {
-        const int a = half * KH + i;
-        pre[i] = (a < sa_n && jb < nsb) ? __ldg(C + (int64_t)ent_target(sEa[a]) * nsb + jb) : 0.f;
-    }
+// Fire-and-forget shared-memory add (no value returned, nothing to wait for).
+__device__ __forceinline__ void red_add_shared(float *p, float v) {
+    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(smem_u32(p)), "f"(v) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t addr) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
 }
 
 template <int NS, int KPAD>
 __global__ void __launch_bounds__(kThreads2, 1)
     k_sigma3_tc(const float *__restrict__ C, float *__restrict__ sig, SpinTables A, SpinTables B,
-                const float *__restrict__ Wf, int npair, int npad, int gcols, uint32_t tmem_cols, int *err) {
+                const float *__restrict__ Wf, int npair, int npad, int gcols, int stages, uint32_t tmem_cols,
+                int *err) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    constexpr int KH = KPAD / 2;  // K values gathered per thread (multiple of 8)
     const int64_t nsb = B.ns;
-    const Layout L = make_layout(NS, KPAD, npad, nsb, A.nsingle, gcols);
+    const Layout L = make_layout(NS, KPAD, npad, nsb, A.nsingle, gcols, stages);
     unsigned char *sB = smem;
     unsigned char *sA = smem + L.offA;
     float *sG = reinterpret_cast<float *>(smem + L.offG);
     float *sSig = reinterpret_cast<float *>(smem + L.offSig);
     uint32_t *sEa = reinterpret_cast<uint32_t *>(smem + L.offEa);
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L.offBar);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + L.offBar + 8);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.offBar);
+    volatile int *s_fail = reinterpret_cast<volatile int *>(smem + L.offBar + 48);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + L.offBar + 56);
+    const uint32_t full0 = smem_u32(bars + 0), done0 = smem_u32(bars + 2), empty0 = smem_u32(bars + 4);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m = tid & (kM - 1);  // tile row (beta string) of this thread
-    const int half = tid >> 7;     // which half of K it gathers / which entries it scatters
     const int gstride = gcols + 1;
+    const int sa_n = A.nsingle, sb_n = B.nsingle;
+    constexpr uint32_t sbo = (uint32_t)(KPAD / 8) * 128u;
+    constexpr int kgroups = KPAD / 8;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -198,24 +229,27 @@ __global__ void __launch_bounds__(kThreads2, 1)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (tid == 0) mbar_init(smem_u32(mbar), 1);
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(full0 + 8 * i, 128);
+            mbar_init(done0 + 8 * i, 1);
+            mbar_init(empty0 + 8 * i, 128);
+        }
+        *s_fail = 0;
+    }
     fence_before();
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tslot;
     const uint32_t idesc = instr_desc(kM, npad);
-    constexpr uint32_t sbo = (uint32_t)(KPAD / 8) * 128u;
-    constexpr int kgroups = KPAD / 8;
-    const int sa_n = A.nsingle, sb_n = B.nsingle;
-    uint32_t phase = 0;
-    bool failed = false;
-    float pre[KH];
+    const int64_t ntiles = (nsb + kM - 1) / kM;
+    int64_t T = 0;  // global tile counter (stage and phase bookkeeping)
 
-    for (int64_t row = blockIdx.x; row < A.ns && !failed; row += gridDim.x) {
+    for (int64_t row = blockIdx.x; row < A.ns; row += gridDim.x) {
+        // ---- row set-up (all threads): alpha list, zero sigma row, B operand ----
         for (int e = tid; e < sa_n; e += kThreads2) sEa[e] = A.tab[(int64_t)e * A.ns + row];
         for (int64_t j = tid; j < nsb; j += kThreads2) sSig[j] = 0.f;
         __syncthreads();
-        // B[q][a] = s_a * (q | p_a), zero padded, NS bf16 slices
         for (int item = tid; item < npad * kgroups; item += kThreads2) {
             const int q = item / kgroups, kg = item % kgroups;
             float v[8];
@@ -230,109 +264,148 @@ __global__ void __launch_bounds__(kThreads2, 1)
                 }
                 v[i] = x;
             }
-            store_split8<NS>(v, sB, L.bytesB, kmajor_offset(q, kg, KPAD));
+            store_split8p<NS>(v, sB, L.bytesB, kmajor_offset(q, kg, KPAD));
         }
-        gather_half<KH>(pre, C, sEa, sa_n, half, m, nsb);
-        for (int64_t t0 = 0; t0 < nsb; t0 += kM) {
-            const int64_t jb = t0 + m;
-            // A tile from the prefetched registers: D[J_b][a] = C(J_a, J_b)
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        fence_after();
+
+        if (warp < 4) {
+            // ---- producers: one beta string of the tile per thread ----
+            const int m = tid;
+            float pre[KPAD];
+            auto gather = [&](int64_t jb) {
 #pragma unroll
-            for (int kg = 0; kg < KH / 8; ++kg) {
-                float v[8];
+                for (int a = 0; a < KPAD; ++a)
+                    pre[a] = (a < sa_n && jb < nsb) ? __ldg(C + (int64_t)ent_target(sEa[a]) * nsb + jb) : 0.f;
+            };
+            gather(m);
+            for (int64_t t = 0; t < ntiles; ++t) {
+                const int64_t Tt = T + t;
+                const int st = (int)(Tt % stages);
+                if (Tt >= stages) {  // MMA of tile Tt - stages has released this A buffer
+                    const int64_t Tp = Tt - stages;
+                    if (!mbar_wait_bounded(done0 + 8 * (uint32_t)(Tp & 1), (uint32_t)((Tp >> 1) & 1))) {
+                        *s_fail = 1;
+                        break;
+                    }
+                }
+                unsigned char *a_st = sA + (uint32_t)st * NS * L.bytesA;
 #pragma unroll
-                for (int i = 0; i < 8; ++i) v[i] = pre[kg * 8 + i];
-                store_split8<NS>(v, sA, L.bytesA, kmajor_offset(m, half * (KH / 8) + kg, KPAD));
+                for (int kg = 0; kg < kgroups; ++kg) store_split8p<NS>(pre + kg * 8, a_st, L.bytesA, kmajor_offset(m, kg, KPAD));
+                fence_async_smem();
+                mbar_arrive(full0 + 8 * (uint32_t)st);
+                if (t + 1 < ntiles) gather((t + 1) * kM + m);
             }
-            fence_async_smem();
-            fence_before();
-            __syncthreads();  // A tile written; previous epilogue finished with sG and TMEM
-            if (tid == 0) {
+        } else if (warp < 8) {
+            // ---- epilogue: lane e of the accumulator is beta string t*128 + e ----
+            const int e = tid - 128;
+            const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+            float *grow = sG + (int64_t)e * gstride;
+            for (int64_t t = 0; t < ntiles; ++t) {
+                const int64_t Tt = T + t;
+                const uint32_t acc = tmem + (uint32_t)((Tt & 1) * npad);
+                if (!mbar_wait_bounded(done0 + 8 * (uint32_t)(Tt & 1), (uint32_t)((Tt >> 1) & 1))) {
+                    *s_fail = 1;
+                    break;
+                }
                 fence_after();
-                uint32_t acc = 0;
+                const int64_t jb = t * kM + e;
+                const bool live = jb < nsb;
+                for (int c_lo = 0; c_lo < npad; c_lo += gcols) {
+                    const int c_hi = min(npad, c_lo + gcols);
+                    for (int cb = c_lo; cb < c_hi; cb += kColBatch) {
+                        uint32_t u[kColBatch];
+#pragma unroll
+                        for (int q = 0; q < kColBatch / 8; ++q) {
+                            const int c0 = cb + q * 8;
+                            if (c0 < c_hi)
+                                asm volatile(
+                                    "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                    : "=r"(u[q * 8 + 0]), "=r"(u[q * 8 + 1]), "=r"(u[q * 8 + 2]), "=r"(u[q * 8 + 3]),
+                                      "=r"(u[q * 8 + 4]), "=r"(u[q * 8 + 5]), "=r"(u[q * 8 + 6]), "=r"(u[q * 8 + 7])
+                                    : "r"(acc + lane_base + (uint32_t)c0));
+                        }
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                        for (int q = 0; q < kColBatch; ++q)
+                            if (cb + q < c_hi) grow[cb - c_lo + q] = __uint_as_float(u[q]);
+                    }
+                    if (c_hi >= npad) {  // accumulator fully read: release it to the MMA warp
+                        fence_before();
+                        mbar_arrive(empty0 + 8 * (uint32_t)(Tt & 1));
+                    }
+                    // scatter this chunk's pairs: sigma(I_a, I_b) += s_b G[J_b][p_b]
+                    if (live) {
+                        // entries that map J_b onto itself (the diagonal pairs (kk), k in J_b)
+                        // are summed in a register and added once
+                        float self = 0.f;
+                        for (int e0 = 0; e0 < sb_n; e0 += kEntBatch) {
+                            uint32_t ent[kEntBatch];
+#pragma unroll
+                            for (int q = 0; q < kEntBatch; ++q)
+                                ent[q] = e0 + q < sb_n ? __ldg(B.tab + (int64_t)(e0 + q) * nsb + jb) : 0u;
+#pragma unroll
+                            for (int q = 0; q < kEntBatch; ++q) {
+                                const int pq = (int)ent_pair(ent[q]);
+                                if (e0 + q < sb_n && pq >= c_lo && pq < c_hi) {
+                                    const float g = grow[pq - c_lo];
+                                    const float v = ent_negative(ent[q]) ? -g : g;
+                                    if ((int64_t)ent_target(ent[q]) == jb) self += v;
+                                    else red_add_shared(&sSig[ent_target(ent[q])], v);
+                                }
+                            }
+                        }
+                        red_add_shared(&sSig[jb], self);
+                    }
+                }
+            }
+        } else if (lane == 0) {
+            // ---- MMA issuer ----
+            for (int64_t t = 0; t < ntiles; ++t) {
+                const int64_t Tt = T + t;
+                const int st = (int)(Tt % stages);
+                const int64_t us = Tt / stages;
+                if (!mbar_wait_bounded(full0 + 8 * (uint32_t)st, (uint32_t)(us & 1))) {
+                    *s_fail = 1;
+                    break;
+                }
+                if (Tt >= 2 && !mbar_wait_bounded(empty0 + 8 * (uint32_t)(Tt & 1), (uint32_t)(((Tt - 2) >> 1) & 1))) {
+                    *s_fail = 1;
+                    break;
+                }
+                fence_after();
+                const uint32_t acc_col = tmem + (uint32_t)((Tt & 1) * npad);
+                const unsigned char *a_st = sA + (uint32_t)st * NS * L.bytesA;
+                uint32_t accf = 0;
 #pragma unroll
                 for (int i = 0; i < NS; ++i)
 #pragma unroll
                     for (int j = 0; j + i < NS; ++j)
 #pragma unroll
                         for (int ks = 0; ks < KPAD / 16; ++ks) {
-                            const uint64_t ad = smem_desc(smem_u32(sA + i * L.bytesA) + ks * 256, 128, sbo);
+                            const uint64_t ad = smem_desc(smem_u32(a_st + i * L.bytesA) + ks * 256, 128, sbo);
                             const uint64_t bd = smem_desc(smem_u32(sB + j * L.bytesB) + ks * 256, 128, sbo);
-                            mma_bf16(tmem, ad, bd, idesc, acc);
-                            acc = 1;
+                            mma_bf16(acc_col, ad, bd, idesc, accf);
+                            accf = 1;
                         }
-                mma_commit(smem_u32(mbar));
+                mma_commit(done0 + 8 * (uint32_t)(Tt & 1));
             }
-            __syncwarp();
-            // prefetch the next tile's gather while the tensor cores run
-            if (t0 + kM < nsb) gather_half<KH>(pre, C, sEa, sa_n, half, t0 + kM + m, nsb);
-            const bool ok = mbar_wait_bounded(smem_u32(mbar), phase);
-            phase ^= 1u;
-            if (__syncthreads_or(!ok)) {
-                if (tid == 0) atomicExch(err, 1);
-                mbar_wait_bounded(smem_u32(mbar), phase ^ 1u);  // let the MMAs drain before freeing TMEM
-                failed = true;
-                break;
-            }
-            fence_after();
-            const bool live = jb < nsb;
-            for (int p = 0; p < L.passes; ++p) {
-                const int c_lo = p * gcols;
-                const int c_hi = min(npad, c_lo + gcols);
-                // stage accumulator columns [c_lo, c_hi): warp w reads lanes 32*(w%4)..,
-                // the two warp groups split the columns
-                const int ncol = c_hi - c_lo;          // multiple of 16
-                const int my_lo = c_lo + half * (ncol / 2);
-                const int my_hi = my_lo + ncol / 2;    // multiple of 8 wide
-                const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-                float *grow = sG + (int64_t)((warp & 3) * 32 + lane) * gstride;
-                // column loads in batches of 48, one wait per batch (ranges are warp-uniform)
-                for (int cb = my_lo; cb < my_hi; cb += kColBatch) {
-                    uint32_t u[kColBatch];
-#pragma unroll
-                    for (int q = 0; q < kColBatch / 8; ++q) {
-                        const int c0 = cb + q * 8;
-                        if (c0 < my_hi)
-                            asm volatile(
-                                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                                : "=r"(u[q * 8 + 0]), "=r"(u[q * 8 + 1]), "=r"(u[q * 8 + 2]), "=r"(u[q * 8 + 3]),
-                                  "=r"(u[q * 8 + 4]), "=r"(u[q * 8 + 5]), "=r"(u[q * 8 + 6]), "=r"(u[q * 8 + 7])
-                                : "r"(tmem + lane_base + (uint32_t)c0));
-                    }
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                    for (int q = 0; q < kColBatch; ++q)
-                        if (cb + q < my_hi) grow[cb - c_lo + q] = __uint_as_float(u[q]);
-                }
-                __syncthreads();
-                // scatter: sigma(I_a, I_b) += s_b G[J_b][p_b]; the two threads of a row split the
-                // entries; entry loads are issued in batches of 24 before any is used
-                if (live) {
-                    const float *gm = sG + (int64_t)m * gstride;
-                    for (int e0 = half; e0 < sb_n; e0 += 2 * kEntBatch) {
-                        uint32_t ent[kEntBatch];
-#pragma unroll
-                        for (int q = 0; q < kEntBatch; ++q) {
-                            const int e = e0 + 2 * q;
-                            ent[q] = e < sb_n ? __ldg(B.tab + (int64_t)e * nsb + jb) : 0u;
-                        }
-#pragma unroll
-                        for (int q = 0; q < kEntBatch; ++q) {
-                            const int pq = (int)ent_pair(ent[q]);
-                            if (e0 + 2 * q < sb_n && pq >= c_lo && pq < c_hi) {
-                                const float g = gm[pq - c_lo];
-                                atomicAdd(&sSig[ent_target(ent[q])], ent_negative(ent[q]) ? -g : g);
-                            }
-                        }
-                    }
-                }
-                if (p + 1 < L.passes) __syncthreads();
-            }
-            fence_before();
         }
+        // ---- row end: everything of this row has been scattered ----
+        fence_before();
         __syncthreads();
-        if (failed) break;
+        fence_after();
+        T += ntiles;
+        if (*s_fail) break;
         for (int64_t j = tid; j < nsb; j += kThreads2) sig[row * nsb + j] += sSig[j];
         __syncthreads();
+    }
+    if (*s_fail && tid == 0) {
+        atomicExch(err, 1);
+        // let any MMA still in flight finish before the accumulator is freed
+        mbar_wait_bounded(done0 + 8 * (uint32_t)((T - 1) & 1), (uint32_t)(((T - 1) >> 1) & 1));
     }
     fence_before();
     __syncthreads();
@@ -345,14 +418,20 @@ __global__ void __launch_bounds__(kThreads2, 1)
 
 static int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
-// Largest staged column count (multiple of 16, dividing the columns into
-// equal-ish passes) whose layout fits in `lim` bytes; 0 if none does.
-static int pick_gcols(int nsplit, int kpad, int npad, int64_t nsb, int nsa_single, int lim) {
-    for (int passes = 1; passes <= npad / 16; ++passes) {
-        const int g = round_up((npad + passes - 1) / passes, 16);
-        if ((int)tc::make_layout(nsplit, kpad, npad, nsb, nsa_single, g).total <= lim) return g;
-    }
-    return 0;
+// Staged columns (multiple of 16) and A buffers whose layout fits in `lim`
+// bytes: two A buffers preferred, then the most columns per chunk.
+static bool pick_layout(int nsplit, int kpad, int npad, int64_t nsb, int nsa_single, int lim, int *gcols,
+                        int *stages) {
+    for (int st = 2; st >= 1; --st)
+        for (int passes = 1; passes <= npad / 16; ++passes) {
+            const int g = round_up((npad + passes - 1) / passes, 16);
+            if ((int)tc::make_layout(nsplit, kpad, npad, nsb, nsa_single, g, st).total <= lim) {
+                *gcols = g;
+                *stages = st;
+                return true;
+            }
+        }
+    return false;
 }
 
 template <int NS>
@@ -376,17 +455,19 @@ int launch_sigma3_tc(fci_ctx *ctx, const float *C, float *sig, int nsplit, cudaS
     int dev = ctx->device, lim = 0, nsm = 0;
     FCI_CUDA(cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     FCI_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const int gcols = pick_gcols(nsplit, kpad, npad, ctx->B.ns, ctx->A.nsingle, lim);
-    if (gcols == 0) return fail(FCI_ERR_ARG, "tensor-core sigma_3: beta string count too large for shared memory");
-    const tc::Layout L = tc::make_layout(nsplit, kpad, npad, ctx->B.ns, ctx->A.nsingle, gcols);
+    int gcols = 0, stages = 0;
+    if (!pick_layout(nsplit, kpad, npad, ctx->B.ns, ctx->A.nsingle, lim, &gcols, &stages))
+        return fail(FCI_ERR_ARG, "tensor-core sigma_3: beta string count too large for shared memory");
+    const tc::Layout L = tc::make_layout(nsplit, kpad, npad, ctx->B.ns, ctx->A.nsingle, gcols, stages);
     uint32_t cols = 32;
-    while (cols < (uint32_t)npad) cols <<= 1;
-    // one CTA per SM (launch bounds); it holds `cols` of the 512 TMEM columns
+    while (cols < (uint32_t)(2 * npad)) cols <<= 1;  // two accumulators
+    if (cols > 512) return fail(FCI_ERR_ARG, "tensor-core sigma_3: accumulators exceed tensor memory");
     FCI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
-    int64_t grid = nsm;
+    int64_t grid = nsm;  // one CTA per SM (launch bounds and shared memory)
     if (grid > ctx->A.ns) grid = ctx->A.ns;
-    void *args[] = {(void *)&C, (void *)&sig, (void *)&ctx->A, (void *)&ctx->B, (void *)&ctx->Wf,
-                    (void *)&ctx->npair, (void *)&npad, (void *)&gcols, (void *)&cols, (void *)&ctx->d_err};
+    void *args[] = {(void *)&C,     (void *)&sig,    (void *)&ctx->A,   (void *)&ctx->B,
+                    (void *)&ctx->Wf, (void *)&ctx->npair, (void *)&npad, (void *)&gcols,
+                    (void *)&stages, (void *)&cols,  (void *)&ctx->d_err};
     FCI_CUDA(cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(tc::kThreads2), args, L.total, s));
     return FCI_OK;
 }
@@ -394,9 +475,9 @@ int launch_sigma3_tc(fci_ctx *ctx, const float *C, float *sig, int nsplit, cudaS
 size_t sigma3_tc_smem(const fci_ctx *ctx, int nsplit) {
     if (ctx->A.nsingle == 0 || ctx->B.nsingle == 0) return 0;
     const int kpad = round_up(ctx->A.nsingle, 16), npad = round_up(ctx->npair, 16);
-    int lim = 232448;
-    const int g = pick_gcols(nsplit, kpad, npad, ctx->B.ns, ctx->A.nsingle, lim);
-    return g ? tc::make_layout(nsplit, kpad, npad, ctx->B.ns, ctx->A.nsingle, g).total : 0;
+    int g = 0, st = 0;
+    if (!pick_layout(nsplit, kpad, npad, ctx->B.ns, ctx->A.nsingle, 232448, &g, &st)) return 0;
+    return tc::make_layout(nsplit, kpad, npad, ctx->B.ns, ctx->A.nsingle, g, st).total;
 }
 
 }  // namespace fci

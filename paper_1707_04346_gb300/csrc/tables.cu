@@ -117,6 +117,34 @@ __global__ void k_sort_by_pair(const uint32_t *tab, int64_t ns, int nsingle, uin
     }
 }
 
+// Off-diagonal entries (k != l) of each string's list, in list order.
+__global__ void k_offdiag_table(const uint32_t *tab, const uint32_t *str, int64_t ns, int nsingle, int noff,
+                                uint32_t *tabo) {
+    int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (x >= ns) return;
+    int o = 0;
+    for (int e = 0; e < nsingle; ++e) {
+        const uint32_t v = tab[(int64_t)e * ns + x];
+        if ((int64_t)ent_target(v) == x) continue;  // only E_kk maps a string onto itself
+        tabo[(int64_t)o * ns + x] = v;
+        ++o;
+    }
+}
+
+// wdiag[p][x] = sum over orbitals l occupied in string x of W[p][(ll)]
+__global__ void k_wdiag(const double *W, int npair, const uint32_t *str, int64_t ns, double *wd) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)npair * ns) return;
+    const int p = (int)(t / ns);
+    const int64_t x = t % ns;
+    double a = 0.0;
+    for (uint32_t m = str[x]; m; m &= m - 1u) {
+        const int l = __ffs(m) - 1;
+        a += W[(int64_t)p * npair + l * (l + 1) / 2 + l];
+    }
+    wd[t] = a;
+}
+
 __device__ __forceinline__ double eri4(const double *eri, int n, int p, int q, int r, int s) {
     return eri[((p * n + q) * n + r) * n + s];
 }
@@ -242,6 +270,9 @@ static int build_spin(fci_ctx *ctx, SpinTables &T, int ne) {
     T.str = (uint32_t *)dalloc(ctx, sizeof(uint32_t) * ns, &rc);
     T.tab = (uint32_t *)dalloc(ctx, sizeof(uint32_t) * ns * T.nsingle, &rc);
     T.tabq = (uint32_t *)dalloc(ctx, sizeof(uint32_t) * ns * T.nsingle, &rc);
+    const int noff = ne * (n - ne);
+    T.tabo = (uint32_t *)dalloc(ctx, sizeof(uint32_t) * ns * (noff > 0 ? noff : 1), &rc);
+    T.wdiag = (double *)dalloc(ctx, sizeof(double) * ns * ctx->npair, &rc);
     T.gcol = (int32_t *)dalloc(ctx, sizeof(int32_t) * ns * T.nsame, &rc);
     T.gval = (double *)dalloc(ctx, sizeof(double) * ns * T.nsame, &rc);
     T.gvalf = (float *)dalloc(ctx, sizeof(float) * ns * T.nsame, &rc);
@@ -253,8 +284,10 @@ static int build_spin(fci_ctx *ctx, SpinTables &T, int ne) {
         k_single_table<<<ceil_div(ns * T.nsingle, 256), 256, 0, s>>>(T.str, ns, n, ne, T.nsingle, T.tab);
         FCI_CUDA(cudaGetLastError());
         k_sort_by_pair<<<ceil_div(ns, 128), 128, 0, s>>>(T.tab, ns, T.nsingle, T.tabq);
+        k_offdiag_table<<<ceil_div(ns, 128), 128, 0, s>>>(T.tab, T.str, ns, T.nsingle, noff, T.tabo);
         FCI_CUDA(cudaGetLastError());
     }
+    k_wdiag<<<ceil_div(ns * ctx->npair, 256), 256, 0, s>>>(ctx->W, ctx->npair, T.str, ns, T.wdiag);
     k_same_spin_rows<<<ceil_div(ns, 64), 64, 0, s>>>(T.str, ns, n, ne, T.nsame, ctx->h1, ctx->eri, T.gcol, T.gval);
     FCI_CUDA(cudaGetLastError());
     k_f64_to_f32<<<ceil_div(ns * T.nsame, 256), 256, 0, s>>>(T.gval, T.gvalf, ns * T.nsame);
@@ -308,6 +341,9 @@ static void free_spin(fci_ctx *ctx, SpinTables &T) {
     dfree(ctx, T.str, sizeof(uint32_t) * T.ns);
     dfree(ctx, T.tab, sizeof(uint32_t) * T.ns * T.nsingle);
     dfree(ctx, T.tabq, sizeof(uint32_t) * T.ns * T.nsingle);
+    const int noff = T.ne * (ctx->norb - T.ne);
+    dfree(ctx, T.tabo, sizeof(uint32_t) * T.ns * (noff > 0 ? noff : 1));
+    dfree(ctx, T.wdiag, sizeof(double) * T.ns * ctx->npair);
     dfree(ctx, T.gcol, sizeof(int32_t) * T.ns * T.nsame);
     dfree(ctx, T.gval, sizeof(double) * T.ns * T.nsame);
     dfree(ctx, T.gvalf, sizeof(float) * T.ns * T.nsame);
