@@ -131,19 +131,43 @@ __global__ void __launch_bounds__(kBlock, 1) k_bsigma(const InstDev *__restrict_
             }
             acc[j] = a;
         }
-        // sigma_3: one staged alpha-replacement row at a time
+        // sigma_3 with the diagonal replacements merged (as in the single-instance
+        // FP64 kernel): first one pass over C(I_a, :) with the summed integral
+        // rows of the alpha E_kk, then the off-diagonal alpha entries against the
+        // off-diagonal beta entries plus sum_l (p_a|ll) C(J_a, I_b)
+        group_sync(g, tpr);
+        for (int q = lt; q < d.npair; q += tpr) {
+            T w = 0;
+            for (int a = 0; a < d.A.nsingle; ++a) {
+                const uint32_t ea = d.A.tab[(int64_t)a * nsa + row];
+                if ((int64_t)ent_target(ea) == row) w += wv<T>(d, (int64_t)ent_pair(ea) * d.npair + q);
+            }
+            wrow[q] = w;
+        }
+        group_sync(g, tpr);
+        for (int64_t j = lt; j < nsb; j += tpr) {
+            T v = 0;
+            for (int b = 0; b < d.B.nsingle; ++b) {
+                const uint32_t eb = d.B.tab[(int64_t)b * nsb + j];
+                v = fma(flipb(wrow[ent_pair(eb)], eb & 0x80000000u), cself[ent_target(eb)], v);
+            }
+            acc[j] += v;
+        }
+        const int noff_b = d.B.ne * (int)(d.npair > 0 ? (d.B.nsingle / (d.B.ne > 0 ? d.B.ne : 1) - 1) : 0);
         for (int a = 0; a < d.A.nsingle; ++a) {
             const uint32_t ea = d.A.tab[(int64_t)a * nsa + row];
             const int64_t ja = ent_target(ea);
+            if (ja == row) continue;
             const int pa = ent_pair(ea);
             group_sync(g, tpr);
             for (int64_t j = lt; j < nsb; j += tpr) ca[j] = C[ja * nsb + j];
             for (int q = lt; q < d.npair; q += tpr) wrow[q] = wv<T>(d, (int64_t)pa * d.npair + q);
             group_sync(g, tpr);
+            const double *wd = d.B.wdiag + (int64_t)pa * nsb;
             for (int64_t j = lt; j < nsb; j += tpr) {
-                T v = 0;
-                for (int b = 0; b < d.B.nsingle; ++b) {
-                    const uint32_t eb = d.B.tab[(int64_t)b * nsb + j];
+                T v = (T)wd[j] * ca[j];
+                for (int b = 0; b < noff_b; ++b) {
+                    const uint32_t eb = d.B.tabo[(int64_t)b * nsb + j];
                     v = fma(flipb(wrow[ent_pair(eb)], eb & 0x80000000u), ca[ent_target(eb)], v);
                 }
                 acc[j] += ent_negative(ea) ? -v : v;
@@ -994,7 +1018,7 @@ extern "C" int fci_batch_davidson(fci_batch *b, int nroots, double tol, double *
                 for (int k = 0; k < nroots; ++k) e_prev[(size_t)i * nroots + k] = hw[(size_t)i * kMaxSub + k];
                 r_ref[i] = rmax;
                 inner[i] = 0;
-            } else if (++inner[i] >= 12 || rmax < drop * r_ref[i] || rmax < std::sqrt(tol)) {
+            } else if (++inner[i] >= 20 || rmax < drop * r_ref[i] || rmax < std::sqrt(tol)) {
                 refine[i] = 1;
                 any_ref = true;
             }

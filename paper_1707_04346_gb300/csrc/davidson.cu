@@ -22,7 +22,7 @@
 // Mixed precision: every new correction gets an FP32 sigma (sigma_3 on the
 // tensor cores); the basis, the projected matrix, orthogonalisation and the
 // residuals stay FP64.  Refinement points: when the residual has fallen by
-// opt.mixed_switch (default 1e-2) since the last one, after 12 corrections,
+// opt.mixed_switch (default 1e-2) since the last one, after 20 corrections,
 // or when it is below sqrt(tol), the FP64 sigma of each Ritz vector x = B v is
 // built and the subspace sigma vectors are corrected along v,
 // S <- S + (sigma64(x) - S v) v^T, together with the projected matrix.  The
@@ -534,7 +534,7 @@ int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *v
             for (int k = 0; k < nr; ++k) e_prev[k] = ev[k];
             r_ref = rmax;
             inner = 0;
-        } else if (++inner >= 12 || rmax < drop * r_ref || rmax < std::sqrt(tol)) {
+        } else if (++inner >= 20 || rmax < drop * r_ref || rmax < std::sqrt(tol)) {
             // refinement: exact FP64 sigma of each Ritz vector; the difference to
             // the subspace estimate corrects every sigma vector along that Ritz
             // direction (S += delta v^T) and the projected matrix with it

@@ -32,6 +32,7 @@ constexpr uint32_t kTargetMask = (1u << kTargetBits) - 1u;
 constexpr int kPairShift = 21;
 constexpr uint32_t kPairMask = 0x3FFu;
 constexpr int kMaxStrings = (1 << kTargetBits) - 1;
+constexpr uint32_t kNoEntry = 0xFFFFFFFFu;  // pair-major table: this string has no entry with that pair
 
 __host__ __device__ inline uint32_t ent_target(uint32_t e) { return e & kTargetMask; }
 __host__ __device__ inline uint32_t ent_pair(uint32_t e) { return (e >> kPairShift) & kPairMask; }
@@ -51,6 +52,7 @@ struct SpinTables {
     uint32_t *tab = nullptr;   // [nsingle][ns] packed entries (entry-major)
     uint32_t *tabq = nullptr;  // [ns][nsingle] the same entries, string-major, sorted by pair index
     uint32_t *tabo = nullptr;  // [ne*(norb-ne)][ns] off-diagonal entries only (k != l), entry-major
+    uint32_t *tabp = nullptr;  // [npair][ns] the entry with pair p of each string, or kNoEntry
     double *wdiag = nullptr;   // [npair][ns]: sum over occupied l of (p | ll)
     int32_t *gcol = nullptr;   // [nsame][ns] same-spin Hamiltonian columns (ELL)
     double *gval = nullptr;    // [nsame][ns]

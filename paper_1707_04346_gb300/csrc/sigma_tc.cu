@@ -169,6 +169,8 @@ struct Layout {
     int stages;  // A tile buffers (1 or 2)
 };
 
+// gcols == 0 selects the private-copy epilogue: no staged accumulator, four
+// copies of the sigma row (one per epilogue warp) instead of one.
 __host__ __device__ inline Layout make_layout(int ns_split, int kpad, int npad, int64_t nsb, int nsingle_a, int gcols,
                                               int stages) {
     Layout L;
@@ -178,9 +180,9 @@ __host__ __device__ inline Layout make_layout(int ns_split, int kpad, int npad, 
     L.stages = stages;
     L.offA = ns_split * L.bytesB;
     L.offG = L.offA + stages * ns_split * L.bytesA;
-    L.offSig = L.offG + (uint32_t)(kM * (gcols + 1) * 4);
+    L.offSig = L.offG + (gcols > 0 ? (uint32_t)(kM * (gcols + 1) * 4) : 0u);
     L.offSig = (L.offSig + 15u) & ~15u;
-    L.offEa = L.offSig + (uint32_t)(((nsb + 3) / 4) * 16);
+    L.offEa = L.offSig + (gcols > 0 ? (uint32_t)(((nsb + 3) / 4) * 16) : 4u * (uint32_t)(((nsb + 32 + 3) / 4) * 16));
     L.offBar = L.offEa + (uint32_t)(((nsingle_a + 3) / 4) * 16);
     L.total = L.offBar + 8 * 8 + 16;  // full[2], done[2], empty[2], fail word, tmem slot
     return L;
@@ -200,7 +202,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t addr) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
 }
 
-template <int NS, int KPAD>
+template <int NS, int KPAD, bool PRIV>
 __global__ void __launch_bounds__(kThreads2, 1)
     k_sigma3_tc(const float *__restrict__ C, float *__restrict__ sig, SpinTables A, SpinTables B,
                 const float *__restrict__ Wf, int npair, int npad, int gcols, int stages, uint32_t tmem_cols,
@@ -248,7 +250,8 @@ __global__ void __launch_bounds__(kThreads2, 1)
     for (int64_t row = blockIdx.x; row < A.ns; row += gridDim.x) {
         // ---- row set-up (all threads): alpha list, zero sigma row, B operand ----
         for (int e = tid; e < sa_n; e += kThreads2) sEa[e] = A.tab[(int64_t)e * A.ns + row];
-        for (int64_t j = tid; j < nsb; j += kThreads2) sSig[j] = 0.f;
+        const int64_t nsig = PRIV ? 4 * (nsb + 32) : nsb;
+        for (int64_t j = tid; j < nsig; j += kThreads2) sSig[j] = 0.f;
         __syncthreads();
         for (int item = tid; item < npad * kgroups; item += kThreads2) {
             const int q = item / kgroups, kg = item % kgroups;
@@ -297,6 +300,57 @@ __global__ void __launch_bounds__(kThreads2, 1)
                 fence_async_smem();
                 mbar_arrive(full0 + 8 * (uint32_t)st);
                 if (t + 1 < ntiles) gather((t + 1) * kM + m);
+            }
+        } else if (warp < 8 && PRIV) {
+            // ---- epilogue, private copies: the warp walks the pair columns in
+            // lock-step; for a fixed pair the 32 targets are distinct, and no other
+            // warp writes this copy, so a plain read-add-write suffices ----
+            const int e = tid - 128;
+            const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+            float *mine = sSig + (int64_t)(warp & 3) * (nsb + 32);
+            for (int64_t t = 0; t < ntiles; ++t) {
+                const int64_t Tt = T + t;
+                const uint32_t acc = tmem + (uint32_t)((Tt & 1) * npad);
+                if (!mbar_wait_bounded(done0 + 8 * (uint32_t)(Tt & 1), (uint32_t)((Tt >> 1) & 1))) {
+                    *s_fail = 1;
+                    break;
+                }
+                fence_after();
+                const int64_t jb = t * kM + e;
+                const bool live = jb < nsb;
+                for (int cb = 0; cb < npad; cb += kColBatch) {
+                    uint32_t u[kColBatch];
+#pragma unroll
+                    for (int q = 0; q < kColBatch / 8; ++q) {
+                        const int c0 = cb + q * 8;
+                        if (c0 < npad)
+                            asm volatile(
+                                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                : "=r"(u[q * 8 + 0]), "=r"(u[q * 8 + 1]), "=r"(u[q * 8 + 2]), "=r"(u[q * 8 + 3]),
+                                  "=r"(u[q * 8 + 4]), "=r"(u[q * 8 + 5]), "=r"(u[q * 8 + 6]), "=r"(u[q * 8 + 7])
+                                : "r"(acc + lane_base + (uint32_t)c0));
+                    }
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (cb + kColBatch >= npad) {  // accumulator fully read: release it
+                        fence_before();
+                        mbar_arrive(empty0 + 8 * (uint32_t)(Tt & 1));
+                    }
+                    uint32_t ent[kColBatch];
+#pragma unroll
+                    for (int q = 0; q < kColBatch; ++q)
+                        ent[q] = (live && cb + q < npair) ? __ldg(B.tabp + (int64_t)(cb + q) * nsb + jb) : kNoEntry;
+                    // branch-free: a missing entry adds 0 to this lane's own dummy slot,
+                    // so the warp stays converged and its read-add-writes stay in order
+#pragma unroll
+                    for (int q = 0; q < kColBatch; ++q) {
+                        const bool has = ent[q] != kNoEntry;
+                        const uint32_t tg = has ? ent_target(ent[q]) : (uint32_t)(nsb + lane);
+                        const float g = __uint_as_float(u[q]);
+                        const float v = has ? (ent_negative(ent[q]) ? -g : g) : 0.f;
+                        mine[tg] += v;
+                    }
+                    __syncwarp();
+                }
             }
         } else if (warp < 8) {
             // ---- epilogue: lane e of the accumulator is beta string t*128 + e ----
@@ -399,7 +453,11 @@ __global__ void __launch_bounds__(kThreads2, 1)
         fence_after();
         T += ntiles;
         if (*s_fail) break;
-        for (int64_t j = tid; j < nsb; j += kThreads2) sig[row * nsb + j] += sSig[j];
+        for (int64_t j = tid; j < nsb; j += kThreads2) {
+            float v = sSig[j];
+            if (PRIV) v += sSig[(nsb + 32) + j] + sSig[2 * (nsb + 32) + j] + sSig[3 * (nsb + 32) + j];
+            sig[row * nsb + j] += v;
+        }
         __syncthreads();
     }
     if (*s_fail && tid == 0) {
@@ -422,6 +480,13 @@ static int round_up(int x, int m) { return (x + m - 1) / m * m; }
 // bytes: two A buffers preferred, then the most columns per chunk.
 static bool pick_layout(int nsplit, int kpad, int npad, int64_t nsb, int nsa_single, int lim, int *gcols,
                         int *stages) {
+    // private-copy epilogue (gcols = 0) when it fits, else staged columns + atomics
+    for (int st = 2; st >= 1; --st)
+        if ((int)tc::make_layout(nsplit, kpad, npad, nsb, nsa_single, 0, st).total <= lim) {
+            *gcols = 0;
+            *stages = st;
+            return true;
+        }
     for (int st = 2; st >= 1; --st)
         for (int passes = 1; passes <= npad / 16; ++passes) {
             const int g = round_up((npad + passes - 1) / passes, 16);
@@ -434,15 +499,15 @@ static bool pick_layout(int nsplit, int kpad, int npad, int64_t nsb, int nsa_sin
     return false;
 }
 
-template <int NS>
+template <int NS, bool PRIV>
 static void *kernel_for(int kpad) {
     switch (kpad) {
-        case 16: return (void *)tc::k_sigma3_tc<NS, 16>;
-        case 32: return (void *)tc::k_sigma3_tc<NS, 32>;
-        case 48: return (void *)tc::k_sigma3_tc<NS, 48>;
-        case 64: return (void *)tc::k_sigma3_tc<NS, 64>;
-        case 80: return (void *)tc::k_sigma3_tc<NS, 80>;
-        case 96: return (void *)tc::k_sigma3_tc<NS, 96>;
+        case 16: return (void *)tc::k_sigma3_tc<NS, 16, PRIV>;
+        case 32: return (void *)tc::k_sigma3_tc<NS, 32, PRIV>;
+        case 48: return (void *)tc::k_sigma3_tc<NS, 48, PRIV>;
+        case 64: return (void *)tc::k_sigma3_tc<NS, 64, PRIV>;
+        case 80: return (void *)tc::k_sigma3_tc<NS, 80, PRIV>;
+        case 96: return (void *)tc::k_sigma3_tc<NS, 96, PRIV>;
         default: return nullptr;
     }
 }
@@ -450,14 +515,16 @@ static void *kernel_for(int kpad) {
 int launch_sigma3_tc(fci_ctx *ctx, const float *C, float *sig, int nsplit, cudaStream_t s) {
     const int kpad = round_up(ctx->A.nsingle, 16), npad = round_up(ctx->npair, 16);
     if (npad > 256) return fail(FCI_ERR_ARG, "tensor-core sigma_3 supports at most 256 orbital pairs (norb <= 22)");
-    void *kern = nsplit == 2 ? kernel_for<2>(kpad) : kernel_for<3>(kpad);
-    if (!kern) return fail(FCI_ERR_ARG, "tensor-core sigma_3 supports at most 96 alpha replacements per string");
+    if (kpad > 96) return fail(FCI_ERR_ARG, "tensor-core sigma_3 supports at most 96 alpha replacements per string");
     int dev = ctx->device, lim = 0, nsm = 0;
     FCI_CUDA(cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     FCI_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     int gcols = 0, stages = 0;
     if (!pick_layout(nsplit, kpad, npad, ctx->B.ns, ctx->A.nsingle, lim, &gcols, &stages))
         return fail(FCI_ERR_ARG, "tensor-core sigma_3: beta string count too large for shared memory");
+    const bool priv = gcols == 0;
+    void *kern = nsplit == 2 ? (priv ? kernel_for<2, true>(kpad) : kernel_for<2, false>(kpad))
+                             : (priv ? kernel_for<3, true>(kpad) : kernel_for<3, false>(kpad));
     const tc::Layout L = tc::make_layout(nsplit, kpad, npad, ctx->B.ns, ctx->A.nsingle, gcols, stages);
     uint32_t cols = 32;
     while (cols < (uint32_t)(2 * npad)) cols <<= 1;  // two accumulators
