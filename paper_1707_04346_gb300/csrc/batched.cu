@@ -48,6 +48,7 @@ struct InstDev {
     const double *hdiag;
     int64_t ndet, off;
     int npair, tpr;
+    int stage_all;  // FP32: all off-diagonal alpha rows of an output row fit in shared memory at once
 };
 
 struct Chunk {
@@ -130,6 +131,74 @@ __global__ void __launch_bounds__(kBlock, 1) k_bsigma(const InstDev *__restrict_
                 a = fma(gv<T>(d.B, ix), cself[d.B.gcol[ix]], a);
             }
             acc[j] = a;
+        }
+        if constexpr (sizeof(T) == 4) {
+            if (d.stage_all && tpr == kBlock) {
+                // FP32, one row group per CTA: stage every off-diagonal alpha row
+                // C(J_a, :) and its signed integral row s_a (p_a|q) once, so each beta
+                // entry is loaded once per determinant
+                const int noff_a = d.A.ne * (d.A.nsingle / (d.A.ne > 0 ? d.A.ne : 1) - 1);
+                const int noff_b = d.B.ne * (d.B.nsingle / (d.B.ne > 0 ? d.B.ne : 1) - 1);
+                T *sR = wrow + ((d.npair + 3) & ~3);            // [noff_a][nsb]
+                T *sW = sR + (int64_t)noff_a * nsb;             // [noff_a][npair]
+                int *sP = reinterpret_cast<int *>(sW + (int64_t)noff_a * d.npair);  // [noff_a] pair of a
+                group_sync(g, tpr);
+                if (lt == 0) {
+                    int o = 0;
+                    for (int a = 0; a < d.A.nsingle; ++a) {
+                        const uint32_t ea = d.A.tab[(int64_t)a * nsa + row];
+                        if ((int64_t)ent_target(ea) != row) sP[o++] = (int)ea;
+                    }
+                }
+                for (int q = lt; q < d.npair; q += tpr) {
+                    T w = 0;
+                    for (int a = 0; a < d.A.nsingle; ++a) {
+                        const uint32_t ea = d.A.tab[(int64_t)a * nsa + row];
+                        if ((int64_t)ent_target(ea) == row) w += wv<T>(d, (int64_t)ent_pair(ea) * d.npair + q);
+                    }
+                    wrow[q] = w;
+                }
+                group_sync(g, tpr);
+                for (int64_t t = lt; t < (int64_t)noff_a * nsb; t += tpr) {
+                    const int a = (int)(t / nsb);
+                    const int64_t j = t % nsb;
+                    sR[t] = C[(int64_t)ent_target((uint32_t)sP[a]) * nsb + j];
+                }
+                for (int t = lt; t < noff_a * d.npair; t += tpr) {
+                    const int a = t / d.npair, q = t % d.npair;
+                    const uint32_t ea = (uint32_t)sP[a];
+                    const T w = wv<T>(d, (int64_t)ent_pair(ea) * d.npair + q);
+                    sW[t] = ent_negative(ea) ? -w : w;
+                }
+                group_sync(g, tpr);
+                for (int64_t j = lt; j < nsb; j += tpr) {
+                    T v = acc[j];
+                    // merged alpha diagonal against every beta entry
+                    for (int b = 0; b < d.B.nsingle; ++b) {
+                        const uint32_t eb = d.B.tab[(int64_t)b * nsb + j];
+                        v = fma(flipb(wrow[ent_pair(eb)], eb & 0x80000000u), cself[ent_target(eb)], v);
+                    }
+                    // off-diagonal alpha against the merged beta diagonal
+                    for (int a = 0; a < noff_a; ++a) {
+                        const uint32_t ea = (uint32_t)sP[a];
+                        const T w = (T)d.B.wdiag[(int64_t)ent_pair(ea) * nsb + j];
+                        const T x = sR[(int64_t)a * nsb + j];
+                        v = fma(ent_negative(ea) ? -w : w, x, v);
+                    }
+                    // off-diagonal alpha against off-diagonal beta
+                    for (int b = 0; b < noff_b; ++b) {
+                        const uint32_t eb = d.B.tabo[(int64_t)b * nsb + j];
+                        const int pb = ent_pair(eb);
+                        const int64_t jb = ent_target(eb);
+                        T t = 0;
+                        for (int a = 0; a < noff_a; ++a) t = fma(sW[a * d.npair + pb], sR[(int64_t)a * nsb + jb], t);
+                        v += ent_negative(eb) ? -t : t;
+                    }
+                    S[row * nsb + j] = v;
+                }
+                group_sync(g, tpr);
+                continue;
+            }
         }
         // sigma_3 with the diagonal replacements merged (as in the single-instance
         // FP64 kernel): first one pass over C(I_a, :) with the summed integral
@@ -221,6 +290,57 @@ __global__ void k_breduce(const int *__restrict__ cfirst, const int *__restrict_
     for (int j = threadIdx.x; j < m; j += blockDim.x) {
         double v = 0.0;
         for (int c = cfirst[i]; c < cfirst[i + 1]; ++c) v += partial[(int64_t)c * MAXM + j];
+        out[i * os + j * js] = v;
+    }
+}
+
+// Per-instance dots with few reductions: CTA (g, i) accumulates a stripe of
+// instance i's elements for all j < m in registers, then reduces once.
+// partial[(i*G + g)*MAXM + j]
+template <int MAXM>
+__global__ void __launch_bounds__(kBlock) k_bdots2(const InstDev *__restrict__ D, const int *__restrict__ on,
+                                                   const double *__restrict__ X, int64_t ntot, int m,
+                                                   const double *__restrict__ y, double *__restrict__ partial) {
+    const int i = blockIdx.y, G = gridDim.x, g = blockIdx.x;
+    double acc[MAXM];
+#pragma unroll
+    for (int j = 0; j < MAXM; ++j) acc[j] = 0.0;
+    const bool act = on[i] != 0;
+    const int64_t off = D[i].off, n = D[i].ndet;
+    if (act && (int64_t)g * kBlock < n) {
+        for (int64_t r = (int64_t)g * kBlock + threadIdx.x; r < n; r += (int64_t)G * kBlock) {
+            const int64_t idx = off + r;
+            const double yv = y[idx];
+#pragma unroll
+            for (int j = 0; j < MAXM; ++j)
+                if (j < m) acc[j] = fma(X[(int64_t)j * ntot + idx], yv, acc[j]);
+        }
+    }
+    __shared__ double red[MAXM][kBlock / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < MAXM; ++j) {
+        double v = acc[j];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[j][warp] = v;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        double v = 0.0;
+        for (int w = 0; w < kBlock / 32; ++w) v += red[j][w];
+        partial[((int64_t)i * G + g) * MAXM + j] = v;
+    }
+}
+
+// out[i*os + j*js] = sum over g of partial[(i*G + g)][j] (fixed order)
+template <int MAXM>
+__global__ void k_breduce2(const int *__restrict__ on, const double *__restrict__ partial, int G, int m,
+                           double *__restrict__ out, int64_t os, int64_t js) {
+    const int i = blockIdx.x;
+    if (!on[i]) return;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        double v = 0.0;
+        for (int g = 0; g < G; ++g) v += partial[((int64_t)i * G + g) * MAXM + j];
         out[i * os + j * js] = v;
     }
 }
@@ -357,22 +477,19 @@ __global__ void k_bjacobi(const int *__restrict__ on, const double *__restrict__
         v[r][c] = (r == c) ? 1.0 : 0.0;
     }
     __syncthreads();
+    // a rotation is skipped when |a_pq| is negligible next to a_pp and a_qq;
+    // the sweeps stop once a whole sweep skipped every pair (60 at most)
+    __shared__ int rotated;
     for (int sweep = 0; sweep < 60; ++sweep) {
-        double off = 0.0, tot = 0.0;
-        for (int r = 0; r < m; ++r)
-            for (int c = 0; c < m; ++c) {
-                const double x = a[r][c] * a[r][c];
-                const bool pad_diag = r == c && a[r][r] >= 0.5 * kPad;  // padding slots stay out of the norm
-                if (!pad_diag) tot += x;
-                if (r != c) off += x;
-            }
-        if (off <= 1e-30 * tot || off == 0.0) break;
+        if (tid == 0) rotated = 0;
+        __syncthreads();
         for (int p = 0; p < m - 1; ++p)
             for (int q = p + 1; q < m; ++q) {
                 if (tid == 0) {
                     const double apq = a[p][q];
                     double c = 1.0, s = 0.0;
-                    if (apq != 0.0) {
+                    if (fabs(apq) > 1e-14 * (fabs(a[p][p]) + fabs(a[q][q]))) {
+                        rotated = 1;
                         const double theta = (a[q][q] - a[p][p]) / (2.0 * apq);
                         const double tt = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
                         c = 1.0 / sqrt(tt * tt + 1.0);
@@ -401,6 +518,8 @@ __global__ void k_bjacobi(const int *__restrict__ on, const double *__restrict__
                 }
                 __syncthreads();
             }
+        __syncthreads();
+        if (!rotated) break;
     }
     if (tid == 0) {
         for (int r = 0; r < m; ++r) order[r] = r;
@@ -665,6 +784,19 @@ int fci_batch_init(fci_batch **out, int ninst, const fci_instance *inst, const f
     b->row_elems32 = (3 * maxnsb + maxnpair + 3) & ~3;
     b->smem64 = sizeof(double) * 8 * b->row_elems64;
     b->smem32 = sizeof(float) * 8 * b->row_elems32;
+    // FP32 stage-all mode (one row group of 256 threads): cself, ca, acc, wrow,
+    // then all off-diagonal alpha rows and their integral rows
+    for (int i = 0; i < ninst; ++i) {
+        const int64_t nsb_i = b->h_inst[i].B.ns;
+        const int noff_a = b->h_inst[i].A.ne * ((int)b->h_inst[i].A.ns > 0 && b->h_inst[i].A.ne > 0
+                                                    ? b->h_inst[i].A.nsingle / b->h_inst[i].A.ne - 1
+                                                    : 0);
+        const int64_t elems = 3 * nsb_i + ((b->h_inst[i].npair + 3) & ~3) + (int64_t)noff_a * nsb_i +
+                              (int64_t)noff_a * b->h_inst[i].npair + noff_a;
+        const size_t bytes = sizeof(float) * (size_t)elems;
+        b->h_inst[i].stage_all = (noff_a > 0 && bytes <= 200 * 1024) ? 1 : 0;
+        if (b->h_inst[i].stage_all) b->smem32 = std::max(b->smem32, bytes);
+    }
     cudaFuncSetAttribute(k_bsigma<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem64);
     cudaFuncSetAttribute(k_bsigma<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem32);
     if (b->smem64 > 227 * 1024) {
@@ -747,6 +879,12 @@ int fci_batch_init(fci_batch **out, int ninst, const fci_instance *inst, const f
         // the FP32 choice is used in mixed mode (most sigma calls), else FP64
         for (int i = 0; i < ninst; ++i)
             b->h_inst[i].tpr = (o.precision == FCI_PREC_MIXED ? best32 : best64)[inst[i].norb];
+        // the FP32 stage-all mode uses one row group of all 256 threads
+        if (o.precision == FCI_PREC_MIXED)
+            for (int i = 0; i < ninst; ++i)
+                if (b->h_inst[i].stage_all) b->h_inst[i].tpr = kBlock;
+        if (o.precision != FCI_PREC_MIXED)
+            for (int i = 0; i < ninst; ++i) b->h_inst[i].stage_all = 0;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) {
             fci_batch_free(b);
@@ -818,6 +956,7 @@ struct BWork {
     double *Bv, *Sv, *X, *HX, *T;   // batch vectors: [maxsub|nroots][ntot]
     float *c32, *s32;               // [ntot]
     double *A, *w, *V, *g, *nrm2, *rn2, *partial;
+    int dotG;                       // stripes per instance in the dot kernels
     int *on, *on_exp, *on_ref;      // masks: active, expanding, refining
     void **ptr32;                   // [2][ninst]: c32 / s32 per instance
     void **ptrBS;                   // [maxsub][2][ninst]: B_j -> S_j per instance
@@ -830,12 +969,13 @@ struct BWork {
 static void bdots(BWork &W, const int *on, const double *X, int m, const double *y, double *out, int64_t os,
                   int64_t js) {
     fci_batch *b = W.b;
+    const dim3 grid(W.dotG, b->ninst);
     if (m <= 8) {
-        k_bdots<8><<<b->nchunks, kBlock, 0, W.s>>>(b->d_chunks, on, X, b->ntot, m, y, W.partial);
-        k_breduce<8><<<b->ninst, 32, 0, W.s>>>(b->d_cfirst, on, W.partial, m, out, os, js);
+        k_bdots2<8><<<grid, kBlock, 0, W.s>>>(b->d_inst, on, X, b->ntot, m, y, W.partial);
+        k_breduce2<8><<<b->ninst, 32, 0, W.s>>>(on, W.partial, W.dotG, m, out, os, js);
     } else {
-        k_bdots<32><<<b->nchunks, kBlock, 0, W.s>>>(b->d_chunks, on, X, b->ntot, m, y, W.partial);
-        k_breduce<32><<<b->ninst, 32, 0, W.s>>>(b->d_cfirst, on, W.partial, m, out, os, js);
+        k_bdots2<32><<<grid, kBlock, 0, W.s>>>(b->d_inst, on, X, b->ntot, m, y, W.partial);
+        k_breduce2<32><<<b->ninst, 32, 0, W.s>>>(on, W.partial, W.dotG, m, out, os, js);
     }
 }
 
@@ -904,7 +1044,13 @@ extern "C" int fci_batch_davidson(fci_batch *b, int nroots, double tol, double *
     W.g = (double *)get(sizeof(double) * ninst * kMaxSub);
     W.nrm2 = (double *)get(sizeof(double) * ninst);
     W.rn2 = (double *)get(sizeof(double) * ninst * kMaxRoots);
-    W.partial = (double *)get(sizeof(double) * (size_t)b->nchunks * 32);
+    {
+        int64_t maxn = 0;
+        for (int i = 0; i < ninst; ++i) maxn = std::max<int64_t>(maxn, b->h_inst[i].ndet);
+        W.dotG = (int)std::max<int64_t>(1, std::min<int64_t>(256, (maxn + kBlock * 8 - 1) / (kBlock * 8)));
+    }
+    W.partial = (double *)get(sizeof(double) * std::max<size_t>((size_t)b->nchunks * 32,
+                                                                (size_t)ninst * W.dotG * 32));
     W.on = (int *)get(sizeof(int) * ninst);
     W.on_exp = (int *)get(sizeof(int) * ninst);
     W.on_ref = (int *)get(sizeof(int) * ninst);
@@ -946,7 +1092,7 @@ extern "C" int fci_batch_davidson(fci_batch *b, int nroots, double tol, double *
     std::vector<int> active(ninst, 1), exact(ninst, W.mixed ? 0 : 1), inner(ninst, 0), refine(ninst, 0), expand(ninst);
     std::vector<double> e_prev((size_t)ninst * nroots, INFINITY), r_ref(ninst, INFINITY);
     std::vector<double> hw((size_t)ninst * kMaxSub), hrn((size_t)ninst * kMaxRoots);
-    const double drop = b->opt.mixed_switch > 0 && b->opt.mixed_switch < 1 ? b->opt.mixed_switch : 1e-2;
+    std::vector<double> r_hist((size_t)ninst * 16, INFINITY);
     auto upload = [&](int *dst, const std::vector<int> &vv) {
         return cudaMemcpyAsync(dst, vv.data(), sizeof(int) * ninst, cudaMemcpyHostToDevice, s);
     };
@@ -1010,6 +1156,8 @@ extern "C" int fci_batch_davidson(fci_batch *b, int nroots, double tol, double *
                 demax = std::max(demax, std::fabs(hw[(size_t)i * kMaxSub + k] - e_prev[(size_t)i * nroots + k]));
             }
             for (int k = 0; k < nroots; ++k) energies[(size_t)i * nroots + k] = hw[(size_t)i * kMaxSub + k];
+            const double r15 = r_hist[(size_t)i * 16 + (it % 16)];  // residual 16 iterations ago
+            r_hist[(size_t)i * 16 + (it % 16)] = rmax;
             if (exact[i]) {
                 if (demax < tol && rmax < std::sqrt(tol)) {
                     active[i] = 0;
@@ -1018,7 +1166,8 @@ extern "C" int fci_batch_davidson(fci_batch *b, int nroots, double tol, double *
                 for (int k = 0; k < nroots; ++k) e_prev[(size_t)i * nroots + k] = hw[(size_t)i * kMaxSub + k];
                 r_ref[i] = rmax;
                 inner[i] = 0;
-            } else if (++inner[i] >= 20 || rmax < drop * r_ref[i] || rmax < std::sqrt(tol)) {
+            } else if (++inner[i] >= 60 || rmax < std::sqrt(tol) ||
+                       (inner[i] >= 15 && rmax > 0.5 * r15)) {
                 refine[i] = 1;
                 any_ref = true;
             }

@@ -21,15 +21,16 @@
 //
 // Mixed precision: every new correction gets an FP32 sigma (sigma_3 on the
 // tensor cores); the basis, the projected matrix, orthogonalisation and the
-// residuals stay FP64.  Refinement points: when the residual has fallen by
-// opt.mixed_switch (default 1e-2) since the last one, after 20 corrections,
-// or when it is below sqrt(tol), the FP64 sigma of each Ritz vector x = B v is
-// built and the subspace sigma vectors are corrected along v,
-// S <- S + (sigma64(x) - S v) v^T, together with the projected matrix.  The
-// Ritz values there are exact Rayleigh quotients and the residuals exact; the
-// FP32 error left in the other directions shrinks with the size of the
-// corrections.  Convergence is tested only at those points, which the
-// iteration log marks with precision 0.
+// residuals stay FP64.  The FP32 error of sigma (about 1e-7 relative) puts a
+// floor of about 1e-7 ||H|| under the residual, below sqrt(tol) for the
+// tolerances used here, so FP64 work is only needed near the end: refinement
+// points come when the residual is below sqrt(tol), when it has not halved in
+// 15 iterations, or after 60 corrections.  There the FP64 sigma of each Ritz
+// vector x = B v is built and the subspace sigma vectors are corrected along
+// v, S <- S + (sigma64(x) - S v) v^T, together with the projected matrix; the
+// Ritz values are then exact Rayleigh quotients and the residuals exact.
+// Convergence is tested only at those points, which the iteration log marks
+// with precision 0.
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -181,20 +182,19 @@ __global__ void k_jacobi(const double *__restrict__ A, int lda, int m, double *_
         v[i][j] = (i == j) ? 1.0 : 0.0;
     }
     __syncthreads();
+    // a rotation is skipped when |a_pq| is negligible next to a_pp and a_qq;
+    // the sweeps stop once a whole sweep skipped every pair (60 at most)
+    __shared__ int rotated;
     for (int sweep = 0; sweep < 60; ++sweep) {
-        double off = 0.0, tot = 0.0;
-        for (int i = 0; i < m; ++i)
-            for (int j = 0; j < m; ++j) {
-                tot += a[i][j] * a[i][j];
-                if (i != j) off += a[i][j] * a[i][j];
-            }
-        if (off <= 1e-30 * tot || off == 0.0) break;
+        if (tid == 0) rotated = 0;
+        __syncthreads();
         for (int p = 0; p < m - 1; ++p)
             for (int q = p + 1; q < m; ++q) {
                 if (tid == 0) {
                     double apq = a[p][q];
                     double c = 1.0, s = 0.0;
-                    if (apq != 0.0) {
+                    if (fabs(apq) > 1e-14 * (fabs(a[p][p]) + fabs(a[q][q]))) {
+                        rotated = 1;
                         double theta = (a[q][q] - a[p][p]) / (2.0 * apq);
                         double tt = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
                         c = 1.0 / sqrt(tt * tt + 1.0);
@@ -224,6 +224,8 @@ __global__ void k_jacobi(const double *__restrict__ A, int lda, int m, double *_
                 }
                 __syncthreads();
             }
+        __syncthreads();
+        if (!rotated) break;
     }
     if (tid == 0) {
         for (int i = 0; i < m; ++i) order[i] = i;
@@ -490,8 +492,9 @@ int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *v
     std::vector<double> e_prev(nroots, INFINITY), ev(kMaxSub), rn(nroots);
     bool converged = false;
     int it = 0, inner = 0;
-    double r_ref = INFINITY;
-    const double drop = ctx->opt.mixed_switch > 0 && ctx->opt.mixed_switch < 1 ? ctx->opt.mixed_switch : 1e-2;
+    double r_ref = INFINITY, r_win = INFINITY;
+    std::vector<double> r_hist;
+    (void)r_ref;
 
     for (it = 1; it <= ctx->opt.max_iter; ++it) {
         // (4) diagonalise the projected matrix
@@ -526,6 +529,9 @@ int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *v
             ctx->log.push_back(el);
             for (int k = 0; k < nroots; ++k) ctx->log.push_back(k < nr ? ev[k] : NAN);
         }
+        // residual 15 iterations ago (stagnation test of the FP32 phase)
+        r_hist.push_back(rmax);
+        r_win = r_hist.size() > 15 ? r_hist[r_hist.size() - 16] : INFINITY;
         if (exact) {
             if (nr == nroots && demax < tol && rmax < std::sqrt(tol)) {
                 converged = true;
@@ -534,7 +540,7 @@ int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *v
             for (int k = 0; k < nr; ++k) e_prev[k] = ev[k];
             r_ref = rmax;
             inner = 0;
-        } else if (++inner >= 20 || rmax < drop * r_ref || rmax < std::sqrt(tol)) {
+        } else if (++inner >= 60 || rmax < std::sqrt(tol) || (inner >= 15 && rmax > 0.5 * r_win)) {
             // refinement: exact FP64 sigma of each Ritz vector; the difference to
             // the subspace estimate corrects every sigma vector along that Ritz
             // direction (S += delta v^T) and the projected matrix with it

@@ -34,10 +34,13 @@ def instances(spec, base_seed=1707):
 SPEC = [(6, 3, 3), (8, 4, 4), (10, 5, 5), (7, 4, 3), (6, 3, 3), (9, 4, 5), (4, 2, 2)]
 
 
-@pytest.mark.parametrize("dtype,rtol", [(torch.float64, 1e-12), (torch.float32, 2e-5)])
-def test_batch_sigma_matches_single_instance(pkg, dtype, rtol):
-    insts = instances(SPEC)
-    batch = pkg.fci_batch_init(insts)
+@pytest.mark.parametrize("dtype,rtol,prec", [(torch.float64, 1e-12, 0), (torch.float32, 2e-5, 0),
+                                             (torch.float32, 2e-5, 1)])
+def test_batch_sigma_matches_single_instance(pkg, dtype, rtol, prec):
+    """prec 1 (mixed) turns on the FP32 path that stages every off-diagonal
+    alpha row of an output row at once (instances up to CAS(12,12) here)."""
+    insts = instances(SPEC + ([(12, 6, 6)] if prec else []))
+    batch = pkg.fci_batch_init(insts, pkg.default_options(precision=prec))
     total = batch.offset(batch.ninst)
     c = torch.from_numpy(fi.make_vector(total, seed=9)).to(DEV, dtype)
     s = torch.empty_like(c)
