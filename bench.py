@@ -94,35 +94,15 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+from paper_1707_04346_gb300 import replicas  # noqa: E402  (pure Python; no library load)
+
+
 def dist_setup(n_gpus):
-    import torch
-
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    return rank, world, local
+    return replicas.setup()
 
 
-def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.barrier()
-
-
-def max_over_ranks(x, world):
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+barrier = replicas.barrier
+max_over_ranks = replicas.max_over_ranks
 
 
 def cpu_baseline(norb, na, nb, h1, eri, c, target_s=15.0, seed=0):
@@ -293,7 +273,7 @@ def run_ours(args):
     pkg.fci_profile_enable(ctx, False)
     prof = prof[-args.steps:]
     t = max_over_ranks(t, world)
-    value = world * N * args.steps / t / 1e9
+    value = replicas.job_throughput(N * args.steps, t, world) / 1e9
     kmean = prof.mean(axis=0) / 1e3  # seconds per launch
     kshare = prof.sum(axis=0) / prof.sum()
     top = int(np.argmax(kmean))

@@ -139,9 +139,11 @@ __global__ void __launch_bounds__(kBlock, 1) k_bsigma(const InstDev *__restrict_
                 // entry is loaded once per determinant
                 const int noff_a = d.A.ne * (d.A.nsingle / (d.A.ne > 0 ? d.A.ne : 1) - 1);
                 const int noff_b = d.B.ne * (d.B.nsingle / (d.B.ne > 0 ? d.B.ne : 1) - 1);
-                T *sR = wrow + ((d.npair + 3) & ~3);            // [noff_a][nsb]
-                T *sW = sR + (int64_t)noff_a * nsb;             // [noff_a][npair]
-                int *sP = reinterpret_cast<int *>(sW + (int64_t)noff_a * d.npair);  // [noff_a] pair of a
+                const int na4 = (noff_a + 3) & ~3;             // row length padded for float4
+                // 16-byte aligned start (float4 loads): offset rounded up to 4 elements
+                T *sR = cself + ((3 * nsb + d.npair + 3) & ~(int64_t)3);  // [nsb][na4]: C(J_a, j) at [j][a]
+                T *sW = sR + (int64_t)na4 * nsb;               // [npair][na4]: s_a (p_a|q) at [q][a]
+                int *sP = reinterpret_cast<int *>(sW + (int64_t)na4 * d.npair);  // [noff_a] entry of a
                 group_sync(g, tpr);
                 if (lt == 0) {
                     int o = 0;
@@ -159,16 +161,20 @@ __global__ void __launch_bounds__(kBlock, 1) k_bsigma(const InstDev *__restrict_
                     wrow[q] = w;
                 }
                 group_sync(g, tpr);
-                for (int64_t t = lt; t < (int64_t)noff_a * nsb; t += tpr) {
+                for (int64_t t = lt; t < (int64_t)na4 * nsb; t += tpr) {
                     const int a = (int)(t / nsb);
                     const int64_t j = t % nsb;
-                    sR[t] = C[(int64_t)ent_target((uint32_t)sP[a]) * nsb + j];
+                    sR[j * na4 + a] = a < noff_a ? C[(int64_t)ent_target((uint32_t)sP[a]) * nsb + j] : T(0);
                 }
-                for (int t = lt; t < noff_a * d.npair; t += tpr) {
+                for (int t = lt; t < na4 * d.npair; t += tpr) {
                     const int a = t / d.npair, q = t % d.npair;
-                    const uint32_t ea = (uint32_t)sP[a];
-                    const T w = wv<T>(d, (int64_t)ent_pair(ea) * d.npair + q);
-                    sW[t] = ent_negative(ea) ? -w : w;
+                    T w = 0;
+                    if (a < noff_a) {
+                        const uint32_t ea = (uint32_t)sP[a];
+                        w = wv<T>(d, (int64_t)ent_pair(ea) * d.npair + q);
+                        if (ent_negative(ea)) w = -w;
+                    }
+                    sW[q * na4 + a] = w;
                 }
                 group_sync(g, tpr);
                 for (int64_t j = lt; j < nsb; j += tpr) {
@@ -182,16 +188,21 @@ __global__ void __launch_bounds__(kBlock, 1) k_bsigma(const InstDev *__restrict_
                     for (int a = 0; a < noff_a; ++a) {
                         const uint32_t ea = (uint32_t)sP[a];
                         const T w = (T)d.B.wdiag[(int64_t)ent_pair(ea) * nsb + j];
-                        const T x = sR[(int64_t)a * nsb + j];
-                        v = fma(ent_negative(ea) ? -w : w, x, v);
+                        v = fma(ent_negative(ea) ? -w : w, sR[j * na4 + a], v);
                     }
-                    // off-diagonal alpha against off-diagonal beta
+                    // off-diagonal alpha against off-diagonal beta: contiguous over a
                     for (int b = 0; b < noff_b; ++b) {
                         const uint32_t eb = d.B.tabo[(int64_t)b * nsb + j];
-                        const int pb = ent_pair(eb);
-                        const int64_t jb = ent_target(eb);
-                        T t = 0;
-                        for (int a = 0; a < noff_a; ++a) t = fma(sW[a * d.npair + pb], sR[(int64_t)a * nsb + jb], t);
+                        const float4 *wq = reinterpret_cast<const float4 *>(sW + (int64_t)ent_pair(eb) * na4);
+                        const float4 *rq = reinterpret_cast<const float4 *>(sR + (int64_t)ent_target(eb) * na4);
+                        float t = 0.f;
+                        for (int a4 = 0; a4 < na4 / 4; ++a4) {
+                            const float4 x = wq[a4], y = rq[a4];
+                            t = fmaf(x.x, y.x, t);
+                            t = fmaf(x.y, y.y, t);
+                            t = fmaf(x.z, y.z, t);
+                            t = fmaf(x.w, y.w, t);
+                        }
                         v += ent_negative(eb) ? -t : t;
                     }
                     S[row * nsb + j] = v;
@@ -258,13 +269,14 @@ __global__ void __launch_bounds__(kBlock) k_bdots(const Chunk *__restrict__ ch, 
     double acc[MAXM];
 #pragma unroll
     for (int j = 0; j < MAXM; ++j) acc[j] = 0.0;
-    if (on[c.inst] && threadIdx.x < c.len) {
-        const int64_t idx = c.start + threadIdx.x;
-        const double yv = y[idx];
+    if (on[c.inst])
+        for (int t = threadIdx.x; t < c.len; t += kBlock) {
+            const int64_t idx = c.start + t;
+            const double yv = y[idx];
 #pragma unroll
-        for (int j = 0; j < MAXM; ++j)
-            if (j < m) acc[j] = X[(int64_t)j * ntot + idx] * yv;
-    }
+            for (int j = 0; j < MAXM; ++j)
+                if (j < m) acc[j] = fma(X[(int64_t)j * ntot + idx], yv, acc[j]);
+        }
     __shared__ double red[MAXM][kBlock / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -598,9 +610,12 @@ struct fci_batch {
     int ninst = 0, nsm = 0;
     InstDev *d_inst = nullptr;
     std::vector<InstDev> h_inst;
-    Chunk *d_chunks = nullptr;
+    Chunk *d_chunks = nullptr;   // <= 256 elements each (element-wise kernels)
     int nchunks = 0;
     int *d_cfirst = nullptr;
+    Chunk *d_dchunks = nullptr;  // <= 2048 elements each (reductions)
+    int ndchunks = 0;
+    int *d_dcfirst = nullptr;
     Item *d_items = nullptr;
     int nitems = 0;
     int *d_counter = nullptr;
@@ -764,8 +779,19 @@ int fci_batch_init(fci_batch **out, int ninst, const fci_instance *inst, const f
     }
     cfirst[ninst] = (int)ch.size();
     b->nchunks = (int)ch.size();
+    std::vector<Chunk> dch;
+    std::vector<int> dcfirst(ninst + 1, 0);
+    for (int i = 0; i < ninst; ++i) {
+        dcfirst[i] = (int)dch.size();
+        for (int64_t s0 = 0; s0 < b->h_inst[i].ndet; s0 += 8 * kChunk)
+            dch.push_back({i, (int)std::min<int64_t>(8 * kChunk, b->h_inst[i].ndet - s0), b->off[i] + s0});
+    }
+    dcfirst[ninst] = (int)dch.size();
+    b->ndchunks = (int)dch.size();
     b->d_chunks = balloc<Chunk>(b, ch.size(), &rc);
     b->d_cfirst = balloc<int>(b, ninst + 1, &rc);
+    b->d_dchunks = balloc<Chunk>(b, dch.size(), &rc);
+    b->d_dcfirst = balloc<int>(b, ninst + 1, &rc);
     b->d_inst = balloc<InstDev>(b, ninst, &rc);
     b->d_counter = balloc<int>(b, 1, &rc);
     b->d_cin = balloc<void *>(b, ninst, &rc);
@@ -777,6 +803,8 @@ int fci_batch_init(fci_batch **out, int ninst, const fci_instance *inst, const f
     }
     cudaMemcpy(b->d_chunks, ch.data(), sizeof(Chunk) * ch.size(), cudaMemcpyHostToDevice);
     cudaMemcpy(b->d_cfirst, cfirst.data(), sizeof(int) * (ninst + 1), cudaMemcpyHostToDevice);
+    cudaMemcpy(b->d_dchunks, dch.data(), sizeof(Chunk) * dch.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(b->d_dcfirst, dcfirst.data(), sizeof(int) * (ninst + 1), cudaMemcpyHostToDevice);
     std::vector<int> ones(ninst, 1);
     cudaMemcpy(b->d_on_all, ones.data(), sizeof(int) * ninst, cudaMemcpyHostToDevice);
     // shared memory: up to 8 row groups (tpr = 32) of 3 rows + one integral row
@@ -791,8 +819,9 @@ int fci_batch_init(fci_batch **out, int ninst, const fci_instance *inst, const f
         const int noff_a = b->h_inst[i].A.ne * ((int)b->h_inst[i].A.ns > 0 && b->h_inst[i].A.ne > 0
                                                     ? b->h_inst[i].A.nsingle / b->h_inst[i].A.ne - 1
                                                     : 0);
-        const int64_t elems = 3 * nsb_i + ((b->h_inst[i].npair + 3) & ~3) + (int64_t)noff_a * nsb_i +
-                              (int64_t)noff_a * b->h_inst[i].npair + noff_a;
+        const int na4 = (noff_a + 3) & ~3;
+        const int64_t elems = ((3 * nsb_i + b->h_inst[i].npair + 3) & ~(int64_t)3) + (int64_t)na4 * nsb_i +
+                              (int64_t)na4 * b->h_inst[i].npair + noff_a;
         const size_t bytes = sizeof(float) * (size_t)elems;
         b->h_inst[i].stage_all = (noff_a > 0 && bytes <= 200 * 1024) ? 1 : 0;
         if (b->h_inst[i].stage_all) b->smem32 = std::max(b->smem32, bytes);
@@ -956,7 +985,6 @@ struct BWork {
     double *Bv, *Sv, *X, *HX, *T;   // batch vectors: [maxsub|nroots][ntot]
     float *c32, *s32;               // [ntot]
     double *A, *w, *V, *g, *nrm2, *rn2, *partial;
-    int dotG;                       // stripes per instance in the dot kernels
     int *on, *on_exp, *on_ref;      // masks: active, expanding, refining
     void **ptr32;                   // [2][ninst]: c32 / s32 per instance
     void **ptrBS;                   // [maxsub][2][ninst]: B_j -> S_j per instance
@@ -965,17 +993,17 @@ struct BWork {
     std::map<int, cudaGraphExec_t> g_ritz, g_expand;
 };
 
-// out[i*os + j*js] = X_j . y for j < m, per instance (masked by on)
+// out[i*os + j*js] = X_j . y for j < m, per instance (masked by on); one CTA per
+// 2048-element chunk (8 elements per thread before the block reduction)
 static void bdots(BWork &W, const int *on, const double *X, int m, const double *y, double *out, int64_t os,
                   int64_t js) {
     fci_batch *b = W.b;
-    const dim3 grid(W.dotG, b->ninst);
     if (m <= 8) {
-        k_bdots2<8><<<grid, kBlock, 0, W.s>>>(b->d_inst, on, X, b->ntot, m, y, W.partial);
-        k_breduce2<8><<<b->ninst, 32, 0, W.s>>>(on, W.partial, W.dotG, m, out, os, js);
+        k_bdots<8><<<b->ndchunks, kBlock, 0, W.s>>>(b->d_dchunks, on, X, b->ntot, m, y, W.partial);
+        k_breduce<8><<<b->ninst, 32, 0, W.s>>>(b->d_dcfirst, on, W.partial, m, out, os, js);
     } else {
-        k_bdots2<32><<<grid, kBlock, 0, W.s>>>(b->d_inst, on, X, b->ntot, m, y, W.partial);
-        k_breduce2<32><<<b->ninst, 32, 0, W.s>>>(on, W.partial, W.dotG, m, out, os, js);
+        k_bdots<32><<<b->ndchunks, kBlock, 0, W.s>>>(b->d_dchunks, on, X, b->ntot, m, y, W.partial);
+        k_breduce<32><<<b->ninst, 32, 0, W.s>>>(b->d_dcfirst, on, W.partial, m, out, os, js);
     }
 }
 
@@ -1044,13 +1072,7 @@ extern "C" int fci_batch_davidson(fci_batch *b, int nroots, double tol, double *
     W.g = (double *)get(sizeof(double) * ninst * kMaxSub);
     W.nrm2 = (double *)get(sizeof(double) * ninst);
     W.rn2 = (double *)get(sizeof(double) * ninst * kMaxRoots);
-    {
-        int64_t maxn = 0;
-        for (int i = 0; i < ninst; ++i) maxn = std::max<int64_t>(maxn, b->h_inst[i].ndet);
-        W.dotG = (int)std::max<int64_t>(1, std::min<int64_t>(256, (maxn + kBlock * 8 - 1) / (kBlock * 8)));
-    }
-    W.partial = (double *)get(sizeof(double) * std::max<size_t>((size_t)b->nchunks * 32,
-                                                                (size_t)ninst * W.dotG * 32));
+    W.partial = (double *)get(sizeof(double) * (size_t)std::max(b->nchunks, b->ndchunks) * 32);
     W.on = (int *)get(sizeof(int) * ninst);
     W.on_exp = (int *)get(sizeof(int) * ninst);
     W.on_ref = (int *)get(sizeof(int) * ninst);
