@@ -480,7 +480,6 @@ __global__ void k_bjacobi(const int *__restrict__ on, const double *__restrict__
     double *V = Vall + (int64_t)i * kMaxSub * kMaxSub;
     __shared__ double a[kMaxSub][kMaxSub + 1];
     __shared__ double v[kMaxSub][kMaxSub + 1];
-    __shared__ double cs[2];
     __shared__ int order[kMaxSub];
     const int tid = threadIdx.x;
     for (int t = tid; t < m * m; t += blockDim.x) {
@@ -489,48 +488,75 @@ __global__ void k_bjacobi(const int *__restrict__ on, const double *__restrict__
         v[r][c] = (r == c) ? 1.0 : 0.0;
     }
     __syncthreads();
-    // a rotation is skipped when |a_pq| is negligible next to a_pp and a_qq;
-    // the sweeps stop once a whole sweep skipped every pair (60 at most)
+    // Parallel cyclic Jacobi with round-robin pair ordering: each step rotates
+    // m/2 disjoint pairs at once (rotations on disjoint index pairs commute).
+    // A rotation is skipped when |a_pq| < 1e-14 (|a_pp| + |a_qq|); the sweeps
+    // stop after a sweep without rotation (60 at most).
     __shared__ int rotated;
+    __shared__ int pos[kMaxSub + 1];
+    __shared__ int pp[kMaxSub / 2 + 1], pq[kMaxSub / 2 + 1];
+    __shared__ double pc[kMaxSub / 2 + 1], psn[kMaxSub / 2 + 1];
+    const int me = m + (m & 1);  // even number of players; index m is a dummy when m is odd
+    const int half = me / 2;
+    for (int t = tid; t < me; t += blockDim.x) pos[t] = t;
+    __syncthreads();
     for (int sweep = 0; sweep < 60; ++sweep) {
         if (tid == 0) rotated = 0;
         __syncthreads();
-        for (int p = 0; p < m - 1; ++p)
-            for (int q = p + 1; q < m; ++q) {
-                if (tid == 0) {
+        for (int step = 0; step < me - 1; ++step) {
+            for (int k = tid; k < half; k += blockDim.x) {
+                int p = pos[k], q = pos[me - 1 - k];
+                if (p > q) { const int t2 = p; p = q; q = t2; }
+                double c = 1.0, sn = 0.0;
+                if (q < m) {
                     const double apq = a[p][q];
-                    double c = 1.0, s = 0.0;
                     if (fabs(apq) > 1e-14 * (fabs(a[p][p]) + fabs(a[q][q]))) {
                         rotated = 1;
                         const double theta = (a[q][q] - a[p][p]) / (2.0 * apq);
                         const double tt = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
                         c = 1.0 / sqrt(tt * tt + 1.0);
-                        s = tt * c;
-                    }
-                    cs[0] = c;
-                    cs[1] = s;
-                }
-                __syncthreads();
-                const double c = cs[0], s = cs[1];
-                if (s != 0.0) {
-                    for (int k = tid; k < m; k += blockDim.x) {
-                        const double akp = a[k][p], akq = a[k][q];
-                        a[k][p] = c * akp - s * akq;
-                        a[k][q] = s * akp + c * akq;
-                    }
-                    __syncthreads();
-                    for (int k = tid; k < m; k += blockDim.x) {
-                        const double apk = a[p][k], aqk = a[q][k];
-                        a[p][k] = c * apk - s * aqk;
-                        a[q][k] = s * apk + c * aqk;
-                        const double vkp = v[k][p], vkq = v[k][q];
-                        v[k][p] = c * vkp - s * vkq;
-                        v[k][q] = s * vkp + c * vkq;
+                        sn = tt * c;
                     }
                 }
-                __syncthreads();
+                pp[k] = p;
+                pq[k] = q;
+                pc[k] = c;
+                psn[k] = sn;
             }
-        __syncthreads();
+            __syncthreads();
+            // columns: a <- a J
+            for (int t = tid; t < half * m; t += blockDim.x) {
+                const int k = t / m, r = t % m;
+                if (psn[k] == 0.0) continue;
+                const int p = pp[k], q = pq[k];
+                const double c = pc[k], sn = psn[k];
+                const double arp = a[r][p], arq = a[r][q];
+                a[r][p] = c * arp - sn * arq;
+                a[r][q] = sn * arp + c * arq;
+            }
+            __syncthreads();
+            // rows: a <- J^T a ; eigenvectors v <- v J
+            for (int t = tid; t < half * m; t += blockDim.x) {
+                const int k = t / m, r = t % m;
+                if (psn[k] == 0.0) continue;
+                const int p = pp[k], q = pq[k];
+                const double c = pc[k], sn = psn[k];
+                const double apr = a[p][r], aqr = a[q][r];
+                a[p][r] = c * apr - sn * aqr;
+                a[q][r] = sn * apr + c * aqr;
+                const double vrp = v[r][p], vrq = v[r][q];
+                v[r][p] = c * vrp - sn * vrq;
+                v[r][q] = sn * vrp + c * vrq;
+            }
+            __syncthreads();
+            // next round-robin pairing: player 0 stays, the others rotate
+            if (tid == 0) {
+                const int last = pos[me - 1];
+                for (int t = me - 1; t > 1; --t) pos[t] = pos[t - 1];
+                pos[1] = last;
+            }
+            __syncthreads();
+        }
         if (!rotated) break;
     }
     if (tid == 0) {
@@ -1145,7 +1171,7 @@ extern "C" int fci_batch_davidson(fci_batch *b, int nroots, double tol, double *
         if (gr == W.g_ritz.end()) {
             cudaGraph_t graph;
             FCI_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-            k_bjacobi<<<ninst, 64, 0, s>>>(W.on, W.A, m, W.w, W.V);
+            k_bjacobi<<<ninst, 128, 0, s>>>(W.on, W.A, m, W.w, W.V);
             for (int k = 0; k < nroots; ++k) {
                 k_blincomb<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on, W.Bv, ntot, m, W.V + k,
                                                           kMaxSub * kMaxSub, m, 1.0, 0.0, W.X + (size_t)k * ntot);

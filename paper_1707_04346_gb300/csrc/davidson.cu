@@ -43,33 +43,63 @@ namespace fci {
 constexpr int kMaxSub = 32;   // subspace limit (vectors)
 constexpr int kDotBlocks = 304;  // 2 x 152 SMs
 
-// partial[b][i] = sum over this block's stripe of X_i . y
-template <int MAXM>
+// partial[b][g*8 + j] = sum over stripe b of X_{g*8+j} . y, j < 8.  The
+// vectors are split into groups of 8 (blockIdx.x % groups) so that each
+// thread keeps 8 accumulators and many blocks fit on an SM; the groups of one
+// stripe run side by side and share y through L2.  On GB300 these products are
+// bound by the FP64 pipe (about 1.2 TFLOP/s against 2 FLOP per 8-byte element),
+// so each element costs exactly one FMA (a single chain per accumulator).
+// VEC = 4 reads 32-byte vectors (n % 4 == 0, 32-byte aligned rows).
+template <int VEC>
 __global__ void __launch_bounds__(256) k_multidot(const double *__restrict__ X, int m, const double *__restrict__ y,
-                                                  int64_t n, double *__restrict__ partial) {
-    double acc[MAXM];
+                                                  int64_t n, int groups, double *__restrict__ partial) {
+    const int g = blockIdx.x % groups;
+    const int stripe = blockIdx.x / groups;
+    const int nstripes = gridDim.x / groups;
+    const int i0 = g * 8;
+    const int mg = m - i0 < 8 ? m - i0 : 8;
+    double acc[8];
 #pragma unroll
-    for (int i = 0; i < MAXM; ++i) acc[i] = 0.0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride) {
-        const double yr = y[r];
+    for (int j = 0; j < 8; ++j) acc[j] = 0.0;
+    const int64_t stride = (int64_t)nstripes * blockDim.x;
+    if (VEC == 4) {
+        const int64_t n4 = n / 4;
+        const double4_32a *y4 = reinterpret_cast<const double4_32a *>(y);
+        for (int64_t r = stripe * (int64_t)blockDim.x + threadIdx.x; r < n4; r += stride) {
+            const double4_32a yr = y4[r];
 #pragma unroll
-        for (int i = 0; i < MAXM; ++i)
-            if (i < m) acc[i] += X[(int64_t)i * n + r] * yr;
+            for (int j = 0; j < 8; ++j)
+                if (j < mg) {
+                    const double4_32a x = reinterpret_cast<const double4_32a *>(X + (int64_t)(i0 + j) * n)[r];
+                    double a = acc[j];
+                    a = fma(x.x, yr.x, a);
+                    a = fma(x.y, yr.y, a);
+                    a = fma(x.z, yr.z, a);
+                    a = fma(x.w, yr.w, a);
+                    acc[j] = a;
+                }
+        }
+    } else {
+        for (int64_t r = stripe * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride) {
+            const double yr = y[r];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (j < mg) acc[j] = fma(X[(int64_t)(i0 + j) * n + r], yr, acc[j]);
+        }
     }
-    __shared__ double red[MAXM][8];
+    __shared__ double red[8][8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int i = 0; i < MAXM; ++i) {
-        double v = acc[i];
+    for (int j = 0; j < 8; ++j) {
+        double v = acc[j];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) red[i][warp] = v;
+        if (lane == 0) red[j][warp] = v;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    if (threadIdx.x < mg) {
         double v = 0.0;
-        for (int w = 0; w < 8; ++w) v += red[i][w];
-        partial[(int64_t)blockIdx.x * MAXM + i] = v;
+        for (int w = 0; w < 8; ++w) v += red[threadIdx.x][w];
+        partial[(int64_t)stripe * 32 + i0 + threadIdx.x] = v;
     }
 }
 
@@ -84,25 +114,79 @@ __global__ void k_reduce_partials(const double *__restrict__ partial, int nb, in
     out[(int64_t)i * out_stride] = v;
 }
 
-// y[r] = beta*y[r] + sum_i coef[i] X_i[r]
+// y[r] = beta*y[r] + sum_i coef[i] X_i[r]; pairs of elements per thread
+// (double2) when n is even and the rows are 16-byte aligned.
+template <int VEC>
 __global__ void k_lincomb(const double *__restrict__ X, int m, const double *__restrict__ coef, int coef_stride,
                           double beta, double *__restrict__ y, int64_t n) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride) {
-        double v = beta == 0.0 ? 0.0 : beta * y[r];
-        for (int i = 0; i < m; ++i) v += coef[(int64_t)i * coef_stride] * X[(int64_t)i * n + r];
-        y[r] = v;
+    if (VEC == 2) {
+        const int64_t n2 = n / 2;
+        for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n2; r += stride) {
+            double2 v = make_double2(0.0, 0.0);
+            if (beta != 0.0) {
+                const double2 y0 = reinterpret_cast<const double2 *>(y)[r];
+                v.x = beta * y0.x;
+                v.y = beta * y0.y;
+            }
+#pragma unroll 8
+            for (int i = 0; i < m; ++i) {
+                const double c = coef[(int64_t)i * coef_stride];
+                const double2 x = reinterpret_cast<const double2 *>(X + (int64_t)i * n)[r];
+                v.x += c * x.x;
+                v.y += c * x.y;
+            }
+            reinterpret_cast<double2 *>(y)[r] = v;
+        }
+    } else {
+        for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride) {
+            double v = beta == 0.0 ? 0.0 : beta * y[r];
+#pragma unroll 8
+            for (int i = 0; i < m; ++i) v += coef[(int64_t)i * coef_stride] * X[(int64_t)i * n + r];
+            y[r] = v;
+        }
     }
 }
 
-// y -= sum_i coef[i] X_i (Gram-Schmidt update with device coefficients)
-__global__ void k_sub_proj(const double *__restrict__ X, int m, const double *__restrict__ coef,
-                           double *__restrict__ y, int64_t n) {
+// y -= sum_i coef[i] X_i (Gram-Schmidt update with device coefficients);
+// partial[block] = this block's share of ||y||^2 after the update.
+template <int VEC>
+__global__ void __launch_bounds__(256) k_sub_proj(const double *__restrict__ X, int m, const double *__restrict__ coef,
+                                                  double *__restrict__ y, int64_t n, double *__restrict__ partial) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride) {
-        double v = y[r];
-        for (int i = 0; i < m; ++i) v -= coef[i] * X[(int64_t)i * n + r];
-        y[r] = v;
+    double nrm = 0.0;
+    if (VEC == 2) {
+        const int64_t n2 = n / 2;
+        for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n2; r += stride) {
+            double2 v = reinterpret_cast<const double2 *>(y)[r];
+#pragma unroll 8
+            for (int i = 0; i < m; ++i) {
+                const double c = coef[i];
+                const double2 x = reinterpret_cast<const double2 *>(X + (int64_t)i * n)[r];
+                v.x = fma(-c, x.x, v.x);
+                v.y = fma(-c, x.y, v.y);
+            }
+            reinterpret_cast<double2 *>(y)[r] = v;
+            nrm = fma(v.x, v.x, nrm);
+            nrm = fma(v.y, v.y, nrm);
+        }
+    } else {
+        for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride) {
+            double v = y[r];
+#pragma unroll 8
+            for (int i = 0; i < m; ++i) v = fma(-coef[i], X[(int64_t)i * n + r], v);
+            y[r] = v;
+            nrm = fma(v, v, nrm);
+        }
+    }
+    __shared__ double red[8];
+    for (int o = 16; o > 0; o >>= 1) nrm += __shfl_down_sync(0xffffffffu, nrm, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int w = 0; w < 8; ++w) v += red[w];
+        partial[blockIdx.x] = v;
     }
 }
 
@@ -173,7 +257,6 @@ __global__ void k_scale(double *__restrict__ y, const double *__restrict__ nrm2,
 __global__ void k_jacobi(const double *__restrict__ A, int lda, int m, double *__restrict__ w, double *__restrict__ V) {
     __shared__ double a[kMaxSub][kMaxSub + 1];
     __shared__ double v[kMaxSub][kMaxSub + 1];
-    __shared__ double cs[2];
     __shared__ int order[kMaxSub];
     const int tid = threadIdx.x;
     for (int t = tid; t < m * m; t += blockDim.x) {
@@ -182,49 +265,75 @@ __global__ void k_jacobi(const double *__restrict__ A, int lda, int m, double *_
         v[i][j] = (i == j) ? 1.0 : 0.0;
     }
     __syncthreads();
-    // a rotation is skipped when |a_pq| is negligible next to a_pp and a_qq;
-    // the sweeps stop once a whole sweep skipped every pair (60 at most)
+    // Parallel cyclic Jacobi with round-robin pair ordering: each step rotates
+    // m/2 disjoint pairs at once (rotations on disjoint index pairs commute).
+    // A rotation is skipped when |a_pq| < 1e-14 (|a_pp| + |a_qq|); the sweeps
+    // stop after a sweep without rotation (60 at most).
     __shared__ int rotated;
+    __shared__ int pos[kMaxSub + 1];
+    __shared__ int pp[kMaxSub / 2 + 1], pq[kMaxSub / 2 + 1];
+    __shared__ double pc[kMaxSub / 2 + 1], psn[kMaxSub / 2 + 1];
+    const int me = m + (m & 1);  // even number of players; index m is a dummy when m is odd
+    const int half = me / 2;
+    for (int t = tid; t < me; t += blockDim.x) pos[t] = t;
+    __syncthreads();
     for (int sweep = 0; sweep < 60; ++sweep) {
         if (tid == 0) rotated = 0;
         __syncthreads();
-        for (int p = 0; p < m - 1; ++p)
-            for (int q = p + 1; q < m; ++q) {
-                if (tid == 0) {
-                    double apq = a[p][q];
-                    double c = 1.0, s = 0.0;
+        for (int step = 0; step < me - 1; ++step) {
+            for (int k = tid; k < half; k += blockDim.x) {
+                int p = pos[k], q = pos[me - 1 - k];
+                if (p > q) { const int t2 = p; p = q; q = t2; }
+                double c = 1.0, sn = 0.0;
+                if (q < m) {
+                    const double apq = a[p][q];
                     if (fabs(apq) > 1e-14 * (fabs(a[p][p]) + fabs(a[q][q]))) {
                         rotated = 1;
-                        double theta = (a[q][q] - a[p][p]) / (2.0 * apq);
-                        double tt = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                        const double theta = (a[q][q] - a[p][p]) / (2.0 * apq);
+                        const double tt = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
                         c = 1.0 / sqrt(tt * tt + 1.0);
-                        s = tt * c;
-                    }
-                    cs[0] = c;
-                    cs[1] = s;
-                }
-                __syncthreads();
-                const double c = cs[0], s = cs[1];
-                if (s != 0.0) {
-                    // rows/cols p and q of a = J^T a J ; v = v J
-                    for (int k = tid; k < m; k += blockDim.x) {
-                        double akp = a[k][p], akq = a[k][q];
-                        a[k][p] = c * akp - s * akq;
-                        a[k][q] = s * akp + c * akq;
-                    }
-                    __syncthreads();
-                    for (int k = tid; k < m; k += blockDim.x) {
-                        double apk = a[p][k], aqk = a[q][k];
-                        a[p][k] = c * apk - s * aqk;
-                        a[q][k] = s * apk + c * aqk;
-                        double vkp = v[k][p], vkq = v[k][q];
-                        v[k][p] = c * vkp - s * vkq;
-                        v[k][q] = s * vkp + c * vkq;
+                        sn = tt * c;
                     }
                 }
-                __syncthreads();
+                pp[k] = p;
+                pq[k] = q;
+                pc[k] = c;
+                psn[k] = sn;
             }
-        __syncthreads();
+            __syncthreads();
+            // columns: a <- a J
+            for (int t = tid; t < half * m; t += blockDim.x) {
+                const int k = t / m, r = t % m;
+                if (psn[k] == 0.0) continue;
+                const int p = pp[k], q = pq[k];
+                const double c = pc[k], sn = psn[k];
+                const double arp = a[r][p], arq = a[r][q];
+                a[r][p] = c * arp - sn * arq;
+                a[r][q] = sn * arp + c * arq;
+            }
+            __syncthreads();
+            // rows: a <- J^T a ; eigenvectors v <- v J
+            for (int t = tid; t < half * m; t += blockDim.x) {
+                const int k = t / m, r = t % m;
+                if (psn[k] == 0.0) continue;
+                const int p = pp[k], q = pq[k];
+                const double c = pc[k], sn = psn[k];
+                const double apr = a[p][r], aqr = a[q][r];
+                a[p][r] = c * apr - sn * aqr;
+                a[q][r] = sn * apr + c * aqr;
+                const double vrp = v[r][p], vrq = v[r][q];
+                v[r][p] = c * vrp - sn * vrq;
+                v[r][q] = sn * vrp + c * vrq;
+            }
+            __syncthreads();
+            // next round-robin pairing: player 0 stays, the others rotate
+            if (tid == 0) {
+                const int last = pos[me - 1];
+                for (int t = me - 1; t > 1; --t) pos[t] = pos[t - 1];
+                pos[1] = last;
+            }
+            __syncthreads();
+        }
         if (!rotated) break;
     }
     if (tid == 0) {
@@ -371,18 +480,30 @@ unsigned grid_for(int64_t n) {
     return (unsigned)(g < 4 * 152 ? (g < 1 ? 1 : g) : 4 * 152);
 }
 
+bool vec2(int64_t n, const void *a, const void *b) {
+    return n % 2 == 0 && (uintptr_t)a % 16 == 0 && (uintptr_t)b % 16 == 0;
+}
+
+// y = beta*y + sum_i coef[i*coef_stride] X_i
+void lincomb(cudaStream_t s, const double *X, int m, const double *coef, int coef_stride, double beta, double *y,
+             int64_t n) {
+    if (vec2(n, X, y))
+        k_lincomb<2><<<grid_for(n / 2), 256, 0, s>>>(X, m, coef, coef_stride, beta, y, n);
+    else
+        k_lincomb<1><<<grid_for(n), 256, 0, s>>>(X, m, coef, coef_stride, beta, y, n);
+}
+
 // out[i*stride] = X_i . y for i < m (m <= 32)
 int dots(Work &W, const double *X, int m, const double *y, double *out, int stride) {
     if (m <= 0) return FCI_OK;
-    if (m <= 8) {
-        k_multidot<8><<<kDotBlocks, 256, 0, W.s>>>(X, m, y, W.n, W.partial);
-        k_reduce_partials<8><<<1, 32, 0, W.s>>>(W.partial, kDotBlocks, m, out, stride);
-    } else if (m <= 32) {
-        k_multidot<32><<<kDotBlocks, 256, 0, W.s>>>(X, m, y, W.n, W.partial);
-        k_reduce_partials<32><<<1, 32, 0, W.s>>>(W.partial, kDotBlocks, m, out, stride);
-    } else {
-        return fail(FCI_ERR_ARG, "subspace larger than 32 vectors");
-    }
+    if (m > 32) return fail(FCI_ERR_ARG, "subspace larger than 32 vectors");
+    const int groups = (m + 7) / 8;
+    const bool vec = (W.n % 4 == 0) && ((uintptr_t)X % 32 == 0) && ((uintptr_t)y % 32 == 0);
+    if (vec)
+        k_multidot<4><<<kDotBlocks * groups, 256, 0, W.s>>>(X, m, y, W.n, groups, W.partial);
+    else
+        k_multidot<1><<<kDotBlocks * groups, 256, 0, W.s>>>(X, m, y, W.n, groups, W.partial);
+    k_reduce_partials<32><<<1, 32, 0, W.s>>>(W.partial, kDotBlocks, m, out, stride);
     FCI_CUDA(cudaGetLastError());
     return FCI_OK;
 }
@@ -401,14 +522,23 @@ int sigma_of(Work &W, bool fp32, const double *x, double *hx) {
 
 // Orthogonalise y against X_0..X_{m-1} twice, normalise; *kept = 1 if kept.
 int orthonormalise(Work &W, const double *X, int m, double *y, int *kept) {
-    for (int pass = 0; pass < 2; ++pass) {
-        if (m > 0) {
+    if (m > 0) {
+        const bool v2 = vec2(W.n, X, y);
+        const unsigned grid = v2 ? grid_for(W.n / 2) : grid_for(W.n);
+        for (int pass = 0; pass < 2; ++pass) {
             if (int rc = dots(W, X, m, y, W.scal, 1)) return rc;
-            k_sub_proj<<<grid_for(W.n), 256, 0, W.s>>>(X, m, W.scal, y, W.n);
+            if (v2)
+                k_sub_proj<2><<<grid, 256, 0, W.s>>>(X, m, W.scal, y, W.n, W.partial);
+            else
+                k_sub_proj<1><<<grid, 256, 0, W.s>>>(X, m, W.scal, y, W.n, W.partial);
             FCI_CUDA(cudaGetLastError());
         }
+        // squared norm from the second pass
+        k_reduce_partials<1><<<1, 32, 0, W.s>>>(W.partial, (int)grid, 1, W.scal + 40, 1);
+        FCI_CUDA(cudaGetLastError());
+    } else if (int rc = dots(W, y, 1, y, W.scal + 40, 1)) {
+        return rc;
     }
-    if (int rc = dots(W, y, 1, y, W.scal + 40, 1)) return rc;
     k_scale<<<grid_for(W.n), 256, 0, W.s>>>(y, W.scal + 40, 1e-10, W.keep, W.n);
     FCI_CUDA(cudaGetLastError());
     int h = 0;
@@ -492,19 +622,18 @@ int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *v
     std::vector<double> e_prev(nroots, INFINITY), ev(kMaxSub), rn(nroots);
     bool converged = false;
     int it = 0, inner = 0;
-    double r_ref = INFINITY, r_win = INFINITY;
+    double r_win = INFINITY;
     std::vector<double> r_hist;
-    (void)r_ref;
 
     for (it = 1; it <= ctx->opt.max_iter; ++it) {
         // (4) diagonalise the projected matrix
-        k_jacobi<<<1, 64, 0, s>>>(W.A, kMaxSub, m, W.w, W.V);
+        k_jacobi<<<1, 256, 0, s>>>(W.A, kMaxSub, m, W.w, W.V);
         FCI_CUDA(cudaGetLastError());
         const int nr = nroots < m ? nroots : m;
         // Ritz vectors, their sigma, residuals and (2)-(3) preconditioned corrections
         for (int k = 0; k < nr; ++k) {
-            k_lincomb<<<grid_for(n), 256, 0, s>>>(W.Bv, m, W.V + k, m, 0.0, W.X + (size_t)k * n, n);
-            k_lincomb<<<grid_for(n), 256, 0, s>>>(W.Sv, m, W.V + k, m, 0.0, W.HX + (size_t)k * n, n);
+            lincomb(s, W.Bv, m, W.V + k, m, 0.0, W.X + (size_t)k * n, n);
+            lincomb(s, W.Sv, m, W.V + k, m, 0.0, W.HX + (size_t)k * n, n);
             k_residual_precond<<<kDotBlocks, 256, 0, s>>>(W.X + (size_t)k * n, W.HX + (size_t)k * n, ctx->hdiag, W.w,
                                                           k, W.T + (size_t)k * n, n, W.partial);
             k_reduce_partials<1><<<1, 32, 0, s>>>(W.partial, kDotBlocks, 1, W.rn2 + k, 1);
@@ -538,7 +667,6 @@ int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *v
                 break;
             }
             for (int k = 0; k < nr; ++k) e_prev[k] = ev[k];
-            r_ref = rmax;
             inner = 0;
         } else if (++inner >= 60 || rmax < std::sqrt(tol) || (inner >= 15 && rmax > 0.5 * r_win)) {
             // refinement: exact FP64 sigma of each Ritz vector; the difference to
@@ -561,8 +689,8 @@ int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *v
             // to rounding) and their sigma
             const int keep = std::min(keepn, m);
             for (int k = nr; k < keep; ++k) {
-                k_lincomb<<<grid_for(n), 256, 0, s>>>(W.Bv, m, W.V + k, m, 0.0, W.X + (size_t)k * n, n);
-                k_lincomb<<<grid_for(n), 256, 0, s>>>(W.Sv, m, W.V + k, m, 0.0, W.HX + (size_t)k * n, n);
+                lincomb(s, W.Bv, m, W.V + k, m, 0.0, W.X + (size_t)k * n, n);
+                lincomb(s, W.Sv, m, W.V + k, m, 0.0, W.HX + (size_t)k * n, n);
             }
             FCI_CUDA(cudaGetLastError());
             FCI_CUDA(cudaMemcpyAsync(W.Bv, W.X, sizeof(double) * keep * n, cudaMemcpyDeviceToDevice, s));

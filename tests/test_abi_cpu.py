@@ -113,3 +113,26 @@ def _load_missing(fci, tmp_path):
         fci.load(str(tmp_path / "nope.so"))
     finally:
         fci._lib = saved
+
+
+def test_option_validation_on_host(lib):
+    from paper_1707_04346_gb300 import fci
+
+    import fci_inputs as fi
+
+    h1, eri = fi.make_integrals(4, 10)
+    for field, bad in (("f32_splits", 4), ("precision", 7), ("max_subspace", 1), ("max_iter", 0)):
+        o = fci.default_options()
+        setattr(o, field, bad)
+        assert _init(lib, 4, 2, 2, h1, eri, o)[0] == fci.FCI_ERR_ARG, field
+
+
+def test_batch_rejects_bad_instances_on_host(lib):
+    from paper_1707_04346_gb300 import fci
+
+    h = ctypes.c_void_p()
+    z = np.zeros(17 ** 4)
+    inst = (fci.fci_instance * 1)(fci.fci_instance(17, 8, 8, z.ctypes.data, z.ctypes.data))
+    assert lib.fci_batch_init(ctypes.byref(h), 1, inst, None) == fci.FCI_ERR_ARG
+    assert lib.fci_batch_init(ctypes.byref(h), 0, inst, None) == fci.FCI_ERR_ARG
+    assert lib.fci_batch_free(None) == fci.FCI_OK
