@@ -21,6 +21,8 @@
 
 namespace fci {
 
+constexpr int kEnt = 8;  // ELL entries whose table loads are issued together (FP32)
+
 template <typename T>
 __device__ __forceinline__ T gval_of(const SpinTables &S, int64_t idx);
 template <>
@@ -38,6 +40,7 @@ __device__ __forceinline__ float gval_of<float>(const SpinTables &S, int64_t idx
 template <typename T, int R>
 __global__ void __launch_bounds__(512) k_sigma1_rows(const T *__restrict__ C, T *__restrict__ sig, SpinTables B,
                                                      int64_t nsa) {
+    constexpr int U = sizeof(T) == 4 ? kEnt : 1;  // FP64 is bound by its FMA pipe
     extern __shared__ unsigned char smem_raw[];
     T *rows = reinterpret_cast<T *>(smem_raw);
     const int64_t nsb = B.ns;
@@ -51,12 +54,22 @@ __global__ void __launch_bounds__(512) k_sigma1_rows(const T *__restrict__ C, T 
         T acc[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) acc[r] = 0;
-        for (int e = 0; e < B.nsame; ++e) {
-            const int64_t idx = (int64_t)e * nsb + ib;
-            const int32_t col = B.gcol[idx];
-            const T v = gval_of<T>(B, idx);
+        // ELL entries in batches of U: all table loads of a batch are in
+        // flight before the first staged value is read
+        for (int e0 = 0; e0 < B.nsame; e0 += U) {
+            int32_t col[U];
+            T v[U];
 #pragma unroll
-            for (int r = 0; r < R; ++r) acc[r] = fma(v, rows[(int64_t)r * nsb + col], acc[r]);
+            for (int u = 0; u < U; ++u) {
+                const bool ok = e0 + u < B.nsame;
+                const int64_t idx = (int64_t)(ok ? e0 + u : 0) * nsb + ib;
+                col[u] = ok ? B.gcol[idx] : 0;
+                v[u] = ok ? gval_of<T>(B, idx) : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int r = 0; r < R; ++r) acc[r] = fma(v[u], rows[(int64_t)r * nsb + col[u]], acc[r]);
         }
 #pragma unroll
         for (int r = 0; r < R; ++r)
@@ -70,6 +83,7 @@ __global__ void __launch_bounds__(512) k_sigma1_rows(const T *__restrict__ C, T 
 template <typename T, int R>
 __global__ void __launch_bounds__(512) k_sigma2_cols(const T *__restrict__ C, T *__restrict__ sig, SpinTables A,
                                                      int64_t nsb) {
+    constexpr int U = sizeof(T) == 4 ? kEnt : 1;  // FP64 is bound by its FMA pipe
     extern __shared__ unsigned char smem_raw[];
     T *cols = reinterpret_cast<T *>(smem_raw);  // [R][nsa]
     const int64_t nsa = A.ns;
@@ -83,16 +97,81 @@ __global__ void __launch_bounds__(512) k_sigma2_cols(const T *__restrict__ C, T 
         T acc[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) acc[r] = 0;
-        for (int e = 0; e < A.nsame; ++e) {
-            const int64_t idx = (int64_t)e * nsa + ia;
-            const int32_t col = A.gcol[idx];
-            const T v = gval_of<T>(A, idx);
+        for (int e0 = 0; e0 < A.nsame; e0 += U) {
+            int32_t col[U];
+            T v[U];
 #pragma unroll
-            for (int r = 0; r < R; ++r) acc[r] = fma(v, cols[(int64_t)r * nsa + col], acc[r]);
+            for (int u = 0; u < U; ++u) {
+                const bool ok = e0 + u < A.nsame;
+                const int64_t idx = (int64_t)(ok ? e0 + u : 0) * nsa + ia;
+                col[u] = ok ? A.gcol[idx] : 0;
+                v[u] = ok ? gval_of<T>(A, idx) : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int r = 0; r < R; ++r) acc[r] = fma(v[u], cols[(int64_t)r * nsa + col[u]], acc[r]);
         }
 #pragma unroll
         for (int r = 0; r < R; ++r)
             if (c0 + r < nsb) sig[ia * nsb + c0 + r] += acc[r];
+    }
+}
+
+// FP32 sigma_1 + sigma_2 in one pass when both spins share one string space
+// (n_alpha = n_beta, identical same-spin tables): a block stages R rows and
+// the same R columns of C, and every ELL entry it reads updates both,
+//   sigma(r0+r, x) += G[x][col] C(r0+r, col)      (sigma_1, row r0+r)
+//   sigma(x, r0+r) += G[x][col] C(col, r0+r)      (sigma_2, column r0+r)
+// which halves the table traffic that bounds the separate FP32 kernels.  Two
+// blocks meet on each element (its row block and its column block), so sigma
+// starts at zero and both adds are atomic; two addends onto zero give the
+// same sum in either order.
+template <int R>
+__global__ void __launch_bounds__(512) k_sigma12_f32(const float *__restrict__ C, float *__restrict__ sig,
+                                                     SpinTables S) {
+    extern __shared__ float smf[];
+    const int64_t ns = S.ns;
+    float *rows = smf;           // [R][ns]
+    float *cols = smf + R * ns;  // [R][ns]
+    const int64_t r0 = (int64_t)blockIdx.x * R;
+    for (int64_t t = threadIdx.x; t < (int64_t)R * ns; t += blockDim.x) {
+        const int64_t r = t / ns, j = t % ns;
+        rows[t] = (r0 + r < ns) ? C[(r0 + r) * ns + j] : 0.f;
+    }
+    for (int64_t i = threadIdx.x; i < ns; i += blockDim.x) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) cols[(int64_t)r * ns + i] = (r0 + r < ns) ? C[i * ns + r0 + r] : 0.f;
+    }
+    __syncthreads();
+    for (int64_t x = threadIdx.x; x < ns; x += blockDim.x) {
+        float ar[R], ac[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) ar[r] = ac[r] = 0.f;
+        for (int e0 = 0; e0 < S.nsame; e0 += kEnt) {
+            int32_t col[kEnt];
+            float v[kEnt];
+#pragma unroll
+            for (int u = 0; u < kEnt; ++u) {
+                const bool ok = e0 + u < S.nsame;
+                const int64_t idx = (int64_t)(ok ? e0 + u : 0) * ns + x;
+                col[u] = ok ? S.gcol[idx] : 0;
+                v[u] = ok ? S.gvalf[idx] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < kEnt; ++u)
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    ar[r] = fmaf(v[u], rows[(int64_t)r * ns + col[u]], ar[r]);
+                    ac[r] = fmaf(v[u], cols[(int64_t)r * ns + col[u]], ac[r]);
+                }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (r0 + r < ns) {
+                atomicAdd(sig + (r0 + r) * ns + x, ar[r]);
+                atomicAdd(sig + x * ns + r0 + r, ac[r]);
+            }
     }
 }
 
@@ -185,31 +264,49 @@ static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s) {
             if ((size_t)r * len * sizeof(T) <= lim) return r;
         return 0;
     };
-    {
-        const int R = pick_r(nsb);
-        if (!R) return fail(FCI_ERR_ARG, "beta string count too large for the sigma_1 kernel");
-        const size_t sm = (size_t)R * nsb * sizeof(T);
-        void *k = R == 8 ? (void *)k_sigma1_rows<T, 8> : R == 4 ? (void *)k_sigma1_rows<T, 4>
-                : R == 2 ? (void *)k_sigma1_rows<T, 2> : (void *)k_sigma1_rows<T, 1>;
+    // FP32 with one string space for both spins: fused sigma_1 + sigma_2
+    // (profiled as sigma1_rows; sigma2_cols then records no time)
+    int fusedR = 0;
+    if (sizeof(T) == 4 && A.ne == B.ne && nsa == nsb)
+        for (int r : {8, 4})
+            if (!fusedR && (size_t)2 * r * nsa * sizeof(float) <= lim) fusedR = r;
+    if (fusedR) {
+        const size_t sm = (size_t)2 * fusedR * nsa * sizeof(float);
+        void *k = fusedR == 8 ? (void *)k_sigma12_f32<8> : (void *)k_sigma12_f32<4>;
         FCI_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        int64_t nsa_ = nsa;
-        SpinTables Bt = B;
-        void *args[] = {(void *)&C, (void *)&sig, (void *)&Bt, (void *)&nsa_};
-        FCI_CUDA(cudaLaunchKernel(k, dim3(ceil_div(nsa, R)), dim3(512), args, sm, s));
+        FCI_CUDA(cudaMemsetAsync(sig, 0, sizeof(float) * (size_t)nsa * (size_t)nsb, s));
+        SpinTables St = A;
+        void *args[] = {(void *)&C, (void *)&sig, (void *)&St};
+        FCI_CUDA(cudaLaunchKernel(k, dim3(ceil_div(nsa, fusedR)), dim3(512), args, sm, s));
         prof_mark(ctx, rec, 0, s);
-    }
-    {
-        const int R = pick_r(nsa);
-        if (!R) return fail(FCI_ERR_ARG, "alpha string count too large for the sigma_2 kernel");
-        const size_t sm = (size_t)R * nsa * sizeof(T);
-        void *k = R == 8 ? (void *)k_sigma2_cols<T, 8> : R == 4 ? (void *)k_sigma2_cols<T, 4>
-                : R == 2 ? (void *)k_sigma2_cols<T, 2> : (void *)k_sigma2_cols<T, 1>;
-        FCI_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        int64_t nsb_ = nsb;
-        SpinTables At = A;
-        void *args[] = {(void *)&C, (void *)&sig, (void *)&At, (void *)&nsb_};
-        FCI_CUDA(cudaLaunchKernel(k, dim3(ceil_div(nsb, R)), dim3(512), args, sm, s));
         prof_mark(ctx, rec, 1, s);
+    } else {
+        {
+            const int R = pick_r(nsb);
+            if (!R) return fail(FCI_ERR_ARG, "beta string count too large for the sigma_1 kernel");
+            const size_t sm = (size_t)R * nsb * sizeof(T);
+            void *k = R == 8 ? (void *)k_sigma1_rows<T, 8> : R == 4 ? (void *)k_sigma1_rows<T, 4>
+                    : R == 2 ? (void *)k_sigma1_rows<T, 2> : (void *)k_sigma1_rows<T, 1>;
+            FCI_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            int64_t nsa_ = nsa;
+            SpinTables Bt = B;
+            void *args[] = {(void *)&C, (void *)&sig, (void *)&Bt, (void *)&nsa_};
+            FCI_CUDA(cudaLaunchKernel(k, dim3(ceil_div(nsa, R)), dim3(512), args, sm, s));
+            prof_mark(ctx, rec, 0, s);
+        }
+        {
+            const int R = pick_r(nsa);
+            if (!R) return fail(FCI_ERR_ARG, "alpha string count too large for the sigma_2 kernel");
+            const size_t sm = (size_t)R * nsa * sizeof(T);
+            void *k = R == 8 ? (void *)k_sigma2_cols<T, 8> : R == 4 ? (void *)k_sigma2_cols<T, 4>
+                    : R == 2 ? (void *)k_sigma2_cols<T, 2> : (void *)k_sigma2_cols<T, 1>;
+            FCI_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            int64_t nsb_ = nsb;
+            SpinTables At = A;
+            void *args[] = {(void *)&C, (void *)&sig, (void *)&At, (void *)&nsb_};
+            FCI_CUDA(cudaLaunchKernel(k, dim3(ceil_div(nsb, R)), dim3(512), args, sm, s));
+            prof_mark(ctx, rec, 1, s);
+        }
     }
     // sigma_3
     if (A.nsingle > 0 && B.nsingle > 0 && sizeof(T) == 4) {

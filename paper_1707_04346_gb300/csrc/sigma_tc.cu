@@ -169,8 +169,9 @@ struct Layout {
     int stages;  // A tile buffers (1 or 2)
 };
 
-// gcols == 0 selects the private-copy epilogue: no staged accumulator, four
-// copies of the sigma row (one per epilogue warp) instead of one.
+// gcols == 0 selects the private-copy epilogue (no staged accumulator, four
+// copies of the sigma row, one per epilogue warp); gcols < 0 the atomic
+// epilogue (no staged accumulator, one sigma row).
 __host__ __device__ inline Layout make_layout(int ns_split, int kpad, int npad, int64_t nsb, int nsingle_a, int gcols,
                                               int stages) {
     Layout L;
@@ -182,7 +183,7 @@ __host__ __device__ inline Layout make_layout(int ns_split, int kpad, int npad, 
     L.offG = L.offA + stages * ns_split * L.bytesA;
     L.offSig = L.offG + (gcols > 0 ? (uint32_t)(kM * (gcols + 1) * 4) : 0u);
     L.offSig = (L.offSig + 15u) & ~15u;
-    L.offEa = L.offSig + (gcols > 0 ? (uint32_t)(((nsb + 3) / 4) * 16) : 4u * (uint32_t)(((nsb + 32 + 3) / 4) * 16));
+    L.offEa = L.offSig + (gcols != 0 ? (uint32_t)(((nsb + 3) / 4) * 16) : 4u * (uint32_t)(((nsb + 32 + 3) / 4) * 16));
     L.offBar = L.offEa + (uint32_t)(((nsingle_a + 3) / 4) * 16);
     L.total = L.offBar + 8 * 8 + 16;  // full[2], done[2], empty[2], fail word, tmem slot
     return L;
@@ -190,6 +191,9 @@ __host__ __device__ inline Layout make_layout(int ns_split, int kpad, int npad, 
 
 // roles: warps 0-3 producers, 4-7 epilogue (TMEM lane quarter = warp % 4), 8 issues the MMAs
 constexpr int kThreads2 = 288;
+// atomic epilogue: warps 0-3 producers, 4-11 epilogue (two warps per TMEM lane
+// quarter, one per half of the pair columns), 12 issues the MMAs
+constexpr int kThreads3 = 416;
 constexpr int kColBatch = 48;  // accumulator columns loaded per tcgen05.wait
 constexpr int kEntBatch = 24;  // replacement-list entries prefetched per batch
 
@@ -202,8 +206,8 @@ __device__ __forceinline__ void mbar_arrive(uint32_t addr) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
 }
 
-template <int NS, int KPAD, bool PRIV>
-__global__ void __launch_bounds__(kThreads2, 1)
+template <int NS, int KPAD, int EPI>
+__global__ void __launch_bounds__(EPI == 2 ? kThreads3 : kThreads2, 1)
     k_sigma3_tc(const float *__restrict__ C, float *__restrict__ sig, SpinTables A, SpinTables B,
                 const float *__restrict__ Wf, int npair, int npad, int gcols, int stages, uint32_t tmem_cols,
                 int *err) {
@@ -221,6 +225,9 @@ __global__ void __launch_bounds__(kThreads2, 1)
     const uint32_t full0 = smem_u32(bars + 0), done0 = smem_u32(bars + 2), empty0 = smem_u32(bars + 4);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int gstride = gcols + 1;
+    constexpr bool PRIV = EPI == 1;
+    constexpr int kThr = EPI == 2 ? kThreads3 : kThreads2;
+    constexpr int kEpiWarps = EPI == 2 ? 8 : 4;
     const int sa_n = A.nsingle, sb_n = B.nsingle;
     constexpr uint32_t sbo = (uint32_t)(KPAD / 8) * 128u;
     constexpr int kgroups = KPAD / 8;
@@ -235,7 +242,7 @@ __global__ void __launch_bounds__(kThreads2, 1)
         for (int i = 0; i < 2; ++i) {
             mbar_init(full0 + 8 * i, 128);
             mbar_init(done0 + 8 * i, 1);
-            mbar_init(empty0 + 8 * i, 128);
+            mbar_init(empty0 + 8 * i, 32 * kEpiWarps);
         }
         *s_fail = 0;
     }
@@ -249,11 +256,11 @@ __global__ void __launch_bounds__(kThreads2, 1)
 
     for (int64_t row = blockIdx.x; row < A.ns; row += gridDim.x) {
         // ---- row set-up (all threads): alpha list, zero sigma row, B operand ----
-        for (int e = tid; e < sa_n; e += kThreads2) sEa[e] = A.tab[(int64_t)e * A.ns + row];
+        for (int e = tid; e < sa_n; e += kThr) sEa[e] = A.tab[(int64_t)e * A.ns + row];
         const int64_t nsig = PRIV ? 4 * (nsb + 32) : nsb;
-        for (int64_t j = tid; j < nsig; j += kThreads2) sSig[j] = 0.f;
+        for (int64_t j = tid; j < nsig; j += kThr) sSig[j] = 0.f;
         __syncthreads();
-        for (int item = tid; item < npad * kgroups; item += kThreads2) {
+        for (int item = tid; item < npad * kgroups; item += kThr) {
             const int q = item / kgroups, kg = item % kgroups;
             float v[8];
 #pragma unroll
@@ -300,6 +307,67 @@ __global__ void __launch_bounds__(kThreads2, 1)
                 fence_async_smem();
                 mbar_arrive(full0 + 8 * (uint32_t)st);
                 if (t + 1 < ntiles) gather((t + 1) * kM + m);
+            }
+        } else if (EPI == 2 && warp < 12) {
+            // ---- epilogue, shared-memory atomics: no dependency between the adds,
+            // so the warp never waits on its own updates; the replacement-list
+            // entries of the next columns are loaded while the current ones are
+            // added, and the first batch before the accumulator is ready ----
+            const int quarter = warp & 3, half = (warp - 4) >> 2;
+            const int e = quarter * 32 + lane;
+            const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+            const int csplit = (npad / 16) * 8;  // npad is a multiple of 16
+            const int c_begin = half ? csplit : 0, c_end = half ? npad : csplit;
+            for (int64_t t = 0; t < ntiles; ++t) {
+                const int64_t Tt = T + t;
+                const uint32_t acc = tmem + (uint32_t)((Tt & 1) * npad);
+                const int64_t jb = t * kM + e;
+                const bool live = jb < nsb;
+                uint32_t ent[16], nxt[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int c = c_begin + q;
+                    ent[q] = (live && c < c_end && c < npair) ? __ldg(B.tabp + (int64_t)c * nsb + jb) : kNoEntry;
+                }
+                if (!mbar_wait_bounded(done0 + 8 * (uint32_t)(Tt & 1), (uint32_t)((Tt >> 1) & 1))) {
+                    *s_fail = 1;
+                    break;
+                }
+                fence_after();
+                float self = 0.f;
+                for (int cb = c_begin; cb < c_end; cb += 16) {
+                    uint32_t u[16];
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                        : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7])
+                        : "r"(acc + lane_base + (uint32_t)cb));
+                    if (cb + 8 < c_end)
+                        asm volatile(
+                            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                            : "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]),
+                              "=r"(u[15])
+                            : "r"(acc + lane_base + (uint32_t)(cb + 8)));
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const int c = cb + 16 + q;
+                        nxt[q] = (live && c < c_end && c < npair) ? __ldg(B.tabp + (int64_t)c * nsb + jb) : kNoEntry;
+                    }
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        if (ent[q] != kNoEntry) {
+                            const float g = __uint_as_float(u[q]);
+                            const float v = ent_negative(ent[q]) ? -g : g;
+                            const uint32_t tg = ent_target(ent[q]);
+                            if ((int64_t)tg == jb) self += v;  // diagonal pairs (kk), k in J_b
+                            else red_add_shared(&sSig[tg], v);
+                        }
+                        ent[q] = nxt[q];
+                    }
+                }
+                fence_before();
+                mbar_arrive(empty0 + 8 * (uint32_t)(Tt & 1));
+                if (live) red_add_shared(&sSig[jb], self);
             }
         } else if (warp < 8 && PRIV) {
             // ---- epilogue, private copies: the warp walks the pair columns in
@@ -415,7 +483,7 @@ __global__ void __launch_bounds__(kThreads2, 1)
                     }
                 }
             }
-        } else if (lane == 0) {
+        } else if (warp == 4 + kEpiWarps && lane == 0) {
             // ---- MMA issuer ----
             for (int64_t t = 0; t < ntiles; ++t) {
                 const int64_t Tt = T + t;
@@ -453,7 +521,7 @@ __global__ void __launch_bounds__(kThreads2, 1)
         fence_after();
         T += ntiles;
         if (*s_fail) break;
-        for (int64_t j = tid; j < nsb; j += kThreads2) {
+        for (int64_t j = tid; j < nsb; j += kThr) {
             float v = sSig[j];
             if (PRIV) v += sSig[(nsb + 32) + j] + sSig[2 * (nsb + 32) + j] + sSig[3 * (nsb + 32) + j];
             sig[row * nsb + j] += v;
@@ -476,17 +544,19 @@ __global__ void __launch_bounds__(kThreads2, 1)
 
 static int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
-// Staged columns (multiple of 16) and A buffers whose layout fits in `lim`
-// bytes: two A buffers preferred, then the most columns per chunk.
+// Epilogue and A buffers whose layout fits in `lim` bytes: private sigma-row
+// copies (gcols = 0) when four rows fit, else the atomic epilogue (gcols = -1)
+// when one row fits, else staged columns (a multiple of 16) with atomics; two
+// A buffers preferred.
 static bool pick_layout(int nsplit, int kpad, int npad, int64_t nsb, int nsa_single, int lim, int *gcols,
                         int *stages) {
-    // private-copy epilogue (gcols = 0) when it fits, else staged columns + atomics
-    for (int st = 2; st >= 1; --st)
-        if ((int)tc::make_layout(nsplit, kpad, npad, nsb, nsa_single, 0, st).total <= lim) {
-            *gcols = 0;
-            *stages = st;
-            return true;
-        }
+    for (int mode : {0, -1})
+        for (int st = 2; st >= 1; --st)
+            if ((int)tc::make_layout(nsplit, kpad, npad, nsb, nsa_single, mode, st).total <= lim) {
+                *gcols = mode;
+                *stages = st;
+                return true;
+            }
     for (int st = 2; st >= 1; --st)
         for (int passes = 1; passes <= npad / 16; ++passes) {
             const int g = round_up((npad + passes - 1) / passes, 16);
@@ -499,15 +569,15 @@ static bool pick_layout(int nsplit, int kpad, int npad, int64_t nsb, int nsa_sin
     return false;
 }
 
-template <int NS, bool PRIV>
+template <int NS, int EPI>
 static void *kernel_for(int kpad) {
     switch (kpad) {
-        case 16: return (void *)tc::k_sigma3_tc<NS, 16, PRIV>;
-        case 32: return (void *)tc::k_sigma3_tc<NS, 32, PRIV>;
-        case 48: return (void *)tc::k_sigma3_tc<NS, 48, PRIV>;
-        case 64: return (void *)tc::k_sigma3_tc<NS, 64, PRIV>;
-        case 80: return (void *)tc::k_sigma3_tc<NS, 80, PRIV>;
-        case 96: return (void *)tc::k_sigma3_tc<NS, 96, PRIV>;
+        case 16: return (void *)tc::k_sigma3_tc<NS, 16, EPI>;
+        case 32: return (void *)tc::k_sigma3_tc<NS, 32, EPI>;
+        case 48: return (void *)tc::k_sigma3_tc<NS, 48, EPI>;
+        case 64: return (void *)tc::k_sigma3_tc<NS, 64, EPI>;
+        case 80: return (void *)tc::k_sigma3_tc<NS, 80, EPI>;
+        case 96: return (void *)tc::k_sigma3_tc<NS, 96, EPI>;
         default: return nullptr;
     }
 }
@@ -522,9 +592,9 @@ int launch_sigma3_tc(fci_ctx *ctx, const float *C, float *sig, int nsplit, cudaS
     int gcols = 0, stages = 0;
     if (!pick_layout(nsplit, kpad, npad, ctx->B.ns, ctx->A.nsingle, lim, &gcols, &stages))
         return fail(FCI_ERR_ARG, "tensor-core sigma_3: beta string count too large for shared memory");
-    const bool priv = gcols == 0;
-    void *kern = nsplit == 2 ? (priv ? kernel_for<2, true>(kpad) : kernel_for<2, false>(kpad))
-                             : (priv ? kernel_for<3, true>(kpad) : kernel_for<3, false>(kpad));
+    const int epi = gcols < 0 ? 2 : (gcols == 0 ? 1 : 0);
+    void *kern = nsplit == 2 ? (epi == 2 ? kernel_for<2, 2>(kpad) : epi == 1 ? kernel_for<2, 1>(kpad) : kernel_for<2, 0>(kpad))
+                             : (epi == 2 ? kernel_for<3, 2>(kpad) : epi == 1 ? kernel_for<3, 1>(kpad) : kernel_for<3, 0>(kpad));
     const tc::Layout L = tc::make_layout(nsplit, kpad, npad, ctx->B.ns, ctx->A.nsingle, gcols, stages);
     uint32_t cols = 32;
     while (cols < (uint32_t)(2 * npad)) cols <<= 1;  // two accumulators
@@ -535,7 +605,7 @@ int launch_sigma3_tc(fci_ctx *ctx, const float *C, float *sig, int nsplit, cudaS
     void *args[] = {(void *)&C,     (void *)&sig,    (void *)&ctx->A,   (void *)&ctx->B,
                     (void *)&ctx->Wf, (void *)&ctx->npair, (void *)&npad, (void *)&gcols,
                     (void *)&stages, (void *)&cols,  (void *)&ctx->d_err};
-    FCI_CUDA(cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(tc::kThreads2), args, L.total, s));
+    FCI_CUDA(cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(epi == 2 ? tc::kThreads3 : tc::kThreads2), args, L.total, s));
     return FCI_OK;
 }
 
