@@ -170,7 +170,8 @@ struct Layout {
 };
 
 // gcols == 0 selects the private-copy epilogue (no staged accumulator, four
-// copies of the sigma row, one per epilogue warp); gcols < 0 the atomic
+// copies of the sigma row, one per epilogue warp), gcols == -2 the same with
+// two copies per warp (even and odd pair columns), gcols == -1 the atomic
 // epilogue (no staged accumulator, one sigma row).
 __host__ __device__ inline Layout make_layout(int ns_split, int kpad, int npad, int64_t nsb, int nsingle_a, int gcols,
                                               int stages) {
@@ -183,7 +184,9 @@ __host__ __device__ inline Layout make_layout(int ns_split, int kpad, int npad, 
     L.offG = L.offA + stages * ns_split * L.bytesA;
     L.offSig = L.offG + (gcols > 0 ? (uint32_t)(kM * (gcols + 1) * 4) : 0u);
     L.offSig = (L.offSig + 15u) & ~15u;
-    L.offEa = L.offSig + (gcols != 0 ? (uint32_t)(((nsb + 3) / 4) * 16) : 4u * (uint32_t)(((nsb + 32 + 3) / 4) * 16));
+    const uint32_t copy_bytes = (uint32_t)(((nsb + 32 + 3) / 4) * 16);
+    L.offEa = L.offSig + (gcols > 0 || gcols == -1 ? (uint32_t)(((nsb + 3) / 4) * 16)
+                          : (gcols == 0 ? 4u : 8u) * copy_bytes);
     L.offBar = L.offEa + (uint32_t)(((nsingle_a + 3) / 4) * 16);
     L.total = L.offBar + 8 * 8 + 16;  // full[2], done[2], empty[2], fail word, tmem slot
     return L;
@@ -225,7 +228,8 @@ __global__ void __launch_bounds__(EPI == 2 ? kThreads3 : kThreads2, 1)
     const uint32_t full0 = smem_u32(bars + 0), done0 = smem_u32(bars + 2), empty0 = smem_u32(bars + 4);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int gstride = gcols + 1;
-    constexpr bool PRIV = EPI == 1;
+    constexpr bool PRIV = EPI == 1 || EPI == 3;
+    constexpr int kCpw = EPI == 3 ? 2 : 1;  // private sigma copies per epilogue warp
     constexpr int kThr = EPI == 2 ? kThreads3 : kThreads2;
     constexpr int kEpiWarps = EPI == 2 ? 8 : 4;
     const int sa_n = A.nsingle, sb_n = B.nsingle;
@@ -257,7 +261,7 @@ __global__ void __launch_bounds__(EPI == 2 ? kThreads3 : kThreads2, 1)
     for (int64_t row = blockIdx.x; row < A.ns; row += gridDim.x) {
         // ---- row set-up (all threads): alpha list, zero sigma row, B operand ----
         for (int e = tid; e < sa_n; e += kThr) sEa[e] = A.tab[(int64_t)e * A.ns + row];
-        const int64_t nsig = PRIV ? 4 * (nsb + 32) : nsb;
+        const int64_t nsig = PRIV ? 4 * kCpw * (nsb + 32) : nsb;
         for (int64_t j = tid; j < nsig; j += kThr) sSig[j] = 0.f;
         __syncthreads();
         for (int item = tid; item < npad * kgroups; item += kThr) {
@@ -372,51 +376,68 @@ __global__ void __launch_bounds__(EPI == 2 ? kThreads3 : kThreads2, 1)
         } else if (warp < 8 && PRIV) {
             // ---- epilogue, private copies: the warp walks the pair columns in
             // lock-step; for a fixed pair the 32 targets are distinct, and no other
-            // warp writes this copy, so a plain read-add-write suffices ----
+            // warp writes this copy, so a plain read-add-write suffices.  Columns
+            // go in batches of 16; the replacement-list entries of the next batch
+            // are loaded while the current one is added, the first batch before
+            // the accumulator is ready ----
             const int e = tid - 128;
             const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-            float *mine = sSig + (int64_t)(warp & 3) * (nsb + 32);
+            float *mine = sSig + (int64_t)(warp & 3) * kCpw * (nsb + 32);
             for (int64_t t = 0; t < ntiles; ++t) {
                 const int64_t Tt = T + t;
                 const uint32_t acc = tmem + (uint32_t)((Tt & 1) * npad);
+                const int64_t jb = t * kM + e;
+                const bool live = jb < nsb;
+                uint32_t ent[16], nxt[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    ent[q] = (live && q < npair) ? __ldg(B.tabp + (int64_t)q * nsb + jb) : kNoEntry;
                 if (!mbar_wait_bounded(done0 + 8 * (uint32_t)(Tt & 1), (uint32_t)((Tt >> 1) & 1))) {
                     *s_fail = 1;
                     break;
                 }
                 fence_after();
-                const int64_t jb = t * kM + e;
-                const bool live = jb < nsb;
-                for (int cb = 0; cb < npad; cb += kColBatch) {
-                    uint32_t u[kColBatch];
+#pragma unroll 1
+                for (int cb = 0; cb < npad; cb += 16) {
+                    uint32_t u[16];
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                        : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+                          "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]),
+                          "=r"(u[15])
+                        : "r"(acc + lane_base + (uint32_t)cb));
 #pragma unroll
-                    for (int q = 0; q < kColBatch / 8; ++q) {
-                        const int c0 = cb + q * 8;
-                        if (c0 < npad)
-                            asm volatile(
-                                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                                : "=r"(u[q * 8 + 0]), "=r"(u[q * 8 + 1]), "=r"(u[q * 8 + 2]), "=r"(u[q * 8 + 3]),
-                                  "=r"(u[q * 8 + 4]), "=r"(u[q * 8 + 5]), "=r"(u[q * 8 + 6]), "=r"(u[q * 8 + 7])
-                                : "r"(acc + lane_base + (uint32_t)c0));
+                    for (int q = 0; q < 16; ++q) {
+                        const int c = cb + 16 + q;
+                        nxt[q] = (live && c < npair) ? __ldg(B.tabp + (int64_t)c * nsb + jb) : kNoEntry;
                     }
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    if (cb + kColBatch >= npad) {  // accumulator fully read: release it
+                    if (cb + 16 >= npad) {  // accumulator fully read: release it
                         fence_before();
                         mbar_arrive(empty0 + 8 * (uint32_t)(Tt & 1));
                     }
-                    uint32_t ent[kColBatch];
-#pragma unroll
-                    for (int q = 0; q < kColBatch; ++q)
-                        ent[q] = (live && cb + q < npair) ? __ldg(B.tabp + (int64_t)(cb + q) * nsb + jb) : kNoEntry;
                     // branch-free: a missing entry adds 0 to this lane's own dummy slot,
                     // so the warp stays converged and its read-add-writes stay in order
 #pragma unroll
-                    for (int q = 0; q < kColBatch; ++q) {
-                        const bool has = ent[q] != kNoEntry;
-                        const uint32_t tg = has ? ent_target(ent[q]) : (uint32_t)(nsb + lane);
-                        const float g = __uint_as_float(u[q]);
-                        const float v = has ? (ent_negative(ent[q]) ? -g : g) : 0.f;
-                        mine[tg] += v;
+                    for (int q = 0; q < 16; q += kCpw) {
+                        // with two copies, columns q and q+1 go to different copies:
+                        // both loads are issued before either store
+                        float old[kCpw], v[kCpw];
+                        uint32_t tg[kCpw];
+#pragma unroll
+                        for (int h = 0; h < kCpw; ++h) {
+                            const uint32_t en = ent[q + h];
+                            const bool has = en != kNoEntry;
+                            tg[h] = (uint32_t)h * (uint32_t)(nsb + 32) + (has ? ent_target(en) : (uint32_t)(nsb + lane));
+                            const float g = __uint_as_float(u[q + h]);
+                            v[h] = has ? (ent_negative(en) ? -g : g) : 0.f;
+                            old[h] = mine[tg[h]];
+                        }
+#pragma unroll
+                        for (int h = 0; h < kCpw; ++h) mine[tg[h]] = old[h] + v[h];
                     }
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) ent[q] = nxt[q];
                     __syncwarp();
                 }
             }
@@ -523,7 +544,8 @@ __global__ void __launch_bounds__(EPI == 2 ? kThreads3 : kThreads2, 1)
         if (*s_fail) break;
         for (int64_t j = tid; j < nsb; j += kThr) {
             float v = sSig[j];
-            if (PRIV) v += sSig[(nsb + 32) + j] + sSig[2 * (nsb + 32) + j] + sSig[3 * (nsb + 32) + j];
+            if (PRIV)
+                for (int c = 1; c < 4 * kCpw; ++c) v += sSig[(int64_t)c * (nsb + 32) + j];
             sig[row * nsb + j] += v;
         }
         __syncthreads();
@@ -550,13 +572,13 @@ static int round_up(int x, int m) { return (x + m - 1) / m * m; }
 // A buffers preferred.
 static bool pick_layout(int nsplit, int kpad, int npad, int64_t nsb, int nsa_single, int lim, int *gcols,
                         int *stages) {
-    for (int mode : {0, -1})
-        for (int st = 2; st >= 1; --st)
-            if ((int)tc::make_layout(nsplit, kpad, npad, nsb, nsa_single, mode, st).total <= lim) {
-                *gcols = mode;
-                *stages = st;
-                return true;
-            }
+    static const int order[][2] = {{-2, 2}, {-2, 1}, {0, 2}, {0, 1}, {-1, 2}, {-1, 1}};  // {epilogue mode, A buffers}
+    for (const auto &o : order)
+        if ((int)tc::make_layout(nsplit, kpad, npad, nsb, nsa_single, o[0], o[1]).total <= lim) {
+            *gcols = o[0];
+            *stages = o[1];
+            return true;
+        }
     for (int st = 2; st >= 1; --st)
         for (int passes = 1; passes <= npad / 16; ++passes) {
             const int g = round_up((npad + passes - 1) / passes, 16);
@@ -592,9 +614,11 @@ int launch_sigma3_tc(fci_ctx *ctx, const float *C, float *sig, int nsplit, cudaS
     int gcols = 0, stages = 0;
     if (!pick_layout(nsplit, kpad, npad, ctx->B.ns, ctx->A.nsingle, lim, &gcols, &stages))
         return fail(FCI_ERR_ARG, "tensor-core sigma_3: beta string count too large for shared memory");
-    const int epi = gcols < 0 ? 2 : (gcols == 0 ? 1 : 0);
-    void *kern = nsplit == 2 ? (epi == 2 ? kernel_for<2, 2>(kpad) : epi == 1 ? kernel_for<2, 1>(kpad) : kernel_for<2, 0>(kpad))
-                             : (epi == 2 ? kernel_for<3, 2>(kpad) : epi == 1 ? kernel_for<3, 1>(kpad) : kernel_for<3, 0>(kpad));
+    const int epi = gcols == -1 ? 2 : gcols == -2 ? 3 : gcols == 0 ? 1 : 0;
+    void *kern = nsplit == 2 ? (epi == 3 ? kernel_for<2, 3>(kpad) : epi == 2 ? kernel_for<2, 2>(kpad)
+                                : epi == 1 ? kernel_for<2, 1>(kpad) : kernel_for<2, 0>(kpad))
+                             : (epi == 3 ? kernel_for<3, 3>(kpad) : epi == 2 ? kernel_for<3, 2>(kpad)
+                                : epi == 1 ? kernel_for<3, 1>(kpad) : kernel_for<3, 0>(kpad));
     const tc::Layout L = tc::make_layout(nsplit, kpad, npad, ctx->B.ns, ctx->A.nsingle, gcols, stages);
     uint32_t cols = 32;
     while (cols < (uint32_t)(2 * npad)) cols <<= 1;  // two accumulators
