@@ -42,6 +42,8 @@ __host__ __device__ inline int pair_index(int k, int l) {
     return hi * (hi + 1) / 2 + lo;
 }
 
+constexpr int kTileStrings = 128;  // beta strings per tensor-core tile (the MMA's M)
+
 // ---- per-spin string data on the device ------------------------------------
 struct SpinTables {
     int ne = 0;
@@ -57,6 +59,18 @@ struct SpinTables {
     int32_t *gcol = nullptr;   // [nsame][ns] same-spin Hamiltonian columns (ELL)
     double *gval = nullptr;    // [nsame][ns]
     float *gvalf = nullptr;    // [nsame][ns] FP32 copy
+    // Tile schedule of the replacement lists for the tensor-core sigma_3
+    // (strings in tiles of kTileStrings): the entries of tile t's strings,
+    // grouped by target, each target's run dealt whole to one of kTileStrings
+    // shares (longest runs first, to the least loaded share), packed as
+    // target | local source string << 16 | pair << 23 | negative << 31 and
+    // stored step-major, entry j of share k at tsched[toff[t] + j*kTileStrings + k].
+    // Shares are padded to the tile's longest share (toff[t+1] - toff[t] = that
+    // length * kTileStrings) with entries for the dummy target ns + k.  Null when
+    // ns > 65536 - kTileStrings or there are more than 256 pairs.
+    uint32_t *tsched = nullptr;
+    int32_t *toff = nullptr;  // [ntiles + 1]
+    int64_t nsched = 0;
     bool owner = true;         // false when aliasing the alpha tables
 };
 

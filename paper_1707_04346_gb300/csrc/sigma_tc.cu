@@ -16,20 +16,24 @@
 // tensor memory: NS = 2 is split-BF16x3, NS = 3 is split-BF16x6 (about FP32
 // accuracy).
 //
-// CTA: 9 warps, one CTA per SM, persistent over output alpha rows, with
-// three roles that run concurrently on consecutive 128-string tiles:
+// CTA: one per SM, persistent over output alpha rows, with three roles that
+// run concurrently on consecutive 128-string tiles:
 //  * warps 0-3 (producers): each thread gathers the K values of one beta
 //    string (the next tile's loads are in flight while the current one is
-//    split into bf16 slices and stored K-major, no swizzle, into one of two A
+//    split into bf16 slices and stored K-major, no swizzle, into one of the A
 //    buffers) and arrives on full[stage];
-//  * warp 8 (one thread) waits for full[stage] and for a free accumulator,
-//    issues the NS(NS+1)/2 x K/16 MMAs into one of two TMEM accumulators and
-//    commits to done[acc];
-//  * warps 4-7 (epilogue): wait for done[acc], copy their 32 accumulator lanes
-//    (tcgen05.ld) into a private shared-memory row, release the accumulator
-//    (empty[acc]) and scatter the string's replacement-list entries into the
-//    sigma row held in shared memory (FP32 atomics; for a fixed pair the map
-//    J_b -> I_b is one-to-one).
+//  * one thread of the last warp waits for full[stage] and for a free
+//    accumulator, issues the NS(NS+1)/2 x K/16 MMAs into one of two TMEM
+//    accumulators and commits to done[acc];
+//  * the epilogue warps wait for done[acc], read the accumulator (tcgen05.ld)
+//    and add s_b G[J_b][p_b] into the sigma row held in shared memory.  The
+//    default epilogue (4 warps) copies the whole accumulator tile to shared
+//    memory, releases it, and then every thread gathers the entries of the
+//    targets it owns in this tile from a precomputed schedule (see
+//    SpinTables::tsched): no atomics, and the adds of a batch of entries hit
+//    distinct slots.  When the schedule or its shared memory is missing, an
+//    atomic epilogue (8 warps, two per TMEM lane quarter) or a staged-column
+//    epilogue with atomics takes over.
 // All waits are bounded; a wait that gives up sets the device error word and
 // the CTA drains and frees its tensor memory.  The pipeline drains at the end
 // of each alpha row, where the sigma row is added to the output and the B
@@ -96,6 +100,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
         : "r"(addr), "r"(parity)
         : "memory");
     return ok != 0;
+}
+
+// Global loads that stay where they are written: a volatile asm is not moved
+// past the (volatile) barrier waits, so a load issued before a wait really is
+// in flight during it (a plain load may be sunk to its first use).
+__device__ __forceinline__ uint32_t ld_early_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.global.nc.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float ld_early_f32(const float *p) {
+    float v;
+    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
 }
 
 // Bounded wait; returns false if the limit was reached.
@@ -169,10 +187,10 @@ struct Layout {
     int stages;  // A tile buffers (1 or 2)
 };
 
-// gcols == 0 selects the private-copy epilogue (no staged accumulator, four
-// copies of the sigma row, one per epilogue warp), gcols == -2 the same with
-// two copies per warp (even and odd pair columns), gcols == -1 the atomic
-// epilogue (no staged accumulator, one sigma row).
+// gcols > 0: staged-column epilogue (gcols accumulator columns per chunk);
+// gcols == -1: atomic epilogue (no staged accumulator, one sigma row);
+// gcols == -3: gather epilogue (the whole accumulator staged, one sigma row
+// with kM dummy slots).
 __host__ __device__ inline Layout make_layout(int ns_split, int kpad, int npad, int64_t nsb, int nsingle_a, int gcols,
                                               int stages) {
     Layout L;
@@ -182,11 +200,9 @@ __host__ __device__ inline Layout make_layout(int ns_split, int kpad, int npad, 
     L.stages = stages;
     L.offA = ns_split * L.bytesB;
     L.offG = L.offA + stages * ns_split * L.bytesA;
-    L.offSig = L.offG + (gcols > 0 ? (uint32_t)(kM * (gcols + 1) * 4) : 0u);
+    L.offSig = L.offG + (gcols > 0 ? (uint32_t)(kM * (gcols + 1) * 4) : gcols == -3 ? (uint32_t)(kM * (npad + 1) * 4) : 0u);
     L.offSig = (L.offSig + 15u) & ~15u;
-    const uint32_t copy_bytes = (uint32_t)(((nsb + 32 + 3) / 4) * 16);
-    L.offEa = L.offSig + (gcols > 0 || gcols == -1 ? (uint32_t)(((nsb + 3) / 4) * 16)
-                          : (gcols == 0 ? 4u : 8u) * copy_bytes);
+    L.offEa = L.offSig + (uint32_t)(((nsb + (gcols == -3 ? kM : 0) + 3) / 4) * 16);
     L.offBar = L.offEa + (uint32_t)(((nsingle_a + 3) / 4) * 16);
     L.total = L.offBar + 8 * 8 + 16;  // full[2], done[2], empty[2], fail word, tmem slot
     return L;
@@ -199,6 +215,7 @@ constexpr int kThreads2 = 288;
 constexpr int kThreads3 = 416;
 constexpr int kColBatch = 48;  // accumulator columns loaded per tcgen05.wait
 constexpr int kEntBatch = 24;  // replacement-list entries prefetched per batch
+constexpr int kGatherPre = 64;  // gather epilogue: schedule entries held in registers per thread
 
 // Fire-and-forget shared-memory add (no value returned, nothing to wait for).
 __device__ __forceinline__ void red_add_shared(float *p, float v) {
@@ -209,8 +226,9 @@ __device__ __forceinline__ void mbar_arrive(uint32_t addr) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
 }
 
+// EPI: 0 staged columns with atomics, 1 atomic (eight epilogue warps), 2 gather
 template <int NS, int KPAD, int EPI>
-__global__ void __launch_bounds__(EPI == 2 ? kThreads3 : kThreads2, 1)
+__global__ void __launch_bounds__(EPI == 1 ? kThreads3 : kThreads2, 1)
     k_sigma3_tc(const float *__restrict__ C, float *__restrict__ sig, SpinTables A, SpinTables B,
                 const float *__restrict__ Wf, int npair, int npad, int gcols, int stages, uint32_t tmem_cols,
                 int *err) {
@@ -228,10 +246,8 @@ __global__ void __launch_bounds__(EPI == 2 ? kThreads3 : kThreads2, 1)
     const uint32_t full0 = smem_u32(bars + 0), done0 = smem_u32(bars + 2), empty0 = smem_u32(bars + 4);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int gstride = gcols + 1;
-    constexpr bool PRIV = EPI == 1 || EPI == 3;
-    constexpr int kCpw = EPI == 3 ? 2 : 1;  // private sigma copies per epilogue warp
-    constexpr int kThr = EPI == 2 ? kThreads3 : kThreads2;
-    constexpr int kEpiWarps = EPI == 2 ? 8 : 4;
+    constexpr int kThr = EPI == 1 ? kThreads3 : kThreads2;
+    constexpr int kEpiWarps = EPI == 1 ? 8 : 4;
     const int sa_n = A.nsingle, sb_n = B.nsingle;
     constexpr uint32_t sbo = (uint32_t)(KPAD / 8) * 128u;
     constexpr int kgroups = KPAD / 8;
@@ -261,8 +277,7 @@ __global__ void __launch_bounds__(EPI == 2 ? kThreads3 : kThreads2, 1)
     for (int64_t row = blockIdx.x; row < A.ns; row += gridDim.x) {
         // ---- row set-up (all threads): alpha list, zero sigma row, B operand ----
         for (int e = tid; e < sa_n; e += kThr) sEa[e] = A.tab[(int64_t)e * A.ns + row];
-        const int64_t nsig = PRIV ? 4 * kCpw * (nsb + 32) : nsb;
-        for (int64_t j = tid; j < nsig; j += kThr) sSig[j] = 0.f;
+        for (int64_t j = tid; j < nsb; j += kThr) sSig[j] = 0.f;
         __syncthreads();
         for (int item = tid; item < npad * kgroups; item += kThr) {
             const int q = item / kgroups, kg = item % kgroups;
@@ -290,9 +305,13 @@ __global__ void __launch_bounds__(EPI == 2 ? kThreads3 : kThreads2, 1)
             const int m = tid;
             float pre[KPAD];
             auto gather = [&](int64_t jb) {
+                // addresses clamped into range, values of padding slots zeroed after the load
+                const int64_t jc = jb < nsb ? jb : nsb - 1;
 #pragma unroll
-                for (int a = 0; a < KPAD; ++a)
-                    pre[a] = (a < sa_n && jb < nsb) ? __ldg(C + (int64_t)ent_target(sEa[a]) * nsb + jb) : 0.f;
+                for (int a = 0; a < KPAD; ++a) {
+                    const float x = ld_early_f32(C + (int64_t)ent_target(sEa[a < sa_n ? a : 0]) * nsb + jc);
+                    pre[a] = (a < sa_n && jb < nsb) ? x : 0.f;
+                }
             };
             gather(m);
             for (int64_t t = 0; t < ntiles; ++t) {
@@ -312,7 +331,98 @@ __global__ void __launch_bounds__(EPI == 2 ? kThreads3 : kThreads2, 1)
                 mbar_arrive(full0 + 8 * (uint32_t)st);
                 if (t + 1 < ntiles) gather((t + 1) * kM + m);
             }
-        } else if (EPI == 2 && warp < 12) {
+        } else if (EPI == 2 && warp < 8) {
+            // ---- epilogue, target-owned gather: the warps copy the accumulator
+            // tile into shared memory (row = source string J_b, column = pair)
+            // and release it; then thread k adds its share of the tile's entries
+            // (each target's entries all in one share, stored step-major so that
+            // a warp's loads are coalesced),
+            //   sigma(I_a, I_b) += s_b G[J_b][p_b]
+            // summing each target's run in a register and adding it once.  Every
+            // target has one owner per tile and tiles are separated by barriers
+            // of the four epilogue warps, so the sigma row needs no atomics ----
+            const int e = tid - 128;
+            const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+            const int gs = npad + 1;
+            for (int64_t t = 0; t < ntiles; ++t) {
+                const int64_t Tt = T + t;
+                const uint32_t acc = tmem + (uint32_t)((Tt & 1) * npad);
+                // this thread's share (step-major: coalesced across the warp),
+                // loaded before the accumulator is ready; `after` is the entry
+                // that follows the registers' window
+                const int32_t sbase = B.toff[t];
+                const int steps = (B.toff[t + 1] - sbase) / kM;
+                const uint32_t *mysched = B.tsched + sbase + e;
+                uint32_t en[kGatherPre];
+#pragma unroll
+                for (int k = 0; k < kGatherPre; ++k) en[k] = ld_early_u32(mysched + (k < steps ? k : steps - 1) * kM);
+                uint32_t after = ld_early_u32(mysched + (kGatherPre < steps ? kGatherPre : steps - 1) * kM);
+                if (!mbar_wait_bounded(done0 + 8 * (uint32_t)(Tt & 1), (uint32_t)((Tt >> 1) & 1))) {
+                    *s_fail = 1;
+                } else {
+                    fence_after();
+#pragma unroll 1
+                    for (int cb = 0; cb < npad; cb += 16) {
+                        uint32_t u[16];
+                        asm volatile(
+                            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                            : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]),
+                              "=r"(u[7]), "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]),
+                              "=r"(u[14]), "=r"(u[15])
+                            : "r"(acc + lane_base + (uint32_t)cb));
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) sG[e * gs + cb + q] = __uint_as_float(u[q]);
+                    }
+                    fence_before();
+                    mbar_arrive(empty0 + 8 * (uint32_t)(Tt & 1));
+                }
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                if (*s_fail) break;
+                // runs end where the next entry has another target; a thread's runs
+                // have distinct targets and targets have one owner, so the adds of
+                // a batch of 8 entries touch distinct sigma slots: all loads of the
+                // batch are issued before any store
+                float run = 0.f;
+                for (int c0 = 0; c0 < steps; c0 += kGatherPre) {
+                    if (c0 > 0) {
+#pragma unroll
+                        for (int k = 0; k < kGatherPre; ++k)
+                            en[k] = ld_early_u32(mysched + (c0 + k < steps ? c0 + k : steps - 1) * kM);
+                        after = ld_early_u32(mysched + (c0 + kGatherPre < steps ? c0 + kGatherPre : steps - 1) * kM);
+                    }
+                    const int nst = steps - c0 < kGatherPre ? steps - c0 : kGatherPre;
+#pragma unroll
+                    for (int b = 0; b < kGatherPre; b += 8) {
+                        if (b >= nst) break;
+                        float g[8], part[8], old[8];
+                        uint32_t tg[8];
+                        bool last[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u)
+                            g[u] = sG[(int)((en[b + u] >> 16) & 127u) * gs + (int)((en[b + u] >> 23) & 255u)];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int k = b + u;
+                            const uint32_t v = en[k];
+                            const uint32_t nxt = k + 1 < kGatherPre ? en[k + 1 < kGatherPre ? k + 1 : k] : after;
+                            const bool valid = k < nst;
+                            tg[u] = v & 0xFFFFu;
+                            run += valid ? ((v >> 31) ? -g[u] : g[u]) : 0.f;
+                            last[u] = valid && (c0 + k + 1 >= steps || (nxt & 0xFFFFu) != tg[u]);
+                            part[u] = run;
+                            if (last[u]) run = 0.f;
+                        }
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) old[u] = last[u] ? sSig[tg[u]] : 0.f;
+#pragma unroll
+                        for (int u = 0; u < 8; ++u)
+                            if (last[u]) sSig[tg[u]] = old[u] + part[u];
+                    }
+                }
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+            }
+        } else if (EPI == 1 && warp < 12) {
             // ---- epilogue, shared-memory atomics: no dependency between the adds,
             // so the warp never waits on its own updates; the replacement-list
             // entries of the next columns are loaded while the current ones are
@@ -372,74 +482,6 @@ __global__ void __launch_bounds__(EPI == 2 ? kThreads3 : kThreads2, 1)
                 fence_before();
                 mbar_arrive(empty0 + 8 * (uint32_t)(Tt & 1));
                 if (live) red_add_shared(&sSig[jb], self);
-            }
-        } else if (warp < 8 && PRIV) {
-            // ---- epilogue, private copies: the warp walks the pair columns in
-            // lock-step; for a fixed pair the 32 targets are distinct, and no other
-            // warp writes this copy, so a plain read-add-write suffices.  Columns
-            // go in batches of 16; the replacement-list entries of the next batch
-            // are loaded while the current one is added, the first batch before
-            // the accumulator is ready ----
-            const int e = tid - 128;
-            const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-            float *mine = sSig + (int64_t)(warp & 3) * kCpw * (nsb + 32);
-            for (int64_t t = 0; t < ntiles; ++t) {
-                const int64_t Tt = T + t;
-                const uint32_t acc = tmem + (uint32_t)((Tt & 1) * npad);
-                const int64_t jb = t * kM + e;
-                const bool live = jb < nsb;
-                uint32_t ent[16], nxt[16];
-#pragma unroll
-                for (int q = 0; q < 16; ++q)
-                    ent[q] = (live && q < npair) ? __ldg(B.tabp + (int64_t)q * nsb + jb) : kNoEntry;
-                if (!mbar_wait_bounded(done0 + 8 * (uint32_t)(Tt & 1), (uint32_t)((Tt >> 1) & 1))) {
-                    *s_fail = 1;
-                    break;
-                }
-                fence_after();
-#pragma unroll 1
-                for (int cb = 0; cb < npad; cb += 16) {
-                    uint32_t u[16];
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                        : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
-                          "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]),
-                          "=r"(u[15])
-                        : "r"(acc + lane_base + (uint32_t)cb));
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        const int c = cb + 16 + q;
-                        nxt[q] = (live && c < npair) ? __ldg(B.tabp + (int64_t)c * nsb + jb) : kNoEntry;
-                    }
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    if (cb + 16 >= npad) {  // accumulator fully read: release it
-                        fence_before();
-                        mbar_arrive(empty0 + 8 * (uint32_t)(Tt & 1));
-                    }
-                    // branch-free: a missing entry adds 0 to this lane's own dummy slot,
-                    // so the warp stays converged and its read-add-writes stay in order
-#pragma unroll
-                    for (int q = 0; q < 16; q += kCpw) {
-                        // with two copies, columns q and q+1 go to different copies:
-                        // both loads are issued before either store
-                        float old[kCpw], v[kCpw];
-                        uint32_t tg[kCpw];
-#pragma unroll
-                        for (int h = 0; h < kCpw; ++h) {
-                            const uint32_t en = ent[q + h];
-                            const bool has = en != kNoEntry;
-                            tg[h] = (uint32_t)h * (uint32_t)(nsb + 32) + (has ? ent_target(en) : (uint32_t)(nsb + lane));
-                            const float g = __uint_as_float(u[q + h]);
-                            v[h] = has ? (ent_negative(en) ? -g : g) : 0.f;
-                            old[h] = mine[tg[h]];
-                        }
-#pragma unroll
-                        for (int h = 0; h < kCpw; ++h) mine[tg[h]] = old[h] + v[h];
-                    }
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) ent[q] = nxt[q];
-                    __syncwarp();
-                }
             }
         } else if (warp < 8) {
             // ---- epilogue: lane e of the accumulator is beta string t*128 + e ----
@@ -542,12 +584,7 @@ __global__ void __launch_bounds__(EPI == 2 ? kThreads3 : kThreads2, 1)
         fence_after();
         T += ntiles;
         if (*s_fail) break;
-        for (int64_t j = tid; j < nsb; j += kThr) {
-            float v = sSig[j];
-            if (PRIV)
-                for (int c = 1; c < 4 * kCpw; ++c) v += sSig[(int64_t)c * (nsb + 32) + j];
-            sig[row * nsb + j] += v;
-        }
+        for (int64_t j = tid; j < nsb; j += kThr) sig[row * nsb + j] += sSig[j];
         __syncthreads();
     }
     if (*s_fail && tid == 0) {
@@ -566,15 +603,15 @@ __global__ void __launch_bounds__(EPI == 2 ? kThreads3 : kThreads2, 1)
 
 static int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
-// Epilogue and A buffers whose layout fits in `lim` bytes: private sigma-row
-// copies (gcols = 0) when four rows fit, else the atomic epilogue (gcols = -1)
-// when one row fits, else staged columns (a multiple of 16) with atomics; two
-// A buffers preferred.
-static bool pick_layout(int nsplit, int kpad, int npad, int64_t nsb, int nsa_single, int lim, int *gcols,
+// Epilogue and A buffers whose layout fits in `lim` bytes: the gather
+// epilogue (gcols = -3, needs the tile schedule), else the atomic epilogue
+// (gcols = -1), else staged columns (a multiple of 16) with atomics; two A
+// buffers preferred.
+static bool pick_layout(int nsplit, int kpad, int npad, int64_t nsb, int nsa_single, int lim, bool sched, int *gcols,
                         int *stages) {
-    static const int order[][2] = {{-2, 2}, {-2, 1}, {0, 2}, {0, 1}, {-1, 2}, {-1, 1}};  // {epilogue mode, A buffers}
+    static const int order[][2] = {{-3, 2}, {-3, 1}, {-1, 2}, {-1, 1}};  // {epilogue mode, A buffers}
     for (const auto &o : order)
-        if ((int)tc::make_layout(nsplit, kpad, npad, nsb, nsa_single, o[0], o[1]).total <= lim) {
+        if ((o[0] != -3 || sched) && (int)tc::make_layout(nsplit, kpad, npad, nsb, nsa_single, o[0], o[1]).total <= lim) {
             *gcols = o[0];
             *stages = o[1];
             return true;
@@ -612,13 +649,11 @@ int launch_sigma3_tc(fci_ctx *ctx, const float *C, float *sig, int nsplit, cudaS
     FCI_CUDA(cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     FCI_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     int gcols = 0, stages = 0;
-    if (!pick_layout(nsplit, kpad, npad, ctx->B.ns, ctx->A.nsingle, lim, &gcols, &stages))
+    if (!pick_layout(nsplit, kpad, npad, ctx->B.ns, ctx->A.nsingle, lim, ctx->B.tsched != nullptr, &gcols, &stages))
         return fail(FCI_ERR_ARG, "tensor-core sigma_3: beta string count too large for shared memory");
-    const int epi = gcols == -1 ? 2 : gcols == -2 ? 3 : gcols == 0 ? 1 : 0;
-    void *kern = nsplit == 2 ? (epi == 3 ? kernel_for<2, 3>(kpad) : epi == 2 ? kernel_for<2, 2>(kpad)
-                                : epi == 1 ? kernel_for<2, 1>(kpad) : kernel_for<2, 0>(kpad))
-                             : (epi == 3 ? kernel_for<3, 3>(kpad) : epi == 2 ? kernel_for<3, 2>(kpad)
-                                : epi == 1 ? kernel_for<3, 1>(kpad) : kernel_for<3, 0>(kpad));
+    const int epi = gcols == -1 ? 1 : gcols == -3 ? 2 : 0;
+    void *kern = nsplit == 2 ? (epi == 2 ? kernel_for<2, 2>(kpad) : epi == 1 ? kernel_for<2, 1>(kpad) : kernel_for<2, 0>(kpad))
+                             : (epi == 2 ? kernel_for<3, 2>(kpad) : epi == 1 ? kernel_for<3, 1>(kpad) : kernel_for<3, 0>(kpad));
     const tc::Layout L = tc::make_layout(nsplit, kpad, npad, ctx->B.ns, ctx->A.nsingle, gcols, stages);
     uint32_t cols = 32;
     while (cols < (uint32_t)(2 * npad)) cols <<= 1;  // two accumulators
@@ -629,7 +664,7 @@ int launch_sigma3_tc(fci_ctx *ctx, const float *C, float *sig, int nsplit, cudaS
     void *args[] = {(void *)&C,     (void *)&sig,    (void *)&ctx->A,   (void *)&ctx->B,
                     (void *)&ctx->Wf, (void *)&ctx->npair, (void *)&npad, (void *)&gcols,
                     (void *)&stages, (void *)&cols,  (void *)&ctx->d_err};
-    FCI_CUDA(cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(epi == 2 ? tc::kThreads3 : tc::kThreads2), args, L.total, s));
+    FCI_CUDA(cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(epi == 1 ? tc::kThreads3 : tc::kThreads2), args, L.total, s));
     return FCI_OK;
 }
 
@@ -637,7 +672,7 @@ size_t sigma3_tc_smem(const fci_ctx *ctx, int nsplit) {
     if (ctx->A.nsingle == 0 || ctx->B.nsingle == 0) return 0;
     const int kpad = round_up(ctx->A.nsingle, 16), npad = round_up(ctx->npair, 16);
     int g = 0, st = 0;
-    if (!pick_layout(nsplit, kpad, npad, ctx->B.ns, ctx->A.nsingle, 232448, &g, &st)) return 0;
+    if (!pick_layout(nsplit, kpad, npad, ctx->B.ns, ctx->A.nsingle, 232448, ctx->B.tsched != nullptr, &g, &st)) return 0;
     return tc::make_layout(nsplit, kpad, npad, ctx->B.ns, ctx->A.nsingle, g, st).total;
 }
 

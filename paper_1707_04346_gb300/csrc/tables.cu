@@ -8,6 +8,10 @@
 #include <cmath>
 #include <cstring>
 
+#include <algorithm>
+#include <utility>
+#include <vector>
+
 #include "internal.cuh"
 
 namespace fci {
@@ -269,6 +273,84 @@ static int64_t host_binom(int n, int k) {
     return r;
 }
 
+// Tile schedule for the gather epilogue of the tensor-core sigma_3 (see
+// SpinTables::tsched): built on the host from the entry-major table.
+static int build_tile_schedule(fci_ctx *ctx, SpinTables &T) {
+    if (T.nsingle == 0 || T.ns > 65536 - kTileStrings || ctx->npair > 256) return FCI_OK;
+    const int64_t ns = T.ns;
+    const int K = T.nsingle, R = kTileStrings;
+    std::vector<uint32_t> tab((size_t)ns * K);
+    FCI_CUDA(cudaMemcpyAsync(tab.data(), T.tab, sizeof(uint32_t) * tab.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    FCI_CUDA(cudaStreamSynchronize(ctx->stream));
+    const int64_t ntiles = (ns + R - 1) / R;
+    std::vector<uint32_t> out;
+    std::vector<int32_t> off((size_t)ntiles + 1);
+    std::vector<std::pair<uint64_t, uint32_t>> keyed;
+    keyed.reserve((size_t)R * K);
+    size_t pos = 0;
+    for (int64_t t = 0; t < ntiles; ++t) {
+        keyed.clear();
+        for (int jl = 0; jl < R && t * R + jl < ns; ++jl)
+            for (int e = 0; e < K; ++e) {
+                const uint32_t v = tab[(size_t)e * ns + t * R + jl];
+                const uint32_t tg = ent_target(v), p = ent_pair(v);
+                const uint32_t rec = tg | ((uint32_t)jl << 16) | (p << 23) | (ent_negative(v) ? 0x80000000u : 0u);
+                keyed.push_back({((uint64_t)tg << 16) | ((uint64_t)jl << 8) | p, rec});
+            }
+        std::sort(keyed.begin(), keyed.end());
+        const size_t cnt = keyed.size();
+        // runs of one target, dealt to the least loaded share (longest runs
+        // first, ties by target and share index) so that shares stay even
+        std::vector<std::pair<size_t, size_t>> runs;  // [begin, end)
+        for (size_t i = 0; i < cnt;) {
+            size_t j = i + 1;
+            while (j < cnt && (keyed[j].second & 0xFFFFu) == (keyed[i].second & 0xFFFFu)) ++j;
+            runs.push_back({i, j});
+            i = j;
+        }
+        std::vector<size_t> order(runs.size());
+        for (size_t r = 0; r < runs.size(); ++r) order[r] = r;
+        std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+            return runs[x].second - runs[x].first > runs[y].second - runs[y].first;
+        });
+        std::vector<size_t> load(R, 0);
+        std::vector<std::vector<size_t>> share(R);
+        for (size_t r : order) {
+            int best = 0;
+            for (int k = 1; k < R; ++k)
+                if (load[k] < load[best]) best = k;
+            load[best] += runs[r].second - runs[r].first;
+            share[best].push_back(r);
+        }
+        size_t kmax = 0;
+        for (int k = 0; k < R; ++k) {
+            std::sort(share[k].begin(), share[k].end());  // runs in target order
+            kmax = std::max(kmax, load[k]);
+        }
+        // stored step-major: entry j of share k at [j][k]; share k is padded
+        // with entries for the dummy target ns + k (pair 0, source 0, sign +)
+        off[t] = (int32_t)pos;
+        out.resize(pos + kmax * R);
+        for (int k = 0; k < R; ++k) {
+            size_t j = 0;
+            for (size_t r : share[k])
+                for (size_t i = runs[r].first; i < runs[r].second; ++i, ++j) out[pos + j * R + k] = keyed[i].second;
+            for (; j < kmax; ++j) out[pos + j * R + k] = (uint32_t)(ns + k);
+        }
+        pos += kmax * R;
+    }
+    off[ntiles] = (int32_t)pos;
+    int rc = FCI_OK;
+    T.nsched = (int64_t)out.size();
+    T.tsched = (uint32_t *)dalloc(ctx, sizeof(uint32_t) * out.size(), &rc);
+    T.toff = (int32_t *)dalloc(ctx, sizeof(int32_t) * off.size(), &rc);
+    if (rc) return rc;
+    FCI_CUDA(cudaMemcpyAsync(T.tsched, out.data(), sizeof(uint32_t) * out.size(), cudaMemcpyHostToDevice, ctx->stream));
+    FCI_CUDA(cudaMemcpyAsync(T.toff, off.data(), sizeof(int32_t) * off.size(), cudaMemcpyHostToDevice, ctx->stream));
+    FCI_CUDA(cudaStreamSynchronize(ctx->stream));
+    return FCI_OK;
+}
+
 static int build_spin(fci_ctx *ctx, SpinTables &T, int ne) {
     const int n = ctx->norb;
     int rc = FCI_OK;
@@ -305,7 +387,7 @@ static int build_spin(fci_ctx *ctx, SpinTables &T, int ne) {
     FCI_CUDA(cudaGetLastError());
     k_f64_to_f32<<<ceil_div(ns * T.nsame, 256), 256, 0, s>>>(T.gval, T.gvalf, ns * T.nsame);
     FCI_CUDA(cudaGetLastError());
-    return FCI_OK;
+    return build_tile_schedule(ctx, T);
 }
 
 int build_tables(fci_ctx *ctx, const double *h1_host, const double *eri_host) {
@@ -361,6 +443,10 @@ static void free_spin(fci_ctx *ctx, SpinTables &T) {
     dfree(ctx, T.gcol, sizeof(int32_t) * T.ns * T.nsame);
     dfree(ctx, T.gval, sizeof(double) * T.ns * T.nsame);
     dfree(ctx, T.gvalf, sizeof(float) * T.ns * T.nsame);
+    if (T.tsched) {
+        dfree(ctx, T.tsched, sizeof(uint32_t) * T.nsched);
+        dfree(ctx, T.toff, sizeof(int32_t) * ((T.ns + kTileStrings - 1) / kTileStrings + 1));
+    }
     T = SpinTables{};
 }
 
