@@ -38,8 +38,10 @@ namespace bt {
 constexpr int kBlock = 256;
 constexpr int kMaxSub = 32;
 constexpr int kMaxRoots = 8;
-constexpr int kChunk = 256;
+constexpr int kChunk = 256;    // elementwise kernels: one CTA per chunk of <= kChunk elements
+constexpr int kDChunk = 8192;  // dot products: 32 elements per thread before the block reduction
 constexpr double kPad = 1e30;
+constexpr int64_t kHybridMinDets = 32768;  // FP32 sigma of instances this large: single-instance kernels
 
 struct InstDev {
     SpinTables A, B;
@@ -260,100 +262,66 @@ __global__ void __launch_bounds__(kBlock, 1) k_bsigma(const InstDev *__restrict_
 
 // ---- flat batch-vector kernels (one CTA per chunk) ---------------------------
 
-// partial[c][j] = sum over chunk c of X_j . y   (j < m)
-template <int MAXM>
+// partial[c][g*8 + j] = sum over chunk c of X_{g*8+j} . y (j < 8); block
+// index = c * G + g.  As in the single-instance solver the FP64 pipe bounds
+// these products, so every element costs one FMA and a block keeps only 8
+// accumulators per thread.
 __global__ void __launch_bounds__(kBlock) k_bdots(const Chunk *__restrict__ ch, const int *__restrict__ on,
-                                                  const double *__restrict__ X, int64_t ntot, int m,
+                                                  const double *__restrict__ X, int64_t ntot, int m, int G,
                                                   const double *__restrict__ y, double *__restrict__ partial) {
-    const Chunk c = ch[blockIdx.x];
-    double acc[MAXM];
+    const int cidx = blockIdx.x / G, g = blockIdx.x % G;
+    const Chunk c = ch[cidx];
+    const int i0 = g * 8, mg = m - i0 < 8 ? m - i0 : 8;
+    double acc[8];
 #pragma unroll
-    for (int j = 0; j < MAXM; ++j) acc[j] = 0.0;
+    for (int j = 0; j < 8; ++j) acc[j] = 0.0;
     if (on[c.inst])
         for (int t = threadIdx.x; t < c.len; t += kBlock) {
             const int64_t idx = c.start + t;
             const double yv = y[idx];
 #pragma unroll
-            for (int j = 0; j < MAXM; ++j)
-                if (j < m) acc[j] = fma(X[(int64_t)j * ntot + idx], yv, acc[j]);
+            for (int j = 0; j < 8; ++j)
+                if (j < mg) acc[j] = fma(X[(int64_t)(i0 + j) * ntot + idx], yv, acc[j]);
         }
-    __shared__ double red[MAXM][kBlock / 32];
+    __shared__ double red[8][kBlock / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int j = 0; j < MAXM; ++j) {
+    for (int j = 0; j < 8; ++j) {
         double v = acc[j];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) red[j][warp] = v;
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    if (threadIdx.x < mg) {
         double v = 0.0;
-        for (int w = 0; w < kBlock / 32; ++w) v += red[j][w];
-        partial[(int64_t)blockIdx.x * MAXM + j] = v;
+        for (int w = 0; w < kBlock / 32; ++w) v += red[threadIdx.x][w];
+        partial[(int64_t)cidx * 32 + i0 + threadIdx.x] = v;
     }
 }
 
-// out[i*os + j*js] = sum of partial[c][j] over instance i's chunks (fixed order)
-template <int MAXM>
-__global__ void k_breduce(const int *__restrict__ cfirst, const int *__restrict__ on,
-                          const double *__restrict__ partial, int m, double *__restrict__ out, int64_t os, int64_t js) {
+// out[i*os + j*js] = sum of partial[c*STRIDE + j] over instance i's chunks:
+// one CTA per instance, a strided sum per thread and a fixed-order tree.
+template <int STRIDE>
+__global__ void __launch_bounds__(kBlock) k_breduce(const int *__restrict__ cfirst, const int *__restrict__ on,
+                                                    const double *__restrict__ partial, int m,
+                                                    double *__restrict__ out, int64_t os, int64_t js) {
     const int i = blockIdx.x;
     if (!on[i]) return;
-    for (int j = threadIdx.x; j < m; j += blockDim.x) {
-        double v = 0.0;
-        for (int c = cfirst[i]; c < cfirst[i + 1]; ++c) v += partial[(int64_t)c * MAXM + j];
-        out[i * os + j * js] = v;
-    }
-}
-
-// Per-instance dots with few reductions: CTA (g, i) accumulates a stripe of
-// instance i's elements for all j < m in registers, then reduces once.
-// partial[(i*G + g)*MAXM + j]
-template <int MAXM>
-__global__ void __launch_bounds__(kBlock) k_bdots2(const InstDev *__restrict__ D, const int *__restrict__ on,
-                                                   const double *__restrict__ X, int64_t ntot, int m,
-                                                   const double *__restrict__ y, double *__restrict__ partial) {
-    const int i = blockIdx.y, G = gridDim.x, g = blockIdx.x;
-    double acc[MAXM];
-#pragma unroll
-    for (int j = 0; j < MAXM; ++j) acc[j] = 0.0;
-    const bool act = on[i] != 0;
-    const int64_t off = D[i].off, n = D[i].ndet;
-    if (act && (int64_t)g * kBlock < n) {
-        for (int64_t r = (int64_t)g * kBlock + threadIdx.x; r < n; r += (int64_t)G * kBlock) {
-            const int64_t idx = off + r;
-            const double yv = y[idx];
-#pragma unroll
-            for (int j = 0; j < MAXM; ++j)
-                if (j < m) acc[j] = fma(X[(int64_t)j * ntot + idx], yv, acc[j]);
-        }
-    }
-    __shared__ double red[MAXM][kBlock / 32];
+    __shared__ double red[kBlock / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int j = 0; j < MAXM; ++j) {
-        double v = acc[j];
+    const int c0 = cfirst[i], c1 = cfirst[i + 1];
+    for (int j = 0; j < m; ++j) {
+        double v = 0.0;
+        for (int c = c0 + threadIdx.x; c < c1; c += kBlock) v += partial[(int64_t)c * STRIDE + j];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) red[j][warp] = v;
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < m; j += blockDim.x) {
-        double v = 0.0;
-        for (int w = 0; w < kBlock / 32; ++w) v += red[j][w];
-        partial[((int64_t)i * G + g) * MAXM + j] = v;
-    }
-}
-
-// out[i*os + j*js] = sum over g of partial[(i*G + g)][j] (fixed order)
-template <int MAXM>
-__global__ void k_breduce2(const int *__restrict__ on, const double *__restrict__ partial, int G, int m,
-                           double *__restrict__ out, int64_t os, int64_t js) {
-    const int i = blockIdx.x;
-    if (!on[i]) return;
-    for (int j = threadIdx.x; j < m; j += blockDim.x) {
-        double v = 0.0;
-        for (int g = 0; g < G; ++g) v += partial[((int64_t)i * G + g) * MAXM + j];
-        out[i * os + j * js] = v;
+        if (lane == 0) red[warp] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < kBlock / 32; ++w) t += red[w];
+            out[i * os + j * js] = t;
+        }
+        __syncthreads();
     }
 }
 
@@ -639,7 +607,7 @@ struct fci_batch {
     Chunk *d_chunks = nullptr;   // <= 256 elements each (element-wise kernels)
     int nchunks = 0;
     int *d_cfirst = nullptr;
-    Chunk *d_dchunks = nullptr;  // <= 2048 elements each (reductions)
+    Chunk *d_dchunks = nullptr;  // <= kDChunk elements each (reductions)
     int ndchunks = 0;
     int *d_dcfirst = nullptr;
     Item *d_items = nullptr;
@@ -648,6 +616,11 @@ struct fci_batch {
     int row_elems64 = 0, row_elems32 = 0;
     size_t smem64 = 0, smem32 = 0;
     std::vector<int> tune;  // triples (norb, dtype, tpr)
+    // instances whose FP32 sigma runs the single-instance kernels (fused
+    // sigma_1 + sigma_2, tensor-core sigma_3) gated by their active flag; their
+    // work items come first in d_items
+    std::vector<int> hyb;
+    int nitems_hyb = 0;
     // sigma call plumbing
     void **d_cin = nullptr, **d_cout = nullptr;
     int *d_on_all = nullptr;
@@ -676,15 +649,24 @@ unsigned grid_flat(int64_t n) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 4 * 152));
 }
 
-// Work items with the instances' current tpr, largest instances first.
+// Work items with the instances' current tpr: the single-instance-kernel
+// instances first, then the others, largest instances first in each group.
 int build_items(fci_batch *b, int *rc) {
-    std::vector<int> order(b->ninst);
+    std::vector<int> order(b->ninst), is_hyb(b->ninst, 0);
+    for (int i : b->hyb) is_hyb[i] = 1;
     for (int i = 0; i < b->ninst; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->h_inst[x].ndet > b->h_inst[y].ndet; });
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        if (is_hyb[x] != is_hyb[y]) return is_hyb[x] > is_hyb[y];
+        return b->h_inst[x].ndet > b->h_inst[y].ndet;
+    });
     std::vector<Item> items;
+    b->nitems_hyb = 0;
     for (int i : order) {
         const int R = kBlock / b->h_inst[i].tpr;
-        for (int64_t r = 0; r < b->h_inst[i].A.ns; r += R) items.push_back({i, (int)r});
+        for (int64_t r = 0; r < b->h_inst[i].A.ns; r += R) {
+            items.push_back({i, (int)r});
+            if (is_hyb[i]) ++b->nitems_hyb;
+        }
     }
     b->nitems = (int)items.size();
     if (!b->d_items) b->d_items = balloc<Item>(b, items.size(), rc);
@@ -809,8 +791,8 @@ int fci_batch_init(fci_batch **out, int ninst, const fci_instance *inst, const f
     std::vector<int> dcfirst(ninst + 1, 0);
     for (int i = 0; i < ninst; ++i) {
         dcfirst[i] = (int)dch.size();
-        for (int64_t s0 = 0; s0 < b->h_inst[i].ndet; s0 += 8 * kChunk)
-            dch.push_back({i, (int)std::min<int64_t>(8 * kChunk, b->h_inst[i].ndet - s0), b->off[i] + s0});
+        for (int64_t s0 = 0; s0 < b->h_inst[i].ndet; s0 += kDChunk)
+            dch.push_back({i, (int)std::min<int64_t>(kDChunk, b->h_inst[i].ndet - s0), b->off[i] + s0});
     }
     dcfirst[ninst] = (int)dch.size();
     b->ndchunks = (int)dch.size();
@@ -852,8 +834,14 @@ int fci_batch_init(fci_batch **out, int ninst, const fci_instance *inst, const f
         b->h_inst[i].stage_all = (noff_a > 0 && bytes <= 200 * 1024) ? 1 : 0;
         if (b->h_inst[i].stage_all) b->smem32 = std::max(b->smem32, bytes);
     }
-    cudaFuncSetAttribute(k_bsigma<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem64);
-    cudaFuncSetAttribute(k_bsigma<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem32);
+    {  // opted in to the device maximum: other batches launch the same kernels
+        cudaError_t e1 = opt_in_max_smem((const void *)k_bsigma<double>, b->device);
+        cudaError_t e2 = opt_in_max_smem((const void *)k_bsigma<float>, b->device);
+        if (e1 != cudaSuccess || e2 != cudaSuccess) {
+            fci_batch_free(b);
+            return cuda_fail(e1 != cudaSuccess ? e1 : e2, "batched CASCI: shared-memory opt-in");
+        }
+    }
     if (b->smem64 > 227 * 1024) {
         fci_batch_free(b);
         return fail(FCI_ERR_ARG, "batched CASCI: an instance is too large for the batched sigma kernel");
@@ -946,7 +934,12 @@ int fci_batch_init(fci_batch **out, int ninst, const fci_instance *inst, const f
             return cuda_fail(e, "batched CASCI tuning");
         }
     }
-    if ((rc = build_items(b, &rc))) {
+    for (int i = 0; i < ninst && rc == FCI_OK; ++i)
+        if (b->h_inst[i].ndet >= kHybridMinDets && sigma_f32_gated_ok(b->ctx[i])) {
+            b->hyb.push_back(i);
+            rc = prepare_sigma_f32_gated(b->ctx[i]);
+        }
+    if (rc || (rc = build_items(b, &rc))) {
         fci_batch_free(b);
         return rc;
     }
@@ -1019,18 +1012,14 @@ struct BWork {
     std::map<int, cudaGraphExec_t> g_ritz, g_expand;
 };
 
-// out[i*os + j*js] = X_j . y for j < m, per instance (masked by on); one CTA per
-// 2048-element chunk (8 elements per thread before the block reduction)
+// out[i*os + j*js] = X_j . y for j < m, per instance (masked by on); one CTA
+// per (kDChunk-element chunk, group of 8 vectors), then one CTA per instance
 static void bdots(BWork &W, const int *on, const double *X, int m, const double *y, double *out, int64_t os,
                   int64_t js) {
     fci_batch *b = W.b;
-    if (m <= 8) {
-        k_bdots<8><<<b->ndchunks, kBlock, 0, W.s>>>(b->d_dchunks, on, X, b->ntot, m, y, W.partial);
-        k_breduce<8><<<b->ninst, 32, 0, W.s>>>(b->d_dcfirst, on, W.partial, m, out, os, js);
-    } else {
-        k_bdots<32><<<b->ndchunks, kBlock, 0, W.s>>>(b->d_dchunks, on, X, b->ntot, m, y, W.partial);
-        k_breduce<32><<<b->ninst, 32, 0, W.s>>>(b->d_dcfirst, on, W.partial, m, out, os, js);
-    }
+    const int G = (m + 7) / 8;
+    k_bdots<<<b->ndchunks * G, kBlock, 0, W.s>>>(b->d_dchunks, on, X, b->ntot, m, G, y, W.partial);
+    k_breduce<32><<<b->ninst, kBlock, 0, W.s>>>(b->d_dcfirst, on, W.partial, m, out, os, js);
 }
 
 // hx = H x for the batch vector x (instances masked by on); FP32 arithmetic when low.
@@ -1040,9 +1029,13 @@ static int bsigma(BWork &W, const int *on, const double *x, double *hx, void **t
     const int n = b->ninst;
     if (low) {
         k_d2f<<<grid_flat(b->ntot), 256, 0, W.s>>>(x, W.c32, b->ntot);
-        if (int rc = launch_bsigma<float>(b, on, (const float *const *)W.ptr32, (float *const *)(W.ptr32 + n), W.s,
-                                          b->d_items, b->nitems))
-            return rc;
+        if (b->nitems > b->nitems_hyb)
+            if (int rc = launch_bsigma<float>(b, on, (const float *const *)W.ptr32, (float *const *)(W.ptr32 + n),
+                                              W.s, b->d_items + b->nitems_hyb, b->nitems - b->nitems_hyb))
+                return rc;
+        for (int i : b->hyb)
+            if (int rc = launch_sigma_f32_gated(b->ctx[i], W.c32 + b->off[i], W.s32 + b->off[i], on + i, W.s))
+                return rc;
         k_f2d<<<grid_flat(b->ntot), 256, 0, W.s>>>(W.s32, hx, b->ntot);
         return FCI_OK;
     }
@@ -1180,7 +1173,7 @@ extern "C" int fci_batch_davidson(fci_batch *b, int nroots, double tol, double *
                 k_bresid<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on, b->d_inst, W.X + (size_t)k * ntot,
                                                         W.HX + (size_t)k * ntot, W.w + k, kMaxSub,
                                                         W.T + (size_t)k * ntot, W.partial);
-                k_breduce<8><<<ninst, 32, 0, s>>>(b->d_cfirst, W.on, W.partial, 1, W.rn2 + k, kMaxRoots, 1);
+                k_breduce<8><<<ninst, kBlock, 0, s>>>(b->d_cfirst, W.on, W.partial, 1, W.rn2 + k, kMaxRoots, 1);
             }
             FCI_CUDA(cudaStreamEndCapture(s, &graph));
             cudaGraphExec_t ex;
@@ -1307,6 +1300,11 @@ extern "C" int fci_batch_davidson(fci_batch *b, int nroots, double tol, double *
     cleanup();
     if (rc) return rc;
     if (e != cudaSuccess) return cuda_fail(e, "batched Davidson");
+    for (int i : b->hyb) {  // bounded waits of the tensor-core sigma_3
+        int derr = 0;
+        FCI_CUDA(cudaMemcpy(&derr, b->ctx[i]->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (derr) return fail(FCI_ERR_TIMEOUT, "batched Davidson: a bounded device wait gave up inside sigma");
+    }
     if (!all_done) return fail(FCI_ERR_NOCONV, "batched Davidson: some instances did not converge within max_iter");
     return FCI_OK;
 }

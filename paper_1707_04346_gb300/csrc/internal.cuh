@@ -124,8 +124,16 @@ void free_tables(fci_ctx *ctx);
 // sigma.cu
 int launch_sigma(fci_ctx *ctx, const void *c, void *sigma, int dtype, cudaStream_t s);
 
-// sigma_tc.cu (tensor-core sigma_3 for FP32 vectors; nsplit = 2 or 3 bf16 slices)
-int launch_sigma3_tc(fci_ctx *ctx, const float *C, float *sig, int nsplit, cudaStream_t s);
+// FP32 sigma of one batched instance, skipped on the device when *active == 0
+bool sigma_f32_gated_ok(const fci_ctx *ctx);
+int prepare_sigma_f32_gated(const fci_ctx *ctx);
+int launch_sigma_f32_gated(fci_ctx *ctx, const float *C, float *sig, const int *active, cudaStream_t s);
+
+// sigma_tc.cu (tensor-core sigma_3 for FP32 vectors; nsplit = 2 or 3 bf16
+// slices; the kernel returns at once when active is non-null and *active == 0)
+int launch_sigma3_tc(fci_ctx *ctx, const float *C, float *sig, int nsplit, cudaStream_t s,
+                     const int *active = nullptr);
+int prepare_sigma3_tc(const fci_ctx *ctx, int nsplit);
 size_t sigma3_tc_smem(const fci_ctx *ctx, int nsplit);
 
 // davidson.cu
@@ -135,5 +143,18 @@ int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *v
 int run_rdm1(fci_ctx *ctx, const void *c, int dtype, double *gamma);
 
 inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+// Opt a kernel in to the device's largest dynamic shared memory (the opt-in
+// maximum less the kernel's static shared memory).  The attribute is only an
+// upper bound, and one value serves every launch of the kernel, including
+// launches captured in graphs while other contexts use the same kernel.
+inline cudaError_t opt_in_max_smem(const void *kern, int device) {
+    int lim = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lim - (int)fa.sharedSizeBytes);
+}
 
 }  // namespace fci

@@ -129,7 +129,8 @@ __global__ void __launch_bounds__(512) k_sigma2_cols(const T *__restrict__ C, T 
 // same sum in either order.
 template <int R>
 __global__ void __launch_bounds__(512) k_sigma12_f32(const float *__restrict__ C, float *__restrict__ sig,
-                                                     SpinTables S) {
+                                                     SpinTables S, const int *__restrict__ active) {
+    if (active != nullptr && *active == 0) return;  // gated launch (batched engine): instance not active
     extern __shared__ float smf[];
     const int64_t ns = S.ns;
     float *rows = smf;           // [R][ns]
@@ -273,10 +274,11 @@ static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s) {
     if (fusedR) {
         const size_t sm = (size_t)2 * fusedR * nsa * sizeof(float);
         void *k = fusedR == 8 ? (void *)k_sigma12_f32<8> : (void *)k_sigma12_f32<4>;
-        FCI_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        FCI_CUDA(opt_in_max_smem(k, ctx->device));
         FCI_CUDA(cudaMemsetAsync(sig, 0, sizeof(float) * (size_t)nsa * (size_t)nsb, s));
         SpinTables St = A;
-        void *args[] = {(void *)&C, (void *)&sig, (void *)&St};
+        const int *no_gate = nullptr;
+        void *args[] = {(void *)&C, (void *)&sig, (void *)&St, (void *)&no_gate};
         FCI_CUDA(cudaLaunchKernel(k, dim3(ceil_div(nsa, fusedR)), dim3(512), args, sm, s));
         prof_mark(ctx, rec, 0, s);
         prof_mark(ctx, rec, 1, s);
@@ -287,7 +289,7 @@ static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s) {
             const size_t sm = (size_t)R * nsb * sizeof(T);
             void *k = R == 8 ? (void *)k_sigma1_rows<T, 8> : R == 4 ? (void *)k_sigma1_rows<T, 4>
                     : R == 2 ? (void *)k_sigma1_rows<T, 2> : (void *)k_sigma1_rows<T, 1>;
-            FCI_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            FCI_CUDA(opt_in_max_smem(k, ctx->device));
             int64_t nsa_ = nsa;
             SpinTables Bt = B;
             void *args[] = {(void *)&C, (void *)&sig, (void *)&Bt, (void *)&nsa_};
@@ -300,7 +302,7 @@ static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s) {
             const size_t sm = (size_t)R * nsa * sizeof(T);
             void *k = R == 8 ? (void *)k_sigma2_cols<T, 8> : R == 4 ? (void *)k_sigma2_cols<T, 4>
                     : R == 2 ? (void *)k_sigma2_cols<T, 2> : (void *)k_sigma2_cols<T, 1>;
-            FCI_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            FCI_CUDA(opt_in_max_smem(k, ctx->device));
             int64_t nsb_ = nsb;
             SpinTables At = A;
             void *args[] = {(void *)&C, (void *)&sig, (void *)&At, (void *)&nsb_};
@@ -316,13 +318,50 @@ static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s) {
             size_t sm = sizeof(double) * (2 * nsb + ctx->npair) + sizeof(uint32_t) * A.nsingle;
             if (sm > lim) return fail(FCI_ERR_ARG, "beta string count too large for the FP64 sigma_3 row kernel");
             if (sm > 48 * 1024)
-                FCI_CUDA(cudaFuncSetAttribute(k_sigma3_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+                FCI_CUDA(opt_in_max_smem((const void *)k_sigma3_exact, ctx->device));
             k_sigma3_exact<<<(unsigned)nsa, 512, sm, s>>>(C, sig, A, B, ctx->W, ctx->npair);
             FCI_CUDA(cudaGetLastError());
         }
     }
     prof_mark(ctx, rec, 2, s);
     return FCI_OK;
+}
+
+// FP32 sigma of one instance of the batched engine, skipped on the device
+// when *active == 0 (so that a captured graph serves any active set).  Only
+// for one string space (fused sigma_1 + sigma_2) with the tensor-core sigma_3;
+// sigma is zeroed even when the instance is skipped.  The kernels' shared
+// memory limits are set once by prepare_sigma_f32_gated (outside any capture).
+bool sigma_f32_gated_ok(const fci_ctx *ctx) {
+    const SpinTables &A = ctx->A, &B = ctx->B;
+    if (A.ne != B.ne || A.ns != B.ns || A.nsingle == 0 || B.nsingle == 0) return false;
+    if ((size_t)2 * 4 * A.ns * sizeof(float) > smem_limit()) return false;
+    return sigma3_tc_smem(ctx, ctx->opt.f32_splits) > 0;
+}
+
+static void *gated_sigma12(int64_t ns, size_t *sm) {
+    const int R = (size_t)2 * 8 * ns * sizeof(float) <= smem_limit() ? 8 : 4;
+    *sm = (size_t)2 * R * ns * sizeof(float);
+    return R == 8 ? (void *)k_sigma12_f32<8> : (void *)k_sigma12_f32<4>;
+}
+
+int prepare_sigma_f32_gated(const fci_ctx *ctx) {
+    size_t sm = 0;
+    void *k = gated_sigma12(ctx->A.ns, &sm);
+    FCI_CUDA(opt_in_max_smem(k, ctx->device));
+    return prepare_sigma3_tc(ctx, ctx->opt.f32_splits);
+}
+
+int launch_sigma_f32_gated(fci_ctx *ctx, const float *C, float *sig, const int *active, cudaStream_t s) {
+    const int64_t ns = ctx->A.ns;
+    size_t sm = 0;
+    void *k = gated_sigma12(ns, &sm);
+    const int R = sm == (size_t)2 * 8 * ns * sizeof(float) ? 8 : 4;
+    FCI_CUDA(cudaMemsetAsync(sig, 0, sizeof(float) * (size_t)ns * (size_t)ns, s));
+    SpinTables St = ctx->A;
+    void *args[] = {(void *)&C, (void *)&sig, (void *)&St, (void *)&active};
+    FCI_CUDA(cudaLaunchKernel(k, dim3(ceil_div(ns, R)), dim3(512), args, sm, s));
+    return launch_sigma3_tc(ctx, C, sig, ctx->opt.f32_splits, s, active);
 }
 
 int launch_sigma(fci_ctx *ctx, const void *c, void *sigma, int dtype, cudaStream_t s) {

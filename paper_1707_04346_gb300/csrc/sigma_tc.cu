@@ -231,7 +231,8 @@ template <int NS, int KPAD, int EPI>
 __global__ void __launch_bounds__(EPI == 1 ? kThreads3 : kThreads2, 1)
     k_sigma3_tc(const float *__restrict__ C, float *__restrict__ sig, SpinTables A, SpinTables B,
                 const float *__restrict__ Wf, int npair, int npad, int gcols, int stages, uint32_t tmem_cols,
-                int *err) {
+                int *err, const int *__restrict__ active) {
+    if (active != nullptr && *active == 0) return;  // gated launch: the instance is not active
     extern __shared__ __align__(1024) unsigned char smem[];
     const int64_t nsb = B.ns;
     const Layout L = make_layout(NS, KPAD, npad, nsb, A.nsingle, gcols, stages);
@@ -641,30 +642,61 @@ static void *kernel_for(int kpad) {
     }
 }
 
-int launch_sigma3_tc(fci_ctx *ctx, const float *C, float *sig, int nsplit, cudaStream_t s) {
+struct TcPlan {
+    void *kern = nullptr;
+    int npad = 0, gcols = 0, stages = 0, threads = 0, lim = 0;
+    uint32_t cols = 0, smem = 0;
+};
+
+static int tc_plan(const fci_ctx *ctx, int nsplit, TcPlan *P) {
     const int kpad = round_up(ctx->A.nsingle, 16), npad = round_up(ctx->npair, 16);
     if (npad > 256) return fail(FCI_ERR_ARG, "tensor-core sigma_3 supports at most 256 orbital pairs (norb <= 22)");
     if (kpad > 96) return fail(FCI_ERR_ARG, "tensor-core sigma_3 supports at most 96 alpha replacements per string");
-    int dev = ctx->device, lim = 0, nsm = 0;
-    FCI_CUDA(cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    FCI_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    int lim = 0;
+    FCI_CUDA(cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
     int gcols = 0, stages = 0;
     if (!pick_layout(nsplit, kpad, npad, ctx->B.ns, ctx->A.nsingle, lim, ctx->B.tsched != nullptr, &gcols, &stages))
         return fail(FCI_ERR_ARG, "tensor-core sigma_3: beta string count too large for shared memory");
     const int epi = gcols == -1 ? 1 : gcols == -3 ? 2 : 0;
-    void *kern = nsplit == 2 ? (epi == 2 ? kernel_for<2, 2>(kpad) : epi == 1 ? kernel_for<2, 1>(kpad) : kernel_for<2, 0>(kpad))
-                             : (epi == 2 ? kernel_for<3, 2>(kpad) : epi == 1 ? kernel_for<3, 1>(kpad) : kernel_for<3, 0>(kpad));
-    const tc::Layout L = tc::make_layout(nsplit, kpad, npad, ctx->B.ns, ctx->A.nsingle, gcols, stages);
+    P->kern = nsplit == 2 ? (epi == 2 ? kernel_for<2, 2>(kpad) : epi == 1 ? kernel_for<2, 1>(kpad) : kernel_for<2, 0>(kpad))
+                          : (epi == 2 ? kernel_for<3, 2>(kpad) : epi == 1 ? kernel_for<3, 1>(kpad) : kernel_for<3, 0>(kpad));
+    P->npad = npad;
+    P->lim = lim;
+    P->gcols = gcols;
+    P->stages = stages;
+    P->threads = epi == 1 ? tc::kThreads3 : tc::kThreads2;
+    P->smem = tc::make_layout(nsplit, kpad, npad, ctx->B.ns, ctx->A.nsingle, gcols, stages).total;
     uint32_t cols = 32;
     while (cols < (uint32_t)(2 * npad)) cols <<= 1;  // two accumulators
     if (cols > 512) return fail(FCI_ERR_ARG, "tensor-core sigma_3: accumulators exceed tensor memory");
-    FCI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+    P->cols = cols;
+    return FCI_OK;
+}
+
+// Opt the chosen kernel into its shared memory (not done while a stream is
+// being captured: the batched engine prepares its instances beforehand).
+int prepare_sigma3_tc(const fci_ctx *ctx, int nsplit) {
+    TcPlan P;
+    if (int rc = tc_plan(ctx, nsplit, &P)) return rc;
+    FCI_CUDA(opt_in_max_smem(P.kern, ctx->device));
+    return FCI_OK;
+}
+
+int launch_sigma3_tc(fci_ctx *ctx, const float *C, float *sig, int nsplit, cudaStream_t s, const int *active) {
+    TcPlan P;
+    if (int rc = tc_plan(ctx, nsplit, &P)) return rc;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    FCI_CUDA(cudaStreamIsCapturing(s, &cap));
+    if (cap == cudaStreamCaptureStatusNone)
+        FCI_CUDA(opt_in_max_smem(P.kern, ctx->device));
+    int nsm = 0;
+    FCI_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
     int64_t grid = nsm;  // one CTA per SM (launch bounds and shared memory)
     if (grid > ctx->A.ns) grid = ctx->A.ns;
     void *args[] = {(void *)&C,     (void *)&sig,    (void *)&ctx->A,   (void *)&ctx->B,
-                    (void *)&ctx->Wf, (void *)&ctx->npair, (void *)&npad, (void *)&gcols,
-                    (void *)&stages, (void *)&cols,  (void *)&ctx->d_err};
-    FCI_CUDA(cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(epi == 1 ? tc::kThreads3 : tc::kThreads2), args, L.total, s));
+                    (void *)&ctx->Wf, (void *)&ctx->npair, (void *)&P.npad, (void *)&P.gcols,
+                    (void *)&P.stages, (void *)&P.cols,  (void *)&ctx->d_err, (void *)&active};
+    FCI_CUDA(cudaLaunchKernel(P.kern, dim3((unsigned)grid), dim3(P.threads), args, P.smem, s));
     return FCI_OK;
 }
 

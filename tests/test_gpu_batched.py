@@ -89,3 +89,38 @@ def test_batch_tuning_table(pkg):
     table = pkg.fci_batch_tuning(batch)
     assert sorted((n, d) for n, d, _ in table) == [(6, 0), (6, 1), (8, 0), (8, 1)]
     assert all(t in (32, 64, 128, 256) for _, _, t in table)
+
+
+def test_batch_mixed_large_instance_first(pkg):
+    """Instances large enough for the single-instance FP32 kernels (gated by
+    their active flags inside the captured graphs), the largest first, so that
+    a smaller instance is prepared after it."""
+    spec = [(12, 6, 6), (10, 5, 5), (8, 4, 4), (6, 3, 3), (10, 5, 5)]
+    insts = instances(spec, base_seed=57)
+    batch = pkg.fci_batch_init(insts, pkg.default_options(precision=pkg.FCI_PREC_MIXED))
+    e = pkg.fci_batch_davidson(batch, 2, 1e-10)
+    for i, (n, na, nb, h1, eri) in enumerate(insts):
+        ctx = pkg.fci_init(n, na, nb, h1, eri)
+        ref = pkg.fci_davidson(ctx, 2, 1e-10)
+        assert np.abs(e[i] - ref).max() < 1e-8, (i, e[i], ref)
+        pkg.fci_free(ctx)
+
+
+def test_interleaved_contexts_fp32_sigma_reproducible(pkg):
+    """FP32 sigma of a large and a small context called alternately gives the
+    same bits each time (one shared-memory opt-in serves both)."""
+    big = instances([(12, 6, 6)], base_seed=5)[0]
+    small = instances([(8, 4, 4)], base_seed=6)[0]
+    cb, cs = pkg.fci_init(*big), pkg.fci_init(*small)
+    xb = torch.from_numpy(fi.make_vector(cb.ndet, seed=1)).to(DEV, torch.float32)
+    xs = torch.from_numpy(fi.make_vector(cs.ndet, seed=2)).to(DEV, torch.float32)
+    outs = []
+    for _ in range(2):
+        sb, ss = torch.empty_like(xb), torch.empty_like(xs)
+        pkg.fci_sigma(cb, xb, sb)
+        pkg.fci_sigma(cs, xs, ss)
+        torch.cuda.synchronize()
+        outs.append((sb.cpu().numpy(), ss.cpu().numpy()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    pkg.fci_free(cb)
+    pkg.fci_free(cs)
