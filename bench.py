@@ -19,6 +19,7 @@ work has: a plain FP64 CPU implementation written from the paper).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -36,6 +37,33 @@ import fci_inputs as fi  # noqa: E402
 
 WORKLOADS = {"cas14": (14, 7, 7, 100), "cas16": (16, 8, 8, 100), "cas12": (12, 6, 6, 100), "cas8": (8, 4, 4, 40)}
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), nominal
+
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture of the CAS(14e,14o) workload (the summaries under profiles/ give the
+# command), keyed to a digest of the kernel's source at capture time: reported
+# only while that source is unchanged.
+NCU_TRAFFIC = {
+    "sigma3_exact": ("paper_1707_04346_gb300/csrc/sigma.cu", "k_sigma3_exact(", "d3fba1cadf6cd31c", 610262016.0),
+    "sigma3_tc": ("paper_1707_04346_gb300/csrc/sigma_tc.cu", "k_sigma3_tc(", "396417047e53d47b", 126671616.0),
+}
+
+
+def kernel_digest(path: str, marker: str) -> str:
+    """sha256 (16 hex digits) of a kernel's source, from its name to its closing brace."""
+    with open(os.path.join(ROOT, path)) as f:
+        src = f.read()
+    i = src.index(marker)
+    return hashlib.sha256(src[i:src.index("\n}\n", i)].encode()).hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, workload: str):
+    if workload != "cas14" or kernel not in NCU_TRAFFIC:
+        return None
+    path, marker, digest, nbytes = NCU_TRAFFIC[kernel]
+    try:
+        return nbytes if kernel_digest(path, marker) == digest else None
+    except (OSError, ValueError):
+        return None
 
 
 def load_peaks():
@@ -293,7 +321,7 @@ def run_ours(args):
     achieved = flops / kmean[top] / 1e12
     peaks = load_peaks()
     roof = {"kernel": names[top], "bound": bound, "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": unit,
-            "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
+            "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": ncu_traffic(names[top], args.workload),
             "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s (no FP64 entry in MEASURED_PEAKS.json)",
             "work_per_launch": f"{flops:.4g} FLOP ({flops / N:.0f} per determinant x {N} determinants)",
             "kernels": {n: {"ms": float(kmean[i] * 1e3), "share": float(kshare[i])} for i, n in enumerate(names)}}
@@ -318,7 +346,8 @@ def run_ours(args):
     itc = names32.index("sigma3_tc")
     roof_tc = {"kernel": "sigma3_tc", "bound": "tensor", "achieved": mma_flops / k32[itc] / 1e12,
                "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
-               "frac": mma_flops / k32[itc] / 1e12 / peaks["bf16_tflops"], "traffic": None,
+               "frac": mma_flops / k32[itc] / 1e12 / peaks["bf16_tflops"],
+               "traffic": ncu_traffic("sigma3_tc", args.workload),
                "work_per_launch": f"{mma_flops:.4g} bf16 MMA FLOP ({products} slice products x 2 x 128 x {npad} x "
                                   f"{kpad} x {tiles} tiles)",
                "kernels": {n: {"ms": float(k32[i] * 1e3)} for i, n in enumerate(names32)}}

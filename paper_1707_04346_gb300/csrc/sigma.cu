@@ -257,8 +257,6 @@ static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s) {
     const SpinTables &A = ctx->A, &B = ctx->B;
     const int64_t nsa = A.ns, nsb = B.ns;
     const size_t lim = smem_limit();
-    static const char *const names[3] = {"sigma1_rows", "sigma2_cols", sizeof(T) == 4 ? "sigma3_tc" : "sigma3_exact"};
-    const int rec = prof_begin(ctx, s, 3, names);
     // sigma_1 then sigma_2: R rows / columns per block, the largest R whose block fits
     auto pick_r = [&](int64_t len) -> int {
         for (int r = 8; r >= 1; r >>= 1)
@@ -266,11 +264,15 @@ static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s) {
         return 0;
     };
     // FP32 with one string space for both spins: fused sigma_1 + sigma_2
-    // (profiled as sigma1_rows; sigma2_cols then records no time)
     int fusedR = 0;
     if (sizeof(T) == 4 && A.ne == B.ne && nsa == nsb)
         for (int r : {8, 4})
             if (!fusedR && (size_t)2 * r * nsa * sizeof(float) <= lim) fusedR = r;
+    // profiled kernels (fci_profile_read): two slots when fused, else three
+    static const char *const names3[3] = {"sigma1_rows", "sigma2_cols", sizeof(T) == 4 ? "sigma3_tc" : "sigma3_exact"};
+    static const char *const names2[2] = {"sigma12_f32", "sigma3_tc"};
+    const int rec = fusedR ? prof_begin(ctx, s, 2, names2) : prof_begin(ctx, s, 3, names3);
+    const int slot3 = fusedR ? 1 : 2;
     if (fusedR) {
         const size_t sm = (size_t)2 * fusedR * nsa * sizeof(float);
         void *k = fusedR == 8 ? (void *)k_sigma12_f32<8> : (void *)k_sigma12_f32<4>;
@@ -281,7 +283,6 @@ static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s) {
         void *args[] = {(void *)&C, (void *)&sig, (void *)&St, (void *)&no_gate};
         FCI_CUDA(cudaLaunchKernel(k, dim3(ceil_div(nsa, fusedR)), dim3(512), args, sm, s));
         prof_mark(ctx, rec, 0, s);
-        prof_mark(ctx, rec, 1, s);
     } else {
         {
             const int R = pick_r(nsb);
@@ -323,7 +324,7 @@ static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s) {
             FCI_CUDA(cudaGetLastError());
         }
     }
-    prof_mark(ctx, rec, 2, s);
+    prof_mark(ctx, rec, slot3, s);
     return FCI_OK;
 }
 
