@@ -52,7 +52,6 @@ struct SpinTables {
     int nsame = 0;         // same-spin Hamiltonian row width: 1 + singles + doubles
     uint32_t *str = nullptr;   // [ns] bitmasks, ascending
     uint32_t *tab = nullptr;   // [nsingle][ns] packed entries (entry-major)
-    uint32_t *tabq = nullptr;  // [ns][nsingle] the same entries, string-major, sorted by pair index
     uint32_t *tabo = nullptr;  // [ne*(norb-ne)][ns] off-diagonal entries only (k != l), entry-major
     uint32_t *tabp = nullptr;  // [npair][ns] the entry with pair p of each string, or kNoEntry
     double *wdiag = nullptr;   // [npair][ns]: sum over occupied l of (p | ll)

@@ -104,23 +104,6 @@ __global__ void k_unpack_table(const uint32_t *tab, const uint32_t *str, int64_t
     if (sg) sg[t] = ent_negative(ent) ? (int8_t)-1 : (int8_t)1;
 }
 
-// String-major copy of the replacement list of each string, sorted by pair
-// index (the order in which the tensor-core sigma_3 epilogue walks the pairs).
-__global__ void k_sort_by_pair(const uint32_t *tab, int64_t ns, int nsingle, uint32_t *tabq) {
-    int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (x >= ns) return;
-    uint32_t *out = tabq + x * nsingle;
-    for (int e = 0; e < nsingle; ++e) {
-        uint32_t v = tab[(int64_t)e * ns + x];
-        int i = e - 1;
-        while (i >= 0 && ent_pair(out[i]) > ent_pair(v)) {
-            out[i + 1] = out[i];
-            --i;
-        }
-        out[i + 1] = v;
-    }
-}
-
 // Off-diagonal entries (k != l) of each string's list, in list order.
 __global__ void k_offdiag_table(const uint32_t *tab, const uint32_t *str, int64_t ns, int nsingle, int noff,
                                 uint32_t *tabo) {
@@ -362,7 +345,6 @@ static int build_spin(fci_ctx *ctx, SpinTables &T, int ne) {
     const int64_t ns = T.ns;
     T.str = (uint32_t *)dalloc(ctx, sizeof(uint32_t) * ns, &rc);
     T.tab = (uint32_t *)dalloc(ctx, sizeof(uint32_t) * ns * T.nsingle, &rc);
-    T.tabq = (uint32_t *)dalloc(ctx, sizeof(uint32_t) * ns * T.nsingle, &rc);
     const int noff = ne * (n - ne);
     T.tabo = (uint32_t *)dalloc(ctx, sizeof(uint32_t) * ns * (noff > 0 ? noff : 1), &rc);
     T.wdiag = (double *)dalloc(ctx, sizeof(double) * ns * ctx->npair, &rc);
@@ -377,7 +359,6 @@ static int build_spin(fci_ctx *ctx, SpinTables &T, int ne) {
     if (T.nsingle > 0) {
         k_single_table<<<ceil_div(ns * T.nsingle, 256), 256, 0, s>>>(T.str, ns, n, ne, T.nsingle, T.tab);
         FCI_CUDA(cudaGetLastError());
-        k_sort_by_pair<<<ceil_div(ns, 128), 128, 0, s>>>(T.tab, ns, T.nsingle, T.tabq);
         k_offdiag_table<<<ceil_div(ns, 128), 128, 0, s>>>(T.tab, T.str, ns, T.nsingle, noff, T.tabo);
         k_pair_table<<<ceil_div(ns, 128), 128, 0, s>>>(T.tab, ns, T.nsingle, ctx->npair, T.tabp);
         FCI_CUDA(cudaGetLastError());
@@ -435,7 +416,6 @@ static void free_spin(fci_ctx *ctx, SpinTables &T) {
     if (!T.owner) return;
     dfree(ctx, T.str, sizeof(uint32_t) * T.ns);
     dfree(ctx, T.tab, sizeof(uint32_t) * T.ns * T.nsingle);
-    dfree(ctx, T.tabq, sizeof(uint32_t) * T.ns * T.nsingle);
     const int noff = T.ne * (ctx->norb - T.ne);
     dfree(ctx, T.tabo, sizeof(uint32_t) * T.ns * (noff > 0 ? noff : 1));
     dfree(ctx, T.wdiag, sizeof(double) * T.ns * ctx->npair);
