@@ -78,6 +78,10 @@ typedef struct fci_options {
     int f32_splits;      /* FCI_F32 sigma_3 on the tensor cores: FP32 operands split into 2
                             (split-BF16x3, ~1e-5 relative) or 3 (split-BF16x6, ~FP32) bf16
                             slices; default 3 */
+    int same_spin_tc;    /* FCI_F32 sigma_1 and sigma_2 through intermediate strings on the
+                            tensor cores (Eq. 8's E_ij E_kl as a pair-matrix contraction):
+                            0 = only when the staged same-spin kernels do not fit in shared
+                            memory (default), 1 = always */
 } fci_options;
 
 /* Fill *opt with the defaults listed above. */

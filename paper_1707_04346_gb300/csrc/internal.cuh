@@ -87,6 +87,8 @@ struct fci_ctx {
     double *eri = nullptr;          // [n^4]
     double *W = nullptr;            // [npair][npair] packed (ij|kl)
     float *Wf = nullptr;
+    float *kf = nullptr;            // [npair] k_kl = h_kl - 1/2 sum_j (kj|jl), FP32 (same-spin tensor-core path)
+    float *ws32 = nullptr;          // [2][ndet] FP32 workspace of that path (allocated on first use)
     double *hdiag = nullptr;        // [ndet]
     int *d_err = nullptr;           // device error word (bounded waits that gave up)
     size_t bytes = 0;
@@ -133,6 +135,8 @@ int launch_sigma_f32_gated(fci_ctx *ctx, const float *C, float *sig, const int *
 int launch_sigma3_tc(fci_ctx *ctx, const float *C, float *sig, int nsplit, cudaStream_t s,
                      const int *active = nullptr);
 int prepare_sigma3_tc(const fci_ctx *ctx, int nsplit);
+int launch_same_spin_tc(fci_ctx *ctx, const float *C, float *sig, const SpinTables &R, const SpinTables &cols,
+                        cudaStream_t s);
 size_t sigma3_tc_smem(const fci_ctx *ctx, int nsplit);
 
 // davidson.cu

@@ -176,6 +176,26 @@ __global__ void __launch_bounds__(512) k_sigma12_f32(const float *__restrict__ C
     }
 }
 
+// out[c][r] = in[r][c] (ADD: out[c][r] += in[r][c]) for a rows x cols matrix,
+// through 32 x 32 tiles in shared memory (block 32 x 8).
+template <bool ADD>
+__global__ void k_transpose_f32(const float *__restrict__ in, float *__restrict__ out, int64_t rows, int64_t cols) {
+    __shared__ float tile[32][33];
+    const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t r = r0 + i, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) tile[i][threadIdx.x] = in[r * cols + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t c = c0 + i, r = r0 + threadIdx.x;
+        if (c < cols && r < rows) {
+            const float v = tile[threadIdx.x][i];
+            out[c * rows + r] = ADD ? out[c * rows + r] + v : v;
+        }
+    }
+}
+
 __device__ __forceinline__ double flip_sign(double x, uint32_t signbit) {
     return __longlong_as_double(__double_as_longlong(x) ^ ((long long)signbit << 32));
 }
@@ -268,12 +288,42 @@ static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s) {
     if (sizeof(T) == 4 && A.ne == B.ne && nsa == nsb)
         for (int r : {8, 4})
             if (!fusedR && (size_t)2 * r * nsa * sizeof(float) <= lim) fusedR = r;
+    // FP32 same-spin terms through intermediate strings on the tensor cores: when
+    // asked for, or when the staged kernels above do not fit (large string spaces)
+    const bool tc_ok = A.nsingle > 0 && B.nsingle > 0 && ctx->npair + 1 <= 256 && A.nsingle <= 96 &&
+                       B.nsingle <= 96;
+    const bool same_tc = sizeof(T) == 4 && tc_ok &&
+                         (ctx->opt.same_spin_tc == 1 ||
+                          (fusedR == 0 && (A.ne == B.ne || pick_r(nsb) < 4 || pick_r(nsa) < 4)));
     // profiled kernels (fci_profile_read): two slots when fused, else three
     static const char *const names3[3] = {"sigma1_rows", "sigma2_cols", sizeof(T) == 4 ? "sigma3_tc" : "sigma3_exact"};
+    static const char *const names3tc[3] = {"sigma2_tc", "sigma1_tc", "sigma3_tc"};
     static const char *const names2[2] = {"sigma12_f32", "sigma3_tc"};
-    const int rec = fusedR ? prof_begin(ctx, s, 2, names2) : prof_begin(ctx, s, 3, names3);
-    const int slot3 = fusedR ? 1 : 2;
-    if (fusedR) {
+    const int rec = same_tc ? prof_begin(ctx, s, 3, names3tc)
+                    : fusedR ? prof_begin(ctx, s, 2, names2) : prof_begin(ctx, s, 3, names3);
+    const int slot3 = (fusedR && !same_tc) ? 1 : 2;
+    if (same_tc) {
+        if constexpr (sizeof(T) == 4) {
+            if (!ctx->ws32) {
+                int rc = FCI_OK;
+                ctx->ws32 = (float *)dalloc(ctx, sizeof(float) * 2 * (size_t)ctx->ndet, &rc);
+                if (rc) return rc;
+            }
+            float *Ct = ctx->ws32, *Tt = ctx->ws32 + ctx->ndet;
+            FCI_CUDA(cudaMemsetAsync(sig, 0, sizeof(float) * (size_t)ctx->ndet, s));
+            // sigma_2: intermediate alpha strings, rows of C
+            if (int rc = launch_same_spin_tc(ctx, (const float *)C, (float *)sig, A, B, s)) return rc;
+            prof_mark(ctx, rec, 0, s);
+            // sigma_1: intermediate beta strings, rows of C transposed
+            const dim3 tb(32, 8);
+            k_transpose_f32<false><<<dim3(ceil_div(nsb, 32), ceil_div(nsa, 32)), tb, 0, s>>>((const float *)C, Ct, nsa, nsb);
+            FCI_CUDA(cudaMemsetAsync(Tt, 0, sizeof(float) * (size_t)ctx->ndet, s));
+            if (int rc = launch_same_spin_tc(ctx, Ct, Tt, B, A, s)) return rc;
+            k_transpose_f32<true><<<dim3(ceil_div(nsa, 32), ceil_div(nsb, 32)), tb, 0, s>>>(Tt, (float *)sig, nsb, nsa);
+            FCI_CUDA(cudaGetLastError());
+            prof_mark(ctx, rec, 1, s);
+        }
+    } else if (fusedR) {
         const size_t sm = (size_t)2 * fusedR * nsa * sizeof(float);
         void *k = fusedR == 8 ? (void *)k_sigma12_f32<8> : (void *)k_sigma12_f32<4>;
         FCI_CUDA(opt_in_max_smem(k, ctx->device));

@@ -190,7 +190,9 @@ struct Layout {
 // gcols > 0: staged-column epilogue (gcols accumulator columns per chunk);
 // gcols == -1: atomic epilogue (no staged accumulator, one sigma row);
 // gcols == -3: gather epilogue (the whole accumulator staged, one sigma row
-// with kM dummy slots).
+// with kM dummy slots); gcols == -4: gather epilogue adding into the sigma
+// row in global memory (no sigma row in shared memory); gcols == -5: the
+// same-spin epilogue (a pair table of npad entries, nothing staged).
 __host__ __device__ inline Layout make_layout(int ns_split, int kpad, int npad, int64_t nsb, int nsingle_a, int gcols,
                                               int stages) {
     Layout L;
@@ -200,9 +202,12 @@ __host__ __device__ inline Layout make_layout(int ns_split, int kpad, int npad, 
     L.stages = stages;
     L.offA = ns_split * L.bytesB;
     L.offG = L.offA + stages * ns_split * L.bytesA;
-    L.offSig = L.offG + (gcols > 0 ? (uint32_t)(kM * (gcols + 1) * 4) : gcols == -3 ? (uint32_t)(kM * (npad + 1) * 4) : 0u);
+    L.offSig = L.offG + (gcols > 0 ? (uint32_t)(kM * (gcols + 1) * 4)
+                         : (gcols == -3 || gcols == -4) ? (uint32_t)(kM * (npad + 1) * 4) : 0u);
     L.offSig = (L.offSig + 15u) & ~15u;
-    L.offEa = L.offSig + (uint32_t)(((nsb + (gcols == -3 ? kM : 0) + 3) / 4) * 16);
+    L.offEa = L.offSig + (gcols == -4   ? 0u
+                          : gcols == -5 ? (uint32_t)(((npad + 3) / 4) * 16)
+                                        : (uint32_t)(((nsb + (gcols == -3 ? kM : 0) + 3) / 4) * 16));
     L.offBar = L.offEa + (uint32_t)(((nsingle_a + 3) / 4) * 16);
     L.total = L.offBar + 8 * 8 + 16;  // full[2], done[2], empty[2], fail word, tmem slot
     return L;
@@ -226,12 +231,22 @@ __device__ __forceinline__ void mbar_arrive(uint32_t addr) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
 }
 
-// EPI: 0 staged columns with atomics, 1 atomic (eight epilogue warps), 2 gather
+// EPI: 0 staged columns with atomics, 1 atomic (eight epilogue warps), 2 gather,
+// 3 gather into the sigma row in global memory, 4 same-spin (see below).
+//
+// EPI 4 computes the same-spin term of the strings of A instead (sigma_2 on C,
+// sigma_1 on C transposed) through intermediate strings K = the rows:
+//   1/2 sum (ij|kl) E_ij E_kl C:  G[J_b][q] = sum_a C(J_a, J_b) s_a (q|p_a) / 2,
+//        sigma(E_q K, J_b) += s_q G[J_b][q]       for each entry (E_q K, q, s_q) of K's list
+//   sum k_kl E_kl C: one more column q = npair with B[npair][a] = s_a k(p_a),
+//        sigma(K, J_b) += G[J_b][npair]
+// The rows of sigma it adds to belong to other intermediate strings too, so the
+// adds are atomic (red.global, coalesced along J_b).
 template <int NS, int KPAD, int EPI>
 __global__ void __launch_bounds__(EPI == 1 ? kThreads3 : kThreads2, 1)
     k_sigma3_tc(const float *__restrict__ C, float *__restrict__ sig, SpinTables A, SpinTables B,
                 const float *__restrict__ Wf, int npair, int npad, int gcols, int stages, uint32_t tmem_cols,
-                int *err, const int *__restrict__ active) {
+                int *err, const int *__restrict__ active, const float *__restrict__ kf) {
     if (active != nullptr && *active == 0) return;  // gated launch: the instance is not active
     extern __shared__ __align__(1024) unsigned char smem[];
     const int64_t nsb = B.ns;
@@ -278,8 +293,14 @@ __global__ void __launch_bounds__(EPI == 1 ? kThreads3 : kThreads2, 1)
     for (int64_t row = blockIdx.x; row < A.ns; row += gridDim.x) {
         // ---- row set-up (all threads): alpha list, zero sigma row, B operand ----
         for (int e = tid; e < sa_n; e += kThr) sEa[e] = A.tab[(int64_t)e * A.ns + row];
-        for (int64_t j = tid; j < nsb; j += kThr) sSig[j] = 0.f;
+        uint32_t *sPair = reinterpret_cast<uint32_t *>(sSig);  // EPI 4: [npad] entry of K's list by pair
+        if (EPI == 4)
+            for (int q = tid; q < npad; q += kThr) sPair[q] = q == npair ? (uint32_t)row : kNoEntry;
+        else if (EPI != 3)
+            for (int64_t j = tid; j < nsb; j += kThr) sSig[j] = 0.f;
         __syncthreads();
+        if (EPI == 4)
+            for (int e = tid; e < sa_n; e += kThr) sPair[ent_pair(sEa[e])] = sEa[e];
         for (int item = tid; item < npad * kgroups; item += kThr) {
             const int q = item / kgroups, kg = item % kgroups;
             float v[8];
@@ -290,6 +311,11 @@ __global__ void __launch_bounds__(EPI == 1 ? kThreads3 : kThreads2, 1)
                 if (q < npair && a < sa_n) {
                     const uint32_t ea = sEa[a];
                     x = __ldg(Wf + (int64_t)q * npair + ent_pair(ea));
+                    if (EPI == 4) x *= 0.5f;
+                    if (ent_negative(ea)) x = -x;
+                } else if (EPI == 4 && q == npair && a < sa_n) {
+                    const uint32_t ea = sEa[a];
+                    x = __ldg(kf + ent_pair(ea));
                     if (ent_negative(ea)) x = -x;
                 }
                 v[i] = x;
@@ -332,7 +358,47 @@ __global__ void __launch_bounds__(EPI == 1 ? kThreads3 : kThreads2, 1)
                 mbar_arrive(full0 + 8 * (uint32_t)st);
                 if (t + 1 < ntiles) gather((t + 1) * kM + m);
             }
-        } else if (EPI == 2 && warp < 8) {
+        } else if (EPI == 4 && warp < 8) {
+            // ---- epilogue, same-spin: column q of the accumulator goes to the sigma
+            // row of K's entry with pair q (uniform over the warp), each lane adding
+            // its own J_b ----
+            const int e = tid - 128;
+            const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+            for (int64_t t = 0; t < ntiles; ++t) {
+                const int64_t Tt = T + t;
+                const uint32_t acc = tmem + (uint32_t)((Tt & 1) * npad);
+                const int64_t jb = t * kM + e;
+                const bool live = jb < nsb;
+                if (!mbar_wait_bounded(done0 + 8 * (uint32_t)(Tt & 1), (uint32_t)((Tt >> 1) & 1))) {
+                    *s_fail = 1;
+                    break;
+                }
+                fence_after();
+#pragma unroll 1
+                for (int cb = 0; cb < npad; cb += 16) {
+                    uint32_t u[16];
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                        : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+                          "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]),
+                          "=r"(u[15])
+                        : "r"(acc + lane_base + (uint32_t)cb));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (cb + 16 >= npad) {  // accumulator fully read: release it
+                        fence_before();
+                        mbar_arrive(empty0 + 8 * (uint32_t)(Tt & 1));
+                    }
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const uint32_t en = sPair[cb + q];
+                        if (en != kNoEntry && live) {
+                            const float g = __uint_as_float(u[q]);
+                            atomicAdd(sig + (int64_t)ent_target(en) * nsb + jb, ent_negative(en) ? -g : g);
+                        }
+                    }
+                }
+            }
+        } else if ((EPI == 2 || EPI == 3) && warp < 8) {
             // ---- epilogue, target-owned gather: the warps copy the accumulator
             // tile into shared memory (row = source string J_b, column = pair)
             // and release it; then thread k adds its share of the tile's entries
@@ -415,10 +481,22 @@ __global__ void __launch_bounds__(EPI == 1 ? kThreads3 : kThreads2, 1)
                             if (last[u]) run = 0.f;
                         }
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) old[u] = last[u] ? sSig[tg[u]] : 0.f;
+                        for (int u = 0; u < 8; ++u) {
+                            if (EPI == 3) {  // sigma row in global memory (stays in L2); no dummy slots there
+                                last[u] = last[u] && tg[u] < (uint32_t)nsb;
+                                old[u] = last[u] ? sig[row * nsb + tg[u]] : 0.f;
+                            } else {
+                                old[u] = last[u] ? sSig[tg[u]] : 0.f;
+                            }
+                        }
 #pragma unroll
                         for (int u = 0; u < 8; ++u)
-                            if (last[u]) sSig[tg[u]] = old[u] + part[u];
+                            if (last[u]) {
+                                if (EPI == 3)
+                                    sig[row * nsb + tg[u]] = old[u] + part[u];
+                                else
+                                    sSig[tg[u]] = old[u] + part[u];
+                            }
                     }
                 }
                 asm volatile("bar.sync 1, 128;" ::: "memory");
@@ -585,7 +663,8 @@ __global__ void __launch_bounds__(EPI == 1 ? kThreads3 : kThreads2, 1)
         fence_after();
         T += ntiles;
         if (*s_fail) break;
-        for (int64_t j = tid; j < nsb; j += kThr) sig[row * nsb + j] += sSig[j];
+        if (EPI != 3 && EPI != 4)
+            for (int64_t j = tid; j < nsb; j += kThr) sig[row * nsb + j] += sSig[j];
         __syncthreads();
     }
     if (*s_fail && tid == 0) {
@@ -605,14 +684,14 @@ __global__ void __launch_bounds__(EPI == 1 ? kThreads3 : kThreads2, 1)
 static int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 // Epilogue and A buffers whose layout fits in `lim` bytes: the gather
-// epilogue (gcols = -3, needs the tile schedule), else the atomic epilogue
-// (gcols = -1), else staged columns (a multiple of 16) with atomics; two A
-// buffers preferred.
+// epilogue (gcols = -3, then -4 with the sigma row in global memory; both need
+// the tile schedule), else the atomic epilogue (gcols = -1), else staged
+// columns (a multiple of 16) with atomics; two A buffers preferred.
 static bool pick_layout(int nsplit, int kpad, int npad, int64_t nsb, int nsa_single, int lim, bool sched, int *gcols,
                         int *stages) {
-    static const int order[][2] = {{-3, 2}, {-3, 1}, {-1, 2}, {-1, 1}};  // {epilogue mode, A buffers}
+    static const int order[][2] = {{-3, 2}, {-3, 1}, {-4, 2}, {-4, 1}, {-1, 2}, {-1, 1}};  // {epilogue mode, A buffers}
     for (const auto &o : order)
-        if ((o[0] != -3 || sched) && (int)tc::make_layout(nsplit, kpad, npad, nsb, nsa_single, o[0], o[1]).total <= lim) {
+        if ((o[0] > -3 || sched) && (int)tc::make_layout(nsplit, kpad, npad, nsb, nsa_single, o[0], o[1]).total <= lim) {
             *gcols = o[0];
             *stages = o[1];
             return true;
@@ -657,9 +736,11 @@ static int tc_plan(const fci_ctx *ctx, int nsplit, TcPlan *P) {
     int gcols = 0, stages = 0;
     if (!pick_layout(nsplit, kpad, npad, ctx->B.ns, ctx->A.nsingle, lim, ctx->B.tsched != nullptr, &gcols, &stages))
         return fail(FCI_ERR_ARG, "tensor-core sigma_3: beta string count too large for shared memory");
-    const int epi = gcols == -1 ? 1 : gcols == -3 ? 2 : 0;
-    P->kern = nsplit == 2 ? (epi == 2 ? kernel_for<2, 2>(kpad) : epi == 1 ? kernel_for<2, 1>(kpad) : kernel_for<2, 0>(kpad))
-                          : (epi == 2 ? kernel_for<3, 2>(kpad) : epi == 1 ? kernel_for<3, 1>(kpad) : kernel_for<3, 0>(kpad));
+    const int epi = gcols == -1 ? 1 : gcols == -3 ? 2 : gcols == -4 ? 3 : 0;
+    P->kern = nsplit == 2 ? (epi == 3 ? kernel_for<2, 3>(kpad) : epi == 2 ? kernel_for<2, 2>(kpad)
+                             : epi == 1 ? kernel_for<2, 1>(kpad) : kernel_for<2, 0>(kpad))
+                          : (epi == 3 ? kernel_for<3, 3>(kpad) : epi == 2 ? kernel_for<3, 2>(kpad)
+                             : epi == 1 ? kernel_for<3, 1>(kpad) : kernel_for<3, 0>(kpad));
     P->npad = npad;
     P->lim = lim;
     P->gcols = gcols;
@@ -693,10 +774,51 @@ int launch_sigma3_tc(fci_ctx *ctx, const float *C, float *sig, int nsplit, cudaS
     FCI_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
     int64_t grid = nsm;  // one CTA per SM (launch bounds and shared memory)
     if (grid > ctx->A.ns) grid = ctx->A.ns;
-    void *args[] = {(void *)&C,     (void *)&sig,    (void *)&ctx->A,   (void *)&ctx->B,
+    const float *no_kf = nullptr;
+    void *args[] = {(void *)&C,      (void *)&sig,    (void *)&ctx->A,   (void *)&ctx->B,
                     (void *)&ctx->Wf, (void *)&ctx->npair, (void *)&P.npad, (void *)&P.gcols,
-                    (void *)&P.stages, (void *)&P.cols,  (void *)&ctx->d_err, (void *)&active};
+                    (void *)&P.stages, (void *)&P.cols,  (void *)&ctx->d_err, (void *)&active,
+                    (void *)&no_kf};
     FCI_CUDA(cudaLaunchKernel(P.kern, dim3((unsigned)grid), dim3(P.threads), args, P.smem, s));
+    return FCI_OK;
+}
+
+// Same-spin term (two-body through intermediate strings plus the one-body
+// part) of the strings R, on the tensor cores: sig[R.ns][cols.ns] += ...;
+// sigma_2 with (R, cols) = (alpha, beta) on C, sigma_1 with (beta, alpha) on
+// C transposed.  The adds are atomic.
+int launch_same_spin_tc(fci_ctx *ctx, const float *C, float *sig, const SpinTables &R, const SpinTables &cols,
+                        cudaStream_t s) {
+    const int nsplit = ctx->opt.f32_splits;
+    const int kpad = round_up(R.nsingle, 16), npad = round_up(ctx->npair + 1, 16);
+    if (npad > 256) return fail(FCI_ERR_ARG, "same-spin tensor-core sigma supports at most 255 orbital pairs");
+    if (kpad > 96) return fail(FCI_ERR_ARG, "same-spin tensor-core sigma supports at most 96 replacements per string");
+    int lim = 0, nsm = 0;
+    FCI_CUDA(cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+    FCI_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+    int gcols = -5, stages = 2;
+    uint32_t smem = tc::make_layout(nsplit, kpad, npad, cols.ns, R.nsingle, gcols, stages).total;
+    if ((int)smem > lim) {
+        stages = 1;
+        smem = tc::make_layout(nsplit, kpad, npad, cols.ns, R.nsingle, gcols, stages).total;
+    }
+    if ((int)smem > lim) return fail(FCI_ERR_ARG, "same-spin tensor-core sigma: operands exceed shared memory");
+    void *kern = nsplit == 2 ? kernel_for<2, 4>(kpad) : kernel_for<3, 4>(kpad);
+    uint32_t tcols = 32;
+    while (tcols < (uint32_t)(2 * npad)) tcols <<= 1;
+    if (tcols > 512) return fail(FCI_ERR_ARG, "same-spin tensor-core sigma: accumulators exceed tensor memory");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    FCI_CUDA(cudaStreamIsCapturing(s, &cap));
+    if (cap == cudaStreamCaptureStatusNone) FCI_CUDA(opt_in_max_smem(kern, ctx->device));
+    int64_t grid = nsm;
+    if (grid > R.ns) grid = R.ns;
+    const int *no_gate = nullptr;
+    SpinTables Rt = R, Ct = cols;
+    void *args[] = {(void *)&C,       (void *)&sig,        (void *)&Rt,      (void *)&Ct,
+                    (void *)&ctx->Wf, (void *)&ctx->npair, (void *)&npad,    (void *)&gcols,
+                    (void *)&stages,  (void *)&tcols,      (void *)&ctx->d_err, (void *)&no_gate,
+                    (void *)&ctx->kf};
+    FCI_CUDA(cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(tc::kThreads2), args, smem, s));
     return FCI_OK;
 }
 

@@ -391,6 +391,19 @@ int build_tables(fci_ctx *ctx, const double *h1_host, const double *eri_host) {
     k_pack_pairs<<<ceil_div((int64_t)ctx->npair * ctx->npair, 256), 256, 0, ctx->stream>>>(ctx->eri, n, ctx->npair,
                                                                                           ctx->W, ctx->Wf);
     FCI_CUDA(cudaGetLastError());
+    {  // one-body part of H written as sum k_kl E_kl + 1/2 sum (ij|kl) E_ij E_kl
+        std::vector<float> kh((size_t)ctx->npair);
+        for (int k = 0; k < n; ++k)
+            for (int l = 0; l <= k; ++l) {
+                double v = h1_host[k * n + l];
+                for (int j = 0; j < n; ++j) v -= 0.5 * eri_host[(((int64_t)k * n + j) * n + j) * n + l];
+                kh[pair_index(k, l)] = (float)v;
+            }
+        ctx->kf = (float *)dalloc(ctx, sizeof(float) * ctx->npair, &rc);
+        if (rc) return rc;
+        FCI_CUDA(cudaMemcpyAsync(ctx->kf, kh.data(), sizeof(float) * ctx->npair, cudaMemcpyHostToDevice, ctx->stream));
+        FCI_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
 
     if ((rc = build_spin(ctx, ctx->A, ctx->A.ne))) return rc;
     if (ctx->B.ne == ctx->A.ne) {
@@ -438,6 +451,10 @@ void free_tables(fci_ctx *ctx) {
     dfree(ctx, ctx->eri, sizeof(double) * (int64_t)n * n * n * n);
     dfree(ctx, ctx->W, sizeof(double) * ctx->npair * ctx->npair);
     dfree(ctx, ctx->Wf, sizeof(float) * ctx->npair * ctx->npair);
+    dfree(ctx, ctx->kf, sizeof(float) * ctx->npair);
+    dfree(ctx, ctx->ws32, sizeof(float) * 2 * ctx->ndet);
+    ctx->kf = nullptr;
+    ctx->ws32 = nullptr;
     dfree(ctx, ctx->hdiag, sizeof(double) * ctx->ndet);
     dfree(ctx, ctx->d_err, sizeof(int));
     ctx->d_err = nullptr;

@@ -58,6 +58,7 @@ class fci_options(ctypes.Structure):
         ("mixed_switch", ctypes.c_double),
         ("symmetry_tol", ctypes.c_double),
         ("f32_splits", ctypes.c_int),
+        ("same_spin_tc", ctypes.c_int),
     ]
 
 

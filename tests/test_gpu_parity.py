@@ -164,6 +164,24 @@ def test_sigma_fp32_tensor_core_splits(pkg, oracle_mod, norb, na, nb, splits, rt
         assert np.abs(got[rows] - ref).max() <= rtol * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("norb,na,nb", [(6, 3, 3), (8, 4, 4), (9, 5, 4), (10, 5, 5), (11, 3, 8), (12, 6, 6)])
+def test_sigma_fp32_same_spin_tensor_core(pkg, oracle_mod, norb, na, nb):
+    """sigma_1 and sigma_2 through intermediate strings on tcgen05 (forced on;
+    the default for large string spaces), n_alpha != n_beta included."""
+    ctx, h1, eri = make_ctx(pkg, norb, na, nb, rank=60, same_spin_tc=1)
+    N = ctx.ndet
+    c = fi.make_vector(N)
+    got = gpu_sigma(pkg, ctx, c, torch.float32)
+    c32 = c.astype(np.float32).astype(np.float64)
+    if N <= 100000:
+        ref = oracle_mod.sigma(norb, na, nb, h1, eri, c32)
+        assert np.abs(got - ref).max() <= 2e-6 * np.abs(ref).max()
+    else:
+        rows = np.unique(np.concatenate([[0, N - 1], np.random.default_rng(5).integers(0, N, 1500)]))
+        ref = oracle_mod.sigma_rows(norb, na, nb, h1, eri, c32, rows)
+        assert np.abs(got[rows] - ref).max() <= 2e-6 * np.abs(ref).max()
+
+
 def test_sigma_fp32_cas14_sampled(pkg, oracle_mod):
     """The benchmark workload in the FP32 launch configuration (split-BF16x6)."""
     ctx, h1, eri = make_ctx(pkg, 14, 7, 7, rank=100)
