@@ -23,7 +23,8 @@ workloads use but which are not available here):
   This is 8-fold symmetric and positive semidefinite as a pair matrix.
 * trial vector ``c``: i.i.d. ``N(0,1)``, normalised in FP64; or the uniform
   vector ``1/sqrt(N)`` that the paper uses for its single-iteration timings
-  (Section 5).
+  (Section 5); or, for spaces too large for host memory, the unnormalised
+  ``c_J = 2 u_J - 1`` that both sides regenerate per index.
 """
 from __future__ import annotations
 
@@ -42,6 +43,7 @@ STREAM_EPS = 2
 STREAM_L = 3
 STREAM_C = 4
 STREAM_SIZES = 5
+STREAM_C_PM1 = 6  # trial vectors too large for the host: c_J = 2 u_J - 1, regenerated per index
 
 DEFAULT_INTEGRAL_SEED = 1707
 DEFAULT_VECTOR_SEED = 4346
@@ -132,6 +134,15 @@ def make_vector(ndet: int, seed: int = DEFAULT_VECTOR_SEED, kind: str = "random"
     c = normals(seed, STREAM_C, ndet)
     nrm = np.linalg.norm(c)
     return c / nrm if nrm > 0 else c
+
+
+def vector_pm1(start: int, count: int, seed: int = DEFAULT_VECTOR_SEED) -> np.ndarray:
+    """Elements ``start .. start+count-1`` of the unnormalised trial vector
+    ``c_J = 2 u_J - 1`` (u from stream STREAM_C_PM1).  Integer mixing and an
+    exact conversion only, so a device implementation of the same definition
+    (``fci_inputs.gpu``) produces the same bits; used for spaces whose
+    vectors do not fit in host memory (CAS(18,18): 2.36e9 elements)."""
+    return 2.0 * uniforms(seed, STREAM_C_PM1, count, start=start) - 1.0
 
 
 def batched_sizes(ninst: int, seed: int = DEFAULT_INTEGRAL_SEED, choices=(6, 8, 10, 12)) -> list[int]:

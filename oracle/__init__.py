@@ -68,6 +68,9 @@ def _load():
             lib.oracle_sigma.argtypes = [i32, i32, i32, dp, dp, dp, dp]
             lib.oracle_sigma_rows.restype = i32
             lib.oracle_sigma_rows.argtypes = [i32, i32, i32, dp, dp, dp, dp, i64, dp]
+            u64 = ctypes.c_uint64
+            lib.oracle_sigma_rows_gen.restype = i32
+            lib.oracle_sigma_rows_gen.argtypes = [i32, i32, i32, dp, dp, u64, u64, dp, i64, dp]
             lib.oracle_hdiag.restype = i32
             lib.oracle_hdiag.argtypes = [i32, i32, i32, dp, dp, dp]
             lib.oracle_rdm1.restype = i32
@@ -162,6 +165,19 @@ def sigma_rows(norb: int, na: int, nb: int, h1, eri, c, rows) -> np.ndarray:
     return out
 
 
+def sigma_rows_generated(norb: int, na: int, nb: int, h1, eri, rows, seed: int, stream: int) -> np.ndarray:
+    """sigma(I) for chosen I with c_J = 2 u_J - 1 from the counter-based
+    generator (seed, stream), evaluated per index (no full vector)."""
+    h1, eri = _f64(h1), _f64(eri)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    out = np.zeros(len(rows))
+    rc = _load().oracle_sigma_rows_gen(norb, na, nb, _ptr(h1), _ptr(eri), ctypes.c_uint64(seed),
+                                       ctypes.c_uint64(stream), _ptr(rows), len(rows), _ptr(out))
+    if rc:
+        raise ValueError("bad space")
+    return out
+
+
 def hdiag(norb: int, na: int, nb: int, h1, eri) -> np.ndarray:
     h1, eri = _f64(h1), _f64(eri)
     out = np.zeros(ndet(norb, na, nb))
@@ -181,5 +197,5 @@ from .davidson import davidson  # noqa: E402  (pure NumPy, no library import)
 
 __all__ = [
     "build", "binom", "strings", "single_table", "ndet", "hamiltonian", "sigma",
-    "sigma_rows", "hdiag", "rdm1", "davidson", "num_threads",
+    "sigma_rows", "sigma_rows_generated", "hdiag", "rdm1", "davidson", "num_threads",
 ]

@@ -26,6 +26,7 @@
  *  oracle_h_slater       explicit H by the Slater-Condon rules (Eq. 6)
  *  oracle_h_operator     explicit H by applying Eq. 6 literally to bitstrings
  *  oracle_sigma_rows     sigma(I) = sum_J H_IJ c_J for chosen I (Eq. 4/5)
+ *  oracle_sigma_rows_gen the same with c_J = 2 u_J - 1 regenerated per index
  *  oracle_sigma          the same for every I (OpenMP over I)
  *  oracle_hdiag          H_II
  *  oracle_rdm1           spin-summed one-particle density <c|E_pq|c>
@@ -343,6 +344,66 @@ int oracle_sigma_rows(int norb, int na, int nb, const double *h, const double *e
     ham_t H = {norb, h, eri};
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t r = 0; r < nrows; ++r) out[r] = sigma_one(&S, &H, c, rows[r]);
+    space_free(&S);
+    return 0;
+}
+
+/* ---- Sampled rows with a regenerated trial vector --------------------------- *
+ * For spaces whose vectors do not fit in host memory, c_J = 2 u_J - 1 with
+ * u_J from the input module's counter-based SplitMix64 (Steele, Lea & Flood,
+ * OOPSLA 2014): u_J = top 53 bits of mix64(key + (J + 1) * GAMMA) * 2^-53,
+ * key = mix64(mix64(seed) ^ stream * 0xD1B54A32D192ED03).  Same direct sum as
+ * sigma_one, with c_J evaluated where it is needed.                        */
+static uint64_t sm_mix64(uint64_t z) {
+    z ^= z >> 30;
+    z *= 0xBF58476D1CE4E5B9ULL;
+    z ^= z >> 27;
+    z *= 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    return z;
+}
+
+static double gen_c(uint64_t key, int64_t J) {
+    uint64_t w = sm_mix64(key + (uint64_t)(J + 1) * 0x9E3779B97F4A7C15ULL);
+    return 2.0 * ((double)(w >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+}
+
+static double sigma_one_gen(const space_t *S, const ham_t *H, uint64_t key, int64_t I) {
+    int n = S->norb;
+    int n2 = 2 * n;
+    det_t dI = make_det(n, S->la[I / S->nsb], S->lb[I % S->nsb]);
+    double acc = sc_diag(H, dI) * gen_c(key, I);
+    int occ[64], vir[64], no = 0, nv = 0;
+    for (int p = 0; p < n2; ++p) {
+        if ((dI >> p) & 1ULL) occ[no++] = p; else vir[nv++] = p;
+    }
+    for (int x = 0; x < no; ++x)
+        for (int y = 0; y < nv; ++y) {
+            if (spin(H, occ[x]) != spin(H, vir[y])) continue;
+            det_t dJ = (dI & ~((det_t)1 << occ[x])) | ((det_t)1 << vir[y]);
+            acc += sc_element(H, dI, dJ) * gen_c(key, det_index(S, dJ));
+        }
+    for (int x1 = 0; x1 < no; ++x1)
+        for (int x2 = x1 + 1; x2 < no; ++x2)
+            for (int y1 = 0; y1 < nv; ++y1)
+                for (int y2 = y1 + 1; y2 < nv; ++y2) {
+                    det_t dJ = dI & ~((det_t)1 << occ[x1]) & ~((det_t)1 << occ[x2]);
+                    dJ |= ((det_t)1 << vir[y1]) | ((det_t)1 << vir[y2]);
+                    int64_t J = det_index(S, dJ);
+                    if (J < 0) continue;
+                    acc += sc_element(H, dI, dJ) * gen_c(key, J);
+                }
+    return acc;
+}
+
+int oracle_sigma_rows_gen(int norb, int na, int nb, const double *h, const double *eri, uint64_t seed,
+                          uint64_t stream, const int64_t *rows, int64_t nrows, double *out) {
+    space_t S;
+    if (space_init(&S, norb, na, nb)) return -1;
+    ham_t H = {norb, h, eri};
+    uint64_t key = sm_mix64(sm_mix64(seed) ^ (stream * 0xD1B54A32D192ED03ULL));
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t r = 0; r < nrows; ++r) out[r] = sigma_one_gen(&S, &H, key, rows[r]);
     space_free(&S);
     return 0;
 }

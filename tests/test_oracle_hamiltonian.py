@@ -219,3 +219,23 @@ def test_sigma_linear_and_transpose_symmetric(oracle_mod):
     # c^T sigma = <c|H|c> with H from the other construction
     H = oracle_mod.hamiltonian(n, ne, ne, h, eri, "operator")
     assert abs(a @ sa - a @ H @ a) < 1e-10 * abs(a @ sa)
+
+
+@pytest.mark.parametrize("norb,na,nb", [(8, 4, 4), (7, 4, 3)])
+def test_sigma_rows_generated_matches_full_vector(oracle_mod, norb, na, nb):
+    """The oracle's per-index generator (for spaces too large for host memory)
+    gives the same rows as the full vector from the input module."""
+    h1, eri = fi.make_integrals(norb, 40)
+    N = oracle_mod.ndet(norb, na, nb)
+    c = fi.vector_pm1(0, N)
+    rows = np.array([0, 1, N // 3, N // 2, N - 1])
+    a = oracle_mod.sigma_rows(norb, na, nb, h1, eri, c, rows)
+    b = oracle_mod.sigma_rows_generated(norb, na, nb, h1, eri, rows, fi.DEFAULT_VECTOR_SEED, fi.STREAM_C_PM1)
+    assert np.array_equal(a, b)
+
+
+def test_vector_pm1_counter_based():
+    """Any slice of the regenerated vector equals the same slice of a longer run."""
+    whole = fi.vector_pm1(0, 1000)
+    assert np.array_equal(fi.vector_pm1(400, 100), whole[400:500])
+    assert whole.min() >= -1.0 and whole.max() < 1.0
