@@ -21,6 +21,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -35,7 +36,9 @@ sys.path.insert(0, ROOT)
 
 import fci_inputs as fi  # noqa: E402
 
-WORKLOADS = {"cas14": (14, 7, 7, 100), "cas16": (16, 8, 8, 100), "cas12": (12, 6, 6, 100), "cas8": (8, 4, 4, 40)}
+WORKLOADS = {"cas14": (14, 7, 7, 100), "cas16": (16, 8, 8, 100), "cas12": (12, 6, 6, 100), "cas8": (8, 4, 4, 40),
+             "cas18": (18, 9, 9, 100)}
+LARGE = {"cas18"}  # FP32 sigma only (no FP64 kernels at this size); trial vector regenerated on the device
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), nominal
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
@@ -64,6 +67,21 @@ def ncu_traffic(kernel: str, workload: str):
         return nbytes if kernel_digest(path, marker) == digest else None
     except (OSError, ValueError):
         return None
+
+
+def metric_name(workload: str) -> str:
+    return "sigma=Hc throughput (FP32)" if workload in LARGE else "sigma=Hc throughput (FP64)"
+
+
+def workload_desc(workload: str) -> str:
+    """The workload string of the JSON line, the same for both arms."""
+    norb, na, nb, rank_eri = WORKLOADS[workload]
+    nsa, nsb = math.comb(norb, na), math.comb(norb, nb)
+    if workload in LARGE:
+        return (f"CAS({na + nb}e,{norb}o) Ms=0 FP32 sigma, {nsa * nsb} determinants ({nsa}x{nsb}), "
+                f"Cholesky-factored integrals rank {rank_eri}, c_J = 2u_J - 1 generated per index")
+    return (f"CAS({na + nb}e,{norb}o) Ms=0 sigma, {nsa * nsb} determinants ({nsa}x{nsb}), "
+            f"Cholesky-factored integrals rank {rank_eri}, seeds 1707/4346")
 
 
 def load_peaks():
@@ -162,21 +180,30 @@ def run_reference(args):
     import oracle
 
     N = oracle.ndet(norb, na, nb)
-    c = fi.make_vector(N)
     rng = np.random.default_rng(1)
-    rows_per_step = 2000
+    if args.workload in LARGE:  # the vector is regenerated per index (no 19 GB host copy)
+        rows_per_step = 64
+
+        def rows_sigma(rows):
+            return oracle.sigma_rows_generated(norb, na, nb, h1, eri, rows, fi.DEFAULT_VECTOR_SEED, fi.STREAM_C_PM1)
+    else:
+        rows_per_step = 2000
+        c = fi.make_vector(N)
+
+        def rows_sigma(rows):
+            return oracle.sigma_rows(norb, na, nb, h1, eri, c, rows)
     for _ in range(args.warmup):
-        oracle.sigma_rows(norb, na, nb, h1, eri, c, rng.integers(0, N, 256))
+        rows_sigma(rng.integers(0, N, 8))
     t = time.perf_counter()
     for _ in range(args.steps):
-        oracle.sigma_rows(norb, na, nb, h1, eri, c, rng.integers(0, N, rows_per_step))
+        rows_sigma(rng.integers(0, N, rows_per_step))
     dt = time.perf_counter() - t
     value = rows_per_step * args.steps / dt / 1e9
-    out = {"impl": "reference", "metric": "sigma=Hc throughput", "value": value, "unit": "Gdet/s",
+    out = {"impl": "reference", "metric": metric_name(args.workload), "value": value, "unit": "Gdet/s",
            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": f"CAS({na + nb}e,{norb}o) Ms=0 sigma, {N} determinants, Cholesky rank {rank_eri}",
-                      "step": f"{rows_per_step} sigma rows per step (bounded sample)"},
+           "config": {"workload": workload_desc(args.workload),
+                      "step": f"{rows_per_step} sigma rows per step (bounded sample, FP64 oracle)"},
            "cpu_baseline": {"value": value, "unit": "Gdet/s", "cores": oracle.num_threads(), "kind": "oracle",
                             "sample": f"{rows_per_step} random rows per step, {args.steps} steps"},
            "e2e": {"value": value, "unit": "Gdet/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -268,6 +295,99 @@ def run_batched(pkg, ninst, nroots=2, tol=1e-8):
         pkg.fci_batch_free(b)
     out["speedup_mixed_vs_sequential"] = out["sequential_fp64_s"] / out["batched_mixed_s"]
     return out
+
+
+def run_large(args):
+    """FP32 sigma of a space whose vectors do not fit in host memory
+    (CAS(18e,18o): 2.36e9 determinants, 9.4 GB per FP32 vector): the trial
+    vector c_J = 2 u_J - 1 is generated on the device from the input module's
+    counter-based generator; the CPU baseline is the oracle's direct sum on
+    sampled rows with c_J regenerated per index."""
+    import torch
+
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_1707_04346_gb300 as pkg
+    from fci_inputs import gpu as fgpu
+
+    norb, na, nb, rank_eri = WORKLOADS[args.workload]
+    h1, eri = fi.make_integrals(norb, rank_eri)
+    ctx = pkg.fci_init(norb, na, nb, h1, eri)
+    N = ctx.ndet
+    nsa, nsb = ctx.nstr
+    c = torch.empty(N, dtype=torch.float32, device=dev)
+    fgpu.fill_pm1(c)
+    s = torch.empty_like(c)
+    stream = torch.cuda.current_stream(dev)
+    pkg.fci_profile_enable(ctx, True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    t = time_sigma_ring(pkg, ctx, [c], [s], args.steps, args.warmup, stream, world)
+    clk = clocks.stop()
+    names, prof = pkg.fci_profile_read(ctx)
+    pkg.fci_profile_enable(ctx, False)
+    t = max_over_ranks(t, world)
+    kmean = prof[-args.steps:].mean(axis=0) / 1e3
+    value = world * N * args.steps / t / 1e9
+    sa = pkg.fci_query(ctx, 4)
+    kpad = -(-sa // 16) * 16
+    npad = -(-(norb * (norb + 1) // 2) // 16) * 16
+    nsplit = pkg.default_options().f32_splits
+    products = nsplit * (nsplit + 1) // 2
+    tiles = nsa * (-(-nsb // 128))
+    mma_flops = products * 2.0 * 128 * npad * kpad * tiles
+    itc = names.index("sigma3_tc")
+    peaks = load_peaks()
+    roof = {"kernel": "sigma3_tc", "bound": "tensor", "achieved": mma_flops / kmean[itc] / 1e12,
+            "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "frac": mma_flops / kmean[itc] / 1e12 / peaks["bf16_tflops"],
+            "traffic": None,
+            "work_per_launch": f"{mma_flops:.4g} bf16 MMA FLOP ({products} slice products x 2 x 128 x {npad} x "
+                               f"{kpad} x {tiles} tiles)",
+            "kernels": {n: {"ms": float(kmean[i] * 1e3), "share": float(kmean[i] / kmean.sum())}
+                        for i, n in enumerate(names)}}
+    # end to end: host vector in, host sigma out, every step (a few steps: 9.4 GB each way)
+    e2e_steps = min(args.steps, 3)
+    hc = c.cpu().pin_memory()
+    hs = torch.empty_like(hc).pin_memory()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        c.copy_(hc, non_blocking=True)
+        pkg.fci_sigma(ctx, c, s, stream=stream)
+        hs.copy_(s, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e = world * N * e2e_steps / (e0.elapsed_time(e1) / 1e3) / 1e9
+    result = {
+        "metric": metric_name(args.workload), "value": value, "unit": "Gdet/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_desc(args.workload),
+                   "l2": f"one input vector of {N * 4 / 1e9:.1f} GB > 129 MB L2", "parallelism": "single GPU"},
+        "roofline": roof, "clocks": clk, "gpu_launches": int(args.steps * 5),  # sigma_2, transpose, sigma_1, transpose-add, sigma_3
+        "e2e": {"value": e2e, "unit": "Gdet/s", "h2d_bytes_per_step": N * 4, "d2h_bytes_per_step": N * 4},
+    }
+    if args.cpu_baseline and rank == 0 and world == 1:
+        import oracle
+
+        rng = np.random.default_rng(7)
+        rows = rng.integers(0, N, 64)
+        oracle.sigma_rows_generated(norb, na, nb, h1, eri, rows[:4], fi.DEFAULT_VECTOR_SEED, fi.STREAM_C_PM1)
+        t0 = time.perf_counter()
+        nrows = 0
+        while time.perf_counter() - t0 < args.cpu_seconds:
+            oracle.sigma_rows_generated(norb, na, nb, h1, eri, rows, fi.DEFAULT_VECTOR_SEED, fi.STREAM_C_PM1)
+            nrows += len(rows)
+        dt = time.perf_counter() - t0
+        result["cpu_baseline"] = {"value": nrows / dt / 1e9, "unit": "Gdet/s", "cores": oracle.num_threads(),
+                                  "kind": "oracle", "sample": f"{nrows} sampled sigma rows of CAS({na + nb}e,{norb}o), "
+                                                              f"direct Slater-Condon sum, FP64, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(result))
+    pkg.fci_free(ctx)
+    return 0
 
 
 def run_ours(args):
@@ -380,11 +500,10 @@ def run_ours(args):
     result = None
     if rank == 0:
         result = {
-            "metric": "sigma=Hc throughput (FP64)", "value": value, "unit": "Gdet/s", "n_gpus": world,
+            "metric": metric_name(args.workload), "value": value, "unit": "Gdet/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"CAS({na + nb}e,{norb}o) Ms=0 sigma, {N} determinants ({nsa}x{nsb}), "
-                                   f"Cholesky-factored integrals rank {rank_eri}, seeds 1707/4346",
+            "config": {"workload": workload_desc(args.workload),
                        "l2": f"input/output ring of {ring} vectors x {N * 8 / 1e6:.0f} MB > 129 MB L2",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roof, "clocks": clk, "gpu_launches": len(names) * args.steps, "e2e": e2e,
@@ -432,6 +551,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload in LARGE:
+        return run_large(args)
     return run_ours(args)
 
 
