@@ -30,7 +30,11 @@
 // v, S <- S + (sigma64(x) - S v) v^T, together with the projected matrix; the
 // Ritz values are then exact Rayleigh quotients and the residuals exact.
 // Convergence is tested only at those points, which the iteration log marks
-// with precision 0.
+// with precision 0.  When a refinement point finds the FP32 sigma error along a
+// Ritz vector above sqrt(tol)/2 and the residual has stopped halving between
+// exact points (the FP32 phase cannot reach the required residual), the
+// subspace collapses onto the Ritz vectors with fresh FP64 sigma and the
+// remaining corrections get FP64 sigma.
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -624,6 +628,14 @@ int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *v
     int it = 0, inner = 0;
     double r_win = INFINITY;
     std::vector<double> r_hist;
+    // FP64 tail: a refinement point measures the FP32 sigma error along each
+    // Ritz vector (||sigma64(x) - S v||).  When that error exceeds sqrt(tol)/2
+    // and the residual at an exact point is not below half of the previous
+    // exact point's, the FP32 phase has stopped making progress: the subspace
+    // collapses onto the Ritz vectors (with fresh FP64 sigma) and every later
+    // correction gets an FP64 sigma
+    bool fp64_tail = false, want_tail = false;
+    double r_exact_prev = INFINITY;
 
     for (it = 1; it <= ctx->opt.max_iter; ++it) {
         // (4) diagonalise the projected matrix
@@ -668,6 +680,20 @@ int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *v
             }
             for (int k = 0; k < nr; ++k) e_prev[k] = ev[k];
             inner = 0;
+            if (mixed && !fp64_tail) {
+                if (want_tail && rmax > 0.5 * r_exact_prev && nr == nroots) {
+                    // collapse onto the Ritz vectors with fresh FP64 sigma
+                    FCI_CUDA(cudaMemcpyAsync(W.Bv, W.X, sizeof(double) * nr * n, cudaMemcpyDeviceToDevice, s));
+                    for (int k = 0; k < nr; ++k)
+                        if (int rc = sigma_of(W, false, W.Bv + (size_t)k * n, W.Sv + (size_t)k * n)) return rc;
+                    m = nr;
+                    FCI_CUDA(cudaMemsetAsync(W.A, 0, sizeof(double) * kMaxSub * kMaxSub, s));
+                    for (int j = 0; j < m; ++j)
+                        if (int rc = dots(W, W.Bv, m, W.Sv + (size_t)j * n, W.A + j, kMaxSub)) return rc;
+                    fp64_tail = true;
+                }
+                r_exact_prev = rmax;
+            }
         } else if (++inner >= 60 || rmax < std::sqrt(tol) || (inner >= 15 && rmax > 0.5 * r_win)) {
             // refinement: exact FP64 sigma of each Ritz vector; the difference to
             // the subspace estimate corrects every sigma vector along that Ritz
@@ -676,10 +702,18 @@ int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *v
                 double *d = W.T + (size_t)k * n;
                 if (int rc = sigma_of(W, false, W.X + (size_t)k * n, d)) return rc;
                 k_sub<<<grid_for(n), 256, 0, s>>>(d, W.HX + (size_t)k * n, d, n);
+                if (int rc = dots(W, d, 1, d, W.scal + 48 + k, 1)) return rc;  // ||sigma error||^2
                 if (int rc = dots(W, W.Bv, m, d, W.scal, 1)) return rc;
                 k_rank1_sigma<<<grid_for(n), 256, 0, s>>>(W.Sv, m, W.V, k, d, n);
                 k_rank1_proj<<<1, 256, 0, s>>>(W.A, kMaxSub, m, W.scal, W.V, k);
                 FCI_CUDA(cudaGetLastError());
+            }
+            {
+                std::vector<double> err2(nr);
+                FCI_CUDA(cudaMemcpyAsync(err2.data(), W.scal + 48, sizeof(double) * nr, cudaMemcpyDeviceToHost, s));
+                FCI_CUDA(cudaStreamSynchronize(s));
+                for (int k = 0; k < nr; ++k)
+                    if (std::sqrt(err2[k]) > 0.5 * std::sqrt(tol)) want_tail = true;
             }
             exact = true;
             continue;
@@ -695,7 +729,7 @@ int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *v
             FCI_CUDA(cudaGetLastError());
             FCI_CUDA(cudaMemcpyAsync(W.Bv, W.X, sizeof(double) * keep * n, cudaMemcpyDeviceToDevice, s));
             FCI_CUDA(cudaMemcpyAsync(W.Sv, W.HX, sizeof(double) * keep * n, cudaMemcpyDeviceToDevice, s));
-            if (mixed && keep > nr) exact = false;  // the extra vectors carry FP32 sigma
+            if (mixed && !fp64_tail && keep > nr) exact = false;  // the extra vectors carry FP32 sigma
             m = keep;
             FCI_CUDA(cudaMemsetAsync(W.A, 0, sizeof(double) * kMaxSub * kMaxSub, s));
             for (int j = 0; j < m; ++j)
@@ -709,7 +743,7 @@ int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *v
             if (int rc = orthonormalise(W, W.Bv, m, b, &kept)) return rc;
             if (!kept) continue;
             // (4) new sigma (FP32 in mixed mode), new row/column of the projected matrix
-            if (int rc = sigma_of(W, mixed, b, W.Sv + (size_t)m * n)) return rc;
+            if (int rc = sigma_of(W, mixed && !fp64_tail, b, W.Sv + (size_t)m * n)) return rc;
             ++m;
             if (int rc = dots(W, W.Bv, m, W.Sv + (size_t)(m - 1) * n, W.A + (m - 1), kMaxSub)) return rc;
             if (int rc = dots(W, W.Sv, m, W.Bv + (size_t)(m - 1) * n, W.A + (size_t)(m - 1) * kMaxSub, 1)) return rc;
@@ -723,7 +757,7 @@ int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *v
             converged = rmax < std::sqrt(tol);
             break;
         }
-        if (mixed) exact = false;
+        if (mixed && !fp64_tail) exact = false;
     }
     ctx->iterations = it > ctx->opt.max_iter ? ctx->opt.max_iter : it;
     for (int k = 0; k < nroots; ++k) energies[k] = ev[k];

@@ -111,3 +111,21 @@ def test_rdm1_of_eigenvector(pkg, oracle_mod):
     assert dx < 1e-4
     assert np.abs(g - oracle_mod.rdm1(norb, na, nb, y)).max() <= 4 * dx + 1e-12
     pkg.fci_free(ctx)
+
+
+def test_mixed_davidson_fp64_tail(pkg):
+    """With split-BF16x3 sigma (about 1e-5 relative error) and tol 1e-12 the
+    FP32 error floor lies far above sqrt(tol): the solver must notice that its
+    refinement points stop reducing the residual, switch to FP64 sigma and
+    still reach the FP64 energies."""
+    h1, eri = fi.make_integrals(10, 60)
+    ref_ctx = pkg.fci_init(10, 5, 5, h1, eri)
+    ref = pkg.fci_davidson(ref_ctx, 2, 1e-12)
+    ctx = pkg.fci_init(10, 5, 5, h1, eri, pkg.default_options(precision=pkg.FCI_PREC_MIXED, f32_splits=2,
+                                                               max_iter=400))
+    e = pkg.fci_davidson(ctx, 2, 1e-12)
+    assert np.abs(e - ref).max() < 1e-10
+    log = pkg.fci_davidson_log(ctx, 2)
+    assert (log[:, 1] == 1).sum() > 0 and log[-1, 1] == 0  # FP32 phase first, exact at the end
+    pkg.fci_free(ctx)
+    pkg.fci_free(ref_ctx)
