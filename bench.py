@@ -47,7 +47,7 @@ FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), nominal
 # only while that source is unchanged.
 NCU_TRAFFIC = {
     "sigma3_exact": ("paper_1707_04346_gb300/csrc/sigma.cu", "k_sigma3_exact(", "d3fba1cadf6cd31c", 610262016.0),
-    "sigma3_tc": ("paper_1707_04346_gb300/csrc/sigma_tc_kernel.cuh", "k_sigma3_tc(", "396417047e53d47b", 126671616.0),
+    "sigma3_tc": ("paper_1707_04346_gb300/csrc/sigma_tc_kernel.cuh", "k_sigma3_tc(", "878aabf229629b81", 124323328.0),
 }
 
 
