@@ -120,9 +120,19 @@ int fci_free(fci_ctx *ctx);
  *            sigma_1/sigma_2 in FP32, sigma_3 on the tensor cores with bf16
  *            slices of the FP32 operands and FP32 accumulation (see
  *            fci_options.f32_splits); the low-precision phase of the mixed
- *            Davidson.
- *  stream    cudaStream_t or NULL.  Asynchronous.
- * Errors: FCI_ERR_ARG, FCI_ERR_CUDA (launch failure).
+ *            Davidson.  For large string spaces (or with
+ *            fci_options.same_spin_tc = 1) sigma_1/sigma_2 also run on the
+ *            tensor cores, through intermediate strings (Eq. 7 operators
+ *            E_ij E_kl); their adds are atomic, so FP32 results may differ in
+ *            the last bits between calls.  FCI_F32 needs the replacement lists
+ *            of both spins to have at most 96 entries (norb 18 at half
+ *            filling) and at most 65408 strings per spin; FCI_F64 needs one
+ *            beta row of C and sigma (2 N_beta doubles) in shared memory
+ *            (N_beta <= about 14000, CAS(16,16)).
+ *  stream    cudaStream_t or NULL.  Asynchronous.  The large-space FP32 path
+ *            allocates a 2N-float workspace on its first use.
+ * Errors: FCI_ERR_ARG (including the size limits above, reported on the host
+ * before any launch), FCI_ERR_OOM, FCI_ERR_CUDA (launch failure).
  */
 int fci_sigma(fci_ctx *ctx, const void *c, void *sigma, int dtype, void *stream);
 

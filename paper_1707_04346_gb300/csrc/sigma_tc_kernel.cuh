@@ -139,40 +139,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t addr, uint32_t parity
     return false;
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&r)[16]) {
-    uint32_t u[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
-          "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) r[i] = __uint_as_float(u[i]);
-}
-
-// Split 8 floats into NS bf16 slices and store each slice's 16 bytes.
-template <int NS>
-__device__ __forceinline__ void store_split8(const float (&v)[8], unsigned char *base, uint32_t slice_bytes,
-                                             uint32_t off) {
-    float rem[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) rem[i] = v[i];
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-        uint32_t w[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            __nv_bfloat16 lo = __float2bfloat16_rn(rem[2 * i]);
-            __nv_bfloat16 hi = __float2bfloat16_rn(rem[2 * i + 1]);
-            rem[2 * i] -= __bfloat162float(lo);
-            rem[2 * i + 1] -= __bfloat162float(hi);
-            w[i] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-        }
-        *reinterpret_cast<uint4 *>(base + s * slice_bytes + off) = make_uint4(w[0], w[1], w[2], w[3]);
-    }
-}
-
 // Packed-conversion split: 8 floats -> NS bf16 slices (round to nearest), the
 // remainder carried to the next slice.
 template <int NS>

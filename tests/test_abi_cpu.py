@@ -121,10 +121,20 @@ def test_option_validation_on_host(lib):
     import fci_inputs as fi
 
     h1, eri = fi.make_integrals(4, 10)
-    for field, bad in (("f32_splits", 4), ("precision", 7), ("max_subspace", 1), ("max_iter", 0)):
+    for field, bad in (("f32_splits", 4), ("precision", 7), ("max_subspace", 1), ("max_iter", 0),
+                       ("same_spin_tc", 2)):
         o = fci.default_options()
         setattr(o, field, bad)
         assert _init(lib, 4, 2, 2, h1, eri, o)[0] == fci.FCI_ERR_ARG, field
+
+
+def test_default_options_match_header(lib):
+    """The binding's struct has the header's layout (struct_size filled by the library)."""
+    from paper_1707_04346_gb300 import fci
+
+    o = fci.default_options()
+    assert o.struct_size == ctypes.sizeof(fci.fci_options)
+    assert (o.max_subspace, o.max_iter, o.f32_splits, o.same_spin_tc) == (24, 300, 3, 0)
 
 
 def test_batch_rejects_bad_instances_on_host(lib):
