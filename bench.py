@@ -473,6 +473,19 @@ def run_ours(args):
                                   f"{kpad} x {tiles} tiles)",
                "kernels": {n: {"ms": float(k32[i] * 1e3)} for i, n in enumerate(names32)}}
 
+    # split-BF16x3 sigma_3 (2 bf16 slices, 3 products; about 1e-5 relative)
+    ctx3 = pkg.fci_init(norb, na, nb, h1, eri, pkg.default_options(f32_splits=2))
+    v32 = [v.float() for v in vecs]
+    o32 = [torch.empty_like(v) for v in v32]
+    pkg.fci_profile_enable(ctx3, True)
+    t3 = time_sigma_ring(pkg, ctx3, v32, o32, args.steps, args.warmup, stream, world)
+    names3, prof3 = pkg.fci_profile_read(ctx3)
+    t3 = max_over_ranks(t3, world)
+    bf16x3 = {"value": world * N * args.steps / t3 / 1e9, "unit": "Gdet/s",
+              "kernels": {n: {"ms": float(prof3[-args.steps:, i].mean())} for i, n in enumerate(names3)}}
+    del v32, o32
+    pkg.fci_free(ctx3)
+
     # end to end through the C ABI with host buffers
     hc = torch.from_numpy(c_host).pin_memory()
     hs = torch.empty(N, dtype=torch.float64).pin_memory()
@@ -509,6 +522,7 @@ def run_ours(args):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roof, "clocks": clk, "gpu_launches": len(names) * args.steps, "e2e": e2e,
             "fp32_sigma": {"value": fp32_value, "unit": "Gdet/s", "roofline": roof_tc},
+            "bf16x3_sigma": bf16x3,
         }
     if args.davidson and rank == 0:
         import torch as _t
