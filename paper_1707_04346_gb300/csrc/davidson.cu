@@ -9,7 +9,8 @@
 // as block Davidson-Liu with
 //   t_k = -(H_diag - E_k)^{-1} r_k,  r_k = H x_k - E_k x_k,
 // denominators with |H_II - E| < 1e-8 replaced by +-1e-8, classical
-// Gram-Schmidt applied twice, corrections with norm < 1e-10 dropped,
+// Gram-Schmidt (a second pass when the first removed more than half of the
+// squared norm), corrections with norm < 1e-10 dropped,
 // convergence when every root has |dE| < tol and ||r|| < sqrt(tol), unit
 // vectors on the lowest diagonal elements as the guess (ties: lower index),
 // and a thick restart when the subspace is full: collapse onto the lowest
@@ -529,17 +530,26 @@ int orthonormalise(Work &W, const double *X, int m, double *y, int *kept) {
     if (m > 0) {
         const bool v2 = vec2(W.n, X, y);
         const unsigned grid = v2 ? grid_for(W.n / 2) : grid_for(W.n);
+        // classical Gram-Schmidt, repeated only when the first pass removed more
+        // than half of ||y||^2 (DGKS criterion, ||y1|| < ||y0||/sqrt(2)); against
+        // an orthonormal basis ||y0||^2 = ||y1||^2 + sum_i c_i^2
         for (int pass = 0; pass < 2; ++pass) {
             if (int rc = dots(W, X, m, y, W.scal, 1)) return rc;
             if (v2)
                 k_sub_proj<2><<<grid, 256, 0, W.s>>>(X, m, W.scal, y, W.n, W.partial);
             else
                 k_sub_proj<1><<<grid, 256, 0, W.s>>>(X, m, W.scal, y, W.n, W.partial);
+            k_reduce_partials<1><<<1, 32, 0, W.s>>>(W.partial, (int)grid, 1, W.scal + 40, 1);
             FCI_CUDA(cudaGetLastError());
+            if (pass == 0) {
+                double h[41];
+                FCI_CUDA(cudaMemcpyAsync(h, W.scal, sizeof(double) * 41, cudaMemcpyDeviceToHost, W.s));
+                FCI_CUDA(cudaStreamSynchronize(W.s));
+                double c2 = 0.0;
+                for (int i = 0; i < m; ++i) c2 += h[i] * h[i];
+                if (h[40] >= c2) break;  // ||y1||^2 >= ||y0||^2 / 2: one pass suffices
+            }
         }
-        // squared norm from the second pass
-        k_reduce_partials<1><<<1, 32, 0, W.s>>>(W.partial, (int)grid, 1, W.scal + 40, 1);
-        FCI_CUDA(cudaGetLastError());
     } else if (int rc = dots(W, y, 1, y, W.scal + 40, 1)) {
         return rc;
     }
