@@ -47,37 +47,41 @@ def build(force: bool = False) -> str:
     return _SO
 
 
+def _bind(lib):
+    """Declare the argument and result types of the oracle's C entry points."""
+    i64, i32, dp = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
+    u64 = ctypes.c_uint64
+    lib.oracle_binom.restype = i64
+    lib.oracle_binom.argtypes = [i32, i32]
+    lib.oracle_strings.restype = i64
+    lib.oracle_strings.argtypes = [i32, i32, dp]
+    lib.oracle_single_table.restype = i32
+    lib.oracle_single_table.argtypes = [i32, i32, dp, dp, dp, dp]
+    for name in ("oracle_h_slater", "oracle_h_operator"):
+        f = getattr(lib, name)
+        f.restype = i32
+        f.argtypes = [i32, i32, i32, dp, dp, dp]
+    lib.oracle_sigma.restype = i32
+    lib.oracle_sigma.argtypes = [i32, i32, i32, dp, dp, dp, dp]
+    lib.oracle_sigma_rows.restype = i32
+    lib.oracle_sigma_rows.argtypes = [i32, i32, i32, dp, dp, dp, dp, i64, dp]
+    lib.oracle_sigma_rows_gen.restype = i32
+    lib.oracle_sigma_rows_gen.argtypes = [i32, i32, i32, dp, dp, u64, u64, dp, i64, dp]
+    lib.oracle_hdiag.restype = i32
+    lib.oracle_hdiag.argtypes = [i32, i32, i32, dp, dp, dp]
+    lib.oracle_rdm1.restype = i32
+    lib.oracle_rdm1.argtypes = [i32, i32, i32, dp, dp]
+    lib.oracle_num_threads.restype = i32
+    lib.oracle_num_threads.argtypes = []
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
             build()
-            lib = ctypes.CDLL(_SO)
-            i64, i32, dp = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
-            lib.oracle_binom.restype = i64
-            lib.oracle_binom.argtypes = [i32, i32]
-            lib.oracle_strings.restype = i64
-            lib.oracle_strings.argtypes = [i32, i32, dp]
-            lib.oracle_single_table.restype = i32
-            lib.oracle_single_table.argtypes = [i32, i32, dp, dp, dp, dp]
-            for name in ("oracle_h_slater", "oracle_h_operator"):
-                f = getattr(lib, name)
-                f.restype = i32
-                f.argtypes = [i32, i32, i32, dp, dp, dp]
-            lib.oracle_sigma.restype = i32
-            lib.oracle_sigma.argtypes = [i32, i32, i32, dp, dp, dp, dp]
-            lib.oracle_sigma_rows.restype = i32
-            lib.oracle_sigma_rows.argtypes = [i32, i32, i32, dp, dp, dp, dp, i64, dp]
-            u64 = ctypes.c_uint64
-            lib.oracle_sigma_rows_gen.restype = i32
-            lib.oracle_sigma_rows_gen.argtypes = [i32, i32, i32, dp, dp, u64, u64, dp, i64, dp]
-            lib.oracle_hdiag.restype = i32
-            lib.oracle_hdiag.argtypes = [i32, i32, i32, dp, dp, dp]
-            lib.oracle_rdm1.restype = i32
-            lib.oracle_rdm1.argtypes = [i32, i32, i32, dp, dp]
-            lib.oracle_num_threads.restype = i32
-            lib.oracle_num_threads.argtypes = []
-            _lib = lib
+            _lib = _bind(ctypes.CDLL(_SO))
     return _lib
 
 
