@@ -56,6 +56,13 @@ def test_cas18_fp32_sigma_sampled(pkg, oracle_mod):
     # FP32: the input rounding (2^-24 relative) and FP32 accumulation of about 1e4
     # terms per element (sqrt(1e4) * 2^-24 relative to the largest term) stay below 1e-5
     assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
+    # split-BF16x3 (2 bf16 slices): about 1e-5 relative per product on top
+    ctx3 = pkg.fci_init(norb, ne, ne, h1, eri, pkg.default_options(f32_splits=2))
+    pkg.fci_sigma(ctx3, c, s)
+    torch.cuda.synchronize()
+    got3 = s[torch.from_numpy(rows).to(DEV)].double().cpu().numpy()
+    pkg.fci_free(ctx3)
+    assert np.abs(got3 - ref).max() <= 1e-4 * np.abs(ref).max()
     del c, s
     # the FP64 path has no kernels for a space this large: a host-side error, no launch
     c64 = torch.zeros(N, dtype=torch.float64, device=DEV)
