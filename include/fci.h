@@ -216,6 +216,33 @@ int fci_get_strings(fci_ctx *ctx, int spin, uint32_t *out);
 int fci_get_single_table(fci_ctx *ctx, int spin, int32_t *tgt, int8_t *k, int8_t *l, int8_t *sign);
 
 /*
+ * Host only, no CUDA call: the tile schedule that the tensor-core sigma_3
+ * epilogue uses for the beta-side scatter of Eq. 8 (sigma_3(I_a, I_b) gets
+ * sign * G(J_b) for every I_b = E_kl J_b), built by the routine fci_init runs
+ * on the beta table, from a single-replacement table in host memory.
+ *  ns, nsingle  strings and entries per string (1 <= ns <= 65408)
+ *  npair        number of packed orbital pairs (1..256); pair index of (k, l)
+ *               is max*(max+1)/2 + min
+ *  tgt, pair, sign  row-major [ns][nsingle] (tgt in [0, ns), pair in
+ *               [0, npair), sign +1 or -1), the layout fci_get_single_table
+ *               returns; entry order within a row does not matter
+ *  sched, cap   output records, uint32: target | (source string - 128 t) << 16
+ *               | pair << 23 | (sign < 0) << 31.  Strings form tiles of 128
+ *               (t = x / 128); each tile's entries are grouped by target and
+ *               every target's entries go whole to one of 128 shares, so no
+ *               two shares of a tile write the same target; entry j of share k
+ *               of tile t is sched[toff[t] + 128 j + k], and shorter shares
+ *               are padded with the dummy target ns + k.  Written only when
+ *               sched != NULL and cap >= *nsched.
+ *  nsched       out: schedule length (call once with sched = NULL to size it)
+ *  toff         out (nullable): [ceil(ns/128) + 1] offsets of the tiles
+ * Returns FCI_ERR_ARG for NULL inputs, sizes out of range or an entry out of
+ * range; nothing is written then.
+ */
+int fci_tile_schedule(int64_t ns, int nsingle, int npair, const int32_t *tgt, const int32_t *pair,
+                      const int8_t *sign, uint32_t *sched, int64_t cap, int64_t *nsched, int32_t *toff);
+
+/*
  * Per-kernel timing (tracing).  While enabled, every fci_sigma call records
  * CUDA events on the caller's stream around each kernel it launches (no
  * synchronisation; the events go into a ring of 1024 records).

@@ -239,6 +239,32 @@ int fci_get_single_table(fci_ctx *ctx, int spin, int32_t *tgt, int8_t *k, int8_t
     return unpack_table(ctx, spin, tgt, k, l, sign);
 }
 
+int fci_tile_schedule(int64_t ns, int nsingle, int npair, const int32_t *tgt, const int32_t *pair,
+                      const int8_t *sign, uint32_t *sched, int64_t cap, int64_t *nsched, int32_t *toff) {
+    if (!tgt || !pair || !sign || !nsched) return fail(FCI_ERR_ARG, "fci_tile_schedule: NULL table or nsched");
+    if (ns < 1 || ns > fci::kMaxScheduleStrings)
+        return fail(FCI_ERR_ARG, "fci_tile_schedule: ns must be in [1, 65408]");
+    if (nsingle < 1 || npair < 1 || npair > 256)
+        return fail(FCI_ERR_ARG, "fci_tile_schedule: nsingle >= 1 and 1 <= npair <= 256 required");
+    // packed entry-major copy, the layout fci_init builds on the device
+    std::vector<uint32_t> tab((size_t)ns * nsingle);
+    for (int64_t x = 0; x < ns; ++x)
+        for (int e = 0; e < nsingle; ++e) {
+            const size_t i = (size_t)x * nsingle + e;
+            if (tgt[i] < 0 || tgt[i] >= ns || pair[i] < 0 || pair[i] >= npair || (sign[i] != 1 && sign[i] != -1))
+                return fail(FCI_ERR_ARG, "fci_tile_schedule: table entry out of range");
+            tab[(size_t)e * ns + x] = (uint32_t)tgt[i] | ((uint32_t)pair[i] << fci::kPairShift) |
+                                      (sign[i] < 0 ? 0x80000000u : 0u);
+        }
+    std::vector<uint32_t> out;
+    std::vector<int32_t> off;
+    fci::tile_schedule_host(tab.data(), ns, nsingle, out, off);
+    *nsched = (int64_t)out.size();
+    if (toff) std::memcpy(toff, off.data(), sizeof(int32_t) * off.size());
+    if (sched && cap >= (int64_t)out.size()) std::memcpy(sched, out.data(), sizeof(uint32_t) * out.size());
+    return FCI_OK;
+}
+
 int fci_profile_enable(fci_ctx *ctx, int on) {
     if (!ctx) return fail(FCI_ERR_ARG, "ctx is NULL");
     FCI_CUDA(cudaSetDevice(ctx->device));

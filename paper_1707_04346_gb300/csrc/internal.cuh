@@ -43,6 +43,7 @@ __host__ __device__ inline int pair_index(int k, int l) {
 }
 
 constexpr int kTileStrings = 128;  // beta strings per tensor-core tile (the MMA's M)
+constexpr int64_t kMaxScheduleStrings = 65536 - kTileStrings;  // targets and dummies fit 16 bits
 
 // ---- per-spin string data on the device ------------------------------------
 struct SpinTables {
@@ -121,6 +122,9 @@ void dfree(fci_ctx *ctx, void *p, size_t bytes);
 // tables.cu
 int build_tables(fci_ctx *ctx, const double *h1_host, const double *eri_host);
 void free_tables(fci_ctx *ctx);
+// tile schedule of a packed entry-major table tab[e * ns + x] (host only; see SpinTables::tsched)
+void tile_schedule_host(const uint32_t *tab, int64_t ns, int K, std::vector<uint32_t> &out,
+                        std::vector<int32_t> &off);
 
 // sigma.cu
 int launch_sigma(fci_ctx *ctx, const void *c, void *sigma, int dtype, cudaStream_t s);

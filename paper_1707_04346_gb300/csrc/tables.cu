@@ -258,16 +258,12 @@ static int64_t host_binom(int n, int k) {
 
 // Tile schedule for the gather epilogue of the tensor-core sigma_3 (see
 // SpinTables::tsched): built on the host from the entry-major table.
-static int build_tile_schedule(fci_ctx *ctx, SpinTables &T) {
-    if (T.nsingle == 0 || T.ns > 65536 - kTileStrings || ctx->npair > 256) return FCI_OK;
-    const int64_t ns = T.ns;
-    const int K = T.nsingle, R = kTileStrings;
-    std::vector<uint32_t> tab((size_t)ns * K);
-    FCI_CUDA(cudaMemcpyAsync(tab.data(), T.tab, sizeof(uint32_t) * tab.size(), cudaMemcpyDeviceToHost, ctx->stream));
-    FCI_CUDA(cudaStreamSynchronize(ctx->stream));
+void tile_schedule_host(const uint32_t *tab, int64_t ns, int K, std::vector<uint32_t> &out,
+                        std::vector<int32_t> &off) {
+    const int R = kTileStrings;
     const int64_t ntiles = (ns + R - 1) / R;
-    std::vector<uint32_t> out;
-    std::vector<int32_t> off((size_t)ntiles + 1);
+    out.clear();
+    off.assign((size_t)ntiles + 1, 0);
     std::vector<std::pair<uint64_t, uint32_t>> keyed;
     keyed.reserve((size_t)R * K);
     size_t pos = 0;
@@ -323,6 +319,16 @@ static int build_tile_schedule(fci_ctx *ctx, SpinTables &T) {
         pos += kmax * R;
     }
     off[ntiles] = (int32_t)pos;
+}
+
+static int build_tile_schedule(fci_ctx *ctx, SpinTables &T) {
+    if (T.nsingle == 0 || T.ns > kMaxScheduleStrings || ctx->npair > 256) return FCI_OK;
+    std::vector<uint32_t> tab((size_t)T.ns * T.nsingle);
+    FCI_CUDA(cudaMemcpyAsync(tab.data(), T.tab, sizeof(uint32_t) * tab.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    FCI_CUDA(cudaStreamSynchronize(ctx->stream));
+    std::vector<uint32_t> out;
+    std::vector<int32_t> off;
+    tile_schedule_host(tab.data(), T.ns, T.nsingle, out, off);
     int rc = FCI_OK;
     T.nsched = (int64_t)out.size();
     T.tsched = (uint32_t *)dalloc(ctx, sizeof(uint32_t) * out.size(), &rc);

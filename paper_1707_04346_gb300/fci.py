@@ -28,7 +28,7 @@ EXPORTED = [
     "fci_davidson_log", "fci_rdm1", "fci_get_strings", "fci_get_single_table", "fci_query",
     "fci_last_error", "fci_profile_enable", "fci_profile_read", "fci_profile_kernel_name",
     "fci_rdm1_noalloc", "fci_batch_init", "fci_batch_davidson", "fci_batch_sigma", "fci_batch_offset",
-    "fci_batch_tuning", "fci_batch_stats", "fci_batch_free",
+    "fci_batch_tuning", "fci_batch_stats", "fci_batch_free", "fci_tile_schedule",
 ]
 
 
@@ -122,6 +122,8 @@ def load(path: str = LIB_PATH):
         lib.fci_rdm1_noalloc.argtypes = [vp, vp, i32, vp, vp]
         lib.fci_profile_kernel_name.restype = ctypes.c_char_p
         lib.fci_profile_kernel_name.argtypes = [vp, i32]
+        lib.fci_tile_schedule.restype = i32
+        lib.fci_tile_schedule.argtypes = [i64, i32, i32, vp, vp, vp, vp, i64, ctypes.POINTER(i64), vp]
         _lib = lib
     return _lib
 
@@ -281,6 +283,28 @@ def fci_get_single_table(ctx: FciContext, spin: int):
     sg = np.zeros((n, per), dtype=np.int8)
     _check(load().fci_get_single_table(ctx.handle, spin, _np_ptr(tgt), _np_ptr(kk), _np_ptr(ll), _np_ptr(sg)))
     return tgt, kk, ll, sg
+
+
+def fci_tile_schedule(tgt, pair, sign, npair: int):
+    """Tile schedule of the tensor-core sigma_3 epilogue for a replacement
+    table given on the host (row-major [ns][nsingle] targets, packed pair
+    indices and signs).  Host-only.  Returns (sched uint32 [nsched],
+    toff int32 [ceil(ns/128) + 1])."""
+    tgt = np.ascontiguousarray(tgt, dtype=np.int32)
+    pair = np.ascontiguousarray(pair, dtype=np.int32)
+    sign = np.ascontiguousarray(sign, dtype=np.int8)
+    if tgt.ndim != 2 or pair.shape != tgt.shape or sign.shape != tgt.shape:
+        raise ValueError("tgt, pair and sign must be [ns][nsingle] arrays of one shape")
+    ns, per = tgt.shape
+    toff = np.zeros((ns + 127) // 128 + 1, dtype=np.int32)
+    n = ctypes.c_int64(0)
+    lib = load()
+    _check(lib.fci_tile_schedule(ns, per, npair, _np_ptr(tgt), _np_ptr(pair), _np_ptr(sign), None, 0,
+                                 ctypes.byref(n), _np_ptr(toff)))
+    sched = np.zeros(n.value, dtype=np.uint32)
+    _check(lib.fci_tile_schedule(ns, per, npair, _np_ptr(tgt), _np_ptr(pair), _np_ptr(sign), _np_ptr(sched),
+                                 n.value, ctypes.byref(n), _np_ptr(toff)))
+    return sched, toff
 
 
 def fci_query(ctx: FciContext, what: int) -> int:
