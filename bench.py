@@ -200,10 +200,11 @@ def run_reference(args):
     dt = time.perf_counter() - t
     value = rows_per_step * args.steps / dt / 1e9
     out = {"impl": "reference", "metric": metric_name(args.workload), "value": value, "unit": "Gdet/s",
-           "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": workload_desc(args.workload),
-                      "step": f"{rows_per_step} sigma rows per step (bounded sample, FP64 oracle)"},
+                      "step": f"{rows_per_step} sigma rows per step (bounded sample, FP64 oracle)",
+                      "device": "host cores of rank 0 (the oracle uses no GPU)"},
            "cpu_baseline": {"value": value, "unit": "Gdet/s", "cores": oracle.num_threads(), "kind": "oracle",
                             "sample": f"{rows_per_step} random rows per step, {args.steps} steps"},
            "e2e": {"value": value, "unit": "Gdet/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
