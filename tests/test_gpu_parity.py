@@ -80,6 +80,19 @@ def test_sigma_fp64_small_elementwise(pkg, oracle_mod, norb, na, nb):
     assert np.allclose(d.cpu().numpy(), np.diag(H), rtol=0, atol=1e-13 * max(1, np.abs(np.diag(H)).max()))
 
 
+@pytest.mark.parametrize("norb,na,nb", SPACES)
+def test_sigma_fp32_degenerate_spaces(pkg, oracle_mod, norb, na, nb):
+    """FP32 sigma (tensor-core sigma_3 where both spins have electrons) on the
+    same edge cases: one orbital, empty or full strings, a single string,
+    one ragged tile of 1..126 strings, n_alpha != n_beta."""
+    ctx, h1, eri = make_ctx(pkg, norb, na, nb)
+    H = oracle_mod.hamiltonian(norb, na, nb, h1, eri)
+    c = fi.make_vector(H.shape[0])
+    got = gpu_sigma(pkg, ctx, c, torch.float32)
+    ref = H @ c.astype(np.float32).astype(np.float64)
+    assert np.abs(got - ref).max() <= 2e-6 * max(np.abs(ref).max(), 1e-30)
+
+
 def test_sigma_fp64_random_non_cholesky_integrals(pkg, oracle_mod):
     rng = np.random.default_rng(5)
     n = 6
