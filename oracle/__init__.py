@@ -11,8 +11,8 @@ What lives here:
 * ``oracle/csrc/oracle.c`` -- plain C, FP64: string lists, the E_kl
   single-replacement lists (Eq. 7), the Hamiltonian of Eq. 6 built two
   independent ways (Slater-Condon rules, and Eq. 6 applied term by term to
-  bitstrings), direct sigma = H c (Eq. 4/5), H diagonal and the spin-summed
-  one-particle density.
+  bitstrings), direct sigma = H c (Eq. 4/5), H diagonal, the spin-summed
+  one-particle density and the total spin <S^2> of an expansion.
 * ``oracle.davidson`` -- a plain NumPy Davidson eigensolver following the
   steps of Section 3.3 (reading of the unspecified parts in its docstring).
 
@@ -71,6 +71,8 @@ def _bind(lib):
     lib.oracle_hdiag.argtypes = [i32, i32, i32, dp, dp, dp]
     lib.oracle_rdm1.restype = i32
     lib.oracle_rdm1.argtypes = [i32, i32, i32, dp, dp]
+    lib.oracle_s2.restype = ctypes.c_double
+    lib.oracle_s2.argtypes = [i32, i32, i32, dp]
     lib.oracle_num_threads.restype = i32
     lib.oracle_num_threads.argtypes = []
     return lib
@@ -197,9 +199,21 @@ def rdm1(norb: int, na: int, nb: int, c) -> np.ndarray:
     return g
 
 
+def s_squared(norb: int, na: int, nb: int, c) -> float:
+    """<c|S^2|c> / <c|c>: total spin of an expansion in the (na, nb) sector
+    (a diagnostic for the roots; Ms = 0 roots of random integrals can have any S)."""
+    c = _f64(c)
+    if c.size != ndet(norb, na, nb):
+        raise ValueError("vector length does not match the space")
+    v = float(_load().oracle_s2(norb, na, nb, _ptr(c)))
+    if v != v:
+        raise ValueError("bad space or zero vector")
+    return v
+
+
 from .davidson import davidson  # noqa: E402  (pure NumPy, no library import)
 
 __all__ = [
     "build", "binom", "strings", "single_table", "ndet", "hamiltonian", "sigma",
-    "sigma_rows", "sigma_rows_generated", "hdiag", "rdm1", "davidson", "num_threads",
+    "sigma_rows", "sigma_rows_generated", "hdiag", "rdm1", "s_squared", "davidson", "num_threads",
 ]

@@ -30,6 +30,7 @@
  *  oracle_sigma          the same for every I (OpenMP over I)
  *  oracle_hdiag          H_II
  *  oracle_rdm1           spin-summed one-particle density <c|E_pq|c>
+ *  oracle_s2             <c|S^2|c> / <c|c> (total spin of an expansion)
  */
 #include <math.h>
 #include <stdint.h>
@@ -452,6 +453,43 @@ int oracle_rdm1(int norb, int na, int nb, const double *c, double *gamma) {
     }
     space_free(&S);
     return 0;
+}
+
+/* Total spin of an expansion c in the (n_alpha, n_beta) sector:
+ *   <S^2> = (||S+ c||^2 + (Sz^2 + Sz) ||c||^2) / ||c||^2,
+ * from S^2 = S- S+ + Sz^2 + Sz with S+ = sum_p a+_{p alpha} a_{p beta} and
+ * Sz = (n_alpha - n_beta) / 2.  S+ c is formed explicitly in the
+ * (n_alpha + 1, n_beta - 1) sector (zero when that sector is empty).  NAN for
+ * a bad space or c = 0. */
+double oracle_s2(int norb, int na, int nb, const double *c) {
+    space_t S;
+    if (space_init(&S, norb, na, nb)) return NAN;
+    const int64_t N = S.nsa * S.nsb;
+    double nrm = 0.0;
+    for (int64_t I = 0; I < N; ++I) nrm += c[I] * c[I];
+    double plus = 0.0;
+    if (nb >= 1 && na + 1 <= norb) {
+        space_t T;
+        space_init(&T, norb, na + 1, nb - 1);
+        const int64_t M = T.nsa * T.nsb;
+        double *v = (double *)calloc((size_t)M, sizeof(double));
+        for (int64_t J = 0; J < N; ++J) {
+            if (c[J] == 0.0) continue;
+            det_t dJ = make_det(norb, S.la[J / S.nsb], S.lb[J % S.nsb]);
+            for (int p = 0; p < norb; ++p) {
+                det_t dI;
+                int ph = op_excite(dJ, p, norb + p, &dI); /* a+_{p alpha} a_{p beta} */
+                if (ph) v[det_index(&T, dI)] += ph * c[J];
+            }
+        }
+        for (int64_t I = 0; I < M; ++I) plus += v[I] * v[I];
+        free(v);
+        space_free(&T);
+    }
+    space_free(&S);
+    if (nrm == 0.0) return NAN;
+    const double sz = 0.5 * (na - nb);
+    return (plus + (sz * sz + sz) * nrm) / nrm;
 }
 
 int oracle_num_threads(void) {

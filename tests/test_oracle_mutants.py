@@ -6,7 +6,8 @@ planted in a temporary copy of ``oracle/csrc/oracle.c`` or
 ``oracle/davidson.py``; the committed oracle is never modified.  The copy is
 built and exercised in a child process (so a mutant that crashes cannot take
 the test run down), against the pins of ``test_oracle_strings.py``,
-``test_oracle_hamiltonian.py`` and ``test_oracle_davidson_rdm.py``.  A mutant
+``test_oracle_hamiltonian.py``, ``test_oracle_davidson_rdm.py`` and
+``test_oracle_spin.py``.  A mutant
 counts as caught when at least one pin fails (or a signal kills the child).  The
 unmodified copy, built the same way, must pass every pin, so the harness itself
 is checked too.
@@ -96,6 +97,12 @@ C_MUTANTS = [
     # string list: the empty string missed (loop starts at 1)
     ("strings_start_at_one", "c",
      "for (uint64_t m = 0; m < lim; ++m)", "for (uint64_t m = 1; m < lim; ++m)"),
+    # <S^2>: the Sz term of S^2 = S- S+ + Sz^2 + Sz dropped
+    ("s2_sz_term_dropped", "c",
+     "return (plus + (sz * sz + sz) * nrm) / nrm;", "return (plus + sz * sz * nrm) / nrm;"),
+    # <S^2>: phase of a+_{p alpha} a_{p beta} dropped
+    ("s2_phase_dropped", "c",
+     "if (ph) v[det_index(&T, dI)] += ph * c[J];", "if (ph) v[det_index(&T, dI)] += c[J];"),
     # regenerated trial vector: counter off by one
     ("generator_counter_off_by_one", "c",
      "sm_mix64(key + (uint64_t)(J + 1) * 0x9E3779B97F4A7C15ULL)",
@@ -119,6 +126,7 @@ def _pins():
     sys.path.insert(0, HERE)
     import test_oracle_davidson_rdm as td
     import test_oracle_hamiltonian as th
+    import test_oracle_spin as tsp
     import test_oracle_strings as ts
 
     return [
@@ -144,6 +152,12 @@ def _pins():
         ("davidson_collapse", td.test_davidson_collapse_path),
         ("rdm1_hellmann_feynman", lambda o: td.test_rdm1_hellmann_feynman(o, 4, 2, 2)),
         ("rdm1_e_pq", td.test_rdm1_equals_expectation_of_e_pq),
+        ("s2_closed_shell", lambda o: tsp.test_closed_shell_is_singlet(o, 4, 2, 0b0110)),
+        ("s2_high_spin", lambda o: tsp.test_high_spin_determinant(o, 4, 3, 1, 0b0111, 0b0010)),
+        ("s2_open_shell", tsp.test_two_electron_open_shell),
+        ("s2_hubbard_singlet", tsp.test_two_site_hubbard_ground_state_is_singlet),
+        ("s2_eigenvectors", lambda o: tsp.test_eigenvectors_are_spin_eigenstates(o, 5, 3, 2)),
+        ("s2_explicit_matrix", lambda o: tsp.test_matches_explicit_s2_matrix(o, 5, 3, 2)),
     ]
 
 
