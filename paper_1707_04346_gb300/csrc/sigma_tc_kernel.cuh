@@ -16,24 +16,24 @@
 // tensor memory: NS = 2 is split-BF16x3, NS = 3 is split-BF16x6 (about FP32
 // accuracy).
 //
-// CTA: one per SM, persistent over output alpha rows, with three roles that
-// run concurrently on consecutive 128-string tiles:
+// CTA (288 threads): one per SM, persistent over output alpha rows, with three
+// roles that run concurrently on consecutive 128-string tiles:
 //  * warps 0-3 (producers): each thread gathers the K values of one beta
 //    string (the next tile's loads are in flight while the current one is
-//    split into bf16 slices and stored K-major, no swizzle, into one of the A
-//    buffers) and arrives on full[stage];
-//  * one thread of the last warp waits for full[stage] and for a free
-//    accumulator, issues the NS(NS+1)/2 x K/16 MMAs into one of two TMEM
-//    accumulators and commits to done[acc];
-//  * the epilogue warps wait for done[acc], read the accumulator (tcgen05.ld)
-//    and add s_b G[J_b][p_b] into the sigma row held in shared memory.  The
-//    default epilogue (4 warps) copies the whole accumulator tile to shared
-//    memory, releases it, and then every thread gathers the entries of the
-//    targets it owns in this tile from a precomputed schedule (see
-//    SpinTables::tsched): no atomics, and the adds of a batch of entries hit
-//    distinct slots.  When the schedule or its shared memory is missing, an
-//    atomic epilogue (8 warps, two per TMEM lane quarter) or a staged-column
-//    epilogue with atomics takes over.
+//    split into bf16 slices) and stores the slices either K-major, no swizzle,
+//    into one of the A buffers in shared memory, or (ATM) into the A stage's
+//    tensor-memory columns with tcgen05.st; then arrives on full[stage];
+//  * lane 0 of warp 8 waits for full[stage] and for a free accumulator,
+//    issues the NS(NS+1)/2 x K/16 MMAs into one of two TMEM accumulators and
+//    commits to done[acc];
+//  * warps 4-7 (epilogue) wait for done[acc], copy the accumulator tile
+//    (tcgen05.ld) to shared memory, release it, and then every thread gathers
+//    the entries of the targets it owns in this tile from a precomputed
+//    schedule (SpinTables::tsched) and adds s_b G[J_b][p_b] into the sigma
+//    row: no atomics, and the adds of a batch of entries hit distinct slots.
+//    The row is held in shared memory (EPI 2) or, when it does not fit, in
+//    global memory, where it stays in L2 (EPI 3).  EPI 4 is the same-spin
+//    mode described at the kernel.
 // All waits are bounded; a wait that gives up sets the device error word and
 // the CTA drains and frees its tensor memory.  The pipeline drains at the end
 // of each alpha row, where the sigma row is added to the output and the B
@@ -211,9 +211,7 @@ __host__ __device__ inline Layout make_layout(int ns_split, int kpad, int npad, 
 }
 
 // roles: warps 0-3 producers, 4-7 epilogue (TMEM lane quarter = warp % 4), 8 issues the MMAs
-constexpr int kThreads2 = 288;
-// atomic epilogue: warps 0-3 producers, 4-11 epilogue (two warps per TMEM lane
-// quarter, one per half of the pair columns), 12 issues the MMAs
+constexpr int kThreads2 = 288;  // warps 0-3 producers, 4-7 epilogue, 8 issues the MMAs
 constexpr int kGatherPre = 64;  // gather epilogue: schedule entries held in registers per thread
 
 __device__ __forceinline__ void mbar_arrive(uint32_t addr) {
