@@ -525,7 +525,7 @@ int sigma_of(Work &W, bool fp32, const double *x, double *hx) {
     return FCI_OK;
 }
 
-// Orthogonalise y against X_0..X_{m-1} twice, normalise; *kept = 1 if kept.
+// Orthogonalise y against X_0..X_{m-1} (a second pass when needed), normalise; *kept = 1 if kept.
 int orthonormalise(Work &W, const double *X, int m, double *y, int *kept) {
     if (m > 0) {
         const bool v2 = vec2(W.n, X, y);
