@@ -151,7 +151,11 @@ int fci_hdiag(fci_ctx *ctx, double *out, void *stream);
  *            FP64 [nroots][N] starting vectors
  * Uses the options given at fci_init (max_subspace, max_iter, precision).
  * Blocking; runs on the context's internal stream.
- * Errors: FCI_ERR_ARG, FCI_ERR_OOM, FCI_ERR_CUDA, FCI_ERR_NOCONV.
+ * Errors: FCI_ERR_ARG (also when no guess vector survives orthonormalisation,
+ * e.g. all-NaN guesses), FCI_ERR_OOM, FCI_ERR_CUDA, FCI_ERR_TIMEOUT,
+ * FCI_ERR_NAN (a Ritz value or residual norm became non-finite, e.g. from an
+ * infinite guess entry; checked every iteration, energies not filled),
+ * FCI_ERR_NOCONV.
  */
 int fci_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *vecs, const void *guess);
 

@@ -680,6 +680,9 @@ int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *v
             ctx->log.push_back(el);
             for (int k = 0; k < nroots; ++k) ctx->log.push_back(k < nr ? ev[k] : NAN);
         }
+        for (int k = 0; k < nr; ++k)
+            if (!std::isfinite(ev[k]) || !std::isfinite(rn[k]))
+                return fail(FCI_ERR_NAN, "Davidson: a Ritz value or residual norm is not finite (non-finite guess?)");
         // residual 15 iterations ago (stagnation test of the FP32 phase)
         r_hist.push_back(rmax);
         r_win = r_hist.size() > 15 ? r_hist[r_hist.size() - 16] : INFINITY;
