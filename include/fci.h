@@ -240,8 +240,10 @@ int fci_get_single_table(fci_ctx *ctx, int spin, int32_t *tgt, int8_t *k, int8_t
  *               sched != NULL and cap >= *nsched.
  *  nsched       out: schedule length (call once with sched = NULL to size it)
  *  toff         out (nullable): [ceil(ns/128) + 1] offsets of the tiles
- * Returns FCI_ERR_ARG for NULL inputs, sizes out of range or an entry out of
- * range; nothing is written then.
+ * Returns FCI_ERR_ARG for NULL inputs, sizes out of range, an entry out of
+ * range or a schedule longer than 2^31 records (degenerate tables with very
+ * long rows); nothing is written then.  fci_init builds no schedule in that
+ * case, and the tensor-core sigma_3 refuses the space.
  */
 int fci_tile_schedule(int64_t ns, int nsingle, int npair, const int32_t *tgt, const int32_t *pair,
                       const int8_t *sign, uint32_t *sched, int64_t cap, int64_t *nsched, int32_t *toff);

@@ -258,7 +258,8 @@ int fci_tile_schedule(int64_t ns, int nsingle, int npair, const int32_t *tgt, co
         }
     std::vector<uint32_t> out;
     std::vector<int32_t> off;
-    fci::tile_schedule_host(tab.data(), ns, nsingle, out, off);
+    if (!fci::tile_schedule_host(tab.data(), ns, nsingle, out, off))
+        return fail(FCI_ERR_ARG, "fci_tile_schedule: schedule longer than 2^31 entries");
     *nsched = (int64_t)out.size();
     if (toff) std::memcpy(toff, off.data(), sizeof(int32_t) * off.size());
     if (sched && cap >= (int64_t)out.size()) std::memcpy(sched, out.data(), sizeof(uint32_t) * out.size());

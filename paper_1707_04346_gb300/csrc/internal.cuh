@@ -122,8 +122,9 @@ void dfree(fci_ctx *ctx, void *p, size_t bytes);
 // tables.cu
 int build_tables(fci_ctx *ctx, const double *h1_host, const double *eri_host);
 void free_tables(fci_ctx *ctx);
-// tile schedule of a packed entry-major table tab[e * ns + x] (host only; see SpinTables::tsched)
-void tile_schedule_host(const uint32_t *tab, int64_t ns, int K, std::vector<uint32_t> &out,
+// tile schedule of a packed entry-major table tab[e * ns + x] (host only; see
+// SpinTables::tsched); false when its length would not fit the int32 offsets
+bool tile_schedule_host(const uint32_t *tab, int64_t ns, int K, std::vector<uint32_t> &out,
                         std::vector<int32_t> &off);
 
 // sigma.cu

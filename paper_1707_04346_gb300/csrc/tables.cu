@@ -258,7 +258,7 @@ static int64_t host_binom(int n, int k) {
 
 // Tile schedule for the gather epilogue of the tensor-core sigma_3 (see
 // SpinTables::tsched): built on the host from the entry-major table.
-void tile_schedule_host(const uint32_t *tab, int64_t ns, int K, std::vector<uint32_t> &out,
+bool tile_schedule_host(const uint32_t *tab, int64_t ns, int K, std::vector<uint32_t> &out,
                         std::vector<int32_t> &off) {
     const int R = kTileStrings;
     const int64_t ntiles = (ns + R - 1) / R;
@@ -308,6 +308,7 @@ void tile_schedule_host(const uint32_t *tab, int64_t ns, int K, std::vector<uint
         }
         // stored step-major: entry j of share k at [j][k]; share k is padded
         // with entries for the dummy target ns + k (pair 0, source 0, sign +)
+        if (pos + kmax * R > (size_t)INT32_MAX) return false;  // offsets are int32
         off[t] = (int32_t)pos;
         out.resize(pos + kmax * R);
         for (int k = 0; k < R; ++k) {
@@ -319,6 +320,7 @@ void tile_schedule_host(const uint32_t *tab, int64_t ns, int K, std::vector<uint
         pos += kmax * R;
     }
     off[ntiles] = (int32_t)pos;
+    return true;
 }
 
 static int build_tile_schedule(fci_ctx *ctx, SpinTables &T) {
@@ -328,7 +330,7 @@ static int build_tile_schedule(fci_ctx *ctx, SpinTables &T) {
     FCI_CUDA(cudaStreamSynchronize(ctx->stream));
     std::vector<uint32_t> out;
     std::vector<int32_t> off;
-    tile_schedule_host(tab.data(), T.ns, T.nsingle, out, off);
+    if (!tile_schedule_host(tab.data(), T.ns, T.nsingle, out, off)) return FCI_OK;  // no schedule
     int rc = FCI_OK;
     T.nsched = (int64_t)out.size();
     T.tsched = (uint32_t *)dalloc(ctx, sizeof(uint32_t) * out.size(), &rc);
