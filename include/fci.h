@@ -107,7 +107,8 @@ void fci_default_options(fci_options *opt);
 int fci_init(fci_ctx **ctx, int norb, int nalpha, int nbeta, const double *h1, const double *eri,
              const fci_options *opt);
 
-/* Release every device buffer of the context.  NULL is accepted. */
+/* Release every device buffer of the context.  NULL is accepted.  (Resource
+ * management; no counterpart in the paper.) */
 int fci_free(fci_ctx *ctx);
 
 /*
@@ -136,7 +137,9 @@ int fci_free(fci_ctx *ctx);
  */
 int fci_sigma(fci_ctx *ctx, const void *c, void *sigma, int dtype, void *stream);
 
-/* Copy the FP64 determinant diagonal H_II (N elements) to device memory `out`. */
+/* Copy the FP64 determinant diagonal H_II of Eq. 6 (N elements) to device
+ * memory `out`: the diagonal preconditioner of Section 3.3 step (2).
+ * Stream-ordered.  Errors: FCI_ERR_ARG, FCI_ERR_CUDA. */
 int fci_hdiag(fci_ctx *ctx, double *out, void *stream);
 
 /*
@@ -160,10 +163,12 @@ int fci_hdiag(fci_ctx *ctx, double *out, void *stream);
 int fci_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *vecs, const void *guess);
 
 /*
- * Per-iteration log of the last fci_davidson call.  Writes up to `cap`
- * records of (nroots + 3) doubles each into HOST `out`: iteration, precision
- * (0 FP64, 1 FP32), elapsed seconds since the call started, then the nroots
- * Ritz values.  Returns the number of records available via *count.
+ * Per-iteration log of the last fci_davidson call (one record per pass through
+ * steps (2)-(4) of Section 3.3).  Writes up to `cap` records of (nroots + 3)
+ * doubles each into HOST `out`: iteration, precision (0: every subspace sigma
+ * FP64-exact, 1: FP32 sigma present), elapsed seconds since the call started,
+ * then the nroots Ritz values.  Returns the number of records available via
+ * *count.
  */
 int fci_davidson_log(fci_ctx *ctx, double *out, int cap, int *count);
 
@@ -210,8 +215,9 @@ int fci_rdm1_noalloc(fci_ctx *ctx, const void *c, int dtype, double *gamma, void
 
 /*
  * Copy tables to the host (for checking): the string list of one spin
- * (spin 0 = alpha, 1 = beta) as uint32 bitmasks [N_spin], and its
- * single-replacement lists [N_spin][n_single]: for string X and each
+ * (spin 0 = alpha, 1 = beta; the strings of Eq. 2) as uint32 bitmasks
+ * [N_spin], and its single-replacement lists (the E_kl of Eq. 7)
+ * [N_spin][n_single]: for string X and each
  * (k, l) with l occupied and k empty or k == l, in the order l ascending
  * then k ascending, a+_k a_l |X> = sign |target>.  Any of tgt/k/l/sign may
  * be NULL.  Blocking.
@@ -249,7 +255,8 @@ int fci_tile_schedule(int64_t ns, int nsingle, int npair, const int32_t *tgt, co
                       const int8_t *sign, uint32_t *sched, int64_t cap, int64_t *nsched, int32_t *toff);
 
 /*
- * Per-kernel timing (tracing).  While enabled, every fci_sigma call records
+ * Per-kernel timing (tracing; no counterpart in the paper, whose tables give
+ * per-step wall times).  While enabled, every fci_sigma call records
  * CUDA events on the caller's stream around each kernel it launches (no
  * synchronisation; the events go into a ring of 1024 records).
  * fci_profile_read waits for the recorded events and returns, per record,
@@ -295,20 +302,24 @@ typedef struct fci_batch fci_batch;
 int fci_batch_init(fci_batch **batch, int ninst, const fci_instance *inst, const fci_options *opt);
 
 /*
- * Lowest nroots eigenvalues of every instance; energies is HOST
+ * Lowest nroots eigenvalues of every instance by the Davidson steps of
+ * Section 3.3, all instances in lock-step; energies is HOST
  * [ninst][nroots].  Returns FCI_ERR_NOCONV if any instance did not converge
  * within max_iter (all energies are still filled).  Blocking.
  */
 int fci_batch_davidson(fci_batch *batch, int nroots, double tol, double *energies);
 
 /*
- * sigma for every instance at once: c and sigma are DEVICE vectors holding
+ * sigma (Eq. 4, split as Eq. 8) for every instance at once: c and sigma are
+ * DEVICE vectors holding
  * the instances' CI vectors back to back (instance i at offset
  * fci_batch_offset(batch, i)), dtype FCI_F64 or FCI_F32.  Stream-ordered.
  */
 int fci_batch_sigma(fci_batch *batch, const void *c, void *sigma, int dtype, void *stream);
 
-/* Offset of instance i in a batch vector; i == ninst gives the total length. */
+/* Offset of instance i in a batch vector; i == ninst gives the total length.
+ * (The following batch queries are bookkeeping with no counterpart in the
+ * paper.) */
 int64_t fci_batch_offset(fci_batch *batch, int i);
 
 /* Tuning table: for each distinct (norb, dtype) writes norb, dtype and the
@@ -322,10 +333,12 @@ int64_t fci_batch_stats(fci_batch *batch, int what);
 
 int fci_batch_free(fci_batch *batch);
 
-/* Sizes and counters (FCI_Q_*); returns -1 for an unknown selector. */
+/* Sizes and counters (FCI_Q_*); returns -1 for an unknown selector.  (No
+ * counterpart in the paper.) */
 int64_t fci_query(fci_ctx *ctx, int what);
 
-/* Message of the last failed call on this thread ("" if none). */
+/* Message of the last failed call on this thread ("" if none).  (Error
+ * reporting; no counterpart in the paper.) */
 const char *fci_last_error(void);
 
 #ifdef __cplusplus
