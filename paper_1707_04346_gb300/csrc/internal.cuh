@@ -32,7 +32,7 @@ constexpr uint32_t kTargetMask = (1u << kTargetBits) - 1u;
 constexpr int kPairShift = 21;
 constexpr uint32_t kPairMask = 0x3FFu;
 constexpr int kMaxStrings = (1 << kTargetBits) - 1;
-constexpr uint32_t kNoEntry = 0xFFFFFFFFu;  // pair-major table: this string has no entry with that pair
+constexpr uint32_t kNoEntry = 0xFFFFFFFFu;  // per-string pair table: no entry with that pair
 
 __host__ __device__ inline uint32_t ent_target(uint32_t e) { return e & kTargetMask; }
 __host__ __device__ inline uint32_t ent_pair(uint32_t e) { return (e >> kPairShift) & kPairMask; }
@@ -54,7 +54,6 @@ struct SpinTables {
     uint32_t *str = nullptr;   // [ns] bitmasks, ascending
     uint32_t *tab = nullptr;   // [nsingle][ns] packed entries (entry-major)
     uint32_t *tabo = nullptr;  // [ne*(norb-ne)][ns] off-diagonal entries only (k != l), entry-major
-    uint32_t *tabp = nullptr;  // [npair][ns] the entry with pair p of each string, or kNoEntry
     double *wdiag = nullptr;   // [npair][ns]: sum over occupied l of (p | ll)
     int32_t *gcol = nullptr;   // [nsame][ns] same-spin Hamiltonian columns (ELL)
     double *gval = nullptr;    // [nsame][ns]

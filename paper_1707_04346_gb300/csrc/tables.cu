@@ -118,17 +118,6 @@ __global__ void k_offdiag_table(const uint32_t *tab, const uint32_t *str, int64_
     }
 }
 
-// Pair-major copy: tabp[p][x] = the entry of string x whose pair index is p.
-__global__ void k_pair_table(const uint32_t *tab, int64_t ns, int nsingle, int npair, uint32_t *tabp) {
-    int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (x >= ns) return;
-    for (int p = 0; p < npair; ++p) tabp[(int64_t)p * ns + x] = kNoEntry;
-    for (int e = 0; e < nsingle; ++e) {
-        const uint32_t v = tab[(int64_t)e * ns + x];
-        tabp[(int64_t)ent_pair(v) * ns + x] = v;
-    }
-}
-
 // wdiag[p][x] = sum over orbitals l occupied in string x of W[p][(ll)]
 __global__ void k_wdiag(const double *W, int npair, const uint32_t *str, int64_t ns, double *wd) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -356,7 +345,6 @@ static int build_spin(fci_ctx *ctx, SpinTables &T, int ne) {
     const int noff = ne * (n - ne);
     T.tabo = (uint32_t *)dalloc(ctx, sizeof(uint32_t) * ns * (noff > 0 ? noff : 1), &rc);
     T.wdiag = (double *)dalloc(ctx, sizeof(double) * ns * ctx->npair, &rc);
-    T.tabp = (uint32_t *)dalloc(ctx, sizeof(uint32_t) * ns * ctx->npair, &rc);
     T.gcol = (int32_t *)dalloc(ctx, sizeof(int32_t) * ns * T.nsame, &rc);
     T.gval = (double *)dalloc(ctx, sizeof(double) * ns * T.nsame, &rc);
     T.gvalf = (float *)dalloc(ctx, sizeof(float) * ns * T.nsame, &rc);
@@ -368,7 +356,6 @@ static int build_spin(fci_ctx *ctx, SpinTables &T, int ne) {
         k_single_table<<<ceil_div(ns * T.nsingle, 256), 256, 0, s>>>(T.str, ns, n, ne, T.nsingle, T.tab);
         FCI_CUDA(cudaGetLastError());
         k_offdiag_table<<<ceil_div(ns, 128), 128, 0, s>>>(T.tab, T.str, ns, T.nsingle, noff, T.tabo);
-        k_pair_table<<<ceil_div(ns, 128), 128, 0, s>>>(T.tab, ns, T.nsingle, ctx->npair, T.tabp);
         FCI_CUDA(cudaGetLastError());
     }
     k_wdiag<<<ceil_div(ns * ctx->npair, 256), 256, 0, s>>>(ctx->W, ctx->npair, T.str, ns, T.wdiag);
@@ -440,7 +427,6 @@ static void free_spin(fci_ctx *ctx, SpinTables &T) {
     const int noff = T.ne * (ctx->norb - T.ne);
     dfree(ctx, T.tabo, sizeof(uint32_t) * T.ns * (noff > 0 ? noff : 1));
     dfree(ctx, T.wdiag, sizeof(double) * T.ns * ctx->npair);
-    dfree(ctx, T.tabp, sizeof(uint32_t) * T.ns * ctx->npair);
     dfree(ctx, T.gcol, sizeof(int32_t) * T.ns * T.nsame);
     dfree(ctx, T.gval, sizeof(double) * T.ns * T.nsame);
     dfree(ctx, T.gvalf, sizeof(float) * T.ns * T.nsame);
