@@ -106,3 +106,14 @@ def test_paper_d2h_counts(oracle_mod):
 def test_gas_loop_counts():
     g = json.load(open(GOLDEN))["gas_loop_counts"]
     assert 6 ** 4 == g["six_gas"] and 8 ** 4 == g["eight_gas"]
+
+
+def test_paper_linear_scaling_reading():
+    """Section 5 extrapolates the CAS(20,20) time linearly in the number of
+    determinants to CAS(22,22): the printed D2h 1Ag counts reproduce the printed
+    4110 s and the "about 30x" ratio (a check of how the counts were read)."""
+    g = json.load(open(GOLDEN))
+    ratio = g["cas22_d2h_ag_sd_count"]["value"] / g["cas20_d2h_ag_sd_count"]["value"]
+    t = g["linear_scaling_times"]
+    assert abs(ratio - 30) < 1.0
+    assert abs(t["cas20_s_per_ci_iteration_2048"] * ratio - t["cas22_extrapolated_s_2048"]) < 2.0
