@@ -230,7 +230,8 @@ int fci_get_single_table(fci_ctx *ctx, int spin, int32_t *tgt, int8_t *k, int8_t
  * epilogue uses for the beta-side scatter of Eq. 8 (sigma_3(I_a, I_b) gets
  * sign * G(J_b) for every I_b = E_kl J_b), built by the routine fci_init runs
  * on the beta table, from a single-replacement table in host memory.
- *  ns, nsingle  strings and entries per string (1 <= ns <= 65408)
+ *  ns, nsingle  strings and entries per string (1 <= ns <= 65408,
+ *               1 <= nsingle <= 1024)
  *  npair        number of packed orbital pairs (1..256); pair index of (k, l)
  *               is max*(max+1)/2 + min
  *  tgt, pair, sign  row-major [ns][nsingle] (tgt in [0, ns), pair in
@@ -248,7 +249,7 @@ int fci_get_single_table(fci_ctx *ctx, int spin, int32_t *tgt, int8_t *k, int8_t
  *  toff         out (nullable): [ceil(ns/128) + 1] offsets of the tiles
  * Returns FCI_ERR_ARG for NULL inputs, sizes out of range, an entry out of
  * range or a schedule longer than 2^31 records (degenerate tables with very
- * long rows); nothing is written then.  fci_init builds no schedule in that
+ * long rows), FCI_ERR_OOM when host memory runs out; nothing is written then.  fci_init builds no schedule in that
  * case, and the tensor-core sigma_3 refuses the space.
  */
 int fci_tile_schedule(int64_t ns, int nsingle, int npair, const int32_t *tgt, const int32_t *pair,

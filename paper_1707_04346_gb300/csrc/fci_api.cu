@@ -239,13 +239,25 @@ int fci_get_single_table(fci_ctx *ctx, int spin, int32_t *tgt, int8_t *k, int8_t
     return unpack_table(ctx, spin, tgt, k, l, sign);
 }
 
+static int tile_schedule_api(int64_t ns, int nsingle, int npair, const int32_t *tgt, const int32_t *pair,
+                             const int8_t *sign, uint32_t *sched, int64_t cap, int64_t *nsched, int32_t *toff);
+
 int fci_tile_schedule(int64_t ns, int nsingle, int npair, const int32_t *tgt, const int32_t *pair,
                       const int8_t *sign, uint32_t *sched, int64_t cap, int64_t *nsched, int32_t *toff) {
     if (!tgt || !pair || !sign || !nsched) return fail(FCI_ERR_ARG, "fci_tile_schedule: NULL table or nsched");
     if (ns < 1 || ns > fci::kMaxScheduleStrings)
         return fail(FCI_ERR_ARG, "fci_tile_schedule: ns must be in [1, 65408]");
-    if (nsingle < 1 || npair < 1 || npair > 256)
-        return fail(FCI_ERR_ARG, "fci_tile_schedule: nsingle >= 1 and 1 <= npair <= 256 required");
+    if (nsingle < 1 || nsingle > 1024 || npair < 1 || npair > 256)
+        return fail(FCI_ERR_ARG, "fci_tile_schedule: 1 <= nsingle <= 1024 and 1 <= npair <= 256 required");
+    try {
+        return tile_schedule_api(ns, nsingle, npair, tgt, pair, sign, sched, cap, nsched, toff);
+    } catch (const std::bad_alloc &) {
+        return fail(FCI_ERR_OOM, "fci_tile_schedule: host allocation failed");
+    }
+}
+
+static int tile_schedule_api(int64_t ns, int nsingle, int npair, const int32_t *tgt, const int32_t *pair,
+                             const int8_t *sign, uint32_t *sched, int64_t cap, int64_t *nsched, int32_t *toff) {
     // packed entry-major copy, the layout fci_init builds on the device
     std::vector<uint32_t> tab((size_t)ns * nsingle);
     for (int64_t x = 0; x < ns; ++x)

@@ -164,6 +164,9 @@ def test_schedule_rejects_bad_tables(pkg):
             pkg.fci_tile_schedule(args["tgt"], args["pair"], args["sign"], 21)
     with pytest.raises(pkg.FciError):
         pkg.fci_tile_schedule(tgt, pair, sign, 300)  # more than 256 pairs
+    wide = np.zeros((4, 1025), dtype=np.int32)
+    with pytest.raises(pkg.FciError):
+        pkg.fci_tile_schedule(wide, wide, np.ones((4, 1025), dtype=np.int8), 1)  # nsingle > 1024
     big = np.zeros((65409, 1), dtype=np.int32)
     with pytest.raises(pkg.FciError):
         pkg.fci_tile_schedule(big, big, np.ones((65409, 1), dtype=np.int8), 1)
