@@ -158,7 +158,12 @@ int fci_init(fci_ctx **out, int norb, int nalpha, int nbeta, const double *h1, c
     cudaError_t e = cudaSetDevice(dev);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) { delete ctx; return cuda_fail(e, "device setup"); }
-    int rc = build_tables(ctx, h1, eri);
+    int rc = FCI_OK;
+    try {
+        rc = build_tables(ctx, h1, eri);
+    } catch (const std::bad_alloc &) {  // host tables: no exception crosses the C ABI
+        rc = fail(FCI_ERR_OOM, "host allocation failed while building the tables");
+    }
     if (rc) {
         std::string msg = g_last_error;
         fci_free(ctx);
@@ -185,7 +190,11 @@ int fci_sigma(fci_ctx *ctx, const void *c, void *sigma, int dtype, void *stream)
     if (!c || !sigma) return fail(FCI_ERR_ARG, "c or sigma is NULL");
     if (c == sigma) return fail(FCI_ERR_ARG, "c and sigma must not overlap");
     FCI_CUDA(cudaSetDevice(ctx->device));
-    return launch_sigma(ctx, c, sigma, dtype, (cudaStream_t)stream);
+    try {
+        return launch_sigma(ctx, c, sigma, dtype, (cudaStream_t)stream);
+    } catch (const std::bad_alloc &) {
+        return fail(FCI_ERR_OOM, "host allocation failed");
+    }
 }
 
 int fci_hdiag(fci_ctx *ctx, double *out, void *stream) {
@@ -201,7 +210,11 @@ int fci_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *v
     if (nroots < 1 || nroots > 8 || nroots > ctx->ndet) return fail(FCI_ERR_ARG, "nroots must be in 1..min(8, N)");
     if (!(tol > 0)) return fail(FCI_ERR_ARG, "tol must be positive");
     FCI_CUDA(cudaSetDevice(ctx->device));
-    return run_davidson(ctx, nroots, tol, energies, vecs, guess);
+    try {
+        return run_davidson(ctx, nroots, tol, energies, vecs, guess);
+    } catch (const std::bad_alloc &) {  // the workspace frees itself on unwinding
+        return fail(FCI_ERR_OOM, "host allocation failed");
+    }
 }
 
 int fci_davidson_log(fci_ctx *ctx, double *out, int cap, int *count) {
@@ -221,7 +234,11 @@ int fci_rdm1(fci_ctx *ctx, const void *c, int dtype, double *gamma) {
     if (dtype != FCI_F64 && dtype != FCI_F32) return fail(FCI_ERR_ARG, "dtype must be FCI_F64 or FCI_F32");
     FCI_CUDA(cudaSetDevice(ctx->device));
     FCI_CUDA(cudaDeviceSynchronize());  // c may still be in flight on the caller's streams
-    return run_rdm1(ctx, c, dtype, gamma);
+    try {
+        return run_rdm1(ctx, c, dtype, gamma);
+    } catch (const std::bad_alloc &) {
+        return fail(FCI_ERR_OOM, "host allocation failed");
+    }
 }
 
 int fci_get_strings(fci_ctx *ctx, int spin, uint32_t *out) {
