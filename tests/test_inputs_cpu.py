@@ -78,3 +78,15 @@ def test_trial_vectors():
     u = fi.make_vector(16, kind="uniform")
     assert np.allclose(u, 0.25)
     assert fi.make_vector(0).size == 0
+
+
+def test_device_fill_library_builds_for_sm103a_and_exports_its_entry_point():
+    """The device fill (same generator, used for vectors too large for the host)
+    cross-compiles here and exports its C entry point; running it needs a GPU
+    (tests/test_gpu_cas18.py checks it bit-exactly against vector_pm1)."""
+    import ctypes
+
+    from fci_inputs import gpu
+
+    lib = ctypes.CDLL(gpu.build())
+    assert hasattr(lib, "fci_inputs_fill_pm1")
