@@ -70,6 +70,10 @@ struct SpinTables {
     uint32_t *tsched = nullptr;
     int32_t *toff = nullptr;  // [ntiles + 1]
     int64_t nsched = 0;
+    // Pair-major copy of the replacement lists for the FP64 sliced sigma_3
+    // (beta spin only): tabp[q][x] = the entry of string x with orbital pair q,
+    // or kNoEntry.  Owned by the context (freed with the sliced tables).
+    uint32_t *tabp = nullptr;
     bool owner = true;         // false when aliasing the alpha tables
 };
 
@@ -89,6 +93,9 @@ struct fci_ctx {
     float *Wf = nullptr;
     float *kf = nullptr;            // [npair] k_kl = h_kl - 1/2 sum_j (kj|jl), FP32 (same-spin tensor-core path)
     float *ws32 = nullptr;          // [2][ndet] FP32 workspace of that path (allocated on first use)
+    uint4 *Wsl = nullptr;           // [npair][npair] six bf16 digit slices of W (FP64 sliced sigma_3)
+    int eW = 0;                     // |W| < 2^eW
+    int *rowexp = nullptr;          // [max(N_alpha, N_beta)] row exponents of C (per FP64 sliced sigma_3 call)
     double *hdiag = nullptr;        // [ndet]
     int *d_err = nullptr;           // device error word (bounded waits that gave up)
     size_t bytes = 0;
@@ -142,6 +149,12 @@ int prepare_sigma3_tc(const fci_ctx *ctx, int nsplit);
 int launch_same_spin_tc(fci_ctx *ctx, const float *C, float *sig, const SpinTables &R, const SpinTables &cols,
                         cudaStream_t s);
 size_t sigma3_tc_smem(const fci_ctx *ctx, int nsplit);
+
+// sigma3_sliced.cu (FP64-accurate sigma_3 on the tensor cores)
+int build_sliced_tables(fci_ctx *ctx, const double *eri_host);
+void free_sliced_tables(fci_ctx *ctx);
+bool sigma3_sliced_ok(const fci_ctx *ctx);
+int launch_sigma3_sliced(fci_ctx *ctx, const double *C, double *sig, cudaStream_t s, int rec, int prof_slot);
 
 // davidson.cu
 int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *vecs, const void *guess);

@@ -35,11 +35,11 @@ __device__ __forceinline__ float gval_of<float>(const SpinTables &S, int64_t idx
 }
 
 // sigma_1 (beta-beta, I_alpha = J_alpha): R rows of C in shared memory,
-//   sigma(Ia, Ib) = sum_e G_b[e][Ib] * C(Ia, col_e)        (overwrites sigma)
+//   sigma(Ia, Ib) = sum_e G_b[e][Ib] * C(Ia, col_e)   (overwrites sigma, or adds when add != 0)
 // Each ELL entry of a beta string is read once per block of R rows.
 template <typename T, int R>
 __global__ void __launch_bounds__(512) k_sigma1_rows(const T *__restrict__ C, T *__restrict__ sig, SpinTables B,
-                                                     int64_t nsa) {
+                                                     int64_t nsa, int add) {
     constexpr int U = sizeof(T) == 4 ? kEnt : 1;  // FP64 is bound by its FMA pipe
     extern __shared__ unsigned char smem_raw[];
     T *rows = reinterpret_cast<T *>(smem_raw);
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(512) k_sigma1_rows(const T *__restrict__ C, T 
         }
 #pragma unroll
         for (int r = 0; r < R; ++r)
-            if (r0 + r < nsa) sig[(r0 + r) * nsb + ib] = acc[r];
+            if (r0 + r < nsa) sig[(r0 + r) * nsb + ib] = add ? sig[(r0 + r) * nsb + ib] + acc[r] : acc[r];
     }
 }
 
@@ -299,9 +299,22 @@ static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s) {
     static const char *const names3[3] = {"sigma1_rows", "sigma2_cols", sizeof(T) == 4 ? "sigma3_tc" : "sigma3_exact"};
     static const char *const names3tc[3] = {"sigma2_tc", "sigma1_tc", "sigma3_tc"};
     static const char *const names2[2] = {"sigma12_f32", "sigma3_tc"};
-    const int rec = same_tc ? prof_begin(ctx, s, 3, names3tc)
+    static const char *const names4[4] = {"row_exponents", "sigma3_sliced", "sigma1_rows", "sigma2_cols"};
+    // FP64 with the sliced tensor-core sigma_3: it runs first and overwrites sigma
+    const bool sliced = sizeof(T) == 8 && A.nsingle > 0 && B.nsingle > 0 && ctx->opt.f64_sigma3 != FCI_F64_SIGMA3_EXACT &&
+                        sigma3_sliced_ok(ctx);
+    const int rec = sliced ? prof_begin(ctx, s, 4, names4)
+                    : same_tc ? prof_begin(ctx, s, 3, names3tc)
                     : fusedR ? prof_begin(ctx, s, 2, names2) : prof_begin(ctx, s, 3, names3);
     const int slot3 = (fusedR && !same_tc) ? 1 : 2;
+    int slot = 0;  // next profiling slot of the staged same-spin kernels
+    int add1 = 0;  // sigma_1 adds to what sigma_3 wrote
+    if (sliced) {
+        if constexpr (sizeof(T) == 8)
+            if (int rc = launch_sigma3_sliced(ctx, C, sig, s, rec, 0)) return rc;
+        slot = 2;
+        add1 = 1;
+    }
     if (same_tc) {
         if constexpr (sizeof(T) == 4) {
             if (!ctx->ws32) {
@@ -343,9 +356,9 @@ static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s) {
             FCI_CUDA(opt_in_max_smem(k, ctx->device));
             int64_t nsa_ = nsa;
             SpinTables Bt = B;
-            void *args[] = {(void *)&C, (void *)&sig, (void *)&Bt, (void *)&nsa_};
+            void *args[] = {(void *)&C, (void *)&sig, (void *)&Bt, (void *)&nsa_, (void *)&add1};
             FCI_CUDA(cudaLaunchKernel(k, dim3(ceil_div(nsa, R)), dim3(512), args, sm, s));
-            prof_mark(ctx, rec, 0, s);
+            prof_mark(ctx, rec, slot, s);
         }
         {
             const int R = pick_r(nsa);
@@ -358,10 +371,11 @@ static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s) {
             SpinTables At = A;
             void *args[] = {(void *)&C, (void *)&sig, (void *)&At, (void *)&nsb_};
             FCI_CUDA(cudaLaunchKernel(k, dim3(ceil_div(nsb, R)), dim3(512), args, sm, s));
-            prof_mark(ctx, rec, 1, s);
+            prof_mark(ctx, rec, slot + 1, s);
         }
     }
     // sigma_3
+    if (sliced) return FCI_OK;
     if (A.nsingle > 0 && B.nsingle > 0 && sizeof(T) == 4) {
         if (int rc = launch_sigma3_tc(ctx, (const float *)C, (float *)sig, ctx->opt.f32_splits, s)) return rc;
     } else if (A.nsingle > 0 && B.nsingle > 0) {

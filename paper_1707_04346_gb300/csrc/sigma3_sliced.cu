@@ -1,0 +1,166 @@
+// Host side of the FP64-accurate tensor-core sigma_3 (sigma3_sliced_kernel.cuh):
+// the tables it needs (built once at fci_init), the per-call row exponents of
+// C, and the launch.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "sigma3_sliced_kernel.cuh"
+
+namespace fci {
+
+static int round_up16(int x) { return (x + 15) / 16 * 16; }
+
+// out[r] = largest biased FP64 exponent field over row r of C (nrows x ncols);
+// one warp per row.
+__global__ void k_row_exponents(const double *__restrict__ C, int64_t nrows, int64_t ncols, int *__restrict__ out) {
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= nrows) return;
+    const unsigned long long *row = reinterpret_cast<const unsigned long long *>(C + r * ncols);
+    unsigned mx = 0;
+    for (int64_t j = lane; j < ncols; j += 32) mx = max(mx, (unsigned)((__ldg(row + j) >> 52) & 0x7FFull));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+    if (lane == 0) out[r] = (int)mx;
+}
+
+// Pair-major copy of a replacement table: tabp[q][x] = the entry of string x
+// whose orbital pair is q (a string has at most one: {k, l} with k == l
+// occupied, or exactly one of k, l occupied), or kNoEntry.
+__global__ void k_pair_table(const uint32_t *__restrict__ tab, int64_t ns, int nsingle, uint32_t *__restrict__ tabp) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ns * nsingle) return;
+    const uint32_t v = tab[t];  // entry-major: t = e * ns + x
+    const int64_t x = t % ns;
+    tabp[(int64_t)ent_pair(v) * ns + x] = v;
+}
+
+// Sizes of the sliced kernel for this context; false when it does not apply.
+static bool sliced_shape(const fci_ctx *ctx, int *kpad, int *npad, int *n0, uint32_t *smem) {
+    const SpinTables &A = ctx->A, &B = ctx->B;
+    if (A.nsingle == 0 || B.nsingle == 0) return false;
+    *kpad = round_up16(A.nsingle);
+    *npad = round_up16(ctx->npair);
+    if (*kpad > 16 * sl::kMaxKSteps || *npad > 128 || B.ns > kMaxStrings) return false;
+    *n0 = round_up16((*npad + 1) / 2);
+    if (*n0 > *npad) *n0 = *npad;
+    *smem = sl::make_layout(*kpad, *npad, B.ns, A.nsingle).total;
+    int lim = 0;
+    if (cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device) != cudaSuccess) return false;
+    return (int)*smem <= lim;
+}
+
+bool sigma3_sliced_ok(const fci_ctx *ctx) { return ctx->Wsl != nullptr && ctx->B.tabp != nullptr; }
+
+// Build, once per context: the integral digits Wsl (six bf16 slices of the
+// pair matrix relative to 2^eW, padded to 8 halves per element), the
+// pair-major beta table and the row-exponent buffer.  Contexts whose shapes
+// the kernel does not cover get none of them (the exact FP64 kernel runs).
+int build_sliced_tables(fci_ctx *ctx, const double *eri_host) {
+    int kpad = 0, npad = 0, n0 = 0;
+    uint32_t smem = 0;
+    if (ctx->opt.f64_sigma3 == FCI_F64_SIGMA3_EXACT || !sliced_shape(ctx, &kpad, &npad, &n0, &smem)) {
+        if (ctx->opt.f64_sigma3 == FCI_F64_SIGMA3_SLICED)
+            return fail(FCI_ERR_ARG, "f64_sigma3 = sliced: the space exceeds the sliced kernel's limits "
+                                     "(at most 128 orbital pairs, 96 alpha replacements, shared memory)");
+        return FCI_OK;
+    }
+    const int n = ctx->norb, np = ctx->npair;
+    const int64_t n2 = (int64_t)n * n;
+    std::vector<double> W((size_t)np * np);
+    double wmax = 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j <= i; ++j)
+            for (int k = 0; k < n; ++k)
+                for (int l = 0; l <= k; ++l) {
+                    const double v = eri_host[i * n2 * n + j * n2 + (int64_t)k * n + l];
+                    W[(size_t)pair_index(i, j) * np + pair_index(k, l)] = v;
+                    wmax = std::fmax(wmax, std::fabs(v));
+                }
+    int eW = 0;
+    if (wmax > 0) std::frexp(wmax, &eW);  // wmax < 2^eW
+    // X = round(W 2^(47 - eW)), |X| <= 2^47; balanced digits of X' = X + 0x8080808080:
+    // d0 = X' >> 40 in [-128, 128], d_s = (byte 5-s of X') - 128 (as in the kernel's digits6)
+    std::vector<uint16_t> sl((size_t)np * np * 8, 0);
+    for (size_t e = 0; e < W.size(); ++e) {
+        const long long X = std::llrint(std::ldexp(W[e], 47 - eW)) + 0x8080808080ll;
+        for (int s = 0; s < sl::kSlices; ++s) {
+            const long long d = s == 0 ? (X >> 40) : ((X >> (40 - 8 * s)) & 255) - 128;
+            const float f = std::ldexp((float)d, -8 * s);  // exact: at most 8 significant bits
+            uint32_t b;
+            std::memcpy(&b, &f, 4);
+            sl[e * 8 + s] = (uint16_t)(b >> 16);  // bf16 of an exactly representable value
+        }
+    }
+    int rc = FCI_OK;
+    ctx->Wsl = (uint4 *)dalloc(ctx, sizeof(uint4) * (size_t)np * np, &rc);
+    const int64_t nrow = ctx->A.ns > ctx->B.ns ? ctx->A.ns : ctx->B.ns;
+    ctx->rowexp = (int *)dalloc(ctx, sizeof(int) * (size_t)nrow, &rc);
+    SpinTables &B = ctx->B;
+    B.tabp = (uint32_t *)dalloc(ctx, sizeof(uint32_t) * (size_t)np * B.ns, &rc);
+    if (rc) return rc;
+    ctx->eW = eW;
+    FCI_CUDA(cudaMemcpyAsync(ctx->Wsl, sl.data(), sizeof(uint4) * (size_t)np * np, cudaMemcpyHostToDevice, ctx->stream));
+    FCI_CUDA(cudaMemsetAsync(B.tabp, 0xFF, sizeof(uint32_t) * (size_t)np * B.ns, ctx->stream));
+    k_pair_table<<<ceil_div(B.ns * B.nsingle, 256), 256, 0, ctx->stream>>>(B.tab, B.ns, B.nsingle, B.tabp);
+    FCI_CUDA(cudaGetLastError());
+    FCI_CUDA(cudaStreamSynchronize(ctx->stream));
+    return FCI_OK;
+}
+
+void free_sliced_tables(fci_ctx *ctx) {
+    const int np = ctx->npair;
+    if (ctx->B.tabp) dfree(ctx, ctx->B.tabp, sizeof(uint32_t) * (size_t)np * ctx->B.ns);
+    ctx->B.tabp = nullptr;
+    const int64_t nrow = ctx->A.ns > ctx->B.ns ? ctx->A.ns : ctx->B.ns;
+    dfree(ctx, ctx->Wsl, sizeof(uint4) * (size_t)np * np);
+    dfree(ctx, ctx->rowexp, sizeof(int) * (size_t)nrow);
+    ctx->Wsl = nullptr;
+    ctx->rowexp = nullptr;
+}
+
+static void *sliced_kernel(int kpad) {
+    switch (kpad) {
+        case 16: return (void *)sl::k_sigma3_sliced<16>;
+        case 32: return (void *)sl::k_sigma3_sliced<32>;
+        case 48: return (void *)sl::k_sigma3_sliced<48>;
+        case 64: return (void *)sl::k_sigma3_sliced<64>;
+        case 80: return (void *)sl::k_sigma3_sliced<80>;
+        case 96: return (void *)sl::k_sigma3_sliced<96>;
+        default: return nullptr;
+    }
+}
+
+// Row exponents of C (stream-ordered), then sigma_3 into sig, which is
+// overwritten.  prof_slot: profiling slot of the row-exponent pass (the
+// kernel takes the next one).
+int launch_sigma3_sliced(fci_ctx *ctx, const double *C, double *sig, cudaStream_t s, int rec, int prof_slot) {
+    int kpad = 0, npad = 0, n0 = 0;
+    uint32_t smem = 0;
+    if (!sigma3_sliced_ok(ctx) || !sliced_shape(ctx, &kpad, &npad, &n0, &smem))
+        return fail(FCI_ERR_STATE, "sliced sigma_3 tables were not built for this context");
+    const SpinTables &A = ctx->A, &B = ctx->B;
+    k_row_exponents<<<ceil_div(A.ns * 32, 256), 256, 0, s>>>(C, A.ns, B.ns, ctx->rowexp);
+    FCI_CUDA(cudaGetLastError());
+    prof_mark(ctx, rec, prof_slot, s);
+    void *kern = sliced_kernel(kpad);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    FCI_CUDA(cudaStreamIsCapturing(s, &cap));
+    if (cap == cudaStreamCaptureStatusNone) FCI_CUDA(opt_in_max_smem(kern, ctx->device));
+    int nsm = 0;
+    FCI_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+    int64_t grid = nsm;  // one CTA per SM
+    if (grid > A.ns) grid = A.ns;
+    SpinTables At = A, Bt = B;
+    const uint4 *wsl = ctx->Wsl;
+    const int *rexp = ctx->rowexp;
+    int npair = ctx->npair, eW = ctx->eW;
+    void *args[] = {(void *)&C,    (void *)&sig,   (void *)&At,   (void *)&Bt, (void *)&wsl,       (void *)&rexp,
+                    (void *)&npair, (void *)&npad, (void *)&n0, (void *)&eW, (void *)&ctx->d_err};
+    FCI_CUDA(cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(sl::kThreads), args, smem, s));
+    prof_mark(ctx, rec, prof_slot + 1, s);
+    return FCI_OK;
+}
+
+}  // namespace fci

@@ -1,0 +1,439 @@
+// FP64-accurate sigma_3 (the alpha-beta term of Eq. 8) on the bf16 tensor
+// cores (tcgen05, sm_103a), for FP64 CI vectors.
+//
+// Per output alpha string I_a with replacement list a = (J_a, p_a, s_a), as in
+// the FP32 kernel (sigma_tc_kernel.cuh):
+//   G[J_b][q] = sum_a C(J_a, J_b) * s_a (q | p_a)           (contraction, K = a)
+//   sigma(I_a, I_b) = sum over beta replacements a+_k a_l |J_b> = s_b |I_b>,
+//                     pair q = {k, l}, of s_b G[J_b][q]      (scatter)
+//
+// FP64-accurate contraction from 8-bit slices (Ozaki splitting):
+//  * every C value gathered for the row is written in fixed point relative to
+//    one power of two 2^eD per alpha row (eD bounds every gathered C row, from
+//    the row exponents of a pre-pass): X = round(|C| 2^(47-eD)) with the sign,
+//    cut into six balanced 8-bit digits X = d0 2^40 + d1 2^32 + ... + d5 with
+//    |d_s| <= 128 (the low digits are centred on zero, so the products that
+//    are left out have zero mean).  Digit s is stored as the bf16 value
+//    d_s 2^(-8s), which bf16 holds exactly;
+//  * the integrals are cut the same way once per context, relative to 2^eW;
+//  * the 21 slice products s + t <= 5 run on the tensor cores with FP32
+//    accumulation in tensor memory, one accumulator per level L = s + t for
+//    L = 0, 1, 2 and one shared by L >= 3.  A level-L product is an integer
+//    times 2^(-8L) of magnitude <= 2^14, so with K <= 96 replacements every
+//    level sum stays below 2^24 units and levels 0-2 are exact; the shared
+//    accumulator rounds at 2^-24 of level 3, 2^-48 of the leading level;
+//  * the epilogue turns the four level sums of G[J_b][q] into one integer
+//    V = round(2^34 sum_L acc_L) (units 2^(eD + eW - 48)) and adds s_b V into
+//    the target's 64-bit slot of the sigma row in shared memory with an
+//    integer atomic: the adds are exact and their order does not matter, so
+//    the result is bit-reproducible;
+//  * at the end of the row the integers are converted to FP64 (integer
+//    arithmetic only, round to nearest even) and written to sigma, which this
+//    kernel overwrites.
+// Per product the representation and the products left out (s + t >= 6) are
+// below about 2^-46 of (largest gathered |C|) x (largest |(pq|rs)|).
+#pragma once
+#include "sigma_tc_kernel.cuh"
+
+namespace fci {
+namespace sl {
+
+using tc::kM;
+
+constexpr int kSlices = 6;    // 8-bit digits per FP64 operand (48 bits)
+constexpr int kThreads = 416; // warps 0-3 producers, 4-11 epilogue, 12 MMA issuer
+constexpr int kEpiThreads = 256;
+constexpr int kMaxKSteps = 6; // K <= 96
+constexpr int kBars = 2 * kMaxKSteps + 5;  // a_full[6], a_free[6], acc_full[2], acc_empty[2], drain
+
+struct Layout {
+    uint32_t bytesA, bytesB, offA, offAcc, offEa, offBar, total;
+};
+
+// Shared memory: B slices [6][npad x kpad], A slices [6][128 x kpad], the sigma
+// row as 64-bit integers [nsb], the alpha list [nsingle_a], barriers and words.
+__host__ __device__ inline Layout make_layout(int kpad, int npad, int64_t nsb, int nsingle_a) {
+    Layout L;
+    L.bytesB = (uint32_t)(npad * kpad * 2);
+    L.bytesA = (uint32_t)(kM * kpad * 2);
+    L.offA = (uint32_t)kSlices * L.bytesB;
+    L.offAcc = L.offA + (uint32_t)kSlices * L.bytesA;
+    L.offEa = L.offAcc + (uint32_t)(((nsb * 8) + 15) / 16 * 16);
+    L.offBar = L.offEa + (uint32_t)(((nsingle_a + 3) / 4) * 16);
+    L.total = L.offBar + kBars * 8 + 16;  // barriers, fail word, tmem slot, row exponent
+    return L;
+}
+
+// Fixed point of an FP64 value (raw bits lo, hi) relative to the biased row
+// exponent emax: round(|x| 2^(47 - eD)) with the sign of x, eD = emax - 1022
+// (|x| < 2^eD, so |X| <= 2^47).
+__device__ __forceinline__ long long fixed47(uint32_t lo, uint32_t hi, int emax) {
+    const int ex = (int)((hi >> 20) & 0x7FFu);
+    const int sh = emax + 6 - ex;  // >= 6 when ex <= emax
+    unsigned long long m = ((unsigned long long)((hi & 0xFFFFFu) | 0x100000u) << 32) | lo;
+    m = (ex == 0 || sh >= 60 || sh < 6) ? 0ull : ((m + (1ull << (sh - 1))) >> sh);
+    const long long X = (long long)m;
+    return (hi >> 31) ? -X : X;
+}
+
+// The six balanced digits of a fixed-point value |X| <= 2^47 as the floats
+// d_s 2^(-8s) (exact): with X' = X + 0x8080808080, d0 = X' >> 40 in
+// [-128, 128] and d_s = (byte 5-s of X') - 128 in [-128, 127].
+__device__ __forceinline__ void digits6(long long X, float (&f)[kSlices]) {
+    X += 0x8080808080ll;
+    const int h32 = (int)(X >> 32);
+    const uint32_t l32 = (uint32_t)X;
+    f[0] = __int2float_rn(h32 >> 8);
+    // byte b: 2^23 + b from a byte permute with the exponent byte 0x4B, then
+    // (2^23 + b) 2^(-8s) - (2^23 + 128) 2^(-8s) = (b - 128) 2^(-8s) in one exact FMA
+    f[1] = fmaf(__uint_as_float(__byte_perm((uint32_t)h32, 0x4B000000u, 0x7440)), 0x1p-8f, -32768.5f);
+    f[2] = fmaf(__uint_as_float(__byte_perm(l32, 0x4B000000u, 0x7443)), 0x1p-16f, -(0x1p7f + 0x1p-9f));
+    f[3] = fmaf(__uint_as_float(__byte_perm(l32, 0x4B000000u, 0x7442)), 0x1p-24f, -(0x1p-1f + 0x1p-17f));
+    f[4] = fmaf(__uint_as_float(__byte_perm(l32, 0x4B000000u, 0x7441)), 0x1p-32f, -(0x1p-9f + 0x1p-25f));
+    f[5] = fmaf(__uint_as_float(__byte_perm(l32, 0x4B000000u, 0x7440)), 0x1p-40f, -(0x1p-17f + 0x1p-33f));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+// T * 2^e2 as FP64, by integer arithmetic (round to nearest even; results
+// below the normal range flush to zero).
+__device__ __forceinline__ double scaled_i64(long long T, int e2) {
+    if (T == 0) return 0.0;
+    const unsigned long long sgn = T < 0 ? 0x8000000000000000ull : 0ull;
+    unsigned long long m = T < 0 ? (unsigned long long)(-T) : (unsigned long long)T;
+    int n = 63 - __clzll((long long)m);
+    if (n > 52) {
+        const int sh = n - 52;
+        const unsigned long long rem = m & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+        m >>= sh;
+        if (rem > half || (rem == half && (m & 1ull))) {
+            m += 1ull;
+            if (m >> 53) {
+                m >>= 1;
+                n += 1;
+            }
+        }
+    } else {
+        m <<= (52 - n);
+    }
+    const int E = n + e2 + 1023;
+    if (E <= 0) return __longlong_as_double((long long)sgn);
+    if (E >= 2047) return __longlong_as_double((long long)(sgn | 0x7FF0000000000000ull));
+    return __longlong_as_double((long long)(sgn | ((unsigned long long)E << 52) | (m & 0xFFFFFFFFFFFFFull)));
+}
+
+__device__ __forceinline__ void ld_early_u64(const double *p, uint32_t &lo, uint32_t &hi) {
+    asm volatile("ld.global.nc.v2.u32 {%0, %1}, [%2];" : "=r"(lo), "=r"(hi) : "l"(p));
+}
+
+// tensor-memory column of level L of accumulator half h
+__device__ __forceinline__ uint32_t acc_col(int h, int L, int n0, int n1) {
+    return (uint32_t)(h == 0 ? L * n0 : 4 * n0 + L * n1);
+}
+
+template <int KPAD>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_sigma3_sliced(const double *__restrict__ C, double *__restrict__ sig, SpinTables A, SpinTables B,
+                    const uint4 *__restrict__ Wsl, const int *__restrict__ rowexp, int npair, int npad, int n0,
+                    int eW, int *err) {
+    constexpr int NKS = KPAD / 16;
+    constexpr int kgroups = KPAD / 8;
+    constexpr uint32_t sbo = (uint32_t)(KPAD / 8) * 128u;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int64_t nsb = B.ns;
+    const Layout L = make_layout(KPAD, npad, nsb, A.nsingle);
+    unsigned char *sB = smem;
+    unsigned char *sA = smem + L.offA;
+    unsigned long long *sAcc = reinterpret_cast<unsigned long long *>(smem + L.offAcc);
+    uint32_t *sEa = reinterpret_cast<uint32_t *>(smem + L.offEa);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L.offBar);
+    volatile int *s_fail = reinterpret_cast<volatile int *>(smem + L.offBar + kBars * 8);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + L.offBar + kBars * 8 + 4);
+    volatile int *s_emax = reinterpret_cast<volatile int *>(smem + L.offBar + kBars * 8 + 8);
+    const uint32_t bar0 = tc::smem_u32(bars);
+    auto a_full = [&](int ks) { return bar0 + 8u * (uint32_t)ks; };
+    auto a_free = [&](int ks) { return bar0 + 8u * (uint32_t)(kMaxKSteps + ks); };
+    auto acc_full = [&](int h) { return bar0 + 8u * (uint32_t)(2 * kMaxKSteps + h); };
+    auto acc_empty = [&](int h) { return bar0 + 8u * (uint32_t)(2 * kMaxKSteps + 2 + h); };
+    const uint32_t drain = bar0 + 8u * (uint32_t)(2 * kMaxKSteps + 4);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int sa_n = A.nsingle;
+    const int n1 = npad - n0;
+    const int nh = n1 > 0 ? 2 : 1;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(tslot)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < NKS; ++i) {
+            tc::mbar_init(a_full(i), 128);
+            tc::mbar_init(a_free(i), 1);
+        }
+        for (int h = 0; h < 2; ++h) {
+            tc::mbar_init(acc_full(h), 1);
+            tc::mbar_init(acc_empty(h), kEpiThreads);
+        }
+        tc::mbar_init(drain, 1);
+        *s_fail = 0;
+    }
+    for (int64_t j = tid; j < nsb; j += kThreads) sAcc[j] = 0ull;
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tslot;
+    const int64_t ntiles = (nsb + kM - 1) / kM;
+    int64_t T = 0;  // tiles done by this CTA (barrier phases)
+
+    for (int64_t row = blockIdx.x; row < A.ns; row += gridDim.x) {
+        // ---- row set-up: alpha list, common exponent, B slices ----
+        for (int e = tid; e < sa_n; e += kThreads) sEa[e] = A.tab[(int64_t)e * A.ns + row];
+        __syncthreads();
+        if (warp == 0) {
+            int mx = 0;
+            for (int e = lane; e < sa_n; e += 32) mx = max(mx, __ldg(rowexp + ent_target(sEa[e])));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+            if (lane == 0) *s_emax = mx;
+        }
+        // B[q][a] = s_a (q | p_a): the context's integral digits, sign of the
+        // replacement applied, K-major per slice
+        for (int item = tid; item < npad * kgroups; item += kThreads) {
+            const int q = item / kgroups, kg = item % kgroups;
+            uint4 w8[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int a = kg * 8 + i;
+                uint4 w = make_uint4(0u, 0u, 0u, 0u);
+                if (q < npair && a < sa_n) {
+                    const uint32_t ea = sEa[a];
+                    w = __ldg(Wsl + (int64_t)q * npair + ent_pair(ea));
+                    if (ent_negative(ea)) {
+                        w.x ^= 0x80008000u;
+                        w.y ^= 0x80008000u;
+                        w.z ^= 0x80008000u;
+                    }
+                }
+                w8[i] = w;
+            }
+            const uint32_t off = tc::kmajor_offset(q, kg, KPAD);
+#pragma unroll
+            for (int s = 0; s < kSlices; ++s) {
+                uint32_t o[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const uint32_t x0 = s < 2 ? w8[2 * i].x : s < 4 ? w8[2 * i].y : w8[2 * i].z;
+                    const uint32_t x1 = s < 2 ? w8[2 * i + 1].x : s < 4 ? w8[2 * i + 1].y : w8[2 * i + 1].z;
+                    o[i] = __byte_perm(x0, x1, (s & 1) ? 0x7632 : 0x5410);
+                }
+                *reinterpret_cast<uint4 *>(sB + (uint32_t)s * L.bytesB + off) = make_uint4(o[0], o[1], o[2], o[3]);
+            }
+        }
+        tc::fence_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        const int emax = *s_emax;
+
+        if (warp < 4) {
+            // ---- producers: beta string 128 t + m, one K-step (16 values) at a time ----
+            const int m = tid;
+            uint32_t clo[16], chi[16], nlo[16], nhi[16];
+            auto load = [&](uint32_t(&lo)[16], uint32_t(&hi)[16], int64_t jb, int ks) {
+                const int64_t jc = jb < nsb ? jb : nsb - 1;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int a = ks * 16 + i;
+                    ld_early_u64(C + (int64_t)ent_target(sEa[a < sa_n ? a : 0]) * nsb + jc, lo[i], hi[i]);
+                }
+            };
+            load(clo, chi, m, 0);
+            for (int64_t t = 0; t < ntiles && !*s_fail; ++t) {
+                const int64_t Tt = T + t;
+                const int64_t jb = t * kM + m;
+                const bool live = jb < nsb;
+#pragma unroll
+                for (int ks = 0; ks < NKS; ++ks) {
+                    if (ks + 1 < NKS)
+                        load(nlo, nhi, jb, ks + 1);
+                    else if (t + 1 < ntiles)
+                        load(nlo, nhi, jb + kM, 0);
+                    if (Tt >= 1 && !tc::mbar_wait_bounded(a_free(ks), (uint32_t)((Tt - 1) & 1))) {
+                        *s_fail = 1;
+                        break;
+                    }
+#pragma unroll
+                    for (int g = 0; g < 2; ++g) {
+                        uint32_t w[kSlices][4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            float f0[kSlices], f1[kSlices];
+                            const int i0 = g * 8 + 2 * i, i1 = i0 + 1;
+                            const bool ok0 = live && ks * 16 + i0 < sa_n, ok1 = live && ks * 16 + i1 < sa_n;
+                            digits6(ok0 ? fixed47(clo[i0], chi[i0], emax) : 0ll, f0);
+                            digits6(ok1 ? fixed47(clo[i1], chi[i1], emax) : 0ll, f1);
+#pragma unroll
+                            for (int s = 0; s < kSlices; ++s) w[s][i] = pack_bf16(f0[s], f1[s]);
+                        }
+                        const uint32_t off = tc::kmajor_offset(m, 2 * ks + g, KPAD);
+#pragma unroll
+                        for (int s = 0; s < kSlices; ++s)
+                            *reinterpret_cast<uint4 *>(sA + (uint32_t)s * L.bytesA + off) =
+                                make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+                    }
+                    tc::fence_async_smem();
+                    tc::mbar_arrive(a_full(ks));
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        clo[i] = nlo[i];
+                        chi[i] = nhi[i];
+                    }
+                }
+            }
+        } else if (warp < 12) {
+            // ---- epilogue: lane m of the tile, 16-column chunks g, g+2, ... of each half ----
+            const int quarter = warp & 3, grp = (warp - 4) >> 2;
+            const int m = quarter * 32 + lane;
+            const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+            for (int64_t t = 0; t < ntiles; ++t) {
+                const int64_t Tt = T + t;
+                const int64_t jb = t * kM + m;
+                const bool live = jb < nsb;
+                const int64_t jc = live ? jb : nsb - 1;
+                for (int h = 0; h < nh; ++h) {
+                    const int q0 = h ? n0 : 0, nchunks = (h ? n1 : n0) / 16;
+                    uint32_t ent[16];
+                    auto prefetch = [&](int c) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            int q = q0 + c * 16 + j;
+                            q = q < npair ? q : npair - 1;
+                            ent[j] = tc::ld_early_u32(B.tabp + (int64_t)q * nsb + jc);
+                        }
+                    };
+                    if (grp < nchunks) prefetch(grp);
+                    if (!tc::mbar_wait_bounded(acc_full(h), (uint32_t)(Tt & 1))) {
+                        *s_fail = 1;
+                        break;
+                    }
+                    tc::fence_after();
+                    if (grp >= nchunks) {
+                        tc::fence_before();
+                        tc::mbar_arrive(acc_empty(h));
+                    }
+                    for (int c = grp; c < nchunks; c += 2) {
+                        uint32_t r[4][16];
+#pragma unroll
+                        for (int lv = 0; lv < 4; ++lv)
+                            asm volatile(
+                                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                                : "=r"(r[lv][0]), "=r"(r[lv][1]), "=r"(r[lv][2]), "=r"(r[lv][3]), "=r"(r[lv][4]),
+                                  "=r"(r[lv][5]), "=r"(r[lv][6]), "=r"(r[lv][7]), "=r"(r[lv][8]), "=r"(r[lv][9]),
+                                  "=r"(r[lv][10]), "=r"(r[lv][11]), "=r"(r[lv][12]), "=r"(r[lv][13]),
+                                  "=r"(r[lv][14]), "=r"(r[lv][15])
+                                : "r"(tmem + lane_base + acc_col(h, lv, n0, n1) + (uint32_t)(c * 16)));
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        if (c + 2 >= nchunks) {  // last chunk of this thread in the half: release it
+                            tc::fence_before();
+                            tc::mbar_arrive(acc_empty(h));
+                        }
+                        uint32_t en[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) en[j] = ent[j];
+                        if (c + 2 < nchunks) prefetch(c + 2);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const uint32_t e = en[j];
+                            if (!live || q0 + c * 16 + j >= npair || e == kNoEntry) continue;
+                            const uint32_t sg = e & 0x80000000u;
+                            const float a0 = __uint_as_float(r[0][j] ^ sg), a1 = __uint_as_float(r[1][j] ^ sg);
+                            const float a2 = __uint_as_float(r[2][j] ^ sg), a3 = __uint_as_float(r[3][j] ^ sg);
+                            // V = round(2^34 (acc0 + acc1 + acc2 + acc3)); levels 0-2 are
+                            // integers after their scaling, level 3+ rounds here
+                            const long long v = ((long long)__float2int_rn(a0) << 34) +
+                                                ((long long)__float2int_rn(a1 * 0x1p8f) << 26) +
+                                                ((long long)__float2int_rn(a2 * 0x1p16f) << 18) +
+                                                __float2ll_rn(a3 * 0x1p34f);
+                            atomicAdd(sAcc + (e & kTargetMask), (unsigned long long)v);
+                        }
+                    }
+                }
+                if (*s_fail) break;
+            }
+        } else if (warp == 12 && lane == 0) {
+            // ---- MMA issuer ----
+            const unsigned char *sAc = sA;
+            for (int64_t t = 0; t < ntiles; ++t) {
+                const int64_t Tt = T + t;
+                bool ok = true;
+                for (int h = 0; h < nh && ok; ++h) {
+                    if (Tt >= 1 && !tc::mbar_wait_bounded(acc_empty(h), (uint32_t)((Tt - 1) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    const int q0 = h ? n0 : 0;
+                    const uint32_t idesc = tc::instr_desc(kM, h ? n1 : n0);
+                    bool fresh[4] = {true, true, true, true};
+#pragma unroll
+                    for (int ks = 0; ks < NKS; ++ks) {
+                        if (h == 0 && !tc::mbar_wait_bounded(a_full(ks), (uint32_t)(Tt & 1))) {
+                            ok = false;
+                            break;
+                        }
+                        tc::fence_after();
+#pragma unroll
+                        for (int s = 0; s < kSlices; ++s)
+#pragma unroll
+                            for (int u = 0; u + s < kSlices; ++u) {
+                                const int lv = s + u < 3 ? s + u : 3;
+                                const uint64_t ad = tc::smem_desc(tc::smem_u32(sAc + s * L.bytesA) + ks * 256, 128, sbo);
+                                const uint64_t bd = tc::smem_desc(
+                                    tc::smem_u32(sB + u * L.bytesB) + (uint32_t)(q0 / 8) * sbo + ks * 256, 128, sbo);
+                                tc::mma_bf16(tmem + acc_col(h, lv, n0, n1), ad, bd, idesc, fresh[lv] ? 0u : 1u);
+                                fresh[lv] = false;
+                            }
+                        if (h == nh - 1) tc::mma_commit(a_free(ks));
+                    }
+                    if (!ok) break;
+                    tc::mma_commit(acc_full(h));
+                }
+                if (!ok) {
+                    *s_fail = 1;
+                    break;
+                }
+            }
+        }
+        // ---- row end: every entry of the row has been added ----
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        T += ntiles;
+        if (*s_fail) break;
+        const int e2 = emax - 1022 + eW - 48;
+        double *out = sig + row * nsb;
+        for (int64_t j = tid; j < nsb; j += kThreads) {
+            out[j] = emax == 0x7FF ? __longlong_as_double(0x7FF8000000000000ll) : scaled_i64((long long)sAcc[j], e2);
+            sAcc[j] = 0ull;
+        }
+        __syncthreads();
+    }
+    // ---- exit: wait for every MMA this CTA issued, then free tensor memory ----
+    if (warp == 12 && lane == 0) {
+        tc::mma_commit(drain);
+        if (!tc::mbar_wait_bounded(drain, 0u)) *s_fail = 1;
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (*s_fail && tid == 0) atomicExch(err, 1);
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+}
+
+}  // namespace sl
+}  // namespace fci
