@@ -40,6 +40,8 @@ WORKLOADS = {"cas14": (14, 7, 7, 100), "cas16": (16, 8, 8, 100), "cas12": (12, 6
              "cas18": (18, 9, 9, 100)}
 LARGE = {"cas18"}  # FP32 sigma only (no FP64 kernels at this size); trial vector regenerated on the device
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), nominal
+GB300_SMS = 152
+FP32_LANES_PER_SM = 128  # FP32 operations issued per SM per clock
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture of the CAS(14e,14o) workload (the summaries under profiles/ give the
@@ -441,22 +443,47 @@ def run_ours(args):
     sb = pkg.fci_query(ctx, 5)
     from paper_1707_04346_gb300 import fci as F
 
-    # algorithmic work per launch
+    # algorithmic work per launch, and the peak of the unit that bounds each kernel
     nsame = 1 + na * (norb - na) + (na * (na - 1) // 2) * ((norb - na) * (norb - na - 1) // 2)
+    peaks = load_peaks()
+    kpad = -(-sa // 16) * 16
+    npad = -(-(norb * (norb + 1) // 2) // 16) * 16
+    tiles = nsa * (-(-nsb // 128))
+    sliced_flops = 21 * 2.0 * 128 * npad * kpad * tiles
+    fp32_pipe = FP32_LANES_PER_SM * GB300_SMS * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # Tops/s
     work = {
         # diagonal replacements merged: 2 * (s_b + (s_a - n_a)(s_b - n_b + 1)) per determinant
-        "sigma3_exact": ("alu", 2.0 * (sb + (sa - na) * (sb - nb + 1)) * N, "TFLOP/s"),
-        "sigma2_cols": ("alu", 2.0 * nsame * N, "TFLOP/s"),
-        "sigma1_rows": ("alu", 2.0 * nsame * N, "TFLOP/s"),
+        "sigma3_exact": ("alu", 2.0 * (sb + (sa - na) * (sb - nb + 1)) * N, "TFLOP/s", FP64_NOMINAL_TFLOPS,
+                         "GB300 FP64 nominal 1.25 TFLOP/s (no FP64 entry in MEASURED_PEAKS.json)",
+                         "FP64 FLOP, %.0f per determinant" % (2.0 * (sb + (sa - na) * (sb - nb + 1)))),
+        # 21 bf16 slice products x 2 x 128 x npad x kpad per 128-string tile (executed MMA FLOP)
+        "sigma3_sliced": ("tensor", sliced_flops, "TFLOP/s", peaks["bf16_tflops"],
+                          "MEASURED_PEAKS.json bf16_tflops (burst; the kernel is timed in short bursts)",
+                          f"bf16 MMA FLOP: 21 slice products x 2 x 128 x {npad} x {kpad} x {tiles} tiles"),
+        # double-float: 12 FP32 operations per ELL term, nsame terms per determinant
+        "sigma1_rows": ("alu", 12.0 * nsame * N, "Tops/s", fp32_pipe,
+                        "FP32 pipe: 128 lanes x 152 SMs x max SM clock",
+                        f"FP32 operations: 12 per term x {nsame} terms per determinant"),
+        "sigma2_cols": ("alu", 12.0 * nsame * N, "Tops/s", fp32_pipe,
+                        "FP32 pipe: 128 lanes x 152 SMs x max SM clock",
+                        f"FP32 operations: 12 per term x {nsame} terms per determinant"),
+        "row_exponents": ("hbm", 8.0 * N, "GB/s", peaks["hbm_gbs"], "MEASURED_PEAKS.json hbm_gbs",
+                          "bytes: one read of C"),
     }
-    bound, flops, unit = work[names[top]]
-    achieved = flops / kmean[top] / 1e12
-    peaks = load_peaks()
-    roof = {"kernel": names[top], "bound": bound, "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": unit,
-            "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": ncu_traffic(names[top], args.workload),
-            "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s (no FP64 entry in MEASURED_PEAKS.json)",
-            "work_per_launch": f"{flops:.4g} FLOP ({flops / N:.0f} per determinant x {N} determinants)",
-            "kernels": {n: {"ms": float(kmean[i] * 1e3), "share": float(kshare[i])} for i, n in enumerate(names)}}
+    def roofline_of(i):
+        bound, amount, unit, peak, src, what = work[names[i]]
+        scale = 1e9 if unit == "GB/s" else 1e12
+        ach = amount / kmean[i] / scale
+        return {"kernel": names[i], "bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+                "traffic": ncu_traffic(names[i], args.workload), "peak_source": src,
+                "work_per_launch": f"{amount:.4g} ({what})"}
+    roof = roofline_of(top)
+    roof["kernels"] = {n: {"ms": float(kmean[i] * 1e3), "share": float(kshare[i]),
+                           "frac": roofline_of(i)["frac"], "unit": work[n][2]} for i, n in enumerate(names)}
+    if "sigma3_sliced" in names:
+        i3 = names.index("sigma3_sliced")
+        exact_sparse = 2.0 * sa * sb * N  # 2 s^2 FLOP per determinant (the method's exact-sparse count)
+        roof["sigma3_sliced_exact_sparse_equivalent_tflops"] = exact_sparse / kmean[i3] / 1e12
 
     # FP32 sigma (sigma_3 on the tensor cores, split-BF16x6 by default)
     v32 = [v.float() for v in vecs]

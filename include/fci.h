@@ -82,27 +82,33 @@ typedef struct fci_options {
                             tensor cores (Eq. 8's E_ij E_kl as a pair-matrix contraction):
                             0 = only when the staged same-spin kernels do not fit in shared
                             memory (default), 1 = always */
-    int f64_sigma3;      /* FCI_F64 sigma_3 kernel: FCI_F64_SIGMA3_AUTO (default: the sliced
-                            tensor-core kernel where the space fits it, else the exact kernel),
-                            FCI_F64_SIGMA3_EXACT (FP64 fused multiply-adds only), or
-                            FCI_F64_SIGMA3_SLICED (fci_init fails with FCI_ERR_ARG where it
-                            does not fit) */
+    int f64_kernels;     /* FCI_F64 sigma kernels: FCI_F64_AUTO (default), FCI_F64_FMA or
+                            FCI_F64_SLICED, below */
 } fci_options;
 
-/* fci_options.f64_sigma3.  The sliced kernel computes sigma_3 to FP64 accuracy
- * on the bf16 tensor cores: C and the integrals are written as 48-bit fixed
- * point (C relative to one power of two per alpha row, the integrals to one
- * per context), cut into six 8-bit slices that bf16 holds exactly, and the 21
- * slice products of total weight <= 5 are accumulated per weight in FP32
- * (exact for weights 0-2); the scatter into sigma adds integers, so the result
- * does not depend on the order of the adds.  Error per alpha-row entry below
- * about 2^-45 of (largest gathered |C|) x (largest |(pq|rs)|) x n_single;
- * limits: at most 128 orbital pairs (norb <= 15), 96 alpha replacements, and
- * the sigma row (8 N_beta bytes) plus 12 (128 + npair) K bytes of operands in
- * shared memory (CAS(14,14) fits; CAS(16,16) does not). */
-#define FCI_F64_SIGMA3_AUTO 0
-#define FCI_F64_SIGMA3_EXACT 1
-#define FCI_F64_SIGMA3_SLICED 2
+/* fci_options.f64_kernels: how the FCI_F64 sigma is computed.  All modes meet
+ * the FP64 accuracy of Eq. 4-8's direct sum (the tests hold each to the same
+ * 1e-12 bars).
+ *  FCI_F64_FMA     FP64 fused multiply-adds throughout (GB300's FP64 pipe).
+ *  FCI_F64_AUTO    sigma_3 on the bf16 tensor cores from 8-bit slices where the
+ *                  space fits the sliced kernel, else FP64 FMAs; sigma_1 and
+ *                  sigma_2 in double-float FP32 arithmetic (each FP64 value as
+ *                  two FP32 parts, 48 significant bits; error-free products and
+ *                  sums to within a few units of 2^-48).
+ *  FCI_F64_SLICED  as AUTO, but fci_init fails with FCI_ERR_ARG where the
+ *                  sliced kernel does not fit.
+ * The sliced sigma_3 writes C and the integrals as 47-bit fixed point (C
+ * relative to one power of two per alpha row, the integrals to one per
+ * context), cuts them into six balanced 8-bit digits that bf16 holds exactly,
+ * and accumulates the 21 digit products of weight <= 5 per weight in FP32
+ * (exact for weights 0-2); its scatter into sigma adds 64-bit integers, so
+ * its result does not depend on the order of the adds.  Limits: at most 128
+ * orbital pairs (norb <= 15), 96 alpha replacements, and the sigma row (8
+ * N_beta bytes) plus 12 (128 + npair) K bytes of operands in shared memory
+ * (CAS(14,14) fits; CAS(16,16) does not). */
+#define FCI_F64_AUTO 0
+#define FCI_F64_FMA 1
+#define FCI_F64_SLICED 2
 
 /* Fill *opt with the defaults listed above. */
 void fci_default_options(fci_options *opt);

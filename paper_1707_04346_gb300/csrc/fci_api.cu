@@ -116,7 +116,7 @@ void fci_default_options(fci_options *opt) {
     opt->symmetry_tol = 1e-10;
     opt->f32_splits = 3;
     opt->same_spin_tc = 0;
-    opt->f64_sigma3 = FCI_F64_SIGMA3_AUTO;
+    opt->f64_kernels = FCI_F64_AUTO;
 }
 
 const char *fci_last_error(void) { return g_last_error.c_str(); }
@@ -142,8 +142,8 @@ int fci_init(fci_ctx **out, int norb, int nalpha, int nbeta, const double *h1, c
     if (o.precision != FCI_PREC_FP64 && o.precision != FCI_PREC_MIXED) return fail(FCI_ERR_ARG, "unknown precision");
     if (o.f32_splits != 2 && o.f32_splits != 3) return fail(FCI_ERR_ARG, "f32_splits must be 2 or 3");
     if (o.same_spin_tc != 0 && o.same_spin_tc != 1) return fail(FCI_ERR_ARG, "same_spin_tc must be 0 or 1");
-    if (o.f64_sigma3 < FCI_F64_SIGMA3_AUTO || o.f64_sigma3 > FCI_F64_SIGMA3_SLICED)
-        return fail(FCI_ERR_ARG, "f64_sigma3 must be FCI_F64_SIGMA3_AUTO, _EXACT or _SLICED");
+    if (o.f64_kernels < FCI_F64_AUTO || o.f64_kernels > FCI_F64_SLICED)
+        return fail(FCI_ERR_ARG, "f64_kernels must be FCI_F64_AUTO, FCI_F64_FMA or FCI_F64_SLICED");
     if (int rc = check_integrals(norb, h1, eri, o.symmetry_tol)) return rc;
 
     fci_ctx *ctx = new (std::nothrow) fci_ctx();

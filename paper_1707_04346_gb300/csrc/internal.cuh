@@ -57,7 +57,8 @@ struct SpinTables {
     double *wdiag = nullptr;   // [npair][ns]: sum over occupied l of (p | ll)
     int32_t *gcol = nullptr;   // [nsame][ns] same-spin Hamiltonian columns (ELL)
     double *gval = nullptr;    // [nsame][ns]
-    float *gvalf = nullptr;    // [nsame][ns] FP32 copy
+    float *gvalf = nullptr;    // [nsame][ns] FP32 copy (the leading part of the double-float pair)
+    float *gvall = nullptr;    // [nsame][ns] fl(gval - gvalf): the trailing part of the double-float pair
     // Tile schedule of the replacement lists for the tensor-core sigma_3
     // (strings in tiles of kTileStrings): the entries of tile t's strings,
     // grouped by target, each target's run dealt whole to one of kTileStrings

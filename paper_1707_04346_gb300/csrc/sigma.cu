@@ -118,6 +118,113 @@ __global__ void __launch_bounds__(512) k_sigma2_cols(const T *__restrict__ C, T 
     }
 }
 
+// ---- FP64 same-spin terms in double-float arithmetic ----
+// GB300 issues FP32 operations 64 times faster than FP64 ones, so the FP64
+// sigma_1 and sigma_2 carry every FP64 value x as the FP32 pair
+// (h, l) = (fl(x), fl(x - h)), 48 significant bits.  A term v c is formed as
+// h_v h_c exactly (the product and its rounding error, recovered by an FMA)
+// plus the cross terms h_v l_c + l_v h_c (l_v l_c, below 2^-48 of the term, is
+// left out), and added to the running pair (s_h, s_l) by TwoSum: twelve FP32
+// operations per term, exact in s_h + s_l up to the FP32 roundings of the
+// low-order parts, i.e. within a few units of 2^-48 of sum |terms|.
+__device__ __forceinline__ float2 df_split(double x) {
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - (double)h));
+}
+
+__device__ __forceinline__ void df_mac(float vh, float vl, float2 c, float &sh, float &sl) {
+    const float ph = vh * c.x;
+    const float pl = fmaf(vh, c.y, fmaf(vl, c.x, fmaf(vh, c.x, -ph)));
+    const float t = sh + ph;
+    const float bp = t - sh;
+    sl += ((sh - (t - bp)) + (ph - bp)) + pl;
+    sh = t;
+}
+
+constexpr int kEntDF = 4;  // ELL entries whose table loads are issued together (double-float kernels)
+
+// sigma_1 in double-float: R rows of C staged as pairs; sigma overwritten or
+// (add != 0) added to.
+template <int R>
+__global__ void __launch_bounds__(512) k_sigma1_rows_df(const double *__restrict__ C, double *__restrict__ sig,
+                                                        SpinTables B, int64_t nsa, int add) {
+    extern __shared__ float2 rows2[];  // [R][nsb]
+    const int64_t nsb = B.ns;
+    const int64_t r0 = (int64_t)blockIdx.x * R;
+    for (int64_t t = threadIdx.x; t < (int64_t)R * nsb; t += blockDim.x) {
+        const int64_t r = t / nsb, j = t % nsb;
+        rows2[t] = (r0 + r < nsa) ? df_split(C[(r0 + r) * nsb + j]) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int64_t ib = threadIdx.x; ib < nsb; ib += blockDim.x) {
+        float sh[R], sl[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) sh[r] = sl[r] = 0.f;
+        for (int e0 = 0; e0 < B.nsame; e0 += kEntDF) {
+            int32_t col[kEntDF];
+            float vh[kEntDF], vl[kEntDF];
+#pragma unroll
+            for (int u = 0; u < kEntDF; ++u) {
+                const bool ok = e0 + u < B.nsame;
+                const int64_t idx = (int64_t)(ok ? e0 + u : 0) * nsb + ib;
+                col[u] = ok ? B.gcol[idx] : 0;
+                vh[u] = ok ? B.gvalf[idx] : 0.f;
+                vl[u] = ok ? B.gvall[idx] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < kEntDF; ++u)
+#pragma unroll
+                for (int r = 0; r < R; ++r) df_mac(vh[u], vl[u], rows2[(int64_t)r * nsb + col[u]], sh[r], sl[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (r0 + r < nsa) {
+                const int64_t o = (r0 + r) * nsb + ib;
+                const double v = (double)sh[r] + (double)sl[r];
+                sig[o] = add ? sig[o] + v : v;
+            }
+    }
+}
+
+// sigma_2 in double-float: R beta columns of C staged as pairs; adds to sigma.
+template <int R>
+__global__ void __launch_bounds__(512) k_sigma2_cols_df(const double *__restrict__ C, double *__restrict__ sig,
+                                                        SpinTables A, int64_t nsb) {
+    extern __shared__ float2 cols2[];  // [R][nsa]
+    const int64_t nsa = A.ns;
+    const int64_t c0 = (int64_t)blockIdx.x * R;
+    for (int64_t ia = threadIdx.x; ia < nsa; ia += blockDim.x) {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            cols2[(int64_t)r * nsa + ia] = (c0 + r < nsb) ? df_split(C[ia * nsb + c0 + r]) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int64_t ia = threadIdx.x; ia < nsa; ia += blockDim.x) {
+        float sh[R], sl[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) sh[r] = sl[r] = 0.f;
+        for (int e0 = 0; e0 < A.nsame; e0 += kEntDF) {
+            int32_t col[kEntDF];
+            float vh[kEntDF], vl[kEntDF];
+#pragma unroll
+            for (int u = 0; u < kEntDF; ++u) {
+                const bool ok = e0 + u < A.nsame;
+                const int64_t idx = (int64_t)(ok ? e0 + u : 0) * nsa + ia;
+                col[u] = ok ? A.gcol[idx] : 0;
+                vh[u] = ok ? A.gvalf[idx] : 0.f;
+                vl[u] = ok ? A.gvall[idx] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < kEntDF; ++u)
+#pragma unroll
+                for (int r = 0; r < R; ++r) df_mac(vh[u], vl[u], cols2[(int64_t)r * nsa + col[u]], sh[r], sl[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (c0 + r < nsb) sig[ia * nsb + c0 + r] += (double)sh[r] + (double)sl[r];
+    }
+}
+
 // FP32 sigma_1 + sigma_2 in one pass when both spins share one string space
 // (n_alpha = n_beta, identical same-spin tables): a block stages R rows and
 // the same R columns of C, and every ELL entry it reads updates both,
@@ -301,7 +408,7 @@ static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s) {
     static const char *const names2[2] = {"sigma12_f32", "sigma3_tc"};
     static const char *const names4[4] = {"row_exponents", "sigma3_sliced", "sigma1_rows", "sigma2_cols"};
     // FP64 with the sliced tensor-core sigma_3: it runs first and overwrites sigma
-    const bool sliced = sizeof(T) == 8 && A.nsingle > 0 && B.nsingle > 0 && ctx->opt.f64_sigma3 != FCI_F64_SIGMA3_EXACT &&
+    const bool sliced = sizeof(T) == 8 && A.nsingle > 0 && B.nsingle > 0 && ctx->opt.f64_kernels != FCI_F64_FMA &&
                         sigma3_sliced_ok(ctx);
     const int rec = sliced ? prof_begin(ctx, s, 4, names4)
                     : same_tc ? prof_begin(ctx, s, 3, names3tc)
@@ -351,8 +458,11 @@ static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s) {
             const int R = pick_r(nsb);
             if (!R) return fail(FCI_ERR_ARG, "beta string count too large for the sigma_1 kernel");
             const size_t sm = (size_t)R * nsb * sizeof(T);
-            void *k = R == 8 ? (void *)k_sigma1_rows<T, 8> : R == 4 ? (void *)k_sigma1_rows<T, 4>
-                    : R == 2 ? (void *)k_sigma1_rows<T, 2> : (void *)k_sigma1_rows<T, 1>;
+            void *k = (sizeof(T) == 8 && ctx->opt.f64_kernels != FCI_F64_FMA)
+                          ? (R == 8 ? (void *)k_sigma1_rows_df<8> : R == 4 ? (void *)k_sigma1_rows_df<4>
+                             : R == 2 ? (void *)k_sigma1_rows_df<2> : (void *)k_sigma1_rows_df<1>)
+                          : (R == 8 ? (void *)k_sigma1_rows<T, 8> : R == 4 ? (void *)k_sigma1_rows<T, 4>
+                             : R == 2 ? (void *)k_sigma1_rows<T, 2> : (void *)k_sigma1_rows<T, 1>);
             FCI_CUDA(opt_in_max_smem(k, ctx->device));
             int64_t nsa_ = nsa;
             SpinTables Bt = B;
@@ -364,8 +474,11 @@ static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s) {
             const int R = pick_r(nsa);
             if (!R) return fail(FCI_ERR_ARG, "alpha string count too large for the sigma_2 kernel");
             const size_t sm = (size_t)R * nsa * sizeof(T);
-            void *k = R == 8 ? (void *)k_sigma2_cols<T, 8> : R == 4 ? (void *)k_sigma2_cols<T, 4>
-                    : R == 2 ? (void *)k_sigma2_cols<T, 2> : (void *)k_sigma2_cols<T, 1>;
+            void *k = (sizeof(T) == 8 && ctx->opt.f64_kernels != FCI_F64_FMA)
+                          ? (R == 8 ? (void *)k_sigma2_cols_df<8> : R == 4 ? (void *)k_sigma2_cols_df<4>
+                             : R == 2 ? (void *)k_sigma2_cols_df<2> : (void *)k_sigma2_cols_df<1>)
+                          : (R == 8 ? (void *)k_sigma2_cols<T, 8> : R == 4 ? (void *)k_sigma2_cols<T, 4>
+                             : R == 2 ? (void *)k_sigma2_cols<T, 2> : (void *)k_sigma2_cols<T, 1>);
             FCI_CUDA(opt_in_max_smem(k, ctx->device));
             int64_t nsb_ = nsb;
             SpinTables At = A;

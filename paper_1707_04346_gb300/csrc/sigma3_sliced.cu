@@ -60,9 +60,9 @@ bool sigma3_sliced_ok(const fci_ctx *ctx) { return ctx->Wsl != nullptr && ctx->B
 int build_sliced_tables(fci_ctx *ctx, const double *eri_host) {
     int kpad = 0, npad = 0, n0 = 0;
     uint32_t smem = 0;
-    if (ctx->opt.f64_sigma3 == FCI_F64_SIGMA3_EXACT || !sliced_shape(ctx, &kpad, &npad, &n0, &smem)) {
-        if (ctx->opt.f64_sigma3 == FCI_F64_SIGMA3_SLICED)
-            return fail(FCI_ERR_ARG, "f64_sigma3 = sliced: the space exceeds the sliced kernel's limits "
+    if (ctx->opt.f64_kernels == FCI_F64_FMA || !sliced_shape(ctx, &kpad, &npad, &n0, &smem)) {
+        if (ctx->opt.f64_kernels == FCI_F64_SLICED)
+            return fail(FCI_ERR_ARG, "f64_kernels = FCI_F64_SLICED: the space exceeds the sliced kernel's limits "
                                      "(at most 128 orbital pairs, 96 alpha replacements, shared memory)");
         return FCI_OK;
     }

@@ -238,6 +238,12 @@ __global__ void k_f64_to_f32(const double *a, float *b, int64_t n) {
     if (t < n) b[t] = (float)a[t];
 }
 
+// Trailing FP32 part of the double-float pair of each value: fl(a - fl(a)).
+__global__ void k_f64_lo(const double *a, float *lo, int64_t n) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < n) lo[t] = (float)(a[t] - (double)(float)a[t]);
+}
+
 static int64_t host_binom(int n, int k) {
     if (k < 0 || k > n) return 0;
     int64_t r = 1;
@@ -348,6 +354,7 @@ static int build_spin(fci_ctx *ctx, SpinTables &T, int ne) {
     T.gcol = (int32_t *)dalloc(ctx, sizeof(int32_t) * ns * T.nsame, &rc);
     T.gval = (double *)dalloc(ctx, sizeof(double) * ns * T.nsame, &rc);
     T.gvalf = (float *)dalloc(ctx, sizeof(float) * ns * T.nsame, &rc);
+    T.gvall = (float *)dalloc(ctx, sizeof(float) * ns * T.nsame, &rc);
     if (rc) return rc;
     cudaStream_t s = ctx->stream;
     k_unrank<<<ceil_div(ns, 256), 256, 0, s>>>(T.str, ns, n, ne);
@@ -362,6 +369,8 @@ static int build_spin(fci_ctx *ctx, SpinTables &T, int ne) {
     k_same_spin_rows<<<ceil_div(ns, 64), 64, 0, s>>>(T.str, ns, n, ne, T.nsame, ctx->h1, ctx->eri, T.gcol, T.gval);
     FCI_CUDA(cudaGetLastError());
     k_f64_to_f32<<<ceil_div(ns * T.nsame, 256), 256, 0, s>>>(T.gval, T.gvalf, ns * T.nsame);
+    FCI_CUDA(cudaGetLastError());
+    k_f64_lo<<<ceil_div(ns * T.nsame, 256), 256, 0, s>>>(T.gval, T.gvall, ns * T.nsame);
     FCI_CUDA(cudaGetLastError());
     return build_tile_schedule(ctx, T);
 }
@@ -431,6 +440,7 @@ static void free_spin(fci_ctx *ctx, SpinTables &T) {
     dfree(ctx, T.gcol, sizeof(int32_t) * T.ns * T.nsame);
     dfree(ctx, T.gval, sizeof(double) * T.ns * T.nsame);
     dfree(ctx, T.gvalf, sizeof(float) * T.ns * T.nsame);
+    dfree(ctx, T.gvall, sizeof(float) * T.ns * T.nsame);
     if (T.tsched) {
         dfree(ctx, T.tsched, sizeof(uint32_t) * T.nsched);
         dfree(ctx, T.toff, sizeof(int32_t) * ((T.ns + kTileStrings - 1) / kTileStrings + 1));

@@ -1,9 +1,10 @@
-"""GPU parity of the FP64 sigma with the sliced tensor-core sigma_3
-(fci_options.f64_sigma3 = FCI_F64_SIGMA3_SLICED) against the CPU oracle.
-
-The sliced kernel computes sigma_3 from six 8-bit slices of C and of the
-integrals on the bf16 tensor cores and adds integers in its scatter, so the
-same bars as the exact FP64 kernel apply:
+"""GPU parity of the FP64 sigma kernels against the CPU oracle, in both
+kernel families (fci_options.f64_kernels):
+* FCI_F64_SLICED: sigma_3 from six 8-bit slices of C and of the integrals on
+  the bf16 tensor cores (an integer scatter), sigma_1 and sigma_2 in
+  double-float FP32 arithmetic;
+* FCI_F64_FMA: FP64 fused multiply-adds throughout.
+Both are held to the same bars:
 * per element on small spaces: |d sigma_I| <= 1e-12 * sum_J |H_IJ||c_J|;
 * normwise elsewhere: max|d sigma| <= 1e-12 * max|sigma|;
 and the result is bit-reproducible (integer adds in any order).
@@ -17,7 +18,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 DEV = "cuda:0"
-EXACT, SLICED = 1, 2
+FMA, SLICED = 1, 2
 
 
 @pytest.fixture(scope="module")
@@ -34,7 +35,7 @@ def pkg():
 
 def ctx_for(pkg, norb, na, nb, mode, rank=40, seed=1707):
     h1, eri = fi.make_integrals(norb, rank, seed)
-    return pkg.fci_init(norb, na, nb, h1, eri, pkg.default_options(f64_sigma3=mode)), h1, eri
+    return pkg.fci_init(norb, na, nb, h1, eri, pkg.default_options(f64_kernels=mode)), h1, eri
 
 
 def sigma(pkg, ctx, c):
@@ -51,9 +52,10 @@ SPACES = [(2, 1, 1), (3, 1, 2), (4, 2, 2), (5, 2, 3), (6, 3, 3), (6, 4, 2), (7, 
           (9, 4, 5), (5, 5, 5), (6, 5, 1), (10, 1, 9)]
 
 
+@pytest.mark.parametrize("mode", [SLICED, FMA])
 @pytest.mark.parametrize("norb,na,nb", SPACES)
-def test_sliced_elementwise_small(pkg, oracle_mod, norb, na, nb):
-    ctx, h1, eri = ctx_for(pkg, norb, na, nb, SLICED)
+def test_sliced_elementwise_small(pkg, oracle_mod, norb, na, nb, mode):
+    ctx, h1, eri = ctx_for(pkg, norb, na, nb, mode)
     H = oracle_mod.hamiltonian(norb, na, nb, h1, eri)
     for kind in ("random", "uniform"):
         c = fi.make_vector(H.shape[0], kind=kind)
@@ -74,12 +76,13 @@ def test_sliced_full_vectors(pkg, oracle_mod, norb, na, nb):
     pkg.fci_free(ctx)
 
 
-def test_sliced_equals_exact_kernel_and_is_reproducible(pkg):
-    """Both FP64 sigma_3 kernels on the same vector agree to the FP64 bar,
-    and two sliced calls give identical bits."""
+def test_sliced_equals_fma_kernels_and_is_reproducible(pkg):
+    """The two FP64 kernel families on the same vector agree to the FP64 bar,
+    and two calls of the sliced family give identical bits (the double-float
+    same-spin kernels sum in a fixed order; the sliced scatter adds integers)."""
     norb, na, nb = 12, 6, 6
     c_s, _, _ = ctx_for(pkg, norb, na, nb, SLICED, rank=100)
-    c_e, _, _ = ctx_for(pkg, norb, na, nb, EXACT, rank=100)
+    c_e, _, _ = ctx_for(pkg, norb, na, nb, FMA, rank=100)
     c = fi.make_vector(c_s.ndet)
     a = sigma(pkg, c_s, c)
     b = sigma(pkg, c_s, c)
@@ -117,8 +120,8 @@ def test_sliced_cas14_sampled_rows(pkg, oracle_mod):
 
 
 def test_sliced_nan_input_propagates(pkg):
-    """A non-finite C value reaches sigma as NaN (the rows whose sigma_3
-    gathers it), as with the exact kernel."""
+    """A non-finite C value reaches sigma as NaN or infinity (the rows whose
+    sigma_3 gathers it), as with the FMA kernels."""
     norb, na, nb = 8, 4, 4
     ctx, _, _ = ctx_for(pkg, norb, na, nb, SLICED)
     c = fi.make_vector(ctx.ndet)
@@ -132,5 +135,5 @@ def test_sliced_nan_input_propagates(pkg):
 def test_sliced_refused_where_it_does_not_fit(pkg):
     h1, eri = fi.make_integrals(16, 10)
     with pytest.raises(pkg.FciError) as ei:
-        pkg.fci_init(16, 8, 8, h1, eri, pkg.default_options(f64_sigma3=SLICED))
+        pkg.fci_init(16, 8, 8, h1, eri, pkg.default_options(f64_kernels=SLICED))
     assert ei.value.code == pkg.fci.FCI_ERR_ARG
