@@ -467,8 +467,9 @@ def run_ours(args):
         "sigma2_cols": ("alu", 12.0 * nsame * N, "Tops/s", fp32_pipe,
                         "FP32 pipe: 128 lanes x 152 SMs x max SM clock",
                         f"FP32 operations: 12 per term x {nsame} terms per determinant"),
-        "row_exponents": ("hbm", 8.0 * N, "GB/s", peaks["hbm_gbs"], "MEASURED_PEAKS.json hbm_gbs",
-                          "bytes: one read of C"),
+        # row exponents (one read of C) and the digit slices (a read of C, 12 bytes written)
+        "slice_c": ("hbm", 28.0 * N, "GB/s", peaks["hbm_gbs"], "MEASURED_PEAKS.json hbm_gbs",
+                    "bytes: two reads of C (8 + 8 per determinant) and 12 written"),
     }
     def roofline_of(i):
         bound, amount, unit, peak, src, what = work[names[i]]

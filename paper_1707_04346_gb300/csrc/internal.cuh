@@ -94,9 +94,14 @@ struct fci_ctx {
     float *Wf = nullptr;
     float *kf = nullptr;            // [npair] k_kl = h_kl - 1/2 sum_j (kj|jl), FP32 (same-spin tensor-core path)
     float *ws32 = nullptr;          // [2][ndet] FP32 workspace of that path (allocated on first use)
-    uint4 *Wsl = nullptr;           // [npair][npair] six bf16 digit slices of W (FP64 sliced sigma_3)
+    // FP64 sliced sigma_3 (sigma3_sliced.cu): fixed-point integrals, the
+    // per-call row exponents of C and its six bf16 digit slices (slices 0-3
+    // and 4-5 as two planes, 12 bytes per determinant)
+    long long *XW = nullptr;        // [npair][npair] round(W 2^(47 - eW))
     int eW = 0;                     // |W| < 2^eW
-    int *rowexp = nullptr;          // [max(N_alpha, N_beta)] row exponents of C (per FP64 sliced sigma_3 call)
+    int *rowexp = nullptr;          // [N_alpha]
+    uint2 *cs0123 = nullptr;        // [ndet]
+    uint32_t *cs45 = nullptr;       // [ndet]
     double *hdiag = nullptr;        // [ndet]
     int *d_err = nullptr;           // device error word (bounded waits that gave up)
     size_t bytes = 0;

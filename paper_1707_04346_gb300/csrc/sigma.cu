@@ -406,7 +406,7 @@ static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s) {
     static const char *const names3[3] = {"sigma1_rows", "sigma2_cols", sizeof(T) == 4 ? "sigma3_tc" : "sigma3_exact"};
     static const char *const names3tc[3] = {"sigma2_tc", "sigma1_tc", "sigma3_tc"};
     static const char *const names2[2] = {"sigma12_f32", "sigma3_tc"};
-    static const char *const names4[4] = {"row_exponents", "sigma3_sliced", "sigma1_rows", "sigma2_cols"};
+    static const char *const names4[4] = {"slice_c", "sigma3_sliced", "sigma1_rows", "sigma2_cols"};
     // FP64 with the sliced tensor-core sigma_3: it runs first and overwrites sigma
     const bool sliced = sizeof(T) == 8 && A.nsingle > 0 && B.nsingle > 0 && ctx->opt.f64_kernels != FCI_F64_FMA &&
                         sigma3_sliced_ok(ctx);

@@ -36,10 +36,24 @@ __global__ void k_pair_table(const uint32_t *__restrict__ tab, int64_t ns, int n
     tabp[(int64_t)ent_pair(v) * ns + x] = v;
 }
 
+// Six bf16 digit slices of every C value, relative to its row's exponent:
+// slices 0-3 to cs0123, 4-5 to cs45 (d_s 2^(-8s), d_s balanced 8-bit digits of
+// round(|C| 2^(47 - e_row)) with the sign).
+__global__ void k_slice_c(const double *__restrict__ C, const int *__restrict__ rowexp, int64_t nrows, int64_t ncols,
+                          uint2 *__restrict__ cs0123, uint32_t *__restrict__ cs45) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nrows * ncols) return;
+    const unsigned long long b = __double_as_longlong(__ldg(C + t));
+    float f[sl::kSlices];
+    sl::digits6(sl::fixed47((uint32_t)b, (uint32_t)(b >> 32), __ldg(rowexp + t / ncols)), f);
+    cs0123[t] = make_uint2(sl::pack_bf16(f[0], f[1]), sl::pack_bf16(f[2], f[3]));
+    cs45[t] = sl::pack_bf16(f[4], f[5]);
+}
+
 // Sizes of the sliced kernel for this context; false when it does not apply.
 static bool sliced_shape(const fci_ctx *ctx, int *kpad, int *npad, int *n0, uint32_t *smem) {
     const SpinTables &A = ctx->A, &B = ctx->B;
-    if (A.nsingle == 0 || B.nsingle == 0) return false;
+    if (A.nsingle == 0 || B.nsingle == 0 || A.nsingle > sl::kMaxK) return false;
     *kpad = round_up16(A.nsingle);
     *npad = round_up16(ctx->npair);
     if (*kpad > 16 * sl::kMaxKSteps || *npad > 128 || B.ns > kMaxStrings) return false;
@@ -51,19 +65,19 @@ static bool sliced_shape(const fci_ctx *ctx, int *kpad, int *npad, int *n0, uint
     return (int)*smem <= lim;
 }
 
-bool sigma3_sliced_ok(const fci_ctx *ctx) { return ctx->Wsl != nullptr && ctx->B.tabp != nullptr; }
+bool sigma3_sliced_ok(const fci_ctx *ctx) { return ctx->XW != nullptr && ctx->B.tabp != nullptr; }
 
-// Build, once per context: the integral digits Wsl (six bf16 slices of the
-// pair matrix relative to 2^eW, padded to 8 halves per element), the
-// pair-major beta table and the row-exponent buffer.  Contexts whose shapes
-// the kernel does not cover get none of them (the exact FP64 kernel runs).
+// Build, once per context: the fixed-point integrals XW = round(W 2^(47 - eW))
+// (|W| < 2^eW), the pair-major beta table, and the buffers of the per-call
+// pre-pass (row exponents, the C digit planes: 4 + 12 N bytes).  Contexts whose
+// shapes the kernel does not cover get none of them (the FMA kernel runs).
 int build_sliced_tables(fci_ctx *ctx, const double *eri_host) {
     int kpad = 0, npad = 0, n0 = 0;
     uint32_t smem = 0;
     if (ctx->opt.f64_kernels == FCI_F64_FMA || !sliced_shape(ctx, &kpad, &npad, &n0, &smem)) {
         if (ctx->opt.f64_kernels == FCI_F64_SLICED)
             return fail(FCI_ERR_ARG, "f64_kernels = FCI_F64_SLICED: the space exceeds the sliced kernel's limits "
-                                     "(at most 128 orbital pairs, 96 alpha replacements, shared memory)");
+                                     "(at most 128 orbital pairs, 85 alpha replacements, shared memory)");
         return FCI_OK;
     }
     const int n = ctx->norb, np = ctx->npair;
@@ -80,28 +94,18 @@ int build_sliced_tables(fci_ctx *ctx, const double *eri_host) {
                 }
     int eW = 0;
     if (wmax > 0) std::frexp(wmax, &eW);  // wmax < 2^eW
-    // X = round(W 2^(47 - eW)), |X| <= 2^47; balanced digits of X' = X + 0x8080808080:
-    // d0 = X' >> 40 in [-128, 128], d_s = (byte 5-s of X') - 128 (as in the kernel's digits6)
-    std::vector<uint16_t> sl((size_t)np * np * 8, 0);
-    for (size_t e = 0; e < W.size(); ++e) {
-        const long long X = std::llrint(std::ldexp(W[e], 47 - eW)) + 0x8080808080ll;
-        for (int s = 0; s < sl::kSlices; ++s) {
-            const long long d = s == 0 ? (X >> 40) : ((X >> (40 - 8 * s)) & 255) - 128;
-            const float f = std::ldexp((float)d, -8 * s);  // exact: at most 8 significant bits
-            uint32_t b;
-            std::memcpy(&b, &f, 4);
-            sl[e * 8 + s] = (uint16_t)(b >> 16);  // bf16 of an exactly representable value
-        }
-    }
+    std::vector<long long> xw(W.size());
+    for (size_t e = 0; e < W.size(); ++e) xw[e] = std::llrint(std::ldexp(W[e], 47 - eW));  // |xw| <= 2^47
     int rc = FCI_OK;
-    ctx->Wsl = (uint4 *)dalloc(ctx, sizeof(uint4) * (size_t)np * np, &rc);
-    const int64_t nrow = ctx->A.ns > ctx->B.ns ? ctx->A.ns : ctx->B.ns;
-    ctx->rowexp = (int *)dalloc(ctx, sizeof(int) * (size_t)nrow, &rc);
+    ctx->XW = (long long *)dalloc(ctx, sizeof(long long) * (size_t)np * np, &rc);
+    ctx->rowexp = (int *)dalloc(ctx, sizeof(int) * (size_t)ctx->A.ns, &rc);
+    ctx->cs0123 = (uint2 *)dalloc(ctx, sizeof(uint2) * (size_t)ctx->ndet, &rc);
+    ctx->cs45 = (uint32_t *)dalloc(ctx, sizeof(uint32_t) * (size_t)ctx->ndet, &rc);
     SpinTables &B = ctx->B;
     B.tabp = (uint32_t *)dalloc(ctx, sizeof(uint32_t) * (size_t)np * B.ns, &rc);
     if (rc) return rc;
     ctx->eW = eW;
-    FCI_CUDA(cudaMemcpyAsync(ctx->Wsl, sl.data(), sizeof(uint4) * (size_t)np * np, cudaMemcpyHostToDevice, ctx->stream));
+    FCI_CUDA(cudaMemcpyAsync(ctx->XW, xw.data(), sizeof(long long) * xw.size(), cudaMemcpyHostToDevice, ctx->stream));
     FCI_CUDA(cudaMemsetAsync(B.tabp, 0xFF, sizeof(uint32_t) * (size_t)np * B.ns, ctx->stream));
     k_pair_table<<<ceil_div(B.ns * B.nsingle, 256), 256, 0, ctx->stream>>>(B.tab, B.ns, B.nsingle, B.tabp);
     FCI_CUDA(cudaGetLastError());
@@ -113,11 +117,14 @@ void free_sliced_tables(fci_ctx *ctx) {
     const int np = ctx->npair;
     if (ctx->B.tabp) dfree(ctx, ctx->B.tabp, sizeof(uint32_t) * (size_t)np * ctx->B.ns);
     ctx->B.tabp = nullptr;
-    const int64_t nrow = ctx->A.ns > ctx->B.ns ? ctx->A.ns : ctx->B.ns;
-    dfree(ctx, ctx->Wsl, sizeof(uint4) * (size_t)np * np);
-    dfree(ctx, ctx->rowexp, sizeof(int) * (size_t)nrow);
-    ctx->Wsl = nullptr;
+    dfree(ctx, ctx->XW, sizeof(long long) * (size_t)np * np);
+    dfree(ctx, ctx->rowexp, sizeof(int) * (size_t)ctx->A.ns);
+    dfree(ctx, ctx->cs0123, sizeof(uint2) * (size_t)ctx->ndet);
+    dfree(ctx, ctx->cs45, sizeof(uint32_t) * (size_t)ctx->ndet);
+    ctx->XW = nullptr;
     ctx->rowexp = nullptr;
+    ctx->cs0123 = nullptr;
+    ctx->cs45 = nullptr;
 }
 
 static void *sliced_kernel(int kpad) {
@@ -132,9 +139,9 @@ static void *sliced_kernel(int kpad) {
     }
 }
 
-// Row exponents of C (stream-ordered), then sigma_3 into sig, which is
-// overwritten.  prof_slot: profiling slot of the row-exponent pass (the
-// kernel takes the next one).
+// Row exponents and digit slices of C (stream-ordered), then sigma_3 into sig,
+// which is overwritten.  prof_slot: profiling slot of the pre-pass (the kernel
+// takes the next one).
 int launch_sigma3_sliced(fci_ctx *ctx, const double *C, double *sig, cudaStream_t s, int rec, int prof_slot) {
     int kpad = 0, npad = 0, n0 = 0;
     uint32_t smem = 0;
@@ -142,6 +149,8 @@ int launch_sigma3_sliced(fci_ctx *ctx, const double *C, double *sig, cudaStream_
         return fail(FCI_ERR_STATE, "sliced sigma_3 tables were not built for this context");
     const SpinTables &A = ctx->A, &B = ctx->B;
     k_row_exponents<<<ceil_div(A.ns * 32, 256), 256, 0, s>>>(C, A.ns, B.ns, ctx->rowexp);
+    FCI_CUDA(cudaGetLastError());
+    k_slice_c<<<ceil_div(ctx->ndet, 256), 256, 0, s>>>(C, ctx->rowexp, A.ns, B.ns, ctx->cs0123, ctx->cs45);
     FCI_CUDA(cudaGetLastError());
     prof_mark(ctx, rec, prof_slot, s);
     void *kern = sliced_kernel(kpad);
@@ -153,11 +162,13 @@ int launch_sigma3_sliced(fci_ctx *ctx, const double *C, double *sig, cudaStream_
     int64_t grid = nsm;  // one CTA per SM
     if (grid > A.ns) grid = A.ns;
     SpinTables At = A, Bt = B;
-    const uint4 *wsl = ctx->Wsl;
+    const uint2 *c0 = ctx->cs0123;
+    const uint32_t *c4 = ctx->cs45;
+    const long long *xw = ctx->XW;
     const int *rexp = ctx->rowexp;
     int npair = ctx->npair, eW = ctx->eW;
-    void *args[] = {(void *)&C,    (void *)&sig,   (void *)&At,   (void *)&Bt, (void *)&wsl,       (void *)&rexp,
-                    (void *)&npair, (void *)&npad, (void *)&n0, (void *)&eW, (void *)&ctx->d_err};
+    void *args[] = {(void *)&c0,   (void *)&c4,   (void *)&sig, (void *)&At, (void *)&Bt,         (void *)&xw,
+                    (void *)&rexp, (void *)&npair, (void *)&npad, (void *)&n0, (void *)&eW, (void *)&ctx->d_err};
     FCI_CUDA(cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(sl::kThreads), args, smem, s));
     prof_mark(ctx, rec, prof_slot + 1, s);
     return FCI_OK;

@@ -8,30 +8,54 @@
 //                     pair q = {k, l}, of s_b G[J_b][q]      (scatter)
 //
 // FP64-accurate contraction from 8-bit slices (Ozaki splitting):
-//  * every C value gathered for the row is written in fixed point relative to
-//    one power of two 2^eD per alpha row (eD bounds every gathered C row, from
-//    the row exponents of a pre-pass): X = round(|C| 2^(47-eD)) with the sign,
-//    cut into six balanced 8-bit digits X = d0 2^40 + d1 2^32 + ... + d5 with
+//  * a pre-pass writes every C value in fixed point relative to the largest
+//    power of two of its own row, X = round(|C| 2^(47 - e_row)) with the sign,
+//    cut into six balanced 8-bit digits X = d0 2^40 + d1 2^32 + ... + d5,
 //    |d_s| <= 128 (the low digits are centred on zero, so the products that
-//    are left out have zero mean).  Digit s is stored as the bf16 value
-//    d_s 2^(-8s), which bf16 holds exactly;
-//  * the integrals are cut the same way once per context, relative to 2^eW;
+//    are left out have zero mean), stored as the bf16 values d_s 2^(-8s),
+//    which bf16 holds exactly (12 bytes per determinant, two planes);
+//  * per alpha row, the rows J_a it gathers share the largest of their
+//    exponents, eD; the factor 2^(e_row(J_a) - eD) of each replacement is
+//    folded into the integral operand, whose digits are rebuilt per row from
+//    the context's fixed-point integrals round((pq|rs) 2^(47 - eW)) shifted
+//    right by eD - e_row(J_a), with the sign s_a;
 //  * the 21 slice products s + t <= 5 run on the tensor cores with FP32
 //    accumulation in tensor memory, one accumulator per level L = s + t for
 //    L = 0, 1, 2 and one shared by L >= 3.  A level-L product is an integer
-//    times 2^(-8L) of magnitude <= 2^14, so with K <= 96 replacements every
-//    level sum stays below 2^24 units and levels 0-2 are exact; the shared
+//    times 2^(-8L) of magnitude <= 2^14, so with K <= 85 replacements every
+//    level sum stays below 2^22 units and levels 0-2 are exact; the shared
 //    accumulator rounds at 2^-24 of level 3, 2^-48 of the leading level;
 //  * the epilogue turns the four level sums of G[J_b][q] into one integer
-//    V = round(2^34 sum_L acc_L) (units 2^(eD + eW - 48)) and adds s_b V into
-//    the target's 64-bit slot of the sigma row in shared memory with an
-//    integer atomic: the adds are exact and their order does not matter, so
-//    the result is bit-reproducible;
+//    V = round(2^34 sum_L acc_L) (units 2^(eD + eW - 48)), with FP32
+//    magic-number roundings only (GB300 runs float-integer conversions on
+//    its slow FP64 pipe), and adds s_b V into the target's 64-bit slot of the
+//    sigma row in shared memory with an integer atomic: the adds are exact
+//    and their order does not matter, so the result is bit-reproducible;
 //  * at the end of the row the integers are converted to FP64 (integer
 //    arithmetic only, round to nearest even) and written to sigma, which this
 //    kernel overwrites.
 // Per product the representation and the products left out (s + t >= 6) are
 // below about 2^-46 of (largest gathered |C|) x (largest |(pq|rs)|).
+//
+// The pair-major beta table (SpinTables::tabp) gives, for lane J_b and pair
+// column q of the accumulator, the one replacement of J_b with pair q (if any),
+// so the epilogue reads the accumulator lane by lane from tensor memory with
+// compile-time register indices and needs no staging of G.
+//
+// CTA (416 threads), one per SM, persistent over alpha rows:
+//  * warps 0-3 (producers): thread m gathers the sliced values C(J_a, J_b) of
+//    beta string J_b = 128 t + m and transposes them into the six A slices,
+//    K-major (no swizzle) in shared memory; each K-step (16 replacements) sits
+//    behind its own pair of barriers so that the next tile's slices are written
+//    while the tensor cores finish this one;
+//  * warp 12 (one thread) issues the MMAs: per tile, the accumulator columns
+//    are split in two halves (pairs 0..N0-1 and N0..npad-1), each with its own
+//    four level accumulators, so the epilogue of one half overlaps the MMAs of
+//    the other;
+//  * warps 4-11 (epilogue): two warps per tensor-memory lane quarter, taking
+//    alternate 8-column chunks.
+// All waits are bounded; a wait that gives up sets the device error word and
+// the CTA drains its MMAs and frees its tensor memory.
 #pragma once
 #include "sigma_tc_kernel.cuh"
 
@@ -43,7 +67,8 @@ using tc::kM;
 constexpr int kSlices = 6;    // 8-bit digits per FP64 operand (48 bits)
 constexpr int kThreads = 416; // warps 0-3 producers, 4-11 epilogue, 12 MMA issuer
 constexpr int kEpiThreads = 256;
-constexpr int kMaxKSteps = 6; // K <= 96
+constexpr int kMaxKSteps = 6; // K <= 96 (the exact level sums need K <= 85)
+constexpr int kMaxK = 85;
 constexpr int kBars = 2 * kMaxKSteps + 5;  // a_full[6], a_free[6], acc_full[2], acc_empty[2], drain
 
 struct Layout {
@@ -78,12 +103,13 @@ __device__ __forceinline__ long long fixed47(uint32_t lo, uint32_t hi, int emax)
 
 // The six balanced digits of a fixed-point value |X| <= 2^47 as the floats
 // d_s 2^(-8s) (exact): with X' = X + 0x8080808080, d0 = X' >> 40 in
-// [-128, 128] and d_s = (byte 5-s of X') - 128 in [-128, 127].
+// [-128, 128] and d_s = (byte 5-s of X') - 128 in [-128, 127].  Only FP32 and
+// integer operations (no conversion instructions).
 __device__ __forceinline__ void digits6(long long X, float (&f)[kSlices]) {
     X += 0x8080808080ll;
     const int h32 = (int)(X >> 32);
     const uint32_t l32 = (uint32_t)X;
-    f[0] = __int2float_rn(h32 >> 8);
+    f[0] = __int_as_float(0x4B400000 + (h32 >> 8)) - 12582912.0f;  // 1.5 2^23 + d0, exact for |d0| < 2^22
     // byte b: 2^23 + b from a byte permute with the exponent byte 0x4B, then
     // (2^23 + b) 2^(-8s) - (2^23 + 128) 2^(-8s) = (b - 128) 2^(-8s) in one exact FMA
     f[1] = fmaf(__uint_as_float(__byte_perm((uint32_t)h32, 0x4B000000u, 0x7440)), 0x1p-8f, -32768.5f);
@@ -125,8 +151,34 @@ __device__ __forceinline__ double scaled_i64(long long T, int e2) {
     return __longlong_as_double((long long)(sgn | ((unsigned long long)E << 52) | (m & 0xFFFFFFFFFFFFFull)));
 }
 
-__device__ __forceinline__ void ld_early_u64(const double *p, uint32_t &lo, uint32_t &hi) {
-    asm volatile("ld.global.nc.v2.u32 {%0, %1}, [%2];" : "=r"(lo), "=r"(hi) : "l"(p));
+__device__ __forceinline__ void ld_early_v2(const uint2 *p, uint32_t &x, uint32_t &y) {
+    asm volatile("ld.global.nc.v2.u32 {%0, %1}, [%2];" : "=r"(x), "=r"(y) : "l"(p));
+}
+
+// round(X 2^-d) for d >= 0 (zero once d >= 60)
+__device__ __forceinline__ long long round_shift(long long X, int d) {
+    if (d <= 0) return X;
+    if (d >= 60) return 0;
+    return (X + (1ll << (d - 1))) >> d;
+}
+
+// The level sums of one accumulator element (sign already applied) as the
+// integer V = round(2^34 (a0 + a1 + a2 + a3)).  a0, 2^8 a1 and 2^16 a2 are
+// integers below 2^22 in magnitude, so adding 1.5 2^23 leaves them in the
+// low mantissa bits; a3 is split into round(2^18 a3) and an exact remainder.
+__device__ __forceinline__ long long levels_to_int(float a0, float a1, float a2, float a3) {
+    constexpr float M = 12582912.0f;  // 1.5 2^23
+    constexpr int MB = 0x4B400000;    // its bit pattern
+    const int i0 = __float_as_int(a0 + M) - MB;
+    const int i1 = __float_as_int(fmaf(a1, 256.f, M)) - MB;
+    const int i2 = __float_as_int(fmaf(a2, 65536.f, M)) - MB;
+    const float t = fmaf(a3, 262144.f, M);
+    const int h = __float_as_int(t) - MB;
+    const float rem = fmaf(-(t - M), 0x1p-18f, a3);  // exact: a3 - h 2^-18
+    const int l = __float_as_int(fmaf(rem, 0x1p34f, M)) - MB;
+    const int hi = i0 * 256 + i1;  // units 2^26 of V
+    const int mid = i2 * 4 + h;    // units 2^16 of V
+    return ((long long)hi << 26) + ((long long)mid << 16) + l;
 }
 
 // tensor-memory column of level L of accumulator half h
@@ -136,9 +188,9 @@ __device__ __forceinline__ uint32_t acc_col(int h, int L, int n0, int n1) {
 
 template <int KPAD>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_sigma3_sliced(const double *__restrict__ C, double *__restrict__ sig, SpinTables A, SpinTables B,
-                    const uint4 *__restrict__ Wsl, const int *__restrict__ rowexp, int npair, int npad, int n0,
-                    int eW, int *err) {
+    k_sigma3_sliced(const uint2 *__restrict__ cs0123, const uint32_t *__restrict__ cs45, double *__restrict__ sig,
+                    SpinTables A, SpinTables B, const long long *__restrict__ XW, const int *__restrict__ rowexp,
+                    int npair, int npad, int n0, int eW, int *err) {
     constexpr int NKS = KPAD / 16;
     constexpr int kgroups = KPAD / 8;
     constexpr uint32_t sbo = (uint32_t)(KPAD / 8) * 128u;
@@ -201,102 +253,102 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
             if (lane == 0) *s_emax = mx;
         }
-        // B[q][a] = s_a (q | p_a): the context's integral digits, sign of the
-        // replacement applied, K-major per slice
+        __syncthreads();
+        const int emax = *s_emax;
+        // B[q][a] = s_a (q | p_a) 2^(e_row(J_a) - eD): digits of the context's
+        // fixed-point integrals shifted by the row's exponent gap, K-major per slice
         for (int item = tid; item < npad * kgroups; item += kThreads) {
             const int q = item / kgroups, kg = item % kgroups;
-            uint4 w8[8];
+            uint32_t w[kSlices][4];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int a = kg * 8 + i;
-                uint4 w = make_uint4(0u, 0u, 0u, 0u);
-                if (q < npair && a < sa_n) {
-                    const uint32_t ea = sEa[a];
-                    w = __ldg(Wsl + (int64_t)q * npair + ent_pair(ea));
-                    if (ent_negative(ea)) {
-                        w.x ^= 0x80008000u;
-                        w.y ^= 0x80008000u;
-                        w.z ^= 0x80008000u;
+            for (int i = 0; i < 4; ++i) {
+                float f[2][kSlices];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int a = kg * 8 + 2 * i + u;
+                    long long X = 0;
+                    if (q < npair && a < sa_n) {
+                        const uint32_t ea = sEa[a];
+                        X = round_shift(__ldg(XW + (int64_t)q * npair + ent_pair(ea)),
+                                        emax - __ldg(rowexp + ent_target(ea)));
+                        if (ent_negative(ea)) X = -X;
                     }
+                    digits6(X, f[u]);
                 }
-                w8[i] = w;
+#pragma unroll
+                for (int sl = 0; sl < kSlices; ++sl) w[sl][i] = pack_bf16(f[0][sl], f[1][sl]);
             }
             const uint32_t off = tc::kmajor_offset(q, kg, KPAD);
 #pragma unroll
-            for (int s = 0; s < kSlices; ++s) {
-                uint32_t o[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const uint32_t x0 = s < 2 ? w8[2 * i].x : s < 4 ? w8[2 * i].y : w8[2 * i].z;
-                    const uint32_t x1 = s < 2 ? w8[2 * i + 1].x : s < 4 ? w8[2 * i + 1].y : w8[2 * i + 1].z;
-                    o[i] = __byte_perm(x0, x1, (s & 1) ? 0x7632 : 0x5410);
-                }
-                *reinterpret_cast<uint4 *>(sB + (uint32_t)s * L.bytesB + off) = make_uint4(o[0], o[1], o[2], o[3]);
-            }
+            for (int sl = 0; sl < kSlices; ++sl)
+                *reinterpret_cast<uint4 *>(sB + (uint32_t)sl * L.bytesB + off) = make_uint4(w[sl][0], w[sl][1], w[sl][2], w[sl][3]);
         }
         tc::fence_async_smem();
         tc::fence_before();
         __syncthreads();
         tc::fence_after();
-        const int emax = *s_emax;
 
         if (warp < 4) {
-            // ---- producers: beta string 128 t + m, one K-step (16 values) at a time ----
+            // ---- producers: beta string 128 t + m, one K-group (8 values) at a time,
+            // the next group's loads in flight while this one is transposed ----
             const int m = tid;
-            uint32_t clo[16], chi[16], nlo[16], nhi[16];
-            auto load = [&](uint32_t(&lo)[16], uint32_t(&hi)[16], int64_t jb, int ks) {
+            uint32_t cx[8], cy[8], cz[8], nx[8], ny[8], nz[8];
+            auto load = [&](uint32_t(&x)[8], uint32_t(&y)[8], uint32_t(&z)[8], int64_t jb, int kg) {
                 const int64_t jc = jb < nsb ? jb : nsb - 1;
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int a = ks * 16 + i;
-                    ld_early_u64(C + (int64_t)ent_target(sEa[a < sa_n ? a : 0]) * nsb + jc, lo[i], hi[i]);
+                for (int i = 0; i < 8; ++i) {
+                    const int a = kg * 8 + i;
+                    const int64_t idx = (int64_t)ent_target(sEa[a < sa_n ? a : 0]) * nsb + jc;
+                    ld_early_v2(cs0123 + idx, x[i], y[i]);
+                    z[i] = tc::ld_early_u32(cs45 + idx);
                 }
             };
-            load(clo, chi, m, 0);
+            load(cx, cy, cz, m, 0);
             for (int64_t t = 0; t < ntiles && !*s_fail; ++t) {
                 const int64_t Tt = T + t;
                 const int64_t jb = t * kM + m;
                 const bool live = jb < nsb;
 #pragma unroll
                 for (int ks = 0; ks < NKS; ++ks) {
-                    if (ks + 1 < NKS)
-                        load(nlo, nhi, jb, ks + 1);
-                    else if (t + 1 < ntiles)
-                        load(nlo, nhi, jb + kM, 0);
                     if (Tt >= 1 && !tc::mbar_wait_bounded(a_free(ks), (uint32_t)((Tt - 1) & 1))) {
                         *s_fail = 1;
                         break;
                     }
 #pragma unroll
                     for (int g = 0; g < 2; ++g) {
-                        uint32_t w[kSlices][4];
+                        const int kg = 2 * ks + g;
+                        if (kg + 1 < kgroups)
+                            load(nx, ny, nz, jb, kg + 1);
+                        else if (t + 1 < ntiles)
+                            load(nx, ny, nz, jb + kM, 0);
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            float f0[kSlices], f1[kSlices];
-                            const int i0 = g * 8 + 2 * i, i1 = i0 + 1;
-                            const bool ok0 = live && ks * 16 + i0 < sa_n, ok1 = live && ks * 16 + i1 < sa_n;
-                            digits6(ok0 ? fixed47(clo[i0], chi[i0], emax) : 0ll, f0);
-                            digits6(ok1 ? fixed47(clo[i1], chi[i1], emax) : 0ll, f1);
+                        for (int i = 0; i < 8; ++i)
+                            if (!(live && kg * 8 + i < sa_n)) cx[i] = cy[i] = cz[i] = 0u;
+                        const uint32_t off = tc::kmajor_offset(m, kg, KPAD);
 #pragma unroll
-                            for (int s = 0; s < kSlices; ++s) w[s][i] = pack_bf16(f0[s], f1[s]);
+                        for (int sl = 0; sl < kSlices; ++sl) {
+                            uint32_t o[4];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const uint32_t x0 = sl < 2 ? cx[2 * i] : sl < 4 ? cy[2 * i] : cz[2 * i];
+                                const uint32_t x1 = sl < 2 ? cx[2 * i + 1] : sl < 4 ? cy[2 * i + 1] : cz[2 * i + 1];
+                                o[i] = __byte_perm(x0, x1, (sl & 1) ? 0x7632 : 0x5410);
+                            }
+                            *reinterpret_cast<uint4 *>(sA + (uint32_t)sl * L.bytesA + off) = make_uint4(o[0], o[1], o[2], o[3]);
                         }
-                        const uint32_t off = tc::kmajor_offset(m, 2 * ks + g, KPAD);
 #pragma unroll
-                        for (int s = 0; s < kSlices; ++s)
-                            *reinterpret_cast<uint4 *>(sA + (uint32_t)s * L.bytesA + off) =
-                                make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+                        for (int i = 0; i < 8; ++i) {
+                            cx[i] = nx[i];
+                            cy[i] = ny[i];
+                            cz[i] = nz[i];
+                        }
                     }
                     tc::fence_async_smem();
                     tc::mbar_arrive(a_full(ks));
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        clo[i] = nlo[i];
-                        chi[i] = nhi[i];
-                    }
                 }
             }
         } else if (warp < 12) {
-            // ---- epilogue: lane m of the tile, 16-column chunks g, g+2, ... of each half ----
+            // ---- epilogue: lane m of the tile, 8-column chunks g, g+2, ... of each half ----
             const int quarter = warp & 3, grp = (warp - 4) >> 2;
             const int m = quarter * 32 + lane;
             const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
@@ -306,12 +358,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const bool live = jb < nsb;
                 const int64_t jc = live ? jb : nsb - 1;
                 for (int h = 0; h < nh; ++h) {
-                    const int q0 = h ? n0 : 0, nchunks = (h ? n1 : n0) / 16;
-                    uint32_t ent[16];
+                    const int q0 = h ? n0 : 0, nchunks = (h ? n1 : n0) / 8;
+                    uint32_t ent[8];
                     auto prefetch = [&](int c) {
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            int q = q0 + c * 16 + j;
+                        for (int j = 0; j < 8; ++j) {
+                            int q = q0 + c * 8 + j;
                             q = q < npair ? q : npair - 1;
                             ent[j] = tc::ld_early_u32(B.tabp + (int64_t)q * nsb + jc);
                         }
@@ -327,38 +379,29 @@ __global__ void __launch_bounds__(kThreads, 1)
                         tc::mbar_arrive(acc_empty(h));
                     }
                     for (int c = grp; c < nchunks; c += 2) {
-                        uint32_t r[4][16];
+                        uint32_t r[4][8];
 #pragma unroll
                         for (int lv = 0; lv < 4; ++lv)
-                            asm volatile(
-                                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                                : "=r"(r[lv][0]), "=r"(r[lv][1]), "=r"(r[lv][2]), "=r"(r[lv][3]), "=r"(r[lv][4]),
-                                  "=r"(r[lv][5]), "=r"(r[lv][6]), "=r"(r[lv][7]), "=r"(r[lv][8]), "=r"(r[lv][9]),
-                                  "=r"(r[lv][10]), "=r"(r[lv][11]), "=r"(r[lv][12]), "=r"(r[lv][13]),
-                                  "=r"(r[lv][14]), "=r"(r[lv][15])
-                                : "r"(tmem + lane_base + acc_col(h, lv, n0, n1) + (uint32_t)(c * 16)));
+                            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                         : "=r"(r[lv][0]), "=r"(r[lv][1]), "=r"(r[lv][2]), "=r"(r[lv][3]),
+                                           "=r"(r[lv][4]), "=r"(r[lv][5]), "=r"(r[lv][6]), "=r"(r[lv][7])
+                                         : "r"(tmem + lane_base + acc_col(h, lv, n0, n1) + (uint32_t)(c * 8)));
                         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                         if (c + 2 >= nchunks) {  // last chunk of this thread in the half: release it
                             tc::fence_before();
                             tc::mbar_arrive(acc_empty(h));
                         }
-                        uint32_t en[16];
+                        uint32_t en[8];
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) en[j] = ent[j];
+                        for (int j = 0; j < 8; ++j) en[j] = ent[j];
                         if (c + 2 < nchunks) prefetch(c + 2);
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
+                        for (int j = 0; j < 8; ++j) {
                             const uint32_t e = en[j];
-                            if (!live || q0 + c * 16 + j >= npair || e == kNoEntry) continue;
+                            if (!live || q0 + c * 8 + j >= npair || e == kNoEntry) continue;
                             const uint32_t sg = e & 0x80000000u;
-                            const float a0 = __uint_as_float(r[0][j] ^ sg), a1 = __uint_as_float(r[1][j] ^ sg);
-                            const float a2 = __uint_as_float(r[2][j] ^ sg), a3 = __uint_as_float(r[3][j] ^ sg);
-                            // V = round(2^34 (acc0 + acc1 + acc2 + acc3)); levels 0-2 are
-                            // integers after their scaling, level 3+ rounds here
-                            const long long v = ((long long)__float2int_rn(a0) << 34) +
-                                                ((long long)__float2int_rn(a1 * 0x1p8f) << 26) +
-                                                ((long long)__float2int_rn(a2 * 0x1p16f) << 18) +
-                                                __float2ll_rn(a3 * 0x1p34f);
+                            const long long v = levels_to_int(__uint_as_float(r[0][j] ^ sg), __uint_as_float(r[1][j] ^ sg),
+                                                              __uint_as_float(r[2][j] ^ sg), __uint_as_float(r[3][j] ^ sg));
                             atomicAdd(sAcc + (e & kTargetMask), (unsigned long long)v);
                         }
                     }
@@ -367,7 +410,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         } else if (warp == 12 && lane == 0) {
             // ---- MMA issuer ----
-            const unsigned char *sAc = sA;
             for (int64_t t = 0; t < ntiles; ++t) {
                 const int64_t Tt = T + t;
                 bool ok = true;
@@ -387,13 +429,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                         tc::fence_after();
 #pragma unroll
-                        for (int s = 0; s < kSlices; ++s)
+                        for (int sa = 0; sa < kSlices; ++sa)
 #pragma unroll
-                            for (int u = 0; u + s < kSlices; ++u) {
-                                const int lv = s + u < 3 ? s + u : 3;
-                                const uint64_t ad = tc::smem_desc(tc::smem_u32(sAc + s * L.bytesA) + ks * 256, 128, sbo);
+                            for (int sb = 0; sa + sb < kSlices; ++sb) {
+                                const int lv = sa + sb < 3 ? sa + sb : 3;
+                                const uint64_t ad = tc::smem_desc(tc::smem_u32(sA + sa * L.bytesA) + ks * 256, 128, sbo);
                                 const uint64_t bd = tc::smem_desc(
-                                    tc::smem_u32(sB + u * L.bytesB) + (uint32_t)(q0 / 8) * sbo + ks * 256, 128, sbo);
+                                    tc::smem_u32(sB + sb * L.bytesB) + (uint32_t)(q0 / 8) * sbo + ks * 256, 128, sbo);
                                 tc::mma_bf16(tmem + acc_col(h, lv, n0, n1), ad, bd, idesc, fresh[lv] ? 0u : 1u);
                                 fresh[lv] = false;
                             }
