@@ -71,10 +71,11 @@ struct SpinTables {
     uint32_t *tsched = nullptr;
     int32_t *toff = nullptr;  // [ntiles + 1]
     int64_t nsched = 0;
-    // Pair-major copy of the replacement lists for the FP64 sliced sigma_3
-    // (beta spin only): tabp[q][x] = the entry of string x with orbital pair q,
-    // or kNoEntry.  Owned by the context (freed with the sliced tables).
-    uint32_t *tabp = nullptr;
+    // Replacement lists by orbital pair for the FP64 sliced sigma_3 (beta spin
+    // only): tabp[x][q] (npad pairs per string, padded) = target | negative << 15
+    // of the entry of string x with pair q, or 0xFFFF.  Owned by the context
+    // (freed with the sliced tables).
+    uint16_t *tabp = nullptr;
     bool owner = true;         // false when aliasing the alpha tables
 };
 

@@ -25,15 +25,17 @@ __global__ void k_row_exponents(const double *__restrict__ C, int64_t nrows, int
     if (lane == 0) out[r] = (int)mx;
 }
 
-// Pair-major copy of a replacement table: tabp[q][x] = the entry of string x
-// whose orbital pair is q (a string has at most one: {k, l} with k == l
-// occupied, or exactly one of k, l occupied), or kNoEntry.
-__global__ void k_pair_table(const uint32_t *__restrict__ tab, int64_t ns, int nsingle, uint32_t *__restrict__ tabp) {
+// Replacement lists by orbital pair: tabp[x][q] = target | negative << 15 of
+// the entry of string x whose orbital pair is q (a string has at most one:
+// {k, l} with k == l occupied, or exactly one of k, l occupied), else 0xFFFF
+// (left by the memset).
+__global__ void k_pair_table(const uint32_t *__restrict__ tab, int64_t ns, int nsingle, int npad,
+                             uint16_t *__restrict__ tabp) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ns * nsingle) return;
     const uint32_t v = tab[t];  // entry-major: t = e * ns + x
     const int64_t x = t % ns;
-    tabp[(int64_t)ent_pair(v) * ns + x] = v;
+    tabp[x * npad + ent_pair(v)] = (uint16_t)(ent_target(v) | (ent_negative(v) ? 0x8000u : 0u));
 }
 
 // Six bf16 digit slices of every C value, relative to its row's exponent:
@@ -53,7 +55,7 @@ __global__ void k_slice_c(const double *__restrict__ C, const int *__restrict__ 
 // Sizes of the sliced kernel for this context; false when it does not apply.
 static bool sliced_shape(const fci_ctx *ctx, int *kpad, int *npad, int *n0, uint32_t *smem) {
     const SpinTables &A = ctx->A, &B = ctx->B;
-    if (A.nsingle == 0 || B.nsingle == 0 || A.nsingle > sl::kMaxK) return false;
+    if (A.nsingle == 0 || B.nsingle == 0 || A.nsingle > sl::kMaxK || B.ns > 0x7FFF) return false;
     *kpad = round_up16(A.nsingle);
     *npad = round_up16(ctx->npair);
     if (*kpad > 16 * sl::kMaxKSteps || *npad > 128 || B.ns > kMaxStrings) return false;
@@ -102,12 +104,12 @@ int build_sliced_tables(fci_ctx *ctx, const double *eri_host) {
     ctx->cs0123 = (uint2 *)dalloc(ctx, sizeof(uint2) * (size_t)ctx->ndet, &rc);
     ctx->cs45 = (uint32_t *)dalloc(ctx, sizeof(uint32_t) * (size_t)ctx->ndet, &rc);
     SpinTables &B = ctx->B;
-    B.tabp = (uint32_t *)dalloc(ctx, sizeof(uint32_t) * (size_t)np * B.ns, &rc);
+    B.tabp = (uint16_t *)dalloc(ctx, sizeof(uint16_t) * (size_t)npad * B.ns, &rc);
     if (rc) return rc;
     ctx->eW = eW;
     FCI_CUDA(cudaMemcpyAsync(ctx->XW, xw.data(), sizeof(long long) * xw.size(), cudaMemcpyHostToDevice, ctx->stream));
-    FCI_CUDA(cudaMemsetAsync(B.tabp, 0xFF, sizeof(uint32_t) * (size_t)np * B.ns, ctx->stream));
-    k_pair_table<<<ceil_div(B.ns * B.nsingle, 256), 256, 0, ctx->stream>>>(B.tab, B.ns, B.nsingle, B.tabp);
+    FCI_CUDA(cudaMemsetAsync(B.tabp, 0xFF, sizeof(uint16_t) * (size_t)npad * B.ns, ctx->stream));
+    k_pair_table<<<ceil_div(B.ns * B.nsingle, 256), 256, 0, ctx->stream>>>(B.tab, B.ns, B.nsingle, npad, B.tabp);
     FCI_CUDA(cudaGetLastError());
     FCI_CUDA(cudaStreamSynchronize(ctx->stream));
     return FCI_OK;
@@ -115,7 +117,7 @@ int build_sliced_tables(fci_ctx *ctx, const double *eri_host) {
 
 void free_sliced_tables(fci_ctx *ctx) {
     const int np = ctx->npair;
-    if (ctx->B.tabp) dfree(ctx, ctx->B.tabp, sizeof(uint32_t) * (size_t)np * ctx->B.ns);
+    if (ctx->B.tabp) dfree(ctx, ctx->B.tabp, sizeof(uint16_t) * (size_t)((np + 15) / 16 * 16) * ctx->B.ns);
     ctx->B.tabp = nullptr;
     dfree(ctx, ctx->XW, sizeof(long long) * (size_t)np * np);
     dfree(ctx, ctx->rowexp, sizeof(int) * (size_t)ctx->A.ns);

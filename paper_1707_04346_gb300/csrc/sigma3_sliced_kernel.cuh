@@ -26,21 +26,24 @@
 //    level sum stays below 2^22 units and levels 0-2 are exact; the shared
 //    accumulator rounds at 2^-24 of level 3, 2^-48 of the leading level;
 //  * the epilogue turns the four level sums of G[J_b][q] into one integer
-//    V = round(2^34 sum_L acc_L) (units 2^(eD + eW - 48)), with FP32
-//    magic-number roundings only (GB300 runs float-integer conversions on
-//    its slow FP64 pipe), and adds s_b V into the target's 64-bit slot of the
-//    sigma row in shared memory with an integer atomic: the adds are exact
-//    and their order does not matter, so the result is bit-reproducible;
+//    V = round(2^34 sum_L acc_L) (units 2^(eD + eW - 48)) without conversion
+//    instructions (GB300 runs float-integer conversions on its slow FP64
+//    pipe): levels 0-2 accumulate on biases that leave their integers in the
+//    low mantissa bits, level 3+ is rounded with FP32 magic-number additions.
+//    It adds s_b V into the target's 64-bit slot of the sigma row in shared
+//    memory with an integer atomic: the adds are exact and their order does
+//    not matter, so the result is bit-reproducible;
 //  * at the end of the row the integers are converted to FP64 (integer
 //    arithmetic only, round to nearest even) and written to sigma, which this
 //    kernel overwrites.
 // Per product the representation and the products left out (s + t >= 6) are
 // below about 2^-46 of (largest gathered |C|) x (largest |(pq|rs)|).
 //
-// The pair-major beta table (SpinTables::tabp) gives, for lane J_b and pair
-// column q of the accumulator, the one replacement of J_b with pair q (if any),
-// so the epilogue reads the accumulator lane by lane from tensor memory with
-// compile-time register indices and needs no staging of G.
+// The beta table by pair (SpinTables::tabp, 16-bit entries, npad per string)
+// gives, for lane J_b and pair column q of the accumulator, the one replacement
+// of J_b with pair q (if any), so the epilogue reads the accumulator lane by
+// lane from tensor memory with compile-time register indices and needs no
+// staging of G; one 16-byte load brings the entries of 8 columns.
 //
 // CTA (416 threads), one per SM, persistent over alpha rows:
 //  * warps 0-3 (producers): thread m gathers the sliced values C(J_a, J_b) of
@@ -162,23 +165,44 @@ __device__ __forceinline__ long long round_shift(long long X, int d) {
     return (X + (1ll << (d - 1))) >> d;
 }
 
-// The level sums of one accumulator element (sign already applied) as the
-// integer V = round(2^34 (a0 + a1 + a2 + a3)).  a0, 2^8 a1 and 2^16 a2 are
-// integers below 2^22 in magnitude, so adding 1.5 2^23 leaves them in the
-// low mantissa bits; a3 is split into round(2^18 a3) and an exact remainder.
-__device__ __forceinline__ long long levels_to_int(float a0, float a1, float a2, float a3) {
+// Levels 0-2 accumulate on a bias that puts their integers in the low mantissa
+// bits: 1.5 2^23 (level 0, integers), 1.5 2^15 (level 1, multiples of 2^-8),
+// 1.5 2^7 (level 2, multiples of 2^-16); with every level sum below 2^22 units
+// the accumulator stays in [2^(e), 2^(e+1)) and its bit pattern minus the
+// bias's is the integer.  Level 3 and above accumulates from zero.
+constexpr uint32_t kBias0 = 0x4B400000u, kBias1 = 0x47400000u, kBias2 = 0x43400000u;
+
+// The integer V = round(2^34 (acc0 + acc1 + acc2 + acc3)) of one accumulator
+// element, times the sign of the replacement (neg = 1: negative), from the raw
+// accumulator words (levels 0-2 biased): 2^34 acc0 + 2^34 acc1 = (i0 2^8 + i1)
+// 2^26, 2^34 acc2 = i2 2^18, and acc3 is split into h = round(2^18 acc3) and an
+// exact remainder rounded at 2^-34.
+__device__ __forceinline__ long long levels_to_int(uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3, uint32_t neg) {
     constexpr float M = 12582912.0f;  // 1.5 2^23
     constexpr int MB = 0x4B400000;    // its bit pattern
-    const int i0 = __float_as_int(a0 + M) - MB;
-    const int i1 = __float_as_int(fmaf(a1, 256.f, M)) - MB;
-    const int i2 = __float_as_int(fmaf(a2, 65536.f, M)) - MB;
+    int hi = (int)(r0 * 256u + r1 - (kBias0 * 256u + kBias1));  // i0 2^8 + i1, exact modulo 2^32
+    int i2 = (int)(r2 - kBias2);
+    const float a3 = __uint_as_float(r3 ^ (neg << 31));
     const float t = fmaf(a3, 262144.f, M);
     const int h = __float_as_int(t) - MB;
     const float rem = fmaf(-(t - M), 0x1p-18f, a3);  // exact: a3 - h 2^-18
     const int l = __float_as_int(fmaf(rem, 0x1p34f, M)) - MB;
-    const int hi = i0 * 256 + i1;  // units 2^26 of V
-    const int mid = i2 * 4 + h;    // units 2^16 of V
-    return ((long long)hi << 26) + ((long long)mid << 16) + l;
+    if (neg) {
+        hi = -hi;
+        i2 = -i2;
+    }
+    return ((long long)hi << 26) + ((long long)(i2 * 4 + h) << 16) + l;
+}
+
+__device__ __forceinline__ uint4 ld_early_v4(const uint4 *p) {
+    uint4 v;
+    asm volatile("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, uint32_t v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr), "r"(v)
+                 : "memory");
 }
 
 // tensor-memory column of level L of accumulator half h
@@ -239,6 +263,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = *tslot;
+    if (warp >= 4 && warp < 12) {  // level 0-2 biases of both accumulator halves (this warp's chunks)
+        const uint32_t lb = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+        for (int h = 0; h < nh; ++h)
+            for (int c = (warp - 4) >> 2; c < (h ? n1 : n0) / 8; c += 2) {
+                tmem_st8(lb + acc_col(h, 0, n0, n1) + (uint32_t)(c * 8), kBias0);
+                tmem_st8(lb + acc_col(h, 1, n0, n1) + (uint32_t)(c * 8), kBias1);
+                tmem_st8(lb + acc_col(h, 2, n0, n1) + (uint32_t)(c * 8), kBias2);
+            }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
     const int64_t ntiles = (nsb + kM - 1) / kM;
     int64_t T = 0;  // tiles done by this CTA (barrier phases)
 
@@ -321,9 +358,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                             load(nx, ny, nz, jb, kg + 1);
                         else if (t + 1 < ntiles)
                             load(nx, ny, nz, jb + kM, 0);
+                        if (!live || kg * 8 + 8 > sa_n) {  // dead lane or padded replacements
 #pragma unroll
-                        for (int i = 0; i < 8; ++i)
-                            if (!(live && kg * 8 + i < sa_n)) cx[i] = cy[i] = cz[i] = 0u;
+                            for (int i = 0; i < 8; ++i)
+                                if (!(live && kg * 8 + i < sa_n)) cx[i] = cy[i] = cz[i] = 0u;
+                        }
                         const uint32_t off = tc::kmajor_offset(m, kg, KPAD);
 #pragma unroll
                         for (int sl = 0; sl < kSlices; ++sl) {
@@ -351,24 +390,20 @@ __global__ void __launch_bounds__(kThreads, 1)
             // ---- epilogue: lane m of the tile, 8-column chunks g, g+2, ... of each half ----
             const int quarter = warp & 3, grp = (warp - 4) >> 2;
             const int m = quarter * 32 + lane;
-            const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+            const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
             for (int64_t t = 0; t < ntiles; ++t) {
                 const int64_t Tt = T + t;
                 const int64_t jb = t * kM + m;
                 const bool live = jb < nsb;
-                const int64_t jc = live ? jb : nsb - 1;
+                // this string's pair entries, 8 per 16-byte load (dead lanes: none)
+                const uint4 *trow = reinterpret_cast<const uint4 *>(B.tabp + (live ? jb : 0) * npad);
                 for (int h = 0; h < nh; ++h) {
-                    const int q0 = h ? n0 : 0, nchunks = (h ? n1 : n0) / 8;
-                    uint32_t ent[8];
-                    auto prefetch = [&](int c) {
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            int q = q0 + c * 8 + j;
-                            q = q < npair ? q : npair - 1;
-                            ent[j] = tc::ld_early_u32(B.tabp + (int64_t)q * nsb + jc);
-                        }
+                    const int c0 = (h ? n0 : 0) / 8, nchunks = (h ? n1 : n0) / 8;
+                    auto fetch = [&](int c) {
+                        return live ? ld_early_v4(trow + c0 + c) : make_uint4(~0u, ~0u, ~0u, ~0u);
                     };
-                    if (grp < nchunks) prefetch(grp);
+                    uint4 ent = make_uint4(~0u, ~0u, ~0u, ~0u);
+                    if (grp < nchunks) ent = fetch(grp);
                     if (!tc::mbar_wait_bounded(acc_full(h), (uint32_t)(Tt & 1))) {
                         *s_fail = 1;
                         break;
@@ -385,64 +420,77 @@ __global__ void __launch_bounds__(kThreads, 1)
                             asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                                          : "=r"(r[lv][0]), "=r"(r[lv][1]), "=r"(r[lv][2]), "=r"(r[lv][3]),
                                            "=r"(r[lv][4]), "=r"(r[lv][5]), "=r"(r[lv][6]), "=r"(r[lv][7])
-                                         : "r"(tmem + lane_base + acc_col(h, lv, n0, n1) + (uint32_t)(c * 8)));
+                                         : "r"(lane_base + acc_col(h, lv, n0, n1) + (uint32_t)(c * 8)));
                         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        // the next tile accumulates levels 0-2 onto their biases again
+                        tmem_st8(lane_base + acc_col(h, 0, n0, n1) + (uint32_t)(c * 8), kBias0);
+                        tmem_st8(lane_base + acc_col(h, 1, n0, n1) + (uint32_t)(c * 8), kBias1);
+                        tmem_st8(lane_base + acc_col(h, 2, n0, n1) + (uint32_t)(c * 8), kBias2);
                         if (c + 2 >= nchunks) {  // last chunk of this thread in the half: release it
+                            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                             tc::fence_before();
                             tc::mbar_arrive(acc_empty(h));
                         }
-                        uint32_t en[8];
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) en[j] = ent[j];
-                        if (c + 2 < nchunks) prefetch(c + 2);
+                        const uint4 en = ent;
+                        if (c + 2 < nchunks) ent = fetch(c + 2);
+                        const uint32_t ew[4] = {en.x, en.y, en.z, en.w};
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
-                            const uint32_t e = en[j];
-                            if (!live || q0 + c * 8 + j >= npair || e == kNoEntry) continue;
-                            const uint32_t sg = e & 0x80000000u;
-                            const long long v = levels_to_int(__uint_as_float(r[0][j] ^ sg), __uint_as_float(r[1][j] ^ sg),
-                                                              __uint_as_float(r[2][j] ^ sg), __uint_as_float(r[3][j] ^ sg));
-                            atomicAdd(sAcc + (e & kTargetMask), (unsigned long long)v);
+                            const uint32_t v16 = (j & 1) ? (ew[j >> 1] >> 16) : (ew[j >> 1] & 0xFFFFu);
+                            if (v16 == 0xFFFFu) continue;
+                            const long long v = levels_to_int(r[0][j], r[1][j], r[2][j], r[3][j], v16 >> 15);
+                            atomicAdd(sAcc + (v16 & 0x7FFFu), (unsigned long long)v);
                         }
                     }
                 }
                 if (*s_fail) break;
             }
         } else if (warp == 12 && lane == 0) {
-            // ---- MMA issuer ----
+            // ---- MMA issuer: descriptors of K-step 0, advanced by 256 bytes (16 in
+            // the address field) per K-step ----
+            uint64_t ad[kSlices], bd0[kSlices], bd1[kSlices];
+#pragma unroll
+            for (int sl = 0; sl < kSlices; ++sl) {
+                ad[sl] = tc::smem_desc(tc::smem_u32(sA + sl * L.bytesA), 128, sbo);
+                bd0[sl] = tc::smem_desc(tc::smem_u32(sB + sl * L.bytesB), 128, sbo);
+                bd1[sl] = tc::smem_desc(tc::smem_u32(sB + sl * L.bytesB) + (uint32_t)(n0 / 8) * sbo, 128, sbo);
+            }
+            const uint32_t id0 = tc::instr_desc(kM, n0), id1 = tc::instr_desc(kM, n1 > 0 ? n1 : 16);
+            uint32_t col0[4], col1[4];
+#pragma unroll
+            for (int lv = 0; lv < 4; ++lv) {
+                col0[lv] = tmem + acc_col(0, lv, n0, n1);
+                col1[lv] = tmem + acc_col(1, lv, n0, n1);
+            }
+            auto issue_half = [&](const uint64_t(&bd)[kSlices], const uint32_t(&col)[4], uint32_t idesc, bool wait_a,
+                                  bool last, int64_t Tt) -> bool {
+                bool fresh3 = true;
+#pragma unroll
+                for (int ks = 0; ks < NKS; ++ks) {
+                    if (wait_a && !tc::mbar_wait_bounded(a_full(ks), (uint32_t)(Tt & 1))) return false;
+                    tc::fence_after();
+#pragma unroll
+                    for (int sa = 0; sa < kSlices; ++sa)
+#pragma unroll
+                        for (int sb = 0; sa + sb < kSlices; ++sb) {
+                            const int lv = sa + sb < 3 ? sa + sb : 3;
+                            const uint32_t accum = (lv < 3 || !fresh3) ? 1u : 0u;
+                            if (lv == 3) fresh3 = false;
+                            tc::mma_bf16(col[lv], ad[sa] + (uint64_t)(ks * 16), bd[sb] + (uint64_t)(ks * 16), idesc, accum);
+                        }
+                    if (last) tc::mma_commit(a_free(ks));
+                }
+                return true;
+            };
             for (int64_t t = 0; t < ntiles; ++t) {
                 const int64_t Tt = T + t;
-                bool ok = true;
-                for (int h = 0; h < nh && ok; ++h) {
-                    if (Tt >= 1 && !tc::mbar_wait_bounded(acc_empty(h), (uint32_t)((Tt - 1) & 1))) {
-                        ok = false;
-                        break;
-                    }
-                    const int q0 = h ? n0 : 0;
-                    const uint32_t idesc = tc::instr_desc(kM, h ? n1 : n0);
-                    bool fresh[4] = {true, true, true, true};
-#pragma unroll
-                    for (int ks = 0; ks < NKS; ++ks) {
-                        if (h == 0 && !tc::mbar_wait_bounded(a_full(ks), (uint32_t)(Tt & 1))) {
-                            ok = false;
-                            break;
-                        }
-                        tc::fence_after();
-#pragma unroll
-                        for (int sa = 0; sa < kSlices; ++sa)
-#pragma unroll
-                            for (int sb = 0; sa + sb < kSlices; ++sb) {
-                                const int lv = sa + sb < 3 ? sa + sb : 3;
-                                const uint64_t ad = tc::smem_desc(tc::smem_u32(sA + sa * L.bytesA) + ks * 256, 128, sbo);
-                                const uint64_t bd = tc::smem_desc(
-                                    tc::smem_u32(sB + sb * L.bytesB) + (uint32_t)(q0 / 8) * sbo + ks * 256, 128, sbo);
-                                tc::mma_bf16(tmem + acc_col(h, lv, n0, n1), ad, bd, idesc, fresh[lv] ? 0u : 1u);
-                                fresh[lv] = false;
-                            }
-                        if (h == nh - 1) tc::mma_commit(a_free(ks));
-                    }
-                    if (!ok) break;
-                    tc::mma_commit(acc_full(h));
+                bool ok = !(Tt >= 1 && !tc::mbar_wait_bounded(acc_empty(0), (uint32_t)((Tt - 1) & 1)));
+                ok = ok && issue_half(bd0, col0, id0, true, nh == 1, Tt);
+                if (ok) tc::mma_commit(acc_full(0));
+                if (ok && nh == 2) {
+                    ok = !(Tt >= 1 && !tc::mbar_wait_bounded(acc_empty(1), (uint32_t)((Tt - 1) & 1)));
+                    ok = ok && issue_half(bd1, col1, id1, false, true, Tt);
+                    if (ok) tc::mma_commit(acc_full(1));
                 }
                 if (!ok) {
                     *s_fail = 1;
