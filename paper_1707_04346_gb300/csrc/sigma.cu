@@ -141,13 +141,12 @@ __device__ __forceinline__ void df_mac(float vh, float vl, float2 c, float &sh, 
     sh = t;
 }
 
-constexpr int kEntDF = 4;  // ELL entries whose table loads are issued together (double-float kernels)
 
 // sigma_1 in double-float: R rows of C staged as pairs; sigma overwritten or
 // (add != 0) added to.
-template <int R>
-__global__ void __launch_bounds__(512) k_sigma1_rows_df(const double *__restrict__ C, double *__restrict__ sig,
-                                                        SpinTables B, int64_t nsa, int add) {
+template <int R, int U = 8>
+__global__ void __launch_bounds__(512, 1) k_sigma1_rows_df(const double *__restrict__ C, double *__restrict__ sig,
+                                                           SpinTables B, int64_t nsa, int add) {
     extern __shared__ float2 rows2[];  // [R][nsb]
     const int64_t nsb = B.ns;
     const int64_t r0 = (int64_t)blockIdx.x * R;
@@ -160,11 +159,11 @@ __global__ void __launch_bounds__(512) k_sigma1_rows_df(const double *__restrict
         float sh[R], sl[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) sh[r] = sl[r] = 0.f;
-        for (int e0 = 0; e0 < B.nsame; e0 += kEntDF) {
-            int32_t col[kEntDF];
-            float vh[kEntDF], vl[kEntDF];
+        for (int e0 = 0; e0 < B.nsame; e0 += U) {
+            int32_t col[U];
+            float vh[U], vl[U];
 #pragma unroll
-            for (int u = 0; u < kEntDF; ++u) {
+            for (int u = 0; u < U; ++u) {
                 const bool ok = e0 + u < B.nsame;
                 const int64_t idx = (int64_t)(ok ? e0 + u : 0) * nsb + ib;
                 col[u] = ok ? B.gcol[idx] : 0;
@@ -172,7 +171,7 @@ __global__ void __launch_bounds__(512) k_sigma1_rows_df(const double *__restrict
                 vl[u] = ok ? B.gvall[idx] : 0.f;
             }
 #pragma unroll
-            for (int u = 0; u < kEntDF; ++u)
+            for (int u = 0; u < U; ++u)
 #pragma unroll
                 for (int r = 0; r < R; ++r) df_mac(vh[u], vl[u], rows2[(int64_t)r * nsb + col[u]], sh[r], sl[r]);
         }
@@ -187,9 +186,9 @@ __global__ void __launch_bounds__(512) k_sigma1_rows_df(const double *__restrict
 }
 
 // sigma_2 in double-float: R beta columns of C staged as pairs; adds to sigma.
-template <int R>
-__global__ void __launch_bounds__(512) k_sigma2_cols_df(const double *__restrict__ C, double *__restrict__ sig,
-                                                        SpinTables A, int64_t nsb) {
+template <int R, int U = 8>
+__global__ void __launch_bounds__(512, 1) k_sigma2_cols_df(const double *__restrict__ C, double *__restrict__ sig,
+                                                           SpinTables A, int64_t nsb) {
     extern __shared__ float2 cols2[];  // [R][nsa]
     const int64_t nsa = A.ns;
     const int64_t c0 = (int64_t)blockIdx.x * R;
@@ -203,11 +202,11 @@ __global__ void __launch_bounds__(512) k_sigma2_cols_df(const double *__restrict
         float sh[R], sl[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) sh[r] = sl[r] = 0.f;
-        for (int e0 = 0; e0 < A.nsame; e0 += kEntDF) {
-            int32_t col[kEntDF];
-            float vh[kEntDF], vl[kEntDF];
+        for (int e0 = 0; e0 < A.nsame; e0 += U) {
+            int32_t col[U];
+            float vh[U], vl[U];
 #pragma unroll
-            for (int u = 0; u < kEntDF; ++u) {
+            for (int u = 0; u < U; ++u) {
                 const bool ok = e0 + u < A.nsame;
                 const int64_t idx = (int64_t)(ok ? e0 + u : 0) * nsa + ia;
                 col[u] = ok ? A.gcol[idx] : 0;
@@ -215,7 +214,7 @@ __global__ void __launch_bounds__(512) k_sigma2_cols_df(const double *__restrict
                 vl[u] = ok ? A.gvall[idx] : 0.f;
             }
 #pragma unroll
-            for (int u = 0; u < kEntDF; ++u)
+            for (int u = 0; u < U; ++u)
 #pragma unroll
                 for (int r = 0; r < R; ++r) df_mac(vh[u], vl[u], cols2[(int64_t)r * nsa + col[u]], sh[r], sl[r]);
         }
