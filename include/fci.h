@@ -84,6 +84,10 @@ typedef struct fci_options {
                             memory (default), 1 = always */
     int f64_kernels;     /* FCI_F64 sigma kernels: FCI_F64_AUTO (default), FCI_F64_FMA or
                             FCI_F64_SLICED, below */
+    double max_device_bytes; /* cap on the device memory one context (with its Davidson
+                            workspace) may hold; an allocation beyond it fails with
+                            FCI_ERR_OOM before cudaMalloc is called.  0 = no cap (default).
+                            (Resource control; no counterpart in the paper.) */
 } fci_options;
 
 /* fci_options.f64_kernels: how the FCI_F64 sigma is computed.  All modes meet
@@ -156,8 +160,12 @@ int fci_free(fci_ctx *ctx);
  *            filling) and at most 65408 strings per spin; FCI_F64 needs one
  *            beta row of C and sigma (2 N_beta doubles) in shared memory
  *            (N_beta <= about 14000, CAS(16,16)).
- *  stream    cudaStream_t or NULL.  Asynchronous.  The large-space FP32 path
- *            allocates a 2N-float workspace on its first use.
+ *  stream    cudaStream_t or NULL.  Asynchronous; allocates nothing (the
+ *            workspaces of the large-space FP32 path, 8N bytes, and of the
+ *            sliced FP64 sigma_3, 12N bytes, are made at fci_init), so it can
+ *            be captured in a CUDA graph.  The context's workspaces are shared
+ *            by its calls: fci_sigma calls on one context must not overlap in
+ *            time (issue them on one stream, or order the streams).
  * Errors: FCI_ERR_ARG (including the size limits above, reported on the host
  * before any launch), FCI_ERR_OOM, FCI_ERR_CUDA (launch failure).
  */
@@ -230,11 +238,15 @@ int fci_rdm1(fci_ctx *ctx, const void *c, int dtype, double *gamma);
  * CAS(16,16)); larger spaces get FCI_ERR_ARG and must use fci_rdm1.
  * The array lives in every GPU that loads the library until the process
  * exits.  The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the one array, which keeps the
- * last call's contents: calls whose GPU work overlaps (other streams,
- * threads or contexts on the same device) race on it and corrupt each
- * other's results, so serialise them.
+ * (cudaGetSymbolAddress) with that device current.  The call is blocking: it
+ * copies gamma to pageable host memory and synchronises `stream`, so it can
+ * never be issued on a capturing stream; the one-time address lookup should
+ * also come before any capture that other threads run in global capture mode.
+ * The call makes ctx's device current while it runs and restores the caller's
+ * current device before returning.  All calls share the one array, which keeps
+ * the last call's contents: calls whose GPU work overlaps (other streams,
+ * threads or contexts on the same device) race on it and corrupt each other's
+ * results, so serialise them.
  */
 #define FCI_RDM1_NOALLOC_MAX_DOUBLES (1 << 21)
 int fci_rdm1_noalloc(fci_ctx *ctx, const void *c, int dtype, double *gamma, void *stream);
@@ -359,6 +371,21 @@ int fci_batch_tuning(fci_batch *batch, int *out, int cap, int *count);
 int64_t fci_batch_stats(fci_batch *batch, int what);
 
 int fci_batch_free(fci_batch *batch);
+
+/*
+ * Self-test of the failure path of the bounded device waits (no counterpart in
+ * the paper).  Every mbarrier wait inside the tensor-core sigma kernels gives
+ * up after a fixed number of polls, sets the context's device error word and
+ * lets the kernel drain and exit, so that a stalled pipeline is reported
+ * instead of hanging the GPU.  This call runs one block that waits, through the
+ * same bounded-wait routine, on a barrier no thread arrives on; the wait gives
+ * up (well under a second on GB300), and the call reads and clears the error
+ * word and returns FCI_ERR_TIMEOUT, as fci_davidson does after a sigma whose
+ * wait gave up.  The context stays usable.  Blocking; runs on the context's
+ * internal stream.  Returns FCI_OK only if the wait did not give up (which
+ * would mean the routine is broken).
+ */
+int fci_check_wait_timeout(fci_ctx *ctx);
 
 /* Sizes and counters (FCI_Q_*); returns -1 for an unknown selector.  (No
  * counterpart in the paper.) */

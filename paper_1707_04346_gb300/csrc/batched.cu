@@ -633,6 +633,7 @@ namespace {
 template <typename P>
 P *balloc(fci_batch *b, size_t count, int *rc) {
     if (*rc || count == 0) return nullptr;
+    b->allocs.push_back({nullptr, 0});  // the slot exists before the allocation (a throw leaks nothing)
     void *p = nullptr;
     cudaError_t e = cudaMalloc(&p, sizeof(P) * count);
     if (e != cudaSuccess) {
@@ -640,7 +641,7 @@ P *balloc(fci_batch *b, size_t count, int *rc) {
         *rc = fail(FCI_ERR_OOM, "batched CASCI: device allocation failed");
         return nullptr;
     }
-    b->allocs.push_back({p, sizeof(P) * count});
+    b->allocs.back() = {p, sizeof(P) * count};
     return (P *)p;
 }
 
@@ -695,7 +696,8 @@ int fci_batch_free(fci_batch *b) {
     if (!b) return FCI_OK;
     cudaSetDevice(b->device);
     if (b->stream) cudaStreamSynchronize(b->stream);
-    for (auto &a : b->allocs) cudaFree(a.first);
+    for (auto &a : b->allocs)
+        if (a.first) cudaFree(a.first);
     for (auto *c : b->ctx) fci_free(c);
     if (b->stream) cudaStreamDestroy(b->stream);
     delete b;
@@ -722,7 +724,31 @@ int64_t fci_batch_stats(fci_batch *b, int what) {
     return b->stats[what];
 }
 
+static int batch_init_impl(fci_batch **out, int ninst, const fci_instance *inst, const fci_options *opt);
+
 int fci_batch_init(fci_batch **out, int ninst, const fci_instance *inst, const fci_options *opt) {
+    if (out) *out = nullptr;
+    try {
+        return batch_init_impl(out, ninst, inst, opt);
+    } catch (const std::bad_alloc &) {  // host tables: no exception crosses the C ABI
+        if (out && *out) {
+            fci_batch_free(*out);
+            *out = nullptr;
+        }
+        return fail(FCI_ERR_OOM, "batched CASCI: host allocation failed");
+    }
+}
+
+// The batch under construction is kept in a guard that frees it (and every
+// context and buffer it holds) unless initialisation completes.
+struct BatchGuard {
+    fci_batch *b = nullptr;
+    ~BatchGuard() {
+        if (b) fci_batch_free(b);
+    }
+};
+
+static int batch_init_impl(fci_batch **out, int ninst, const fci_instance *inst, const fci_options *opt) {
     if (!out || !inst || ninst < 1) return fail(FCI_ERR_ARG, "batched CASCI: bad arguments");
     *out = nullptr;
     fci_options o;
@@ -735,16 +761,18 @@ int fci_batch_init(fci_batch **out, int ninst, const fci_instance *inst, const f
         if (inst[i].norb < 1 || inst[i].norb > 16) return fail(FCI_ERR_ARG, "batched CASCI: norb must be in 1..16");
     fci_batch *b = new (std::nothrow) fci_batch();
     if (!b) return fail(FCI_ERR_OOM, "host allocation failed");
+    BatchGuard guard;
+    guard.b = b;
     b->opt = o;
     b->ninst = ninst;
     int rc = FCI_OK;
     {
         int dev = o.device;
-        if (dev < 0) cudaGetDevice(&dev);
+        if (dev < 0) FCI_CUDA(cudaGetDevice(&dev));
         b->device = dev;
-        cudaSetDevice(dev);
-        cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        FCI_CUDA(cudaSetDevice(dev));
+        FCI_CUDA(cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev));
+        FCI_CUDA(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
     }
     fci_options oi = o;
     oi.device = b->device;
@@ -772,6 +800,7 @@ int fci_batch_init(fci_batch **out, int ninst, const fci_instance *inst, const f
     }
     if (rc) {
         std::string msg = fci_last_error();
+        guard.b = nullptr;
         fci_batch_free(b);
         set_error(msg);
         return rc;
@@ -805,16 +834,13 @@ int fci_batch_init(fci_batch **out, int ninst, const fci_instance *inst, const f
     b->d_cin = balloc<void *>(b, ninst, &rc);
     b->d_cout = balloc<void *>(b, ninst, &rc);
     b->d_on_all = balloc<int>(b, ninst, &rc);
-    if (rc) {
-        fci_batch_free(b);
-        return rc;
-    }
-    cudaMemcpy(b->d_chunks, ch.data(), sizeof(Chunk) * ch.size(), cudaMemcpyHostToDevice);
-    cudaMemcpy(b->d_cfirst, cfirst.data(), sizeof(int) * (ninst + 1), cudaMemcpyHostToDevice);
-    cudaMemcpy(b->d_dchunks, dch.data(), sizeof(Chunk) * dch.size(), cudaMemcpyHostToDevice);
-    cudaMemcpy(b->d_dcfirst, dcfirst.data(), sizeof(int) * (ninst + 1), cudaMemcpyHostToDevice);
+    if (rc) return rc;
+    FCI_CUDA(cudaMemcpy(b->d_chunks, ch.data(), sizeof(Chunk) * ch.size(), cudaMemcpyHostToDevice));
+    FCI_CUDA(cudaMemcpy(b->d_cfirst, cfirst.data(), sizeof(int) * (ninst + 1), cudaMemcpyHostToDevice));
+    FCI_CUDA(cudaMemcpy(b->d_dchunks, dch.data(), sizeof(Chunk) * dch.size(), cudaMemcpyHostToDevice));
+    FCI_CUDA(cudaMemcpy(b->d_dcfirst, dcfirst.data(), sizeof(int) * (ninst + 1), cudaMemcpyHostToDevice));
     std::vector<int> ones(ninst, 1);
-    cudaMemcpy(b->d_on_all, ones.data(), sizeof(int) * ninst, cudaMemcpyHostToDevice);
+    FCI_CUDA(cudaMemcpy(b->d_on_all, ones.data(), sizeof(int) * ninst, cudaMemcpyHostToDevice));
     // shared memory: up to 8 row groups (tpr = 32) of 3 rows + one integral row
     b->row_elems64 = (3 * maxnsb + maxnpair + 1) & ~1;
     b->row_elems32 = (3 * maxnsb + maxnpair + 3) & ~3;
@@ -838,12 +864,10 @@ int fci_batch_init(fci_batch **out, int ninst, const fci_instance *inst, const f
         cudaError_t e1 = opt_in_max_smem((const void *)k_bsigma<double>, b->device);
         cudaError_t e2 = opt_in_max_smem((const void *)k_bsigma<float>, b->device);
         if (e1 != cudaSuccess || e2 != cudaSuccess) {
-            fci_batch_free(b);
             return cuda_fail(e1 != cudaSuccess ? e1 : e2, "batched CASCI: shared-memory opt-in");
         }
     }
     if (b->smem64 > 227 * 1024) {
-        fci_batch_free(b);
         return fail(FCI_ERR_ARG, "batched CASCI: an instance is too large for the batched sigma kernel");
     }
 
@@ -861,7 +885,6 @@ int fci_batch_init(fci_batch **out, int ninst, const fci_instance *inst, const f
         Item *titems = balloc<Item>(b, 1 << 16, &rc);
         int *ton = balloc<int>(b, ninst, &rc);
         if (rc) {
-            fci_batch_free(b);
             return rc;
         }
         cudaMemsetAsync(x64, 0, sizeof(double) * maxn, b->stream);
@@ -874,22 +897,22 @@ int fci_batch_init(fci_batch **out, int ninst, const fci_instance *inst, const f
             const int i = kv.second;
             std::vector<int> onv(ninst, 0);
             onv[i] = 1;
-            cudaMemcpy(ton, onv.data(), sizeof(int) * ninst, cudaMemcpyHostToDevice);
+            FCI_CUDA(cudaMemcpy(ton, onv.data(), sizeof(int) * ninst, cudaMemcpyHostToDevice));
             std::vector<void *> pin(ninst, nullptr), pout(ninst, nullptr);
             for (int dt = 0; dt < 2; ++dt) {
                 pin[i] = dt == 0 ? (void *)x64 : (void *)x32;
                 pout[i] = dt == 0 ? (void *)y64 : (void *)y32;
-                cudaMemcpy(b->d_cin, pin.data(), sizeof(void *) * ninst, cudaMemcpyHostToDevice);
-                cudaMemcpy(b->d_cout, pout.data(), sizeof(void *) * ninst, cudaMemcpyHostToDevice);
+                FCI_CUDA(cudaMemcpy(b->d_cin, pin.data(), sizeof(void *) * ninst, cudaMemcpyHostToDevice));
+                FCI_CUDA(cudaMemcpy(b->d_cout, pout.data(), sizeof(void *) * ninst, cudaMemcpyHostToDevice));
                 float best_ms = 1e30f;
                 int best = 128;
                 for (int tpr : cands) {
                     b->h_inst[i].tpr = tpr;
-                    cudaMemcpy(b->d_inst + i, &b->h_inst[i], sizeof(InstDev), cudaMemcpyHostToDevice);
+                    FCI_CUDA(cudaMemcpy(b->d_inst + i, &b->h_inst[i], sizeof(InstDev), cudaMemcpyHostToDevice));
                     std::vector<Item> it;
                     const int R = kBlock / tpr;
                     for (int64_t r = 0; r < b->h_inst[i].A.ns && it.size() < (1u << 16); r += R) it.push_back({i, (int)r});
-                    cudaMemcpy(titems, it.data(), sizeof(Item) * it.size(), cudaMemcpyHostToDevice);
+                    FCI_CUDA(cudaMemcpy(titems, it.data(), sizeof(Item) * it.size(), cudaMemcpyHostToDevice));
                     float tmin = 1e30f;
                     for (int rep = 0; rep < 3; ++rep) {
                         cudaEventRecord(e0, b->stream);
@@ -930,7 +953,6 @@ int fci_batch_init(fci_batch **out, int ninst, const fci_instance *inst, const f
             for (int i = 0; i < ninst; ++i) b->h_inst[i].stage_all = 0;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) {
-            fci_batch_free(b);
             return cuda_fail(e, "batched CASCI tuning");
         }
     }
@@ -940,9 +962,9 @@ int fci_batch_init(fci_batch **out, int ninst, const fci_instance *inst, const f
             rc = prepare_sigma_f32_gated(b->ctx[i]);
         }
     if (rc || (rc = build_items(b, &rc))) {
-        fci_batch_free(b);
         return rc;
     }
+    guard.b = nullptr;  // complete: the caller owns the batch
     *out = b;
     return FCI_OK;
 }
@@ -1046,35 +1068,32 @@ static int bsigma(BWork &W, const int *on, const double *x, double *hx, void **t
 }  // namespace bt
 }  // namespace fci
 
-extern "C" int fci_batch_davidson(fci_batch *b, int nroots, double tol, double *energies) {
-    using namespace fci::bt;
-    if (!b || !energies) return fail(FCI_ERR_ARG, "NULL argument");
-    if (nroots < 1 || nroots > kMaxRoots) return fail(FCI_ERR_ARG, "nroots must be in 1..8");
-    for (int i = 0; i < b->ninst; ++i)
-        if (b->h_inst[i].ndet < 2 * nroots) return fail(FCI_ERR_ARG, "an instance has fewer than 2*nroots determinants");
-    if (!(tol > 0)) return fail(FCI_ERR_ARG, "tol must be positive");
-    FCI_CUDA(cudaSetDevice(b->device));
-    FCI_CUDA(cudaDeviceSynchronize());
+namespace fci {
+namespace bt {
+// The Davidson iterations of fci_batch_davidson.  Every device buffer it makes
+// is recorded in `mine` and every graph in W; the caller frees them on every
+// return path, also when this function returns early or throws.
+static int batch_davidson_run(fci_batch *b, int nroots, double tol, double *energies, BWork &W,
+                              std::vector<std::pair<void *, size_t>> &mine) {
     const int ninst = b->ninst;
     const int64_t ntot = b->ntot;
     int rc = FCI_OK;
-    BWork W{};
     W.b = b;
     W.s = b->stream;
     W.nroots = nroots;
     W.mixed = b->opt.precision == FCI_PREC_MIXED;
     const int maxsub = std::min(kMaxSub, std::max(b->opt.max_subspace, 2 * nroots));
     W.maxsub = maxsub;
-    std::vector<std::pair<void *, size_t>> mine;
     auto get = [&](size_t bytes) -> void * {
         if (rc) return nullptr;
+        mine.push_back({nullptr, 0});  // the slot exists before the allocation
         void *p = nullptr;
         if (cudaMalloc(&p, bytes) != cudaSuccess) {
             cudaGetLastError();
             rc = fail(FCI_ERR_OOM, "batched Davidson: device allocation failed");
             return nullptr;
         }
-        mine.push_back({p, bytes});
+        mine.back() = {p, bytes};
         return p;
     };
     W.Bv = (double *)get(sizeof(double) * maxsub * ntot);
@@ -1098,15 +1117,7 @@ extern "C" int fci_batch_davidson(fci_batch *b, int nroots, double tol, double *
     W.ptr32 = (void **)get(sizeof(void *) * 2 * ninst);
     W.ptrBS = (void **)get(sizeof(void *) * 2 * ninst * maxsub);
     W.ptrXT = (void **)get(sizeof(void *) * 2 * ninst * nroots);
-    auto cleanup = [&]() {
-        for (auto &kv : W.g_ritz) cudaGraphExecDestroy(kv.second);
-        for (auto &kv : W.g_expand) cudaGraphExecDestroy(kv.second);
-        for (auto &a : mine) cudaFree(a.first);
-    };
-    if (rc) {
-        cleanup();
-        return rc;
-    }
+    if (rc) return rc;
     cudaStream_t s = W.s;
     {
         std::vector<void *> t(2 * ninst);
@@ -1114,21 +1125,21 @@ extern "C" int fci_batch_davidson(fci_batch *b, int nroots, double tol, double *
             t[i] = W.c32 + b->off[i];
             t[ninst + i] = W.s32 + b->off[i];
         }
-        cudaMemcpy(W.ptr32, t.data(), sizeof(void *) * 2 * ninst, cudaMemcpyHostToDevice);
+        FCI_CUDA(cudaMemcpy(W.ptr32, t.data(), sizeof(void *) * 2 * ninst, cudaMemcpyHostToDevice));
         std::vector<void *> u(2 * ninst * maxsub);
         for (int j = 0; j < maxsub; ++j)
             for (int i = 0; i < ninst; ++i) {
                 u[(size_t)j * 2 * ninst + i] = W.Bv + (size_t)j * ntot + b->off[i];
                 u[(size_t)j * 2 * ninst + ninst + i] = W.Sv + (size_t)j * ntot + b->off[i];
             }
-        cudaMemcpy(W.ptrBS, u.data(), sizeof(void *) * u.size(), cudaMemcpyHostToDevice);
+        FCI_CUDA(cudaMemcpy(W.ptrBS, u.data(), sizeof(void *) * u.size(), cudaMemcpyHostToDevice));
         std::vector<void *> v(2 * ninst * nroots);
         for (int k = 0; k < nroots; ++k)
             for (int i = 0; i < ninst; ++i) {
                 v[(size_t)k * 2 * ninst + i] = W.X + (size_t)k * ntot + b->off[i];
                 v[(size_t)k * 2 * ninst + ninst + i] = W.T + (size_t)k * ntot + b->off[i];
             }
-        cudaMemcpy(W.ptrXT, v.data(), sizeof(void *) * v.size(), cudaMemcpyHostToDevice);
+        FCI_CUDA(cudaMemcpy(W.ptrXT, v.data(), sizeof(void *) * v.size(), cudaMemcpyHostToDevice));
     }
     std::vector<int> active(ninst, 1), exact(ninst, W.mixed ? 0 : 1), inner(ninst, 0), refine(ninst, 0), expand(ninst);
     std::vector<double> e_prev((size_t)ninst * nroots, INFINITY), r_ref(ninst, INFINITY);
@@ -1150,10 +1161,7 @@ extern "C" int fci_batch_davidson(fci_batch *b, int nroots, double tol, double *
     int m = nroots;
     for (int j = 0; j < m && !rc; ++j)
         bdots(W, W.on, W.Bv, m, W.Sv + (size_t)j * ntot, W.A + j, kMaxSub * kMaxSub, kMaxSub);
-    if (rc) {
-        cleanup();
-        return rc;
-    }
+    if (rc) return rc;
 
     int it = 0;
     bool all_done = false;
@@ -1297,7 +1305,6 @@ extern "C" int fci_batch_davidson(fci_batch *b, int nroots, double tol, double *
     }
     b->stats[0] = it > b->opt.max_iter ? b->opt.max_iter : it;
     cudaError_t e = cudaStreamSynchronize(s);
-    cleanup();
     if (rc) return rc;
     if (e != cudaSuccess) return cuda_fail(e, "batched Davidson");
     for (int i : b->hyb) {  // bounded waits of the tensor-core sigma_3
@@ -1307,4 +1314,38 @@ extern "C" int fci_batch_davidson(fci_batch *b, int nroots, double tol, double *
     }
     if (!all_done) return fail(FCI_ERR_NOCONV, "batched Davidson: some instances did not converge within max_iter");
     return FCI_OK;
+}
+}  // namespace bt
+}  // namespace fci
+
+extern "C" int fci_batch_davidson(fci_batch *b, int nroots, double tol, double *energies) {
+    using namespace fci::bt;
+    if (!b || !energies) return fail(FCI_ERR_ARG, "NULL argument");
+    if (nroots < 1 || nroots > kMaxRoots) return fail(FCI_ERR_ARG, "nroots must be in 1..8");
+    for (int i = 0; i < b->ninst; ++i)
+        if (b->h_inst[i].ndet < 2 * nroots) return fail(FCI_ERR_ARG, "an instance has fewer than 2*nroots determinants");
+    if (!(tol > 0)) return fail(FCI_ERR_ARG, "tol must be positive");
+    FCI_CUDA(cudaSetDevice(b->device));
+    FCI_CUDA(cudaDeviceSynchronize());
+    BWork W{};
+    std::vector<std::pair<void *, size_t>> mine;
+    int rc = FCI_OK;
+    try {
+        rc = batch_davidson_run(b, nroots, tol, energies, W, mine);
+    } catch (const std::bad_alloc &) {  // host vectors: no exception crosses the C ABI
+        rc = fail(FCI_ERR_OOM, "batched Davidson: host allocation failed");
+    }
+    // an error between stream capture begin and end leaves the stream capturing
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(b->stream, &cap) == cudaSuccess && cap != cudaStreamCaptureStatusNone) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(b->stream, &g);
+        if (g) cudaGraphDestroy(g);
+    }
+    cudaStreamSynchronize(b->stream);
+    for (auto &kv : W.g_ritz) cudaGraphExecDestroy(kv.second);
+    for (auto &kv : W.g_expand) cudaGraphExecDestroy(kv.second);
+    for (auto &a : mine)
+        if (a.first) cudaFree(a.first);
+    return rc;
 }

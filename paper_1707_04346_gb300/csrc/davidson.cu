@@ -466,17 +466,19 @@ struct Work {
     std::vector<void *> allocs;
     std::vector<size_t> sizes;
 
+    // The bookkeeping slots are made before the device allocation, so a host
+    // allocation failure (bad_alloc) can never leave a device buffer unrecorded.
     template <typename P>
     P *get(size_t count) {
+        allocs.push_back(nullptr);
+        sizes.push_back(0);
         P *p = (P *)dalloc(ctx, sizeof(P) * count, &rc);
-        if (p) {
-            allocs.push_back(p);
-            sizes.push_back(sizeof(P) * count);
-        }
+        allocs.back() = p;
+        sizes.back() = p ? sizeof(P) * count : 0;
         return p;
     }
     ~Work() {
-        for (size_t i = 0; i < allocs.size(); ++i) dfree(ctx, allocs[i], sizes[i]);
+        for (size_t i = 0; i < allocs.size() && i < sizes.size(); ++i) dfree(ctx, allocs[i], sizes[i]);
     }
 };
 

@@ -27,6 +27,14 @@ int cuda_fail(cudaError_t e, const char *what) {
 
 void *dalloc(fci_ctx *ctx, size_t bytes, int *rc) {
     if (*rc != FCI_OK || bytes == 0) return nullptr;
+    if (ctx->opt.max_device_bytes > 0 && (double)ctx->bytes + (double)bytes > ctx->opt.max_device_bytes) {
+        char buf[200];
+        snprintf(buf, sizeof(buf), "allocation of %zu bytes would exceed fci_options.max_device_bytes (%.0f; %zu held)",
+                 bytes, ctx->opt.max_device_bytes, ctx->bytes);
+        set_error(buf);
+        *rc = FCI_ERR_OOM;
+        return nullptr;
+    }
     void *p = nullptr;
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) {
@@ -142,6 +150,7 @@ int fci_init(fci_ctx **out, int norb, int nalpha, int nbeta, const double *h1, c
     if (o.precision != FCI_PREC_FP64 && o.precision != FCI_PREC_MIXED) return fail(FCI_ERR_ARG, "unknown precision");
     if (o.f32_splits != 2 && o.f32_splits != 3) return fail(FCI_ERR_ARG, "f32_splits must be 2 or 3");
     if (o.same_spin_tc != 0 && o.same_spin_tc != 1) return fail(FCI_ERR_ARG, "same_spin_tc must be 0 or 1");
+    if (!(o.max_device_bytes >= 0)) return fail(FCI_ERR_ARG, "max_device_bytes must be >= 0");
     if (o.f64_kernels < FCI_F64_AUTO || o.f64_kernels > FCI_F64_SLICED)
         return fail(FCI_ERR_ARG, "f64_kernels must be FCI_F64_AUTO, FCI_F64_FMA or FCI_F64_SLICED");
     if (int rc = check_integrals(norb, h1, eri, o.symmetry_tol)) return rc;
@@ -339,6 +348,21 @@ int fci_profile_read(fci_ctx *ctx, double *ms, int cap_records, int *nrecords, i
 const char *fci_profile_kernel_name(fci_ctx *ctx, int i) {
     if (!ctx || i < 0 || i >= (int)ctx->prof_names.size()) return nullptr;
     return ctx->prof_names[i];
+}
+
+int fci_check_wait_timeout(fci_ctx *ctx) {
+    if (!ctx) return fail(FCI_ERR_ARG, "ctx is NULL");
+    FCI_CUDA(cudaSetDevice(ctx->device));
+    FCI_CUDA(cudaStreamSynchronize(ctx->stream));
+    FCI_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+    if (int rc = launch_wait_timeout_probe(ctx)) return rc;
+    int h = 0;
+    FCI_CUDA(cudaMemcpyAsync(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    FCI_CUDA(cudaStreamSynchronize(ctx->stream));
+    FCI_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+    FCI_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (h) return fail(FCI_ERR_TIMEOUT, "a bounded device wait gave up (self-test: no thread arrives on its barrier)");
+    return FCI_OK;
 }
 
 int64_t fci_query(fci_ctx *ctx, int what) {

@@ -142,6 +142,8 @@ bool tile_schedule_host(const uint32_t *tab, int64_t ns, int K, std::vector<uint
 
 // sigma.cu
 int launch_sigma(fci_ctx *ctx, const void *c, void *sigma, int dtype, cudaStream_t s);
+bool f32_same_spin_tc(const fci_ctx *ctx);
+int alloc_sigma_workspace(fci_ctx *ctx);  // at fci_init: ws32 when the FP32 same-spin tensor-core path is used
 
 // FP32 sigma of one batched instance, skipped on the device when *active == 0
 bool sigma_f32_gated_ok(const fci_ctx *ctx);
@@ -156,6 +158,7 @@ int prepare_sigma3_tc(const fci_ctx *ctx, int nsplit);
 int launch_same_spin_tc(fci_ctx *ctx, const float *C, float *sig, const SpinTables &R, const SpinTables &cols,
                         cudaStream_t s);
 size_t sigma3_tc_smem(const fci_ctx *ctx, int nsplit);
+int launch_wait_timeout_probe(fci_ctx *ctx);  // fci_check_wait_timeout
 
 // sigma3_sliced.cu (FP64-accurate sigma_3 on the tensor cores)
 int build_sliced_tables(fci_ctx *ctx, const double *eri_host);

@@ -196,8 +196,14 @@ extern "C" int fci_rdm1_noalloc(fci_ctx *ctx, const void *c, int dtype, double *
     using namespace fci;
     if (!ctx || !c || !gamma) return fail(FCI_ERR_ARG, "NULL argument");
     if (dtype != FCI_F64 && dtype != FCI_F32) return fail(FCI_ERR_ARG, "dtype must be FCI_F64 or FCI_F32");
+    // the caller's current device is restored on every return path
+    int prev = -1;
+    FCI_CUDA(cudaGetDevice(&prev));
     FCI_CUDA(cudaSetDevice(ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
-    if (dtype == FCI_F64) return rdm_noalloc_impl<double>(ctx, (const double *)c, gamma, s);
-    return rdm_noalloc_impl<float>(ctx, (const float *)c, gamma, s);
+    const int rc = dtype == FCI_F64 ? rdm_noalloc_impl<double>(ctx, (const double *)c, gamma, s)
+                                    : rdm_noalloc_impl<float>(ctx, (const float *)c, gamma, s);
+    const cudaError_t e = cudaSetDevice(prev);
+    if (rc == FCI_OK && e != cudaSuccess) return cuda_fail(e, "cudaSetDevice (restoring the caller's device)");
+    return rc;
 }

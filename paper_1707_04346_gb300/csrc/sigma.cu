@@ -378,6 +378,26 @@ static size_t smem_limit() {
     return (size_t)lim;
 }
 
+// Whether FP32 sigma_1/sigma_2 run through intermediate strings on the tensor
+// cores (asked for, or the staged same-spin kernels do not fit); that path
+// needs the 2N-float workspace ws32, which fci_init allocates.
+bool f32_same_spin_tc(const fci_ctx *ctx) {
+    const SpinTables &A = ctx->A, &B = ctx->B;
+    const size_t lim = smem_limit();
+    auto fits = [&](int r, int64_t len) { return (size_t)r * len * sizeof(float) <= lim; };
+    const bool fused = A.ne == B.ne && A.ns == B.ns && fits(8, A.ns);  // 2 x 4 rows of the fused kernel
+    const bool tc_ok = A.nsingle > 0 && B.nsingle > 0 && ctx->npair + 1 <= 256 && A.nsingle <= 96 &&
+                       B.nsingle <= 96;
+    return tc_ok && (ctx->opt.same_spin_tc == 1 || (!fused && (A.ne == B.ne || !fits(4, B.ns) || !fits(4, A.ns))));
+}
+
+int alloc_sigma_workspace(fci_ctx *ctx) {
+    if (!f32_same_spin_tc(ctx) || ctx->ws32) return FCI_OK;
+    int rc = FCI_OK;
+    ctx->ws32 = (float *)dalloc(ctx, sizeof(float) * 2 * (size_t)ctx->ndet, &rc);
+    return rc;
+}
+
 template <typename T>
 static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s) {
     const SpinTables &A = ctx->A, &B = ctx->B;
@@ -396,11 +416,7 @@ static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s) {
             if (!fusedR && (size_t)2 * r * nsa * sizeof(float) <= lim) fusedR = r;
     // FP32 same-spin terms through intermediate strings on the tensor cores: when
     // asked for, or when the staged kernels above do not fit (large string spaces)
-    const bool tc_ok = A.nsingle > 0 && B.nsingle > 0 && ctx->npair + 1 <= 256 && A.nsingle <= 96 &&
-                       B.nsingle <= 96;
-    const bool same_tc = sizeof(T) == 4 && tc_ok &&
-                         (ctx->opt.same_spin_tc == 1 ||
-                          (fusedR == 0 && (A.ne == B.ne || pick_r(nsb) < 4 || pick_r(nsa) < 4)));
+    const bool same_tc = sizeof(T) == 4 && f32_same_spin_tc(ctx);
     // profiled kernels (fci_profile_read): two slots when fused, else three
     static const char *const names3[3] = {"sigma1_rows", "sigma2_cols", sizeof(T) == 4 ? "sigma3_tc" : "sigma3_exact"};
     static const char *const names3tc[3] = {"sigma2_tc", "sigma1_tc", "sigma3_tc"};
@@ -423,11 +439,7 @@ static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s) {
     }
     if (same_tc) {
         if constexpr (sizeof(T) == 4) {
-            if (!ctx->ws32) {
-                int rc = FCI_OK;
-                ctx->ws32 = (float *)dalloc(ctx, sizeof(float) * 2 * (size_t)ctx->ndet, &rc);
-                if (rc) return rc;
-            }
+            if (!ctx->ws32) return fail(FCI_ERR_STATE, "FP32 same-spin workspace missing (made at fci_init)");
             float *Ct = ctx->ws32, *Tt = ctx->ws32 + ctx->ndet;
             FCI_CUDA(cudaMemsetAsync(sig, 0, sizeof(float) * (size_t)ctx->ndet, s));
             // sigma_2: intermediate alpha strings, rows of C

@@ -143,6 +143,27 @@ int launch_same_spin_tc(fci_ctx *ctx, const float *C, float *sig, const SpinTabl
     return FCI_OK;
 }
 
+// One block waits, through the bounded wait of the tensor-core kernels, on a
+// barrier that no thread arrives on; when the wait gives up it sets the error
+// word, as those kernels do, and then completes the barrier's phase itself so
+// that nothing is left pending.
+__global__ void k_wait_timeout_probe(int *err) {
+    __shared__ uint64_t bar;
+    const uint32_t a = tc::smem_u32(&bar);
+    if (threadIdx.x == 0) tc::mbar_init(a, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (!tc::mbar_wait_bounded(a, 0u)) atomicExch(err, 1);
+        tc::mbar_arrive(a);
+    }
+}
+
+int launch_wait_timeout_probe(fci_ctx *ctx) {
+    k_wait_timeout_probe<<<1, 32, 0, ctx->stream>>>(ctx->d_err);
+    FCI_CUDA(cudaGetLastError());
+    return FCI_OK;
+}
+
 size_t sigma3_tc_smem(const fci_ctx *ctx, int nsplit) {
     if (ctx->A.nsingle == 0 || ctx->B.nsingle == 0 || !ctx->B.tsched) return 0;
     const int kpad = round_up(ctx->A.nsingle, 16), npad = round_up(ctx->npair, 16);

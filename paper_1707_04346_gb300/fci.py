@@ -29,7 +29,7 @@ EXPORTED = [
     "fci_davidson_log", "fci_rdm1", "fci_get_strings", "fci_get_single_table", "fci_query",
     "fci_last_error", "fci_profile_enable", "fci_profile_read", "fci_profile_kernel_name",
     "fci_rdm1_noalloc", "fci_batch_init", "fci_batch_davidson", "fci_batch_sigma", "fci_batch_offset",
-    "fci_batch_tuning", "fci_batch_stats", "fci_batch_free", "fci_tile_schedule",
+    "fci_batch_tuning", "fci_batch_stats", "fci_batch_free", "fci_tile_schedule", "fci_check_wait_timeout",
 ]
 
 
@@ -61,6 +61,7 @@ class fci_options(ctypes.Structure):
         ("f32_splits", ctypes.c_int),
         ("same_spin_tc", ctypes.c_int),
         ("f64_kernels", ctypes.c_int),
+        ("max_device_bytes", ctypes.c_double),
     ]
 
 
@@ -120,6 +121,8 @@ def load(path: str = LIB_PATH):
         lib.fci_batch_stats.argtypes = [vp, i32]
         lib.fci_batch_free.restype = i32
         lib.fci_batch_free.argtypes = [vp]
+        lib.fci_check_wait_timeout.restype = i32
+        lib.fci_check_wait_timeout.argtypes = [vp]
         lib.fci_rdm1_noalloc.restype = i32
         lib.fci_rdm1_noalloc.argtypes = [vp, vp, i32, vp, vp]
         lib.fci_profile_kernel_name.restype = ctypes.c_char_p

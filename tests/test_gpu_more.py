@@ -75,17 +75,21 @@ def test_davidson_not_converged_reports_energies(pkg):
     pkg.fci_free(ctx)
 
 
-def test_profile_api(pkg):
+@pytest.mark.parametrize("mode,expect", [
+    (0, ["slice_c", "sigma3_sliced", "sigma1_rows", "sigma2_cols"]),  # FCI_F64_AUTO
+    (1, ["sigma1_rows", "sigma2_cols", "sigma3_exact"]),  # FCI_F64_FMA
+])
+def test_profile_api(pkg, mode, expect):
     h1, eri = fi.make_integrals(10, 60)
-    ctx = pkg.fci_init(10, 5, 5, h1, eri)
+    ctx = pkg.fci_init(10, 5, 5, h1, eri, pkg.default_options(f64_kernels=mode))
     c = torch.from_numpy(fi.make_vector(ctx.ndet)).to(DEV)
     s = torch.empty_like(c)
     pkg.fci_profile_enable(ctx, True)
     for _ in range(3):
         pkg.fci_sigma(ctx, c, s)
     names, ms = pkg.fci_profile_read(ctx)
-    assert names == ["sigma1_rows", "sigma2_cols", "sigma3_exact"]
-    assert ms.shape == (3, 3) and np.all(ms > 0)
+    assert names == expect
+    assert ms.shape == (3, len(expect)) and np.all(ms > 0)
     pkg.fci_profile_enable(ctx, False)
     pkg.fci_free(ctx)
 
