@@ -88,6 +88,10 @@ typedef struct fci_options {
                             workspace) may hold; an allocation beyond it fails with
                             FCI_ERR_OOM before cudaMalloc is called.  0 = no cap (default).
                             (Resource control; no counterpart in the paper.) */
+    int f32_row_global;  /* FCI_F32 tensor-core sigma_3: 1 = keep the sigma row in global
+                            memory (the epilogue large spaces such as CAS(18,18) need) even
+                            where it fits in shared memory, so that small spaces exercise
+                            it; 0 = shared memory where it fits (default) */
 } fci_options;
 
 /* fci_options.f64_kernels: how the FCI_F64 sigma is computed.  All modes meet

@@ -151,6 +151,7 @@ int fci_init(fci_ctx **out, int norb, int nalpha, int nbeta, const double *h1, c
     if (o.f32_splits != 2 && o.f32_splits != 3) return fail(FCI_ERR_ARG, "f32_splits must be 2 or 3");
     if (o.same_spin_tc != 0 && o.same_spin_tc != 1) return fail(FCI_ERR_ARG, "same_spin_tc must be 0 or 1");
     if (!(o.max_device_bytes >= 0)) return fail(FCI_ERR_ARG, "max_device_bytes must be >= 0");
+    if (o.f32_row_global != 0 && o.f32_row_global != 1) return fail(FCI_ERR_ARG, "f32_row_global must be 0 or 1");
     if (o.f64_kernels < FCI_F64_AUTO || o.f64_kernels > FCI_F64_SLICED)
         return fail(FCI_ERR_ARG, "f64_kernels must be FCI_F64_AUTO, FCI_F64_FMA or FCI_F64_SLICED");
     if (int rc = check_integrals(norb, h1, eri, o.symmetry_tol)) return rc;

@@ -30,12 +30,12 @@ static int tmem_columns(int npad, int kpad, int nsplit, int stages, bool atm) {
 // A placement that fit in `lim` bytes of shared memory and 512 tensor-memory
 // columns; A in tensor memory and two A buffers preferred.
 static bool pick_layout(int nsplit, int kpad, int npad, int64_t nsb, int nsa_single, int lim, int *epi, int *stages,
-                        bool *atm) {
+                        bool *atm, bool global_row = false) {
     // {epilogue, A buffers, A in tensor memory}
     static const int order[][3] = {{2, 2, 1}, {2, 2, 0}, {2, 1, 1}, {2, 1, 0},
                                    {3, 2, 1}, {3, 1, 1}, {3, 2, 0}, {3, 1, 0}};
     for (const auto &o : order)
-        if (tmem_columns(npad, kpad, nsplit, o[1], o[2] != 0) <= 512 &&
+        if ((o[0] == 3 || !global_row) && tmem_columns(npad, kpad, nsplit, o[1], o[2] != 0) <= 512 &&
             (int)tc::make_layout(nsplit, kpad, npad, nsb, nsa_single, o[0], o[1], o[2] != 0).total <= lim) {
             *epi = o[0];
             *stages = o[1];
@@ -60,7 +60,7 @@ static int tc_plan(const fci_ctx *ctx, int nsplit, TcPlan *P) {
     if (!ctx->B.tsched) return fail(FCI_ERR_ARG, "tensor-core sigma_3: no tile schedule (more than 65408 beta strings)");
     int epi = 0, stages = 0;
     bool atm = false;
-    if (!pick_layout(nsplit, kpad, npad, ctx->B.ns, ctx->A.nsingle, lim, &epi, &stages, &atm))
+    if (!pick_layout(nsplit, kpad, npad, ctx->B.ns, ctx->A.nsingle, lim, &epi, &stages, &atm, ctx->opt.f32_row_global != 0))
         return fail(FCI_ERR_ARG, "tensor-core sigma_3: operands exceed shared or tensor memory");
     P->kern = tc_kernel(nsplit, kpad, epi, atm);
     P->npad = npad;

@@ -62,6 +62,7 @@ class fci_options(ctypes.Structure):
         ("same_spin_tc", ctypes.c_int),
         ("f64_kernels", ctypes.c_int),
         ("max_device_bytes", ctypes.c_double),
+        ("f32_row_global", ctypes.c_int),
     ]
 
 

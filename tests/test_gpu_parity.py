@@ -267,6 +267,44 @@ def test_davidson_cas14_vs_oracle_davidson(pkg, oracle_mod):
     assert np.abs(hx - e64[0] * x[rows]).max() < 1e-4
 
 
+def _rayleigh_tie(pkg, oracle_mod, norb, tol, precision):
+    """The GPU Davidson energy against the Rayleigh quotient of its vector
+    formed with one full oracle sigma (the oracle's direct Slater-Condon sum):
+    the quotient's error is second order in the vector's error, so it pins the
+    energy to about ||r||^2 <= tol, and the oracle residual bounds ||r||."""
+    ne = norb // 2
+    ctx, h1, eri = make_ctx(pkg, norb, ne, ne, rank=100, precision=precision)
+    vec = torch.empty((1, ctx.ndet), dtype=torch.float64, device=DEV)
+    e = pkg.fci_davidson(ctx, 1, tol, vecs=vec)[0]
+    x = vec[0].cpu().numpy()
+    hx = oracle_mod.sigma(norb, ne, ne, h1, eri, x)
+    rq = float(x @ hx / (x @ x))
+    r = np.linalg.norm(hx - rq * x) / np.linalg.norm(x)
+    pkg.fci_free(ctx)
+    return e, rq, r
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_davidson_cas12_energy_tied_to_oracle(pkg, oracle_mod, precision):
+    """CAS(12,12) (853,776 determinants), FP64 and mixed precision: the
+    energy equals the oracle Rayleigh quotient of the returned vector within
+    1e-9 Eh, and the oracle residual is below sqrt(tol)."""
+    e, rq, r = _rayleigh_tie(pkg, oracle_mod, 12, 1e-10, precision)
+    assert abs(e - rq) < 1e-9, (e, rq)
+    assert r < 1e-5, r
+
+
+@pytest.mark.skipif(not __import__("os").environ.get("FCI_SLOW_TESTS"),
+                    reason="one full oracle sigma at CAS(14,14) takes minutes on the host (set FCI_SLOW_TESTS=1)")
+def test_davidson_cas14_energy_tied_to_oracle(pkg, oracle_mod):
+    """The benchmark's CAS(14,14) (11,778,624 determinants) FP64 energy against
+    the oracle Rayleigh quotient of its vector, within 1e-9 Eh."""
+    e, rq, r = _rayleigh_tie(pkg, oracle_mod, 14, 1e-10, 0)
+    print(f"CAS(14,14): E_gpu {e:.12f}  E_oracle_rayleigh {rq:.12f}  |dE| {abs(e - rq):.2e}  ||r|| {r:.2e}")
+    assert abs(e - rq) < 1e-9, (e, rq)
+    assert r < 1e-5, r
+
+
 @pytest.mark.parametrize("norb,na,nb", [(6, 3, 3), (7, 4, 3), (8, 4, 4), (5, 0, 2)])
 def test_rdm1(pkg, oracle_mod, norb, na, nb):
     ctx, _, _ = make_ctx(pkg, norb, na, nb)
