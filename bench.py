@@ -173,6 +173,115 @@ def cpu_baseline(norb, na, nb, h1, eri, c, target_s=15.0, seed=0):
                       f"{dt:.1f} s"}
 
 
+def kernel_work(name, norb, na, nb, N, sa, sb, nsa, nsb, peaks, f32_splits=3):
+    """(bound, amount per launch, unit, peak, peak source, description) of one
+    sigma kernel: the algorithmic work each kernel's roofline is taken on."""
+    nsame = 1 + na * (norb - na) + (na * (na - 1) // 2) * ((norb - na) * (norb - na - 1) // 2)
+    npair = norb * (norb + 1) // 2
+    kpad = -(-sa // 16) * 16
+    npad = -(-npair // 16) * 16
+    npad1 = -(-(npair + 1) // 16) * 16
+    tiles = nsa * (-(-nsb // 128))
+    fp32_pipe = FP32_LANES_PER_SM * GB300_SMS * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # Tops/s
+    bf16 = (peaks["bf16_tflops"], "MEASURED_PEAKS.json bf16_tflops (burst; the kernel is timed in short bursts)")
+    fp32src = "FP32 pipe: 128 lanes x 152 SMs x max SM clock"
+    prods32 = f32_splits * (f32_splits + 1) // 2
+    if name == "sigma3_exact":  # diagonal replacements merged
+        f = 2.0 * (sb + (sa - na) * (sb - nb + 1))
+        return ("alu", f * N, "TFLOP/s", FP64_NOMINAL_TFLOPS,
+                "GB300 FP64 nominal 1.25 TFLOP/s (no FP64 entry in MEASURED_PEAKS.json)", f"FP64 FLOP, {f:.0f} per determinant")
+    if name == "sigma3_sliced":
+        return ("tensor", 21 * 2.0 * 128 * npad * kpad * tiles, "TFLOP/s", *bf16,
+                f"bf16 MMA FLOP: 21 slice products x 2 x 128 x {npad} x {kpad} x {tiles} tiles")
+    if name in ("sigma1_rows", "sigma2_cols"):  # FP64 path: double-float, 12 FP32 operations per term
+        return ("alu", 12.0 * nsame * N, "Tops/s", fp32_pipe, fp32src,
+                f"FP32 operations: 12 per term x {nsame} terms per determinant")
+    if name == "sigma12_f32":  # FP32 sigma_1 + sigma_2: one FMA per term
+        return ("alu", 2.0 * nsame * N, "Tops/s", fp32_pipe, fp32src,
+                f"FP32 FMAs: {nsame} terms per determinant, two spins")
+    if name == "sigma3_tc":
+        return ("tensor", prods32 * 2.0 * 128 * npad * kpad * tiles, "TFLOP/s", *bf16,
+                f"bf16 MMA FLOP: {prods32} slice products x 2 x 128 x {npad} x {kpad} x {tiles} tiles")
+    if name in ("sigma2_tc", "sigma1_tc"):  # same-spin terms through intermediate strings
+        return ("tensor", prods32 * 2.0 * 128 * npad1 * kpad * tiles, "TFLOP/s", *bf16,
+                f"bf16 MMA FLOP: {prods32} slice products x 2 x 128 x {npad1} x {kpad} x {tiles} tiles")
+    if name == "slice_c":  # row exponents (one read of C) and the digit slices (a read, 12 bytes written)
+        return ("hbm", 28.0 * N, "GB/s", peaks["hbm_gbs"], "MEASURED_PEAKS.json hbm_gbs",
+                "bytes: two reads of C (8 + 8 per determinant) and 12 written")
+    return None
+
+
+def roofline_table(names, kmean, kshare, norb, na, nb, N, sa, sb, nsa, nsb, peaks, workload):
+    """Roofline of every kernel of one sigma pipeline; the dominant one first."""
+    def one(i):
+        w = kernel_work(names[i], norb, na, nb, N, sa, sb, nsa, nsb, peaks)
+        if w is None:
+            return {"kernel": names[i], "ms": float(kmean[i] * 1e3)}
+        bound, amount, unit, peak, src, what = w
+        ach = amount / kmean[i] / (1e9 if unit == "GB/s" else 1e12)
+        return {"kernel": names[i], "bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+                "traffic": ncu_traffic(names[i], workload), "peak_source": src,
+                "work_per_launch": f"{amount:.4g} ({what})"}
+    top = int(np.argmax(kmean))
+    roof = one(top)
+    roof["kernels"] = {n: {"ms": float(kmean[i] * 1e3), "share": float(kshare[i]),
+                           **({"frac": one(i)["frac"], "unit": one(i)["unit"]} if "frac" in one(i) else {})}
+                       for i, n in enumerate(names)}
+    return roof
+
+
+def sigma_leg(pkg, workload, steps, warmup, stream, world, cpu_seconds, dtypes=("f64", "f32")):
+    """sigma = H c throughput of one more configuration (the device fills the
+    trial vector c_J = 2 u_J - 1 from the input module's generator; one vector
+    is larger than L2), per precision: Gdet/s, per-kernel times and rooflines,
+    and the oracle on sampled rows of the same vector on the host cores."""
+    import torch
+    from fci_inputs import gpu as fgpu
+
+    norb, na, nb, rank_eri = WORKLOADS[workload]
+    h1, eri = fi.make_integrals(norb, rank_eri)
+    t0 = time.perf_counter()
+    ctx = pkg.fci_init(norb, na, nb, h1, eri)
+    out = {"workload": workload_desc(workload).replace("seeds 1707/4346", "c_J = 2u_J - 1 generated per index"),
+           "init_s": time.perf_counter() - t0}
+    N = ctx.ndet
+    nsa, nsb = ctx.nstr
+    sa, sb = pkg.fci_query(ctx, 4), pkg.fci_query(ctx, 5)
+    peaks = load_peaks()
+    for dt in dtypes:
+        tdt = torch.float64 if dt == "f64" else torch.float32
+        c = torch.empty(N, dtype=tdt, device=stream.device)
+        fgpu.fill_pm1(c)
+        sgm = torch.empty_like(c)
+        pkg.fci_profile_enable(ctx, True)
+        t = time_sigma_ring(pkg, ctx, [c], [sgm], steps, warmup, stream, world)
+        names, prof = pkg.fci_profile_read(ctx)
+        pkg.fci_profile_enable(ctx, False)
+        t = max_over_ranks(t, world)
+        prof = prof[-steps:]
+        kmean = prof.mean(axis=0) / 1e3
+        kshare = prof.sum(axis=0) / prof.sum()
+        out[dt] = {"value": world * N * steps / t / 1e9, "unit": "Gdet/s", "ms_per_step": t / steps * 1e3,
+                   "steps": steps, "warmup": warmup,
+                   "roofline": roofline_table(names, kmean, kshare, norb, na, nb, N, sa, sb, nsa, nsb, peaks, workload)}
+        del c, sgm
+    pkg.fci_free(ctx)
+    if cpu_seconds > 0:
+        import oracle
+
+        rows = np.random.default_rng(7).integers(0, N, 16)
+        oracle.sigma_rows_generated(norb, na, nb, h1, eri, rows[:2], fi.DEFAULT_VECTOR_SEED, fi.STREAM_C_PM1)
+        t0, nrows = time.perf_counter(), 0
+        while time.perf_counter() - t0 < cpu_seconds:
+            oracle.sigma_rows_generated(norb, na, nb, h1, eri, rows, fi.DEFAULT_VECTOR_SEED, fi.STREAM_C_PM1)
+            nrows += len(rows)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": nrows / dt / 1e9, "unit": "Gdet/s", "cores": oracle.num_threads(),
+                               "kind": "oracle", "sample": f"{nrows} sampled sigma rows of CAS({na + nb}e,{norb}o), "
+                                                          f"direct Slater-Condon sum, FP64, {dt:.1f} s"}
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -441,46 +550,9 @@ def run_ours(args):
     top = int(np.argmax(kmean))
     sa = pkg.fci_query(ctx, 4)
     sb = pkg.fci_query(ctx, 5)
-    from paper_1707_04346_gb300 import fci as F
 
-    # algorithmic work per launch, and the peak of the unit that bounds each kernel
-    nsame = 1 + na * (norb - na) + (na * (na - 1) // 2) * ((norb - na) * (norb - na - 1) // 2)
     peaks = load_peaks()
-    kpad = -(-sa // 16) * 16
-    npad = -(-(norb * (norb + 1) // 2) // 16) * 16
-    tiles = nsa * (-(-nsb // 128))
-    sliced_flops = 21 * 2.0 * 128 * npad * kpad * tiles
-    fp32_pipe = FP32_LANES_PER_SM * GB300_SMS * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # Tops/s
-    work = {
-        # diagonal replacements merged: 2 * (s_b + (s_a - n_a)(s_b - n_b + 1)) per determinant
-        "sigma3_exact": ("alu", 2.0 * (sb + (sa - na) * (sb - nb + 1)) * N, "TFLOP/s", FP64_NOMINAL_TFLOPS,
-                         "GB300 FP64 nominal 1.25 TFLOP/s (no FP64 entry in MEASURED_PEAKS.json)",
-                         "FP64 FLOP, %.0f per determinant" % (2.0 * (sb + (sa - na) * (sb - nb + 1)))),
-        # 21 bf16 slice products x 2 x 128 x npad x kpad per 128-string tile (executed MMA FLOP)
-        "sigma3_sliced": ("tensor", sliced_flops, "TFLOP/s", peaks["bf16_tflops"],
-                          "MEASURED_PEAKS.json bf16_tflops (burst; the kernel is timed in short bursts)",
-                          f"bf16 MMA FLOP: 21 slice products x 2 x 128 x {npad} x {kpad} x {tiles} tiles"),
-        # double-float: 12 FP32 operations per ELL term, nsame terms per determinant
-        "sigma1_rows": ("alu", 12.0 * nsame * N, "Tops/s", fp32_pipe,
-                        "FP32 pipe: 128 lanes x 152 SMs x max SM clock",
-                        f"FP32 operations: 12 per term x {nsame} terms per determinant"),
-        "sigma2_cols": ("alu", 12.0 * nsame * N, "Tops/s", fp32_pipe,
-                        "FP32 pipe: 128 lanes x 152 SMs x max SM clock",
-                        f"FP32 operations: 12 per term x {nsame} terms per determinant"),
-        # row exponents (one read of C) and the digit slices (a read of C, 12 bytes written)
-        "slice_c": ("hbm", 28.0 * N, "GB/s", peaks["hbm_gbs"], "MEASURED_PEAKS.json hbm_gbs",
-                    "bytes: two reads of C (8 + 8 per determinant) and 12 written"),
-    }
-    def roofline_of(i):
-        bound, amount, unit, peak, src, what = work[names[i]]
-        scale = 1e9 if unit == "GB/s" else 1e12
-        ach = amount / kmean[i] / scale
-        return {"kernel": names[i], "bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
-                "traffic": ncu_traffic(names[i], args.workload), "peak_source": src,
-                "work_per_launch": f"{amount:.4g} ({what})"}
-    roof = roofline_of(top)
-    roof["kernels"] = {n: {"ms": float(kmean[i] * 1e3), "share": float(kshare[i]),
-                           "frac": roofline_of(i)["frac"], "unit": work[n][2]} for i, n in enumerate(names)}
+    roof = roofline_table(names, kmean, kshare, norb, na, nb, N, sa, sb, nsa, nsb, peaks, args.workload)
     if "sigma3_sliced" in names:
         i3 = names.index("sigma3_sliced")
         exact_sparse = 2.0 * sa * sb * N  # 2 s^2 FLOP per determinant (the method's exact-sparse count)
@@ -496,21 +568,13 @@ def run_ours(args):
     t32 = max_over_ranks(t32, world)
     fp32_value = world * N * args.steps / t32 / 1e9
     del v32, o32
-    k32 = prof32[-args.steps:].mean(axis=0) / 1e3
-    kpad = -(-sa // 16) * 16
-    npad = -(-(norb * (norb + 1) // 2) // 16) * 16
-    nsplit = pkg.default_options().f32_splits
-    products = nsplit * (nsplit + 1) // 2
-    tiles = nsa * (-(-nsb // 128))
-    mma_flops = products * 2.0 * 128 * npad * kpad * tiles
-    itc = names32.index("sigma3_tc")
-    roof_tc = {"kernel": "sigma3_tc", "bound": "tensor", "achieved": mma_flops / k32[itc] / 1e12,
-               "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
-               "frac": mma_flops / k32[itc] / 1e12 / peaks["bf16_tflops"],
-               "traffic": ncu_traffic("sigma3_tc", args.workload),
-               "work_per_launch": f"{mma_flops:.4g} bf16 MMA FLOP ({products} slice products x 2 x 128 x {npad} x "
-                                  f"{kpad} x {tiles} tiles)",
-               "kernels": {n: {"ms": float(k32[i] * 1e3)} for i, n in enumerate(names32)}}
+    p32 = prof32[-args.steps:]
+    roof_tc = roofline_table(names32, p32.mean(axis=0) / 1e3, p32.sum(axis=0) / p32.sum(), norb, na, nb, N, sa, sb,
+                             nsa, nsb, peaks, args.workload)
+    if roof_tc["kernel"] != "sigma3_tc":  # report the tensor-core kernel's own roofline next to the top one
+        k = list(names32).index("sigma3_tc")
+        roof_tc["sigma3_tc"] = roofline_table(names32[k:k + 1], p32.mean(axis=0)[k:k + 1] / 1e3, np.ones(1), norb, na,
+                                              nb, N, sa, sb, nsa, nsb, peaks, args.workload)
 
     # split-BF16x3 sigma_3 (2 bf16 slices, 3 products; about 1e-5 relative)
     ctx3 = pkg.fci_init(norb, na, nb, h1, eri, pkg.default_options(f32_splits=2))
@@ -610,6 +674,17 @@ def run_ours(args):
             pkg.fci_free(ctxm)
     if args.batched and rank == 0:
         result["batched"] = run_batched(pkg, args.batch_instances)
+    if args.extra and args.workload == "cas14":
+        # the other sigma configurations: CAS(16,16) in both precisions,
+        # CAS(18,18) in FP32 (its FP64 sigma is not built)
+        legs = {}
+        legs["cas16_sigma"] = sigma_leg(pkg, "cas16", max(3, args.steps // 4), 3, stream, world,
+                                        args.cpu_seconds / 3 if (args.cpu_baseline and world == 1) else 0)
+        legs["cas18_sigma_fp32"] = sigma_leg(pkg, "cas18", 3, 3, stream, world,
+                                             args.cpu_seconds / 3 if (args.cpu_baseline and world == 1) else 0,
+                                             dtypes=("f32",))
+        if rank == 0:
+            result.update(legs)
     if args.cpu_baseline and rank == 0 and world == 1:
         result["cpu_baseline"] = cpu_baseline(norb, na, nb, h1, eri, c_host, target_s=args.cpu_seconds)
     if rank == 0:
@@ -630,6 +705,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--batch-instances", type=int, default=64)
+    ap.add_argument("--no-extra", dest="extra", action="store_false",
+                    help="skip the CAS(16,16) and CAS(18,18) sigma legs")
     ap.add_argument("--roots", type=int, default=1, help="Davidson roots (CAS(16,16) configuration: 3)")
     ap.add_argument("--ref-from-mixed", action="store_true",
                     help="FP64 reference energies from an FP64 solve started at the mixed solution")
