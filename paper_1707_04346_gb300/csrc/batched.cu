@@ -616,9 +616,10 @@ struct fci_batch {
     int row_elems64 = 0, row_elems32 = 0;
     size_t smem64 = 0, smem32 = 0;
     std::vector<int> tune;  // triples (norb, dtype, tpr)
-    // instances whose FP32 sigma runs the single-instance kernels (fused
-    // sigma_1 + sigma_2, tensor-core sigma_3) gated by their active flag; their
-    // work items come first in d_items
+    // instances whose sigma runs the single-instance kernels gated by their
+    // active flag (FP32: fused sigma_1 + sigma_2, tensor-core sigma_3; FP64:
+    // sliced sigma_3, double-float sigma_1 and sigma_2); their work items come
+    // first in d_items
     std::vector<int> hyb;
     int nitems_hyb = 0;
     // sigma call plumbing
@@ -956,10 +957,12 @@ static int batch_init_impl(fci_batch **out, int ninst, const fci_instance *inst,
             return cuda_fail(e, "batched CASCI tuning");
         }
     }
+    // large instances run the single-instance kernels in both precisions
     for (int i = 0; i < ninst && rc == FCI_OK; ++i)
-        if (b->h_inst[i].ndet >= kHybridMinDets && sigma_f32_gated_ok(b->ctx[i])) {
+        if (b->h_inst[i].ndet >= kHybridMinDets && sigma_f32_gated_ok(b->ctx[i]) && sigma_f64_gated_ok(b->ctx[i])) {
             b->hyb.push_back(i);
             rc = prepare_sigma_f32_gated(b->ctx[i]);
+            if (!rc) rc = prepare_sigma_f64_gated(b->ctx[i]);
         }
     if (rc || (rc = build_items(b, &rc))) {
         return rc;
@@ -983,10 +986,16 @@ int fci_batch_sigma(fci_batch *b, const void *c, void *sigma, int dtype, void *s
     FCI_CUDA(cudaMemcpyAsync(b->d_cin, pin.data(), sizeof(void *) * b->ninst, cudaMemcpyHostToDevice, s));
     FCI_CUDA(cudaMemcpyAsync(b->d_cout, pout.data(), sizeof(void *) * b->ninst, cudaMemcpyHostToDevice, s));
     int rc;
-    if (dtype == FCI_F64)
-        rc = launch_bsigma<double>(b, b->d_on_all, (const double *const *)b->d_cin, (double *const *)b->d_cout, s,
-                                   b->d_items, b->nitems);
-    else
+    if (dtype == FCI_F64) {
+        rc = b->nitems > b->nitems_hyb
+                 ? launch_bsigma<double>(b, b->d_on_all, (const double *const *)b->d_cin, (double *const *)b->d_cout, s,
+                                         b->d_items + b->nitems_hyb, b->nitems - b->nitems_hyb)
+                 : FCI_OK;
+        for (int i : b->hyb)
+            if (!rc)
+                rc = launch_sigma_f64_gated(b->ctx[i], (const double *)c + b->off[i], (double *)sigma + b->off[i],
+                                            b->d_on_all + i, s);
+    } else
         rc = launch_bsigma<float>(b, b->d_on_all, (const float *const *)b->d_cin, (float *const *)b->d_cout, s,
                                   b->d_items, b->nitems);
     if (rc) return rc;
@@ -1061,8 +1070,13 @@ static int bsigma(BWork &W, const int *on, const double *x, double *hx, void **t
         k_f2d<<<grid_flat(b->ntot), 256, 0, W.s>>>(W.s32, hx, b->ntot);
         return FCI_OK;
     }
-    return launch_bsigma<double>(b, on, (const double *const *)tab, (double *const *)(tab + n), W.s, b->d_items,
-                                 b->nitems);
+    if (b->nitems > b->nitems_hyb)
+        if (int rc = launch_bsigma<double>(b, on, (const double *const *)tab, (double *const *)(tab + n), W.s,
+                                           b->d_items + b->nitems_hyb, b->nitems - b->nitems_hyb))
+            return rc;
+    for (int i : b->hyb)
+        if (int rc = launch_sigma_f64_gated(b->ctx[i], x + b->off[i], hx + b->off[i], on + i, W.s)) return rc;
+    return FCI_OK;
 }
 
 }  // namespace bt

@@ -145,6 +145,12 @@ int launch_sigma(fci_ctx *ctx, const void *c, void *sigma, int dtype, cudaStream
 bool f32_same_spin_tc(const fci_ctx *ctx);
 int alloc_sigma_workspace(fci_ctx *ctx);  // at fci_init: ws32 when the FP32 same-spin tensor-core path is used
 
+// FP64 sigma of one batched instance (sliced sigma_3, double-float same-spin
+// terms), skipped on the device when *active == 0; opted in beforehand
+bool sigma_f64_gated_ok(const fci_ctx *ctx);
+int prepare_sigma_f64_gated(const fci_ctx *ctx);
+int launch_sigma_f64_gated(fci_ctx *ctx, const double *C, double *sig, const int *active, cudaStream_t s);
+
 // FP32 sigma of one batched instance, skipped on the device when *active == 0
 bool sigma_f32_gated_ok(const fci_ctx *ctx);
 int prepare_sigma_f32_gated(const fci_ctx *ctx);
@@ -164,7 +170,9 @@ int launch_wait_timeout_probe(fci_ctx *ctx);  // fci_check_wait_timeout
 int build_sliced_tables(fci_ctx *ctx, const double *eri_host);
 void free_sliced_tables(fci_ctx *ctx);
 bool sigma3_sliced_ok(const fci_ctx *ctx);
-int launch_sigma3_sliced(fci_ctx *ctx, const double *C, double *sig, cudaStream_t s, int rec, int prof_slot);
+int launch_sigma3_sliced(fci_ctx *ctx, const double *C, double *sig, cudaStream_t s, int rec, int prof_slot,
+                         const int *active = nullptr);
+int prepare_sigma3_sliced(const fci_ctx *ctx);
 
 // davidson.cu
 int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *vecs, const void *guess);

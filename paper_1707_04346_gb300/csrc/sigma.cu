@@ -146,7 +146,9 @@ __device__ __forceinline__ void df_mac(float vh, float vl, float2 c, float &sh, 
 // (add != 0) added to.
 template <int R, int U = 8>
 __global__ void __launch_bounds__(512, 1) k_sigma1_rows_df(const double *__restrict__ C, double *__restrict__ sig,
-                                                           SpinTables B, int64_t nsa, int add) {
+                                                           SpinTables B, int64_t nsa, int add,
+                                                           const int *__restrict__ active) {
+    if (active != nullptr && *active == 0) return;  // gated launch (batched engine)
     extern __shared__ float2 rows2[];  // [R][nsb]
     const int64_t nsb = B.ns;
     const int64_t r0 = (int64_t)blockIdx.x * R;
@@ -188,7 +190,8 @@ __global__ void __launch_bounds__(512, 1) k_sigma1_rows_df(const double *__restr
 // sigma_2 in double-float: R beta columns of C staged as pairs; adds to sigma.
 template <int R, int U = 8>
 __global__ void __launch_bounds__(512, 1) k_sigma2_cols_df(const double *__restrict__ C, double *__restrict__ sig,
-                                                           SpinTables A, int64_t nsb) {
+                                                           SpinTables A, int64_t nsb, const int *__restrict__ active) {
+    if (active != nullptr && *active == 0) return;
     extern __shared__ float2 cols2[];  // [R][nsa]
     const int64_t nsa = A.ns;
     const int64_t c0 = (int64_t)blockIdx.x * R;
@@ -477,7 +480,8 @@ static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s) {
             FCI_CUDA(opt_in_max_smem(k, ctx->device));
             int64_t nsa_ = nsa;
             SpinTables Bt = B;
-            void *args[] = {(void *)&C, (void *)&sig, (void *)&Bt, (void *)&nsa_, (void *)&add1};
+            const int *no_gate = nullptr;  // the double-float kernel's gate (others take one argument fewer)
+            void *args[] = {(void *)&C, (void *)&sig, (void *)&Bt, (void *)&nsa_, (void *)&add1, (void *)&no_gate};
             FCI_CUDA(cudaLaunchKernel(k, dim3(ceil_div(nsa, R)), dim3(512), args, sm, s));
             prof_mark(ctx, rec, slot, s);
         }
@@ -493,7 +497,8 @@ static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s) {
             FCI_CUDA(opt_in_max_smem(k, ctx->device));
             int64_t nsb_ = nsb;
             SpinTables At = A;
-            void *args[] = {(void *)&C, (void *)&sig, (void *)&At, (void *)&nsb_};
+            const int *no_gate = nullptr;
+            void *args[] = {(void *)&C, (void *)&sig, (void *)&At, (void *)&nsb_, (void *)&no_gate};
             FCI_CUDA(cudaLaunchKernel(k, dim3(ceil_div(nsb, R)), dim3(512), args, sm, s));
             prof_mark(ctx, rec, slot + 1, s);
         }
@@ -551,6 +556,50 @@ int launch_sigma_f32_gated(fci_ctx *ctx, const float *C, float *sig, const int *
     void *args[] = {(void *)&C, (void *)&sig, (void *)&St, (void *)&active};
     FCI_CUDA(cudaLaunchKernel(k, dim3(ceil_div(ns, R)), dim3(512), args, sm, s));
     return launch_sigma3_tc(ctx, C, sig, ctx->opt.f32_splits, s, active);
+}
+
+// FP64 sigma of one batched instance with the single-instance kernels (sliced
+// sigma_3, then the double-float sigma_1 and sigma_2 adding to it), every
+// kernel skipped on the device when *active == 0, so that a captured graph
+// serves any active set.  Shared-memory opt-ins: prepare_sigma_f64_gated.
+static int df_rows(int64_t len) {
+    for (int r = 8; r >= 1; r >>= 1)
+        if ((size_t)r * len * sizeof(double) <= smem_limit()) return r;
+    return 0;
+}
+
+static void *df_kernel1(int R) {
+    return R == 8 ? (void *)k_sigma1_rows_df<8> : R == 4 ? (void *)k_sigma1_rows_df<4>
+           : R == 2 ? (void *)k_sigma1_rows_df<2> : (void *)k_sigma1_rows_df<1>;
+}
+static void *df_kernel2(int R) {
+    return R == 8 ? (void *)k_sigma2_cols_df<8> : R == 4 ? (void *)k_sigma2_cols_df<4>
+           : R == 2 ? (void *)k_sigma2_cols_df<2> : (void *)k_sigma2_cols_df<1>;
+}
+
+bool sigma_f64_gated_ok(const fci_ctx *ctx) {
+    return sigma3_sliced_ok(ctx) && df_rows(ctx->A.ns) > 0 && df_rows(ctx->B.ns) > 0;
+}
+
+int prepare_sigma_f64_gated(const fci_ctx *ctx) {
+    if (int rc = prepare_sigma3_sliced(ctx)) return rc;
+    FCI_CUDA(opt_in_max_smem(df_kernel1(df_rows(ctx->B.ns)), ctx->device));
+    FCI_CUDA(opt_in_max_smem(df_kernel2(df_rows(ctx->A.ns)), ctx->device));
+    return FCI_OK;
+}
+
+int launch_sigma_f64_gated(fci_ctx *ctx, const double *C, double *sig, const int *active, cudaStream_t s) {
+    if (int rc = launch_sigma3_sliced(ctx, C, sig, s, -1, 0, active)) return rc;
+    const SpinTables &A = ctx->A, &B = ctx->B;
+    int64_t nsa = A.ns, nsb = B.ns;
+    int add = 1;
+    SpinTables At = A, Bt = B;
+    const int R1 = df_rows(nsb), R2 = df_rows(nsa);
+    void *a1[] = {(void *)&C, (void *)&sig, (void *)&Bt, (void *)&nsa, (void *)&add, (void *)&active};
+    FCI_CUDA(cudaLaunchKernel(df_kernel1(R1), dim3(ceil_div(nsa, R1)), dim3(512), a1, (size_t)R1 * nsb * 8, s));
+    void *a2[] = {(void *)&C, (void *)&sig, (void *)&At, (void *)&nsb, (void *)&active};
+    FCI_CUDA(cudaLaunchKernel(df_kernel2(R2), dim3(ceil_div(nsb, R2)), dim3(512), a2, (size_t)R2 * nsa * 8, s));
+    return FCI_OK;
 }
 
 int launch_sigma(fci_ctx *ctx, const void *c, void *sigma, int dtype, cudaStream_t s) {

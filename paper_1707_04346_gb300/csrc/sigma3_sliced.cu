@@ -13,7 +13,9 @@ static int round_up16(int x) { return (x + 15) / 16 * 16; }
 
 // out[r] = largest biased FP64 exponent field over row r of C (nrows x ncols);
 // one warp per row.
-__global__ void k_row_exponents(const double *__restrict__ C, int64_t nrows, int64_t ncols, int *__restrict__ out) {
+__global__ void k_row_exponents(const double *__restrict__ C, int64_t nrows, int64_t ncols, int *__restrict__ out,
+                                const int *__restrict__ active) {
+    if (active != nullptr && *active == 0) return;  // gated launch (batched engine): instance not active
     const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (r >= nrows) return;
@@ -42,7 +44,8 @@ __global__ void k_pair_table(const uint32_t *__restrict__ tab, int64_t ns, int n
 // slices 0-3 to cs0123, 4-5 to cs45 (d_s 2^(-8s), d_s balanced 8-bit digits of
 // round(|C| 2^(47 - e_row)) with the sign).
 __global__ void k_slice_c(const double *__restrict__ C, const int *__restrict__ rowexp, int64_t nrows, int64_t ncols,
-                          uint2 *__restrict__ cs0123, uint32_t *__restrict__ cs45) {
+                          uint2 *__restrict__ cs0123, uint32_t *__restrict__ cs45, const int *__restrict__ active) {
+    if (active != nullptr && *active == 0) return;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nrows * ncols) return;
     const unsigned long long b = __double_as_longlong(__ldg(C + t));
@@ -129,6 +132,18 @@ void free_sliced_tables(fci_ctx *ctx) {
     ctx->cs45 = nullptr;
 }
 
+static void *sliced_kernel(int kpad);
+
+// Opt the kernel into its shared memory outside any stream capture.
+int prepare_sigma3_sliced(const fci_ctx *ctx) {
+    int kpad = 0, npad = 0, n0 = 0;
+    uint32_t smem = 0;
+    if (!sigma3_sliced_ok(ctx) || !sliced_shape(ctx, &kpad, &npad, &n0, &smem))
+        return fail(FCI_ERR_STATE, "sliced sigma_3 tables were not built for this context");
+    FCI_CUDA(opt_in_max_smem(sliced_kernel(kpad), ctx->device));
+    return FCI_OK;
+}
+
 static void *sliced_kernel(int kpad) {
     switch (kpad) {
         case 16: return (void *)sl::k_sigma3_sliced<16>;
@@ -143,23 +158,25 @@ static void *sliced_kernel(int kpad) {
 
 // Row exponents and digit slices of C (stream-ordered), then sigma_3 into sig,
 // which is overwritten.  prof_slot: profiling slot of the pre-pass (the kernel
-// takes the next one).
-int launch_sigma3_sliced(fci_ctx *ctx, const double *C, double *sig, cudaStream_t s, int rec, int prof_slot) {
+// takes the next one).  active: null, or a device flag; the kernels return at
+// once when it is 0 (batched engine: one captured graph for any active set).
+int launch_sigma3_sliced(fci_ctx *ctx, const double *C, double *sig, cudaStream_t s, int rec, int prof_slot,
+                         const int *active) {
     int kpad = 0, npad = 0, n0 = 0;
     uint32_t smem = 0;
     if (!sigma3_sliced_ok(ctx) || !sliced_shape(ctx, &kpad, &npad, &n0, &smem))
         return fail(FCI_ERR_STATE, "sliced sigma_3 tables were not built for this context");
     const SpinTables &A = ctx->A, &B = ctx->B;
-    k_row_exponents<<<ceil_div(A.ns * 32, 256), 256, 0, s>>>(C, A.ns, B.ns, ctx->rowexp);
+    k_row_exponents<<<ceil_div(A.ns * 32, 256), 256, 0, s>>>(C, A.ns, B.ns, ctx->rowexp, active);
     FCI_CUDA(cudaGetLastError());
-    k_slice_c<<<ceil_div(ctx->ndet, 256), 256, 0, s>>>(C, ctx->rowexp, A.ns, B.ns, ctx->cs0123, ctx->cs45);
+    k_slice_c<<<ceil_div(ctx->ndet, 256), 256, 0, s>>>(C, ctx->rowexp, A.ns, B.ns, ctx->cs0123, ctx->cs45, active);
     FCI_CUDA(cudaGetLastError());
     prof_mark(ctx, rec, prof_slot, s);
     void *kern = sliced_kernel(kpad);
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     FCI_CUDA(cudaStreamIsCapturing(s, &cap));
     if (cap == cudaStreamCaptureStatusNone) FCI_CUDA(opt_in_max_smem(kern, ctx->device));
-    int nsm = 0;
+    int nsm = 0;  // (a captured launch relies on prepare_sigma3_sliced having opted in)
     FCI_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
     int64_t grid = nsm;  // one CTA per SM
     if (grid > A.ns) grid = A.ns;
@@ -169,8 +186,9 @@ int launch_sigma3_sliced(fci_ctx *ctx, const double *C, double *sig, cudaStream_
     const long long *xw = ctx->XW;
     const int *rexp = ctx->rowexp;
     int npair = ctx->npair, eW = ctx->eW;
-    void *args[] = {(void *)&c0,   (void *)&c4,   (void *)&sig, (void *)&At, (void *)&Bt,         (void *)&xw,
-                    (void *)&rexp, (void *)&npair, (void *)&npad, (void *)&n0, (void *)&eW, (void *)&ctx->d_err};
+    void *args[] = {(void *)&c0,   (void *)&c4,    (void *)&sig,  (void *)&At, (void *)&Bt,         (void *)&xw,
+                    (void *)&rexp, (void *)&npair, (void *)&npad, (void *)&n0, (void *)&eW, (void *)&ctx->d_err,
+                    (void *)&active};
     FCI_CUDA(cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(sl::kThreads), args, smem, s));
     prof_mark(ctx, rec, prof_slot + 1, s);
     return FCI_OK;

@@ -214,7 +214,8 @@ template <int KPAD>
 __global__ void __launch_bounds__(kThreads, 1)
     k_sigma3_sliced(const uint2 *__restrict__ cs0123, const uint32_t *__restrict__ cs45, double *__restrict__ sig,
                     SpinTables A, SpinTables B, const long long *__restrict__ XW, const int *__restrict__ rowexp,
-                    int npair, int npad, int n0, int eW, int *err) {
+                    int npair, int npad, int n0, int eW, int *err, const int *__restrict__ active) {
+    if (active != nullptr && *active == 0) return;  // gated launch (batched engine): instance not active
     constexpr int NKS = KPAD / 16;
     constexpr int kgroups = KPAD / 8;
     constexpr uint32_t sbo = (uint32_t)(KPAD / 8) * 128u;
