@@ -43,6 +43,9 @@ extern "C" {
 #define FCI_ERR_TIMEOUT 5 /* a bounded device wait gave up */
 #define FCI_ERR_STATE 6   /* call not valid in the context's current state */
 #define FCI_ERR_NAN 7     /* non-finite value detected in an input or result */
+#define FCI_ERR_RANGE 8   /* a level sum of the wide FP64 tensor-core sigma left the range in
+                             which it is exact (needs C and integral digits aligned across
+                             more than 73 replacements; detected, never silent) */
 
 /* ---- element types of CI vectors --------------------------------------- */
 #define FCI_F64 0
@@ -62,8 +65,9 @@ extern "C" {
 #define FCI_Q_DEVICE_BYTES 7  /* device memory held by the context */
 #define FCI_Q_ITERATIONS 8    /* iterations of the last fci_davidson call */
 #define FCI_Q_SIGMA_CALLS 9   /* sigma builds done inside the last fci_davidson */
-#define FCI_Q_DEVICE_ERROR 10 /* device error word: nonzero if a bounded wait inside a kernel
-                                 gave up (blocking read; the word is then cleared) */
+#define FCI_Q_DEVICE_ERROR 10 /* device error word (blocking read; the word is then cleared):
+                                 bit 0 = a bounded wait inside a kernel gave up, bit 1 = a
+                                 level sum of the wide FP64 sigma left its exact range */
 
 typedef struct fci_ctx fci_ctx;
 
@@ -82,8 +86,8 @@ typedef struct fci_options {
                             tensor cores (Eq. 8's E_ij E_kl as a pair-matrix contraction):
                             0 = only when the staged same-spin kernels do not fit in shared
                             memory (default), 1 = always */
-    int f64_kernels;     /* FCI_F64 sigma kernels: FCI_F64_AUTO (default), FCI_F64_FMA or
-                            FCI_F64_SLICED, below */
+    int f64_kernels;     /* FCI_F64 sigma kernels: FCI_F64_AUTO (default), FCI_F64_FMA,
+                            FCI_F64_SLICED or FCI_F64_WIDE, below */
     double max_device_bytes; /* cap on the device memory one context (with its Davidson
                             workspace) may hold; an allocation beyond it fails with
                             FCI_ERR_OOM before cudaMalloc is called.  0 = no cap (default).
@@ -99,24 +103,38 @@ typedef struct fci_options {
  * 1e-12 bars).
  *  FCI_F64_FMA     FP64 fused multiply-adds throughout (GB300's FP64 pipe).
  *  FCI_F64_AUTO    sigma_3 on the bf16 tensor cores from 8-bit slices where the
- *                  space fits the sliced kernel, else FP64 FMAs; sigma_1 and
- *                  sigma_2 in double-float FP32 arithmetic (each FP64 value as
- *                  two FP32 parts, 48 significant bits; error-free products and
- *                  sums to within a few units of 2^-48).
- *  FCI_F64_SLICED  as AUTO, but fci_init fails with FCI_ERR_ARG where the
- *                  sliced kernel does not fit.
- * The sliced sigma_3 writes C and the integrals as 47-bit fixed point (C
- * relative to one power of two per alpha row, the integrals to one per
- * context), cuts them into six balanced 8-bit digits that bf16 holds exactly,
- * and accumulates the 21 digit products of weight <= 5 per weight in FP32
- * (exact for weights 0-2); its scatter into sigma adds 64-bit integers, so
- * its result does not depend on the order of the adds.  Limits: at most 128
- * orbital pairs (norb <= 15), 96 alpha replacements, and the sigma row (8
- * N_beta bytes) plus 12 (128 + npair) K bytes of operands in shared memory
- * (CAS(14,14) fits; CAS(16,16) does not). */
+ *                  space fits the per-row sliced kernel (CAS(14,14)), with
+ *                  sigma_1 and sigma_2 in double-float FP32 arithmetic (each
+ *                  FP64 value as two FP32 parts, 48 significant bits;
+ *                  error-free products and sums to within a few units of
+ *                  2^-48); where it does not fit and both spins have
+ *                  electrons, all three terms on the tensor cores through the
+ *                  wide kernels (CAS(16,16), CAS(18,18)); else FP64 FMAs.
+ *  FCI_F64_SLICED  as AUTO, but fci_init fails with FCI_ERR_ARG where neither
+ *                  tensor-core FP64 path fits.
+ *  FCI_F64_WIDE    the wide kernels on every space they cover (FCI_ERR_ARG
+ *                  elsewhere); lets small spaces exercise the large-space path.
+ * The sliced kernels write C and the integrals as 47-bit fixed point, cut
+ * into six balanced 8-bit digits that bf16 holds exactly, and accumulate the
+ * 21 digit products of weight <= 5 per weight in FP32 (exact for weights
+ * 0-2); their adds into sigma are 64-bit integers, so the result does not
+ * depend on the order of the adds.  The per-row kernel takes C relative to
+ * one power of two per alpha row and holds the sigma row in shared memory:
+ * at most 128 orbital pairs (norb <= 15), 85 alpha replacements, and the
+ * sigma row (8 N_beta bytes) plus 12 (128 + npair) K bytes of operands in
+ * shared memory.  The wide kernels take C relative to one power of two for
+ * the whole vector (errors are relative to max|C|), cut the pair columns into
+ * parts of at most 64, and accumulate in global memory; the same-spin terms
+ * go through intermediate strings (1/2 sum (ij|kl) E_ij E_kl with the
+ * identity resolved over single replacements, plus the one-body operator
+ * k_kl = h_kl - 1/2 sum_j (kj|jl)).  Limits: at most 96 replacements per
+ * string and 255 orbital pairs (norb <= 21); 20 bytes per determinant of
+ * workspace (12 of digit planes, 8 of accumulator, shared with the FCI_F32
+ * same-spin workspace). */
 #define FCI_F64_AUTO 0
 #define FCI_F64_FMA 1
 #define FCI_F64_SLICED 2
+#define FCI_F64_WIDE 3
 
 /* Fill *opt with the defaults listed above. */
 void fci_default_options(fci_options *opt);

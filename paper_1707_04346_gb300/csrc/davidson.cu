@@ -668,7 +668,8 @@ int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *v
         int derr = 0;
         FCI_CUDA(cudaMemcpyAsync(&derr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
         FCI_CUDA(cudaStreamSynchronize(s));
-        if (derr) return fail(FCI_ERR_TIMEOUT, "a bounded device wait gave up inside sigma");
+        if (derr & 1) return fail(FCI_ERR_TIMEOUT, "a bounded device wait gave up inside sigma");
+        if (derr) return fail(FCI_ERR_RANGE, "a level sum of the FP64 tensor-core sigma left its exact range");
         double rmax = 0.0, demax = 0.0;
         for (int k = 0; k < nr; ++k) {
             rn[k] = std::sqrt(rn[k]);

@@ -152,8 +152,8 @@ int fci_init(fci_ctx **out, int norb, int nalpha, int nbeta, const double *h1, c
     if (o.same_spin_tc != 0 && o.same_spin_tc != 1) return fail(FCI_ERR_ARG, "same_spin_tc must be 0 or 1");
     if (!(o.max_device_bytes >= 0)) return fail(FCI_ERR_ARG, "max_device_bytes must be >= 0");
     if (o.f32_row_global != 0 && o.f32_row_global != 1) return fail(FCI_ERR_ARG, "f32_row_global must be 0 or 1");
-    if (o.f64_kernels < FCI_F64_AUTO || o.f64_kernels > FCI_F64_SLICED)
-        return fail(FCI_ERR_ARG, "f64_kernels must be FCI_F64_AUTO, FCI_F64_FMA or FCI_F64_SLICED");
+    if (o.f64_kernels < FCI_F64_AUTO || o.f64_kernels > FCI_F64_WIDE)
+        return fail(FCI_ERR_ARG, "f64_kernels must be FCI_F64_AUTO, FCI_F64_FMA, FCI_F64_SLICED or FCI_F64_WIDE");
     if (int rc = check_integrals(norb, h1, eri, o.symmetry_tol)) return rc;
 
     fci_ctx *ctx = new (std::nothrow) fci_ctx();

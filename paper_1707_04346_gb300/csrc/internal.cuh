@@ -76,6 +76,9 @@ struct SpinTables {
     // of the entry of string x with pair q, or 0xFFFF.  Owned by the context
     // (freed with the sliced tables).
     uint16_t *tabp = nullptr;
+    // The same with 32-bit packed entries (kNoEntry where none), for the wide
+    // FP64 kernels (sigma_wide.cu; beta spin only, owned by the context).
+    uint32_t *tabp32 = nullptr;
     bool owner = true;         // false when aliasing the alpha tables
 };
 
@@ -103,6 +106,14 @@ struct fci_ctx {
     int *rowexp = nullptr;          // [N_alpha]
     uint2 *cs0123 = nullptr;        // [ndet]
     uint32_t *cs45 = nullptr;       // [ndet]
+    // FP64 sigma for large spaces (sigma_wide.cu): the fixed-point integral
+    // table, the exponent of the call's C, and the 64-bit accumulator
+    // (aliases ws32 when the context has it)
+    long long *XT = nullptr;        // [npair + 1][npair]: round((q|p) 2^(47 - eC)), round(k_p 2^(48 - eC - sh1))
+    int eC = 0;
+    int sh1 = 0;
+    int *d_eG = nullptr;            // device: largest biased exponent of C
+    long long *wsacc = nullptr;     // [ndet] when ws32 is absent
     double *hdiag = nullptr;        // [ndet]
     int *d_err = nullptr;           // device error word (bounded waits that gave up)
     size_t bytes = 0;
@@ -167,12 +178,20 @@ size_t sigma3_tc_smem(const fci_ctx *ctx, int nsplit);
 int launch_wait_timeout_probe(fci_ctx *ctx);  // fci_check_wait_timeout
 
 // sigma3_sliced.cu (FP64-accurate sigma_3 on the tensor cores)
-int build_sliced_tables(fci_ctx *ctx, const double *eri_host);
+int build_sliced_tables(fci_ctx *ctx, const double *h1_host, const double *eri_host);
 void free_sliced_tables(fci_ctx *ctx);
 bool sigma3_sliced_ok(const fci_ctx *ctx);
 int launch_sigma3_sliced(fci_ctx *ctx, const double *C, double *sig, cudaStream_t s, int rec, int prof_slot,
                          const int *active = nullptr);
 int prepare_sigma3_sliced(const fci_ctx *ctx);
+
+// sigma_wide.cu (FP64-accurate sigma for large spaces: all three terms on the
+// tensor cores, one integer accumulator)
+bool sigma_wide_fits(const fci_ctx *ctx);
+bool sigma_wide_ok(const fci_ctx *ctx);
+int build_wide_tables(fci_ctx *ctx, const double *h1_host, const double *eri_host);
+void free_wide_tables(fci_ctx *ctx);
+int launch_sigma_f64_wide(fci_ctx *ctx, const double *C, double *sig, cudaStream_t s);
 
 // davidson.cu
 int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *vecs, const void *guess);

@@ -403,6 +403,8 @@ int alloc_sigma_workspace(fci_ctx *ctx) {
 
 template <typename T>
 static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s) {
+    if constexpr (sizeof(T) == 8)
+        if (sigma_wide_ok(ctx)) return launch_sigma_f64_wide(ctx, C, sig, s);
     const SpinTables &A = ctx->A, &B = ctx->B;
     const int64_t nsa = A.ns, nsb = B.ns;
     const size_t lim = smem_limit();

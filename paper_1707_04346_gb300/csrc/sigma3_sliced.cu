@@ -76,13 +76,23 @@ bool sigma3_sliced_ok(const fci_ctx *ctx) { return ctx->XW != nullptr && ctx->B.
 // (|W| < 2^eW), the pair-major beta table, and the buffers of the per-call
 // pre-pass (row exponents, the C digit planes: 4 + 12 N bytes).  Contexts whose
 // shapes the kernel does not cover get none of them (the FMA kernel runs).
-int build_sliced_tables(fci_ctx *ctx, const double *eri_host) {
+//
+// Kernel choice (fci_options.f64_kernels): FMA builds nothing; WIDE builds the
+// wide kernels' tables (sigma_wide.cu) on any space they cover; AUTO and
+// SLICED take this per-row kernel where it fits, else the wide kernels where
+// both spins have electrons and they fit; else AUTO keeps the FMA kernels and
+// SLICED and WIDE fail.
+int build_sliced_tables(fci_ctx *ctx, const double *h1_host, const double *eri_host) {
     int kpad = 0, npad = 0, n0 = 0;
     uint32_t smem = 0;
-    if (ctx->opt.f64_kernels == FCI_F64_FMA || !sliced_shape(ctx, &kpad, &npad, &n0, &smem)) {
-        if (ctx->opt.f64_kernels == FCI_F64_SLICED)
-            return fail(FCI_ERR_ARG, "f64_kernels = FCI_F64_SLICED: the space exceeds the sliced kernel's limits "
-                                     "(at most 128 orbital pairs, 85 alpha replacements, shared memory)");
+    const int mode = ctx->opt.f64_kernels;
+    if (mode == FCI_F64_FMA) return FCI_OK;
+    if (mode == FCI_F64_WIDE || !sliced_shape(ctx, &kpad, &npad, &n0, &smem)) {
+        const bool both = ctx->A.nsingle > 0 && ctx->B.nsingle > 0;
+        if ((mode == FCI_F64_WIDE || both) && sigma_wide_fits(ctx)) return build_wide_tables(ctx, h1_host, eri_host);
+        if (mode == FCI_F64_SLICED || mode == FCI_F64_WIDE)
+            return fail(FCI_ERR_ARG, "f64_kernels: the space exceeds the tensor-core FP64 kernels' limits "
+                                     "(at most 96 replacements per string and 255 orbital pairs)");
         return FCI_OK;
     }
     const int n = ctx->norb, np = ctx->npair;

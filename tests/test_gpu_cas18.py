@@ -1,7 +1,8 @@
 """CAS(18e,18o): 48620 x 48620 = 2.36e9 determinants, FP32 sigma streamed
 through HBM (same-spin terms through intermediate strings and sigma_3 with the
-gather epilogue into a global sigma row, both on the tensor cores), checked on
-sampled rows against the oracle, which regenerates the trial vector per index."""
+gather epilogue into a global sigma row, both on the tensor cores) and the FP64
+sigma (the wide sliced kernels), checked on sampled rows against the oracle,
+which regenerates the trial vector per index."""
 import numpy as np
 import pytest
 
@@ -64,10 +65,14 @@ def test_cas18_fp32_sigma_sampled(pkg, oracle_mod):
     pkg.fci_free(ctx3)
     assert np.abs(got3 - ref).max() <= 1e-4 * np.abs(ref).max()
     del c, s
-    # the FP64 path has no kernels for a space this large: a host-side error, no launch
-    c64 = torch.zeros(N, dtype=torch.float64, device=DEV)
+    # FP64: all three terms through the wide tensor-core kernels (six 8-bit
+    # slices, 64-bit integer accumulation), at the FP64 bar
+    c64 = torch.empty(N, dtype=torch.float64, device=DEV)
+    gpu.fill_pm1(c64)
     s64 = torch.empty_like(c64)
-    with pytest.raises(pkg.FciError):
-        pkg.fci_sigma(ctx, c64, s64)
+    pkg.fci_sigma(ctx, c64, s64)
+    torch.cuda.synchronize()
+    got64 = s64[torch.from_numpy(rows).to(DEV)].cpu().numpy()
+    assert np.abs(got64 - ref).max() <= 1e-12 * np.abs(ref).max()
     del c64, s64
     pkg.fci_free(ctx)

@@ -133,7 +133,10 @@ def test_sliced_nan_input_propagates(pkg):
 
 
 def test_sliced_refused_where_it_does_not_fit(pkg):
-    h1, eri = fi.make_integrals(16, 10)
-    with pytest.raises(pkg.FciError) as ei:
-        pkg.fci_init(16, 8, 8, h1, eri, pkg.default_options(f64_kernels=SLICED))
-    assert ei.value.code == pkg.fci.FCI_ERR_ARG
+    """Beyond both tensor-core FP64 paths (100 beta replacements per string,
+    more than 96): FCI_F64_SLICED and FCI_F64_WIDE refuse at fci_init."""
+    h1, eri = fi.make_integrals(19, 10)
+    for mode in (SLICED, 3):
+        with pytest.raises(pkg.FciError) as ei:
+            pkg.fci_init(19, 1, 10, h1, eri, pkg.default_options(f64_kernels=mode))
+        assert ei.value.code == pkg.fci.FCI_ERR_ARG
