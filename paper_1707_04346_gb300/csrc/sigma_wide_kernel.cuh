@@ -26,7 +26,14 @@
 //    memory together, and the five accumulators of a part fit twice in tensor
 //    memory: tiles alternate between the two buffers, so the epilogue of one
 //    tile runs under the MMAs of the next.  The parts of one row are
-//    consecutive items, so their gathers of the same C rows meet in L2.
+//    consecutive items, so their gathers of the same C rows meet in L2;
+//  * the six B slices of a part are stacked along N (rows t np .. t np + np - 1)
+//    and the five levels of an accumulator buffer sit side by side in tensor
+//    memory (columns L np ..), so that A slice s times B slices 0..4-s is ONE
+//    MMA of N = (5 - s) np writing levels s..4, plus one N = np MMA for
+//    t = 5 - s into level 4: 11 MMAs per K-step instead of 21.  An M = 128
+//    MMA reads its 4 KB A slice from shared memory each time, which at
+//    N = 48 takes as long as the multiply itself; stacking amortises it.
 //
 // MODE 0 (sigma_3), row = output alpha string I_a with replacement list
 // a = (J_a, p_a, s_a), lanes = beta strings J_b:
@@ -65,7 +72,7 @@ constexpr int kEpiThreads = 256;
 constexpr int kMaxKSteps = 6;      // K <= 96
 constexpr int kPartMax = 48;       // pair columns per part
 constexpr int kLevels = 5;         // accumulators per element
-constexpr int kBufCols = 256;      // tensor-memory columns of one accumulator buffer (5 x 48 used)
+constexpr int kBufCols = 256;      // tensor-memory columns of one accumulator buffer (5 x np used)
 constexpr uint32_t kBias3 = 0x3F400000u;  // 1.5 2^-1: level 3 (multiples of 2^-24) in the low bits
 constexpr int kBars = 2 * kMaxKSteps + 5;  // a_full[6], a_free[6], acc_full[2], acc_empty[2], drain
 
@@ -73,7 +80,7 @@ struct Layout {
     uint32_t bytesA, bytesB, offA, offEa, offPair, offBar, total;
 };
 
-// Shared memory: B slices [6][48 x kpad], A slices [6][128 x kpad], the row's
+// Shared memory: B slices stacked [6 x 48 rows][kpad], A slices [6][128 x kpad], the row's
 // replacement list, its entries by pair (MODE 1), barriers and words.
 __host__ __device__ inline Layout make_layout(int kpad, int npad, int nsingle) {
     Layout L;
@@ -95,7 +102,18 @@ __host__ __device__ inline void part_range(int npad, int nparts, int p, int *q0,
     *np = 16 * (base + (p < extra ? 1 : 0));
 }
 
-__device__ __forceinline__ uint32_t acc_col(int buf, int L) { return (uint32_t)(buf * kBufCols + L * kPartMax); }
+// tensor-memory column of level L of accumulator buffer buf for parts np wide
+__device__ __forceinline__ uint32_t acc_col(int buf, int L, int np) { return (uint32_t)(buf * kBufCols + L * np); }
+
+// Write the starting words of one 8-column chunk of every level: the biases of
+// levels 0-3 and zero for level 4.
+__device__ __forceinline__ void init_chunk(uint32_t lane_base, int buf, int np, int c) {
+    sl::tmem_st8(lane_base + acc_col(buf, 0, np) + (uint32_t)(c * 8), sl::kBias0);
+    sl::tmem_st8(lane_base + acc_col(buf, 1, np) + (uint32_t)(c * 8), sl::kBias1);
+    sl::tmem_st8(lane_base + acc_col(buf, 2, np) + (uint32_t)(c * 8), sl::kBias2);
+    sl::tmem_st8(lane_base + acc_col(buf, 3, np) + (uint32_t)(c * 8), kBias3);
+    sl::tmem_st8(lane_base + acc_col(buf, 4, np) + (uint32_t)(c * 8), 0u);
+}
 
 // The integer V = round(2^34 (acc0 + ... + acc4)) of one element, times the
 // sign (neg = 1: negative), from the raw words (levels 0-3 biased):
@@ -168,20 +186,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = *tslot;
-    if (warp >= 4 && warp < 12) {  // level 0-3 biases of both buffers, all 48 columns (this warp's chunks)
-        const uint32_t lb = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-        for (int b = 0; b < 2; ++b)
-            for (int c = (warp - 4) >> 2; c < kPartMax / 8; c += 2) {
-                sl::tmem_st8(lb + acc_col(b, 0) + (uint32_t)(c * 8), sl::kBias0);
-                sl::tmem_st8(lb + acc_col(b, 1) + (uint32_t)(c * 8), sl::kBias1);
-                sl::tmem_st8(lb + acc_col(b, 2) + (uint32_t)(c * 8), sl::kBias2);
-                sl::tmem_st8(lb + acc_col(b, 3) + (uint32_t)(c * 8), kBias3);
-            }
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-    }
-    tc::fence_before();
-    __syncthreads();
-    tc::fence_after();
     const int64_t ntiles = (ncols + kM - 1) / kM;
     const int64_t nitems = R.ns * (int64_t)nparts;
     int64_t T = 0;  // tiles done by this CTA (barrier phases)
@@ -218,10 +222,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int s = 0; s < kSlices; ++s) w[s][i] = sl::pack_bf16(f[0][s], f[1][s]);
             }
-            const uint32_t off = tc::kmajor_offset(ql, kg, KPAD);
 #pragma unroll
             for (int s = 0; s < kSlices; ++s)
-                *reinterpret_cast<uint4 *>(sB + (uint32_t)s * L.bytesB + off) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+                *reinterpret_cast<uint4 *>(sB + tc::kmajor_offset(s * np + ql, kg, KPAD)) =
+                    make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+        }
+        if (warp >= 4 && warp < 12) {  // starting words of both buffers in this item's layout
+            const uint32_t lb = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+            for (int b = 0; b < 2; ++b)
+                for (int c = (warp - 4) >> 2; c < np / 8; c += 2) init_chunk(lb, b, np, c);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         }
         tc::fence_async_smem();
         tc::fence_before();
@@ -329,13 +339,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                         asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                                      : "=r"(r[lv][0]), "=r"(r[lv][1]), "=r"(r[lv][2]), "=r"(r[lv][3]), "=r"(r[lv][4]),
                                        "=r"(r[lv][5]), "=r"(r[lv][6]), "=r"(r[lv][7])
-                                     : "r"(lane_base + acc_col(b, lv) + (uint32_t)(c * 8)));
+                                     : "r"(lane_base + acc_col(b, lv, np) + (uint32_t)(c * 8)));
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    // the next use of this buffer accumulates levels 0-3 onto their biases again
-                    sl::tmem_st8(lane_base + acc_col(b, 0) + (uint32_t)(c * 8), sl::kBias0);
-                    sl::tmem_st8(lane_base + acc_col(b, 1) + (uint32_t)(c * 8), sl::kBias1);
-                    sl::tmem_st8(lane_base + acc_col(b, 2) + (uint32_t)(c * 8), sl::kBias2);
-                    sl::tmem_st8(lane_base + acc_col(b, 3) + (uint32_t)(c * 8), kBias3);
+                    init_chunk(lane_base, b, np, c);  // the next use of this buffer starts from these
                     if (c + 2 >= nch) {  // last chunk of this thread: release the buffer
                         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                         tc::fence_before();
@@ -362,35 +368,33 @@ __global__ void __launch_bounds__(kThreads, 1)
         } else if (warp == 12 && lane == 0) {
             // ---- MMA issuer: descriptors of K-step 0, advanced by 256 bytes (16 in
             // the address field) per K-step ----
+            // A slice s: levels s..4 from B slices 0..4-s (stacked, one MMA of
+            // N = (5 - s) np), then B slice 5 - s into level 4 (N = np)
             uint64_t ad[kSlices], bd[kSlices];
 #pragma unroll
             for (int s = 0; s < kSlices; ++s) {
                 ad[s] = tc::smem_desc(tc::smem_u32(sA + s * L.bytesA), 128, sbo);
-                bd[s] = tc::smem_desc(tc::smem_u32(sB + s * L.bytesB), 128, sbo);
+                bd[s] = tc::smem_desc(tc::smem_u32(sB) + (uint32_t)(s * np / 8) * sbo, 128, sbo);
             }
-            const uint32_t idesc = tc::instr_desc(kM, np);
+            uint32_t idn[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) idn[k] = tc::instr_desc(kM, (k + 1) * np);
             for (int64_t t = 0; t < ntiles; ++t) {
                 const int64_t Tt = T + t;
                 const int b = (int)(Tt & 1);
                 bool ok = !(Tt >= 2 && !tc::mbar_wait_bounded(acc_empty(b), (uint32_t)(((Tt - 2) >> 1) & 1)));
-                uint32_t col[kLevels];
-#pragma unroll
-                for (int lv = 0; lv < kLevels; ++lv) col[lv] = tmem + acc_col(b, lv);
-                bool fresh4 = true;
 #pragma unroll
                 for (int ks = 0; ks < NKS; ++ks) {
                     if (ok && !tc::mbar_wait_bounded(a_full(ks), (uint32_t)(Tt & 1))) ok = false;
                     if (!ok) break;
                     tc::fence_after();
 #pragma unroll
-                    for (int sa = 0; sa < kSlices; ++sa)
-#pragma unroll
-                        for (int sb = 0; sa + sb < kSlices; ++sb) {
-                            const int lv = sa + sb < 4 ? sa + sb : 4;
-                            const uint32_t accum = (lv < 4 || !fresh4) ? 1u : 0u;
-                            if (lv == 4) fresh4 = false;
-                            tc::mma_bf16(col[lv], ad[sa] + (uint64_t)(ks * 16), bd[sb] + (uint64_t)(ks * 16), idesc, accum);
-                        }
+                    for (int sa = 0; sa < kSlices; ++sa) {
+                        const uint64_t a = ad[sa] + (uint64_t)(ks * 16);
+                        if (sa < 5)
+                            tc::mma_bf16(tmem + acc_col(b, sa, np), a, bd[0] + (uint64_t)(ks * 16), idn[4 - sa], 1u);
+                        tc::mma_bf16(tmem + acc_col(b, 4, np), a, bd[5 - sa] + (uint64_t)(ks * 16), idn[0], 1u);
+                    }
                     tc::mma_commit(a_free(ks));
                 }
                 if (!ok) {
