@@ -96,6 +96,11 @@ typedef struct fci_options {
                             memory (the epilogue large spaces such as CAS(18,18) need) even
                             where it fits in shared memory, so that small spaces exercise
                             it; 0 = shared memory where it fits (default) */
+    int basis_f32;       /* FCI_PREC_MIXED Davidson: store the subspace basis and its sigma
+                            vectors in FP32 (Ritz vectors and refinement sigma stay FP64).
+                            0 = only when the FP64 basis does not fit in free device memory
+                            (default; then at most 8 vectors, fewer if memory asks), 1 =
+                            always (max_subspace vectors), 2 = never */
 } fci_options;
 
 /* fci_options.f64_kernels: how the FCI_F64 sigma is computed.  All modes meet
@@ -208,7 +213,10 @@ int fci_hdiag(fci_ctx *ctx, double *out, void *stream);
  *  vecs      NULL, or DEVICE FP64 [nroots][N]: normalised eigenvectors
  *  guess     NULL (unit vectors on the lowest diagonal elements), or DEVICE
  *            FP64 [nroots][N] starting vectors
- * Uses the options given at fci_init (max_subspace, max_iter, precision).
+ * Uses the options given at fci_init (max_subspace, max_iter, precision,
+ * basis_f32).  In FCI_PREC_MIXED with an FP32 basis (large spaces: the FP64
+ * basis of CAS(18,18) would need 300 GB) the device workspace is
+ * 8 (2 m + 1) / 2 + 16 nroots bytes per determinant for m basis vectors.
  * Blocking; runs on the context's internal stream.
  * Errors: FCI_ERR_ARG (also when no guess vector survives orthonormalisation,
  * e.g. all-NaN guesses), FCI_ERR_OOM, FCI_ERR_CUDA, FCI_ERR_TIMEOUT,

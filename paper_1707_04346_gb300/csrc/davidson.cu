@@ -362,36 +362,69 @@ __global__ void k_jacobi(const double *__restrict__ A, int lda, int m, double *_
 }
 
 // k smallest diagonal entries, ties broken by index: one pass per root over
-// the whole diagonal, excluding indices already chosen.
-__global__ void __launch_bounds__(1024) k_argmin_excl(const double *__restrict__ d, int64_t n,
-                                                       const int64_t *__restrict__ chosen, int nchosen,
-                                                       int64_t *__restrict__ out) {
-    double best = INFINITY;
-    int64_t bi = INT64_MAX;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        bool skip = false;
-        for (int c = 0; c < nchosen; ++c) skip |= (chosen[c] == i);
-        if (skip) continue;
-        double v = d[i];
-        if (v < best || (v == best && i < bi)) { best = v; bi = i; }
-    }
-    __shared__ double sb[1024];
-    __shared__ int64_t si[1024];
+// the whole diagonal, excluding indices already chosen.  Two stages: each
+// block reduces a grid-strided share into (pv, pi)[block], then one block
+// reduces those (the order of (value, index) is total, so the result does not
+// depend on the split).
+__device__ __forceinline__ bool less_vi(double v, int64_t i, double bv, int64_t bi) {
+    return v < bv || (v == bv && i < bi);
+}
+
+template <int NT>
+__device__ void block_min_vi(double &best, int64_t &bi, double *sb, int64_t *si) {
     sb[threadIdx.x] = best;
     si[threadIdx.x] = bi;
     __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            double v = sb[threadIdx.x + s];
-            int64_t j = si[threadIdx.x + s];
-            if (v < sb[threadIdx.x] || (v == sb[threadIdx.x] && j < si[threadIdx.x])) {
-                sb[threadIdx.x] = v;
-                si[threadIdx.x] = j;
-            }
+    for (int s = NT / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s && less_vi(sb[threadIdx.x + s], si[threadIdx.x + s], sb[threadIdx.x], si[threadIdx.x])) {
+            sb[threadIdx.x] = sb[threadIdx.x + s];
+            si[threadIdx.x] = si[threadIdx.x + s];
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) *out = si[0];
+    best = sb[0];
+    bi = si[0];
+}
+
+__global__ void __launch_bounds__(256) k_argmin_excl_part(const double *__restrict__ d, int64_t n,
+                                                          const int64_t *__restrict__ chosen, int nchosen,
+                                                          double *__restrict__ pv, int64_t *__restrict__ pi) {
+    double best = INFINITY;
+    int64_t bi = INT64_MAX;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        bool skip = false;
+        for (int c = 0; c < nchosen; ++c) skip |= (chosen[c] == i);
+        if (skip) continue;
+        const double v = d[i];
+        if (less_vi(v, i, best, bi)) {
+            best = v;
+            bi = i;
+        }
+    }
+    __shared__ double sb[256];
+    __shared__ int64_t si[256];
+    block_min_vi<256>(best, bi, sb, si);
+    if (threadIdx.x == 0) {
+        pv[blockIdx.x] = best;
+        pi[blockIdx.x] = bi;
+    }
+}
+
+// out = index of the smallest (pv, pi) pair (one block of 256 threads)
+__global__ void __launch_bounds__(256) k_argmin_final(const double *__restrict__ pv, const int64_t *__restrict__ pi,
+                                                      int nb, int64_t *__restrict__ out) {
+    double best = INFINITY;
+    int64_t bi = INT64_MAX;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+        if (less_vi(pv[b], pi[b], best, bi)) {
+            best = pv[b];
+            bi = pi[b];
+        }
+    __shared__ double sb[256];
+    __shared__ int64_t si[256];
+    block_min_vi<256>(best, bi, sb, si);
+    if (threadIdx.x == 0) *out = bi;
 }
 
 __global__ void k_set_unit(double *__restrict__ y, int64_t n, const int64_t *__restrict__ idx) {
@@ -409,39 +442,233 @@ __global__ void k_cvt_f2d(const float *__restrict__ a, double *__restrict__ b, i
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) b[i] = (double)a[i];
 }
 
-// sign fix: make the element of largest magnitude positive
-__global__ void __launch_bounds__(1024) k_absmax_sign(const double *__restrict__ x, int64_t n, double *__restrict__ sgn) {
-    double best = -1.0, val = 0.0;
+// sign fix: make the element of largest magnitude positive (ties: lower index).
+// Stage 1 per block (the key -|x_i| with index i, so the minimum is wanted);
+// stage 2 takes the sign of the winner.
+__global__ void __launch_bounds__(256) k_absmax_part(const double *__restrict__ x, int64_t n, double *__restrict__ pv,
+                                                     int64_t *__restrict__ pi) {
+    double best = INFINITY;
     int64_t bi = INT64_MAX;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        double a = fabs(x[i]);
-        if (a > best || (a == best && i < bi)) { best = a; bi = i; val = x[i]; }
-    }
-    __shared__ double sb[1024], sv[1024];
-    __shared__ int64_t si[1024];
-    sb[threadIdx.x] = best;
-    sv[threadIdx.x] = val;
-    si[threadIdx.x] = bi;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            double v = sb[threadIdx.x + s];
-            int64_t j = si[threadIdx.x + s];
-            if (v > sb[threadIdx.x] || (v == sb[threadIdx.x] && j < si[threadIdx.x])) {
-                sb[threadIdx.x] = v;
-                si[threadIdx.x] = j;
-                sv[threadIdx.x] = sv[threadIdx.x + s];
-            }
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const double v = -fabs(x[i]);
+        if (less_vi(v, i, best, bi)) {
+            best = v;
+            bi = i;
         }
-        __syncthreads();
     }
-    if (threadIdx.x == 0) *sgn = sv[0] < 0 ? -1.0 : 1.0;
+    __shared__ double sb[256];
+    __shared__ int64_t si[256];
+    block_min_vi<256>(best, bi, sb, si);
+    if (threadIdx.x == 0) {
+        pv[blockIdx.x] = best;
+        pi[blockIdx.x] = bi;
+    }
+}
+
+__global__ void k_sign_of(const double *__restrict__ x, const int64_t *__restrict__ at, double *__restrict__ sgn) {
+    *sgn = x[*at] < 0 ? -1.0 : 1.0;
+}
+
+// *q = *a / *b
+__global__ void k_quotient(const double *__restrict__ a, const double *__restrict__ b, double *__restrict__ q) {
+    *q = *a / *b;
 }
 
 __global__ void k_scale_by(double *__restrict__ y, const double *__restrict__ s, int64_t n) {
     const double f = *s;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) y[i] *= f;
+}
+
+// ---- FP32 basis (large spaces): the basis vectors and their sigma vectors
+// are stored in FP32, the Ritz vectors and their sigma in FP64 ----
+
+// a b added exactly to the double-float pair (sh, sl): error-free product by
+// FMA, TwoSum of the leading parts (GB300 issues FP32 64 times faster than FP64)
+__device__ __forceinline__ void df_acc(float a, float b, float &sh, float &sl) {
+    const float p = a * b;
+    const float e = fmaf(a, b, -p);
+    const float t = sh + p;
+    const float bp = t - sh;
+    sl += ((sh - (t - bp)) + (p - bp)) + e;
+    sh = t;
+}
+
+// partial[stripe][32] = this stripe's share of X_i . y for FP32 X [m][n] and
+// y [n]: double-float sums per thread, FP64 across threads (layout as k_multidot)
+__global__ void __launch_bounds__(256) k_multidot_f32(const float *__restrict__ X, int m, const float *__restrict__ y,
+                                                      int64_t n, int groups, double *__restrict__ partial) {
+    const int g = blockIdx.x % groups;
+    const int stripe = blockIdx.x / groups;
+    const int nstripes = gridDim.x / groups;
+    const int i0 = g * 8;
+    const int mg = m - i0 < 8 ? m - i0 : 8;
+    float sh[8], sl[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) sh[j] = sl[j] = 0.f;
+    const int64_t stride = (int64_t)nstripes * blockDim.x;
+    for (int64_t r = stripe * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride) {
+        const float yr = y[r];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (j < mg) df_acc(X[(int64_t)(i0 + j) * n + r], yr, sh[j], sl[j]);
+    }
+    __shared__ double red[8][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        double v = (double)sh[j] + (double)sl[j];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[j][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < mg) {
+        double v = 0.0;
+        for (int w = 0; w < 8; ++w) v += red[threadIdx.x][w];
+        partial[(int64_t)stripe * 32 + i0 + threadIdx.x] = v;
+    }
+}
+
+// y = sum_i coef[i coef_stride] X_i (FP32 X, FP64 y and sums)
+__global__ void k_lincomb_f32(const float *__restrict__ X, int m, const double *__restrict__ coef, int coef_stride,
+                              double *__restrict__ y, int64_t n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride) {
+        double v = 0.0;
+        for (int i = 0; i < m; ++i) v = fma(coef[(int64_t)i * coef_stride], (double)X[(int64_t)i * n + r], v);
+        y[r] = v;
+    }
+}
+
+// y -= sum_i coef[i] X_i in FP32 (Gram-Schmidt on the FP32 basis); partial[block]
+// = the block's share of ||y||^2 after the update
+__global__ void __launch_bounds__(256) k_sub_proj_f32(const float *__restrict__ X, int m, const double *__restrict__ coef,
+                                                      float *__restrict__ y, int64_t n, double *__restrict__ partial) {
+    __shared__ float c[32];
+    if (threadIdx.x < m) c[threadIdx.x] = (float)coef[threadIdx.x];
+    __syncthreads();
+    float sh = 0.f, sl = 0.f;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride) {
+        float v = y[r];
+        for (int i = 0; i < m; ++i) v = fmaf(-c[i], X[(int64_t)i * n + r], v);
+        y[r] = v;
+        df_acc(v, v, sh, sl);
+    }
+    double acc = (double)sh + (double)sl;
+    __shared__ double red[8];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int w = 0; w < 8; ++w) v += red[w];
+        partial[blockIdx.x] = v;
+    }
+}
+
+__global__ void k_scale_f32(float *__restrict__ y, const double *__restrict__ nrm2, double floor_norm,
+                            int *__restrict__ keep, int64_t n) {
+    const double nn = sqrt(*nrm2);
+    const bool ok = nn >= floor_norm;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *keep = ok ? 1 : 0;
+    if (!ok) return;
+    const float sc = (float)(1.0 / nn);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) y[i] *= sc;
+}
+
+// X_k <- sum_i V[i][k] X_i for k < keep, in place (every element's m values
+// are read before any is written; m <= 32, keep <= 8)
+__global__ void __launch_bounds__(256) k_collapse_f32(float *__restrict__ X, int m, const double *__restrict__ V,
+                                                      int keep, int64_t n) {
+    __shared__ float c[32][8];
+    for (int t = threadIdx.x; t < 32 * 8; t += blockDim.x) {
+        const int i = t / 8, k = t % 8;
+        c[i][k] = (i < m && k < keep) ? (float)V[i * m + k] : 0.f;
+    }
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride) {
+        float b[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) b[i] = i < m ? X[(int64_t)i * n + r] : 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (k >= keep) break;
+            float a = 0.f;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) a = fmaf(c[i][k], b[i], a);
+            X[(int64_t)k * n + r] = a;
+        }
+    }
+}
+
+__global__ void k_set_unit_f32(float *__restrict__ y, int64_t n, const int64_t *__restrict__ idx) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t at = *idx;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) y[i] = (i == at) ? 1.f : 0.f;
+}
+
+// partial[block] = share of ||hx - e x||^2 (e = ev[k])
+__global__ void __launch_bounds__(256) k_resnorm(const double *__restrict__ x, const double *__restrict__ hx,
+                                                 const double *__restrict__ ev, int k, int64_t n,
+                                                 double *__restrict__ partial) {
+    const double e = ev[k];
+    double acc = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const double r = hx[i] - e * x[i];
+        acc = fma(r, r, acc);
+    }
+    __shared__ double red[8];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int w = 0; w < 8; ++w) v += red[w];
+        partial[blockIdx.x] = v;
+    }
+}
+
+// t = -(hx - e x) / (d - e) with the denominator floor, stored in FP32
+__global__ void k_precond_f32(const double *__restrict__ x, const double *__restrict__ hx,
+                              const double *__restrict__ diag, const double *__restrict__ ev, int k,
+                              float *__restrict__ t, int64_t n) {
+    const double e = ev[k];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        double d = diag[i] - e;
+        if (fabs(d) < 1e-8) d = d < 0 ? -1e-8 : 1e-8;
+        t[i] = (float)(-(hx[i] - e * x[i]) / d);
+    }
+}
+
+// delta = hx - sum_i V[i][k] S_i (the FP64 sigma of a Ritz vector less the
+// subspace estimate), stored in FP32
+__global__ void k_sigma_delta_f32(const double *__restrict__ hx, const float *__restrict__ S, int m,
+                                  const double *__restrict__ V, int k, float *__restrict__ delta, int64_t n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride) {
+        double v = hx[r];
+        for (int i = 0; i < m; ++i) v = fma(-V[i * m + k], (double)S[(int64_t)i * n + r], v);
+        delta[r] = (float)v;
+    }
+}
+
+// S_j += V[j][k] delta for j < m (FP32 storage)
+__global__ void k_rank1_sigma_f32(float *__restrict__ S, int m, const double *__restrict__ V, int k,
+                                  const float *__restrict__ delta, int64_t n) {
+    __shared__ float c[32];
+    if (threadIdx.x < m) c[threadIdx.x] = (float)V[threadIdx.x * m + k];
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride) {
+        const float d = delta[r];
+        for (int j = 0; j < m; ++j) S[(int64_t)j * n + r] = fmaf(c[j], d, S[(int64_t)j * n + r]);
+    }
 }
 
 namespace {
@@ -455,6 +682,8 @@ struct Work {
     double *X = nullptr, *HX = nullptr;     // [nroots][n]
     double *T = nullptr;                    // [nroots][n] corrections
     float *c32 = nullptr, *s32 = nullptr;   // [n] mixed-precision sigma buffers
+    float *Bf = nullptr, *Sf = nullptr;     // FP32 basis: [maxsub][n] vectors and their sigma
+    float *y32 = nullptr;                   // FP32 basis: [n] scratch
     double *A = nullptr;                    // [kMaxSub][kMaxSub] projected matrix
     double *w = nullptr, *V = nullptr;      // eigenvalues, eigenvectors
     double *partial = nullptr;              // [kDotBlocks][32]
@@ -462,6 +691,7 @@ struct Work {
     double *rn2 = nullptr;                  // [nroots] residual norms squared
     int *keep = nullptr;
     int64_t *idx = nullptr;                 // [nroots]
+    int64_t *pidx = nullptr;                // [kDotBlocks + 1] reduction scratch (indices)
     int rc = FCI_OK;
     std::vector<void *> allocs;
     std::vector<size_t> sizes;
@@ -485,6 +715,19 @@ struct Work {
 unsigned grid_for(int64_t n) {
     int64_t g = (n + 255) / 256;
     return (unsigned)(g < 4 * 152 ? (g < 1 ? 1 : g) : 4 * 152);
+}
+
+// W.idx[k] = index of the smallest diagonal entry not among W.idx[0..k)
+void argmin_excl(Work &W, const double *d, int k) {
+    k_argmin_excl_part<<<kDotBlocks, 256, 0, W.s>>>(d, W.n, W.idx, k, W.partial, W.pidx);
+    k_argmin_final<<<1, 256, 0, W.s>>>(W.partial, W.pidx, kDotBlocks, W.idx + k);
+}
+
+// *sgn = the sign of the element of x of largest magnitude (lowest index on ties)
+void sign_of_absmax(Work &W, const double *x, double *sgn) {
+    k_absmax_part<<<kDotBlocks, 256, 0, W.s>>>(x, W.n, W.partial, W.pidx);
+    k_argmin_final<<<1, 256, 0, W.s>>>(W.partial, W.pidx, kDotBlocks, W.pidx + kDotBlocks);
+    k_sign_of<<<1, 1, 0, W.s>>>(x, W.pidx + kDotBlocks, sgn);
 }
 
 bool vec2(int64_t n, const void *a, const void *b) {
@@ -564,9 +807,293 @@ int orthonormalise(Work &W, const double *X, int m, double *y, int *kept) {
     return FCI_OK;
 }
 
+
+// out[i*stride] = X_i . y for FP32 X [m][n] and y (m <= 32), double-float sums
+int dots_f32(Work &W, const float *X, int m, const float *y, double *out, int stride) {
+    if (m <= 0) return FCI_OK;
+    if (m > 32) return fail(FCI_ERR_ARG, "subspace larger than 32 vectors");
+    const int groups = (m + 7) / 8;
+    k_multidot_f32<<<kDotBlocks * groups, 256, 0, W.s>>>(X, m, y, W.n, groups, W.partial);
+    k_reduce_partials<32><<<1, 32, 0, W.s>>>(W.partial, kDotBlocks, m, out, stride);
+    FCI_CUDA(cudaGetLastError());
+    return FCI_OK;
+}
+
+// orthonormalise the FP32 vector y against the FP32 basis X_0..X_{m-1} (the
+// same criterion for a second pass as orthonormalise), normalise; *kept = 1 if kept
+int orthonormalise_f32(Work &W, const float *X, int m, float *y, int *kept) {
+    const unsigned grid = grid_for(W.n);
+    if (m > 0) {
+        for (int pass = 0; pass < 2; ++pass) {
+            if (int rc = dots_f32(W, X, m, y, W.scal, 1)) return rc;
+            k_sub_proj_f32<<<grid, 256, 0, W.s>>>(X, m, W.scal, y, W.n, W.partial);
+            k_reduce_partials<1><<<1, 32, 0, W.s>>>(W.partial, (int)grid, 1, W.scal + 40, 1);
+            FCI_CUDA(cudaGetLastError());
+            if (pass == 0) {
+                double h[41];
+                FCI_CUDA(cudaMemcpyAsync(h, W.scal, sizeof(double) * 41, cudaMemcpyDeviceToHost, W.s));
+                FCI_CUDA(cudaStreamSynchronize(W.s));
+                double c2 = 0.0;
+                for (int i = 0; i < m; ++i) c2 += h[i] * h[i];
+                if (h[40] >= c2) break;
+            }
+        }
+    } else if (int rc = dots_f32(W, y, 1, y, W.scal + 40, 1)) {
+        return rc;
+    }
+    k_scale_f32<<<grid, 256, 0, W.s>>>(y, W.scal + 40, 1e-10, W.keep, W.n);
+    FCI_CUDA(cudaGetLastError());
+    int h = 0;
+    FCI_CUDA(cudaMemcpyAsync(&h, W.keep, sizeof(int), cudaMemcpyDeviceToHost, W.s));
+    FCI_CUDA(cudaStreamSynchronize(W.s));
+    *kept = h;
+    return FCI_OK;
+}
+
 }  // namespace
 
+// Mixed-precision Davidson with an FP32 basis, for spaces whose FP64 basis
+// does not fit in device memory (CAS(18,18): one FP64 vector is 18.9 GB).
+// The same iteration as the FP64-basis mixed mode: FP32 sigma for every new
+// correction, refinement points where the FP64 sigma of each Ritz vector
+// x = B v corrects the subspace sigma vectors along v (S <- S + (sigma64(x) -
+// S v) v^T) and the projected matrix with them, convergence tested only there
+// (exact Rayleigh quotients and residuals of the FP64 Ritz vectors).  The
+// basis B and S are stored in FP32 (orthonormal to FP32 rounding, products
+// summed in double-float), the Ritz vectors and their sigma in FP64.  The FP32
+// storage of S puts a floor of about 1e-7 ||H|| under the residual, below
+// sqrt(tol) for tol >= 1e-9; a thick restart collapses B and S in place onto
+// the lowest Ritz directions (S v keeps the FP64 sigma of refined Ritz vectors).
+static int run_davidson_f32basis(fci_ctx *ctx, int nroots, double tol, double *energies, void *vecs,
+                                 const void *guess, int maxsub) {
+    using clk = std::chrono::steady_clock;
+    const auto t0 = clk::now();
+    Work W;
+    W.ctx = ctx;
+    W.s = ctx->stream;
+    W.n = ctx->ndet;
+    W.nroots = nroots;
+    W.maxsub = maxsub;
+    const int64_t n = W.n;
+    cudaStream_t s = W.s;
+    W.Bf = W.get<float>((size_t)maxsub * n);
+    W.Sf = W.get<float>((size_t)maxsub * n);
+    W.y32 = W.get<float>(n);
+    W.X = W.get<double>((size_t)nroots * n);
+    W.HX = W.get<double>((size_t)nroots * n);
+    W.A = W.get<double>(kMaxSub * kMaxSub);
+    W.w = W.get<double>(kMaxSub);
+    W.V = W.get<double>(kMaxSub * kMaxSub);
+    W.partial = W.get<double>(kDotBlocks * 32);
+    W.scal = W.get<double>(64);
+    W.rn2 = W.get<double>(8);
+    W.keep = W.get<int>(1);
+    W.idx = W.get<int64_t>(8);
+    W.pidx = W.get<int64_t>(kDotBlocks + 1);
+    if (W.rc) return W.rc;
+    ctx->log.clear();
+    ctx->log_width = nroots + 3;
+    ctx->iterations = 0;
+    ctx->sigma_calls = 0;
+    auto sigma32 = [&](int i) {
+        ctx->sigma_calls++;
+        return launch_sigma(ctx, W.Bf + (size_t)i * n, W.Sf + (size_t)i * n, FCI_F32, s);
+    };
+    auto sigma64 = [&](int k) {
+        ctx->sigma_calls++;
+        return launch_sigma(ctx, W.X + (size_t)k * n, W.HX + (size_t)k * n, FCI_F64, s);
+    };
+    auto project = [&](int m) -> int {  // A = B^T S (columns j < m)
+        FCI_CUDA(cudaMemsetAsync(W.A, 0, sizeof(double) * kMaxSub * kMaxSub, s));
+        for (int j = 0; j < m; ++j)
+            if (int rc = dots_f32(W, W.Bf, m, W.Sf + (size_t)j * n, W.A + j, kMaxSub)) return rc;
+        return FCI_OK;
+    };
+
+    // (1) initial subspace
+    int m = 0;
+    for (int k = 0; k < nroots; ++k) {
+        float *b = W.Bf + (size_t)m * n;
+        if (guess) {
+            k_cvt_d2f<<<grid_for(n), 256, 0, s>>>((const double *)guess + (size_t)k * n, b, n);
+        } else {
+            argmin_excl(W, ctx->hdiag, k);
+            k_set_unit_f32<<<grid_for(n), 256, 0, s>>>(b, n, W.idx + k);
+        }
+        FCI_CUDA(cudaGetLastError());
+        int kept = 0;
+        if (int rc = orthonormalise_f32(W, W.Bf, m, b, &kept)) return rc;
+        if (kept) ++m;
+    }
+    if (m == 0) return fail(FCI_ERR_ARG, "initial guess vectors are linearly dependent");
+    for (int i = 0; i < m; ++i)
+        if (int rc = sigma32(i)) return rc;
+    if (int rc = project(m)) return rc;
+
+    // Ritz values and residuals of the FP32 subspace guide the iteration; at a
+    // refinement point the reported values are the exact Rayleigh quotients
+    // x.sigma64(x) / x.x of the FP64 Ritz vectors and their exact residuals
+    // (the FP32-stored basis and sigma vectors hold the projected matrix only
+    // to about 1e-7 relative, so its eigenvalues are not the energies)
+    std::vector<double> e_prev(nroots, INFINITY), ev(kMaxSub), rn(nroots);
+    bool converged = false;
+    int it = 0, inner = 0;
+    std::vector<double> r_hist;
+    auto read_back = [&](int nr, double *rmax, bool exact) -> int {
+        FCI_CUDA(cudaMemcpyAsync(ev.data(), W.w, sizeof(double) * nr, cudaMemcpyDeviceToHost, s));
+        FCI_CUDA(cudaMemcpyAsync(rn.data(), W.rn2, sizeof(double) * nr, cudaMemcpyDeviceToHost, s));
+        int derr = 0;
+        FCI_CUDA(cudaMemcpyAsync(&derr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        FCI_CUDA(cudaStreamSynchronize(s));
+        if (derr & 1) return fail(FCI_ERR_TIMEOUT, "a bounded device wait gave up inside sigma");
+        if (derr) return fail(FCI_ERR_RANGE, "a level sum of the FP64 tensor-core sigma left its exact range");
+        *rmax = 0.0;
+        for (int k = 0; k < nr; ++k) {
+            rn[k] = std::sqrt(rn[k]);
+            *rmax = std::max(*rmax, rn[k]);
+        }
+        const double el = std::chrono::duration<double>(clk::now() - t0).count();
+        ctx->log.push_back((double)it);
+        ctx->log.push_back(exact ? 0.0 : 1.0);
+        ctx->log.push_back(el);
+        for (int k = 0; k < nroots; ++k) ctx->log.push_back(k < nr ? ev[k] : NAN);
+        for (int k = 0; k < nr; ++k)
+            if (!std::isfinite(ev[k]) || !std::isfinite(rn[k]))
+                return fail(FCI_ERR_NAN, "Davidson: a Ritz value or residual norm is not finite (non-finite guess?)");
+        return FCI_OK;
+    };
+    auto residuals = [&](int nr) -> int {
+        for (int k = 0; k < nr; ++k) {
+            k_resnorm<<<kDotBlocks, 256, 0, s>>>(W.X + (size_t)k * n, W.HX + (size_t)k * n, W.w, k, n, W.partial);
+            k_reduce_partials<1><<<1, 32, 0, s>>>(W.partial, kDotBlocks, 1, W.rn2 + k, 1);
+        }
+        FCI_CUDA(cudaGetLastError());
+        return FCI_OK;
+    };
+    for (it = 1; it <= ctx->opt.max_iter; ++it) {
+        k_jacobi<<<1, 256, 0, s>>>(W.A, kMaxSub, m, W.w, W.V);
+        FCI_CUDA(cudaGetLastError());
+        const int nr = nroots < m ? nroots : m;
+        for (int k = 0; k < nr; ++k) {
+            k_lincomb_f32<<<grid_for(n), 256, 0, s>>>(W.Bf, m, W.V + k, m, W.X + (size_t)k * n, n);
+            k_lincomb_f32<<<grid_for(n), 256, 0, s>>>(W.Sf, m, W.V + k, m, W.HX + (size_t)k * n, n);
+        }
+        if (int rc = residuals(nr)) return rc;
+        double rmax = 0.0;
+        if (int rc = read_back(nr, &rmax, false)) return rc;
+        r_hist.push_back(rmax);
+        const double r_win = r_hist.size() > 15 ? r_hist[r_hist.size() - 16] : INFINITY;
+        if (++inner >= 60 || rmax < std::sqrt(tol) || (inner >= 15 && rmax > 0.5 * r_win)) {
+            // refinement point: FP64 sigma of each Ritz vector; its difference to
+            // the subspace estimate corrects S along v (and the projected matrix),
+            // and the exact Rayleigh quotient and residual replace the estimates
+            for (int k = 0; k < nr; ++k) {
+                double *x = W.X + (size_t)k * n, *hx = W.HX + (size_t)k * n;
+                if (int rc = sigma64(k)) return rc;
+                k_sigma_delta_f32<<<grid_for(n), 256, 0, s>>>(hx, W.Sf, m, W.V, k, W.y32, n);
+                if (int rc = dots_f32(W, W.Bf, m, W.y32, W.scal, 1)) return rc;
+                k_rank1_sigma_f32<<<grid_for(n), 256, 0, s>>>(W.Sf, m, W.V, k, W.y32, n);
+                k_rank1_proj<<<1, 256, 0, s>>>(W.A, kMaxSub, m, W.scal, W.V, k);
+                if (int rc = dots(W, x, 1, hx, W.scal + 52, 1)) return rc;
+                if (int rc = dots(W, x, 1, x, W.scal + 53, 1)) return rc;
+                k_quotient<<<1, 1, 0, s>>>(W.scal + 52, W.scal + 53, W.w + k);
+                FCI_CUDA(cudaGetLastError());
+            }
+            if (int rc = residuals(nr)) return rc;
+            if (int rc = read_back(nr, &rmax, true)) return rc;
+            double demax = 0.0;
+            for (int k = 0; k < nr; ++k) demax = std::max(demax, std::fabs(ev[k] - e_prev[k]));
+            if (nr == nroots && demax < tol && rmax < std::sqrt(tol)) {
+                converged = true;
+                break;
+            }
+            for (int k = 0; k < nr; ++k) e_prev[k] = ev[k];
+            inner = 0;
+        }
+        if (m + nr > maxsub) {
+            // thick restart in place: B and S collapse onto the lowest `keep` Ritz
+            // directions (B v_k, S v_k); along a refined Ritz vector S v_k is its
+            // FP64 sigma (stored in FP32), so no FP32 sigma error enters along it
+            const int keep = std::min(m, std::max(nr, std::min(4, maxsub / 2)));
+            k_collapse_f32<<<grid_for(n), 256, 0, s>>>(W.Bf, m, W.V, keep, n);
+            k_collapse_f32<<<grid_for(n), 256, 0, s>>>(W.Sf, m, W.V, keep, n);
+            FCI_CUDA(cudaGetLastError());
+            m = keep;
+            if (int rc = project(m)) return rc;
+        }
+        int added = 0;
+        for (int k = 0; k < nr && m < maxsub; ++k) {
+            float *b = W.Bf + (size_t)m * n;
+            k_precond_f32<<<grid_for(n), 256, 0, s>>>(W.X + (size_t)k * n, W.HX + (size_t)k * n, ctx->hdiag, W.w, k, b, n);
+            FCI_CUDA(cudaGetLastError());
+            int kept = 0;
+            if (int rc = orthonormalise_f32(W, W.Bf, m, b, &kept)) return rc;
+            if (!kept) continue;
+            if (int rc = sigma32(m)) return rc;
+            ++m;
+            if (int rc = dots_f32(W, W.Bf, m, W.Sf + (size_t)(m - 1) * n, W.A + (m - 1), kMaxSub)) return rc;
+            if (int rc = dots_f32(W, W.Sf, m, W.Bf + (size_t)(m - 1) * n, W.A + (size_t)(m - 1) * kMaxSub, 1))
+                return rc;
+            ++added;
+        }
+        if (added == 0) {
+            if (inner == 0) {  // an exact point that adds nothing: no further progress
+                converged = rmax < std::sqrt(tol);
+                break;
+            }
+            inner = 1 << 20;  // refine on the next pass
+        }
+    }
+    ctx->iterations = it > ctx->opt.max_iter ? ctx->opt.max_iter : it;
+    for (int k = 0; k < nroots; ++k) energies[k] = ev[k];
+    if (vecs) {
+        for (int k = 0; k < nroots; ++k) {
+            double *x = W.X + (size_t)k * n;
+            if (int rc = dots(W, x, 1, x, W.scal + 54, 1)) return rc;
+            k_scale<<<grid_for(n), 256, 0, s>>>(x, W.scal + 54, 0.0, W.keep, n);
+            sign_of_absmax(W, x, W.scal + 50);
+            k_scale_by<<<grid_for(n), 256, 0, s>>>(x, W.scal + 50, n);
+            FCI_CUDA(cudaMemcpyAsync((double *)vecs + (size_t)k * n, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        }
+    }
+    FCI_CUDA(cudaStreamSynchronize(s));
+    if (!converged) return fail(FCI_ERR_NOCONV, "Davidson did not converge within max_iter");
+    return FCI_OK;
+}
+
+// Device bytes of the FP64-basis workspace, and the largest FP32-basis
+// subspace (<= want) that fits in `avail` bytes (0 when none does).
+static size_t f64_basis_bytes(int64_t n, int maxsub, int keepn, int nroots, bool mixed) {
+    return (size_t)n * 8 * (size_t)(2 * maxsub + 2 * keepn + nroots) + (mixed ? (size_t)n * 8 : 0);
+}
+static int f32_basis_fit(int64_t n, int nroots, int want, size_t avail) {
+    for (int m = want; m >= 2 * nroots && m >= 2; --m)
+        if ((size_t)n * 4 * (size_t)(2 * m + 1) + (size_t)n * 8 * 2 * nroots <= avail) return m;
+    return 0;
+}
+
 int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *vecs, const void *guess) {
+    {  // basis storage: FP64, or FP32 (mixed precision) where asked for or where FP64 does not fit
+        int maxsub = std::min(32, std::max(ctx->opt.max_subspace, 2 * nroots));
+        if (maxsub > ctx->ndet) maxsub = (int)ctx->ndet;
+        const int keepn = std::max(nroots, std::min(8, maxsub / 2));
+        const bool mixed = ctx->opt.precision == FCI_PREC_MIXED;
+        size_t fr = 0, tot = 0;
+        FCI_CUDA(cudaMemGetInfo(&fr, &tot));
+        size_t avail = fr > ((size_t)2 << 30) ? fr - ((size_t)2 << 30) : 0;  // 2 GiB left for the runtime
+        if (ctx->opt.max_device_bytes > 0) {
+            const double cap = ctx->opt.max_device_bytes - (double)ctx->bytes;
+            avail = std::min(avail, cap > 0 ? (size_t)cap : (size_t)0);
+        }
+        const bool f32b = mixed && (ctx->opt.basis_f32 == 1 ||
+                                    (ctx->opt.basis_f32 == 0 && f64_basis_bytes(ctx->ndet, maxsub, keepn, nroots, mixed) > avail));
+        if (f32b) {
+            FCI_CUDA(cudaDeviceSynchronize());  // caller's guess buffer is complete
+            const int m = ctx->opt.basis_f32 == 1 ? maxsub : f32_basis_fit(ctx->ndet, nroots, std::min(maxsub, 8), avail);
+            if (m == 0) return fail(FCI_ERR_OOM, "Davidson: not even an FP32 basis of 2 vectors per root fits");
+            return run_davidson_f32basis(ctx, nroots, tol, energies, vecs, guess, m);
+        }
+    }
     using clk = std::chrono::steady_clock;
     const auto t0 = clk::now();
     FCI_CUDA(cudaDeviceSynchronize());  // caller's guess buffer is complete
@@ -600,6 +1127,7 @@ int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *v
     W.rn2 = W.get<double>(8);
     W.keep = W.get<int>(1);
     W.idx = W.get<int64_t>(8);
+    W.pidx = W.get<int64_t>(kDotBlocks + 1);
     if (W.rc) return W.rc;
     const int64_t n = W.n;
     cudaStream_t s = W.s;
@@ -617,7 +1145,7 @@ int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *v
             FCI_CUDA(cudaMemcpyAsync(b, (const double *)guess + (size_t)k * n, sizeof(double) * n,
                                      cudaMemcpyDeviceToDevice, s));
         } else {
-            k_argmin_excl<<<1, 1024, 0, s>>>(ctx->hdiag, n, W.idx, k, W.idx + k);
+            argmin_excl(W, ctx->hdiag, k);
             k_set_unit<<<grid_for(n), 256, 0, s>>>(b, n, W.idx + k);
             FCI_CUDA(cudaGetLastError());
         }
@@ -780,7 +1308,7 @@ int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *v
     if (vecs) {
         for (int k = 0; k < nroots; ++k) {
             double *dst = (double *)vecs + (size_t)k * n;
-            k_absmax_sign<<<1, 1024, 0, s>>>(W.X + (size_t)k * n, n, W.scal + 50);
+            sign_of_absmax(W, W.X + (size_t)k * n, W.scal + 50);
             k_scale_by<<<grid_for(n), 256, 0, s>>>(W.X + (size_t)k * n, W.scal + 50, n);
             FCI_CUDA(cudaMemcpyAsync(dst, W.X + (size_t)k * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
         }

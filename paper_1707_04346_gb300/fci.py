@@ -64,6 +64,7 @@ class fci_options(ctypes.Structure):
         ("f64_kernels", ctypes.c_int),
         ("max_device_bytes", ctypes.c_double),
         ("f32_row_global", ctypes.c_int),
+        ("basis_f32", ctypes.c_int),
     ]
 
 
