@@ -38,7 +38,7 @@ import fci_inputs as fi  # noqa: E402
 
 WORKLOADS = {"cas14": (14, 7, 7, 100), "cas16": (16, 8, 8, 100), "cas12": (12, 6, 6, 100), "cas8": (8, 4, 4, 40),
              "cas18": (18, 9, 9, 100)}
-LARGE = {"cas18"}  # FP32 sigma only (no FP64 kernels at this size); trial vector regenerated on the device
+LARGE = {"cas18"}  # vectors too large for the host: trial vector regenerated on the device
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), nominal
 GB300_SMS = 152
 FP32_LANES_PER_SM = 128  # FP32 operations issued per SM per clock
@@ -205,6 +205,21 @@ def kernel_work(name, norb, na, nb, N, sa, sb, nsa, nsb, peaks, f32_splits=3):
     if name in ("sigma2_tc", "sigma1_tc"):  # same-spin terms through intermediate strings
         return ("tensor", prods32 * 2.0 * 128 * npad1 * kpad * tiles, "TFLOP/s", *bf16,
                 f"bf16 MMA FLOP: {prods32} slice products x 2 x 128 x {npad1} x {kpad} x {tiles} tiles")
+    if name in ("sigma3_wide", "sigma1_wide", "sigma2_wide"):  # wide FP64 kernels: 21 products per tile and part
+        if name == "sigma3_wide":
+            kp, npd, t = kpad, npad, tiles
+        elif name == "sigma2_wide":
+            kp, npd, t = kpad, npad1, tiles
+        else:  # beta strings as rows, over C transposed
+            kp, npd, t = -(-sb // 16) * 16, npad1, nsb * (-(-nsa // 128))
+        return ("tensor", 21 * 2.0 * 128 * npd * kp * t, "TFLOP/s", *bf16,
+                f"bf16 MMA FLOP: 21 slice products x 2 x 128 x {npd} x {kp} x {t} tiles")
+    if name == "transpose_slice":  # C transposed (read 8, write 8) and sliced (read 8, write 12)
+        return ("hbm", 36.0 * N, "GB/s", peaks["hbm_gbs"], "MEASURED_PEAKS.json hbm_gbs",
+                "bytes: transpose of C (8 + 8 per determinant) and its digit slices (8 + 12)")
+    if name == "convert":  # 64-bit integers in, FP64 out
+        return ("hbm", 16.0 * N, "GB/s", peaks["hbm_gbs"], "MEASURED_PEAKS.json hbm_gbs",
+                "bytes: 8 read and 8 written per determinant")
     if name == "slice_c":  # row exponents (one read of C) and the digit slices (a read, 12 bytes written)
         return ("hbm", 28.0 * N, "GB/s", peaks["hbm_gbs"], "MEASURED_PEAKS.json hbm_gbs",
                 "bytes: two reads of C (8 + 8 per determinant) and 12 written")
@@ -493,6 +508,38 @@ def run_large(args):
         "e2e": {"value": e2e, "unit": "Gdet/s", "h2d_bytes_per_step": N * 4, "d2h_bytes_per_step": N * 4},
         "bf16x3_sigma": bf16x3,
     }
+    if args.davidson and rank == 0:
+        # the mixed-precision solve of this space: FP32 basis of at most 8
+        # vectors (the FP64 basis does not fit), FP32 sigma for the
+        # corrections, FP64 sigma at refinement points, to 1e-8 Eh
+        del hc, hs, c, s
+        torch.cuda.empty_cache()
+        ctxm = pkg.fci_init(norb, na, nb, h1, eri,
+                            pkg.default_options(precision=pkg.FCI_PREC_MIXED, max_iter=args.max_iter))
+        t0 = time.perf_counter()
+        try:
+            em = pkg.fci_davidson(ctxm, args.roots, 1e-8)
+            conv = True
+        except pkg.FciError as ex:
+            if ex.code != pkg.fci.FCI_ERR_NOCONV:
+                raise
+            em, conv = None, False
+        wall = time.perf_counter() - t0
+        log = pkg.fci_davidson_log(ctxm, args.roots)
+        exact = log[log[:, 1] == 0]
+        last32 = log[log[:, 1] == 1]
+        result["davidson"] = {
+            "roots": args.roots, "tol": 1e-8, "converged": conv, "wall_s": wall,
+            "E_exact": [float(x) for x in (exact[-1, 3:] if len(exact) else [])],
+            "E_fp32_subspace_last": [float(x) for x in (last32[-1, 3:] if len(last32) else [])],
+            "abs_diff_fp32_subspace_vs_exact": (float(np.abs(last32[-1, 3:] - exact[-1, 3:]).max())
+                                                if len(exact) and len(last32) else None),
+            "iterations": int(pkg.fci_query(ctxm, 8)), "sigma_calls": int(pkg.fci_query(ctxm, 9)),
+            "refinement_points": int(len(exact)),
+            "exact_energies": [[float(r[0]), float(r[2]), float(r[3])] for r in exact],
+            "basis": "FP32 (fci_options.basis_f32 = 0 chose it: the FP64 basis does not fit)",
+        }
+        pkg.fci_free(ctxm)
     if args.cpu_baseline and rank == 0 and world == 1:
         import oracle
 
@@ -675,14 +722,13 @@ def run_ours(args):
     if args.batched and rank == 0:
         result["batched"] = run_batched(pkg, args.batch_instances)
     if args.extra and args.workload == "cas14":
-        # the other sigma configurations: CAS(16,16) in both precisions,
-        # CAS(18,18) in FP32 (its FP64 sigma is not built)
+        # the other sigma configurations: CAS(16,16) and CAS(18,18), both
+        # precisions (an FP64 sigma at CAS(18,18) takes about 10 s: two steps)
         legs = {}
         legs["cas16_sigma"] = sigma_leg(pkg, "cas16", max(3, args.steps // 4), 3, stream, world,
                                         args.cpu_seconds / 3 if (args.cpu_baseline and world == 1) else 0)
-        legs["cas18_sigma_fp32"] = sigma_leg(pkg, "cas18", 3, 3, stream, world,
-                                             args.cpu_seconds / 3 if (args.cpu_baseline and world == 1) else 0,
-                                             dtypes=("f32",))
+        legs["cas18_sigma"] = sigma_leg(pkg, "cas18", 2, 2, stream, world,
+                                        args.cpu_seconds / 3 if (args.cpu_baseline and world == 1) else 0)
         if rank == 0:
             result.update(legs)
     if args.cpu_baseline and rank == 0 and world == 1:
@@ -708,6 +754,7 @@ def main():
     ap.add_argument("--no-extra", dest="extra", action="store_false",
                     help="skip the CAS(16,16) and CAS(18,18) sigma legs")
     ap.add_argument("--roots", type=int, default=1, help="Davidson roots (CAS(16,16) configuration: 3)")
+    ap.add_argument("--max-iter", type=int, default=600, help="Davidson iteration limit of the CAS(18,18) solve")
     ap.add_argument("--ref-from-mixed", action="store_true",
                     help="FP64 reference energies from an FP64 solve started at the mixed solution")
     args = ap.parse_args()

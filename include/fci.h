@@ -397,7 +397,10 @@ int64_t fci_batch_offset(fci_batch *batch, int i);
 int fci_batch_tuning(fci_batch *batch, int *out, int cap, int *count);
 
 /* Iterations and sigma launches of the last fci_batch_davidson: what = 0
- * iterations, 1 batched sigma launches, 2 graph launches. */
+ * iterations (of the slowest instance), 1 batched sigma launches issued
+ * (instances masked off skip them on the device), 2 graph launches (one per
+ * chunk of up to 8 iterations), 3 host synchronisations (one per chunk: the
+ * convergence, refinement and expansion decisions are made on the device). */
 int64_t fci_batch_stats(fci_batch *batch, int what);
 
 int fci_batch_free(fci_batch *batch);

@@ -16,8 +16,11 @@
 //    formulas as the single-instance kernels;
 //  * `tpr` is tuned per (norb, precision) at init by timing 32/64/128/256 on
 //    the first instance of that size;
-//  * the per-iteration kernel sequences are captured in CUDA graphs (one per
-//    subspace size), with every per-instance parameter in device memory.
+//  * the iterations are captured in CUDA graphs, up to eight iterations (to
+//    the next thick restart) per graph, with every per-instance parameter and
+//    every decision (convergence, refinement, expansion) in device memory; the
+//    host launches one graph per chunk of iterations and reads back one
+//    counter (the converged instances).
 // An instance that converged is masked off; a slot an instance does not fill
 // in an iteration (dropped correction, refinement step, or converged) is a
 // zero vector whose projected-matrix diagonal is set to 1e30, so it never
@@ -42,6 +45,7 @@ constexpr int kChunk = 256;    // elementwise kernels: one CTA per chunk of <= k
 constexpr int kDChunk = 8192;  // dot products: 32 elements per thread before the block reduction
 constexpr double kPad = 1e30;
 constexpr int64_t kHybridMinDets = 32768;  // FP32 sigma of instances this large: single-instance kernels
+constexpr int kRefinePeriod = 4;           // mixed precision: refinements on every 4th non-restart iteration
 
 struct InstDev {
     SpinTables A, B;
@@ -625,7 +629,7 @@ struct fci_batch {
     // sigma call plumbing
     void **d_cin = nullptr, **d_cout = nullptr;
     int *d_on_all = nullptr;
-    int64_t stats[3] = {0, 0, 0};
+    int64_t stats[4] = {0, 0, 0, 0};  // iterations, sigma launches, graph launches, host synchronisations
     std::vector<std::pair<void *, size_t>> allocs;
 };
 
@@ -721,7 +725,7 @@ int fci_batch_tuning(fci_batch *b, int *out, int cap, int *count) {
 }
 
 int64_t fci_batch_stats(fci_batch *b, int what) {
-    if (!b || what < 0 || what > 2) return -1;
+    if (!b || what < 0 || what > 3) return -1;
     return b->stats[what];
 }
 
@@ -1027,6 +1031,63 @@ __global__ void __launch_bounds__(kBlock) k_badd(const Chunk *__restrict__ ch, c
     h[idx] += d[idx];
 }
 
+// Per-instance decisions of one batched Davidson iteration, on the device (one
+// thread per instance), from the Ritz values w and squared residual norms rn2
+// just computed: energies, convergence (only where the subspace sigma is
+// FP64-exact), and whether the instance refines (mixed precision) or expands
+// this iteration.  State per instance: iteration count, iterations since the
+// last exact point, the energies of the last exact point, the last 16
+// residuals.  *ndone counts converged instances.  Refinements happen only on
+// iterations with can_refine set (every kRefinePeriod-th iteration that is not
+// a thick restart): an instance whose test passes in between refines at the
+// next such iteration, and the other iterations carry no refinement launches.
+__global__ void k_bdecide(int ninst, int nroots, double tol, int mixed, int can_refine, const double *__restrict__ w,
+                          const double *__restrict__ rn2, int *__restrict__ active, int *__restrict__ refine,
+                          int *__restrict__ expand, int *__restrict__ exact, int *__restrict__ inner,
+                          int *__restrict__ its, double *__restrict__ eprev, double *__restrict__ rhist,
+                          double *__restrict__ energy, int *__restrict__ ndone) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ninst) return;
+    refine[i] = 0;
+    expand[i] = 0;
+    if (!active[i]) return;
+    const int it = ++its[i];
+    double rmax = 0.0, demax = 0.0;
+    for (int k = 0; k < nroots; ++k) {
+        const double e = w[(int64_t)i * kMaxSub + k];
+        rmax = fmax(rmax, sqrt(rn2[(int64_t)i * kMaxRoots + k]));
+        demax = fmax(demax, fabs(e - eprev[(int64_t)i * kMaxRoots + k]));
+        energy[(int64_t)i * kMaxRoots + k] = e;
+    }
+    double *rh = rhist + (int64_t)i * 16;
+    const double r15 = rh[it % 16];  // residual 16 iterations ago
+    rh[it % 16] = rmax;
+    if (exact[i]) {
+        if (demax < tol && rmax < sqrt(tol)) {
+            active[i] = 0;
+            atomicAdd(ndone, 1);
+            return;
+        }
+        for (int k = 0; k < nroots; ++k) eprev[(int64_t)i * kMaxRoots + k] = w[(int64_t)i * kMaxSub + k];
+        inner[i] = 0;
+    } else if (mixed && (++inner[i] >= 60 || rmax < sqrt(tol) || (inner[i] >= 15 && rmax > 0.5 * r15)) &&
+               can_refine) {
+        refine[i] = 1;
+    }
+    expand[i] = refine[i] ? 0 : 1;
+}
+
+// exact <- 1 where the instance refined; exact <- 0 where it expanded with FP32
+// sigma (mixed) or, when all is set, everywhere (a collapse kept FP32 vectors)
+__global__ void k_bexact(int ninst, const int *__restrict__ refine, const int *__restrict__ expand, int all,
+                         int *__restrict__ exact) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ninst) return;
+    if (all) exact[i] = 0;
+    else if (refine && refine[i]) exact[i] = 1;
+    else if (expand && expand[i]) exact[i] = 0;
+}
+
 struct BWork {
     fci_batch *b;
     cudaStream_t s;
@@ -1036,11 +1097,13 @@ struct BWork {
     float *c32, *s32;               // [ntot]
     double *A, *w, *V, *g, *nrm2, *rn2, *partial;
     int *on, *on_exp, *on_ref;      // masks: active, expanding, refining
+    int *exact, *inner, *its, *ndone;  // per-instance decision state (device)
+    double *eprev, *rhist, *energy;    // [ninst][kMaxRoots], [ninst][16], [ninst][kMaxRoots]
     void **ptr32;                   // [2][ninst]: c32 / s32 per instance
     void **ptrBS;                   // [maxsub][2][ninst]: B_j -> S_j per instance
     void **ptrXT;                   // [nroots][2][ninst]: X_k -> T_k per instance
     void **ptrD2;                   // [2][ninst]: scratch for the initial guesses
-    std::map<int, cudaGraphExec_t> g_ritz, g_expand;
+    std::map<int, cudaGraphExec_t> g_chunk;  // iterations from subspace size m to the next restart (<= 8)
 };
 
 // out[i*os + j*js] = X_j . y for j < m, per instance (masked by on); one CTA
@@ -1131,6 +1194,13 @@ static int batch_davidson_run(fci_batch *b, int nroots, double tol, double *ener
     W.ptr32 = (void **)get(sizeof(void *) * 2 * ninst);
     W.ptrBS = (void **)get(sizeof(void *) * 2 * ninst * maxsub);
     W.ptrXT = (void **)get(sizeof(void *) * 2 * ninst * nroots);
+    W.exact = (int *)get(sizeof(int) * ninst);
+    W.inner = (int *)get(sizeof(int) * ninst);
+    W.its = (int *)get(sizeof(int) * ninst);
+    W.ndone = (int *)get(sizeof(int));
+    W.eprev = (double *)get(sizeof(double) * ninst * kMaxRoots);
+    W.rhist = (double *)get(sizeof(double) * ninst * 16);
+    W.energy = (double *)get(sizeof(double) * ninst * kMaxRoots);
     if (rc) return rc;
     cudaStream_t s = W.s;
     {
@@ -1155,17 +1225,22 @@ static int batch_davidson_run(fci_batch *b, int nroots, double tol, double *ener
             }
         FCI_CUDA(cudaMemcpy(W.ptrXT, v.data(), sizeof(void *) * v.size(), cudaMemcpyHostToDevice));
     }
-    std::vector<int> active(ninst, 1), exact(ninst, W.mixed ? 0 : 1), inner(ninst, 0), refine(ninst, 0), expand(ninst);
-    std::vector<double> e_prev((size_t)ninst * nroots, INFINITY), r_ref(ninst, INFINITY);
-    std::vector<double> hw((size_t)ninst * kMaxSub), hrn((size_t)ninst * kMaxRoots);
-    std::vector<double> r_hist((size_t)ninst * 16, INFINITY);
-    auto upload = [&](int *dst, const std::vector<int> &vv) {
-        return cudaMemcpyAsync(dst, vv.data(), sizeof(int) * ninst, cudaMemcpyHostToDevice, s);
-    };
-    b->stats[0] = b->stats[1] = b->stats[2] = 0;
+    // decision state on the device: every instance active, exact in FP64 mode
+    {
+        std::vector<int> ones(ninst, 1), ex(ninst, W.mixed ? 0 : 1);
+        std::vector<double> inf_r((size_t)ninst * kMaxRoots, INFINITY), inf_h((size_t)ninst * 16, INFINITY);
+        FCI_CUDA(cudaMemcpy(W.on, ones.data(), sizeof(int) * ninst, cudaMemcpyHostToDevice));
+        FCI_CUDA(cudaMemcpy(W.exact, ex.data(), sizeof(int) * ninst, cudaMemcpyHostToDevice));
+        FCI_CUDA(cudaMemset(W.inner, 0, sizeof(int) * ninst));
+        FCI_CUDA(cudaMemset(W.its, 0, sizeof(int) * ninst));
+        FCI_CUDA(cudaMemset(W.ndone, 0, sizeof(int)));
+        FCI_CUDA(cudaMemcpy(W.eprev, inf_r.data(), sizeof(double) * inf_r.size(), cudaMemcpyHostToDevice));
+        FCI_CUDA(cudaMemcpy(W.energy, inf_r.data(), sizeof(double) * inf_r.size(), cudaMemcpyHostToDevice));
+        FCI_CUDA(cudaMemcpy(W.rhist, inf_h.data(), sizeof(double) * inf_h.size(), cudaMemcpyHostToDevice));
+    }
+    for (int i = 0; i < 4; ++i) b->stats[i] = 0;
 
     // (1) initial subspace: unit vectors on the lowest diagonal elements, their sigma
-    FCI_CUDA(upload(W.on, active));
     FCI_CUDA(cudaMemsetAsync(W.A, 0, sizeof(double) * ninst * kMaxSub * kMaxSub, s));
     k_bguess<<<ninst, 256, 0, s>>>(b->d_inst, nroots, W.Bv, ntot);
     for (int k = 0; k < nroots && !rc; ++k)
@@ -1177,71 +1252,31 @@ static int batch_davidson_run(fci_batch *b, int nroots, double tol, double *ener
         bdots(W, W.on, W.Bv, m, W.Sv + (size_t)j * ntot, W.A + j, kMaxSub * kMaxSub, kMaxSub);
     if (rc) return rc;
 
-    int it = 0;
-    bool all_done = false;
-    for (it = 1; it <= b->opt.max_iter && !rc; ++it) {
-        // (4) diagonalise; Ritz vectors, residuals and (2)-(3) corrections: one graph per m
-        FCI_CUDA(upload(W.on, active));
-        auto gr = W.g_ritz.find(m);
-        if (gr == W.g_ritz.end()) {
-            cudaGraph_t graph;
-            FCI_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-            k_bjacobi<<<ninst, 128, 0, s>>>(W.on, W.A, m, W.w, W.V);
-            for (int k = 0; k < nroots; ++k) {
-                k_blincomb<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on, W.Bv, ntot, m, W.V + k,
-                                                          kMaxSub * kMaxSub, m, 1.0, 0.0, W.X + (size_t)k * ntot);
-                k_blincomb<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on, W.Sv, ntot, m, W.V + k,
-                                                          kMaxSub * kMaxSub, m, 1.0, 0.0, W.HX + (size_t)k * ntot);
-                k_bresid<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on, b->d_inst, W.X + (size_t)k * ntot,
-                                                        W.HX + (size_t)k * ntot, W.w + k, kMaxSub,
-                                                        W.T + (size_t)k * ntot, W.partial);
-                k_breduce<8><<<ninst, kBlock, 0, s>>>(b->d_cfirst, W.on, W.partial, 1, W.rn2 + k, kMaxRoots, 1);
-            }
-            FCI_CUDA(cudaStreamEndCapture(s, &graph));
-            cudaGraphExec_t ex;
-            FCI_CUDA(cudaGraphInstantiate(&ex, graph, 0));
-            cudaGraphDestroy(graph);
-            gr = W.g_ritz.emplace(m, ex).first;
+    // One iteration as a kernel sequence whose every decision lives on the
+    // device: (4) diagonalise, Ritz vectors and residuals, the per-instance
+    // decisions (k_bdecide), the refinement of the instances that refine
+    // (mixed precision; sigma64 of the Ritz vectors corrects S along v), a thick
+    // restart when the subspace is full (the subspace size m follows the same
+    // sequence for every instance, so the host knows it), and (2)-(3) one new
+    // preconditioned, orthonormalised vector per root with its sigma for the
+    // instances that expand (padding elsewhere).  Returns m after the iteration.
+    const int keep = std::min(keepn, maxsub);
+    const unsigned gi = (unsigned)((ninst + 127) / 128);
+    auto iteration = [&](int mi, bool can_refine, int *sig_launches) -> int {
+        k_bjacobi<<<ninst, 128, 0, s>>>(W.on, W.A, mi, W.w, W.V);
+        for (int k = 0; k < nroots; ++k) {
+            k_blincomb<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on, W.Bv, ntot, mi, W.V + k, kMaxSub * kMaxSub, mi,
+                                                      1.0, 0.0, W.X + (size_t)k * ntot);
+            k_blincomb<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on, W.Sv, ntot, mi, W.V + k, kMaxSub * kMaxSub, mi,
+                                                      1.0, 0.0, W.HX + (size_t)k * ntot);
+            k_bresid<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on, b->d_inst, W.X + (size_t)k * ntot,
+                                                    W.HX + (size_t)k * ntot, W.w + k, kMaxSub, W.T + (size_t)k * ntot,
+                                                    W.partial);
+            k_breduce<8><<<ninst, kBlock, 0, s>>>(b->d_cfirst, W.on, W.partial, 1, W.rn2 + k, kMaxRoots, 1);
         }
-        FCI_CUDA(cudaGraphLaunch(gr->second, s));
-        b->stats[2]++;
-        FCI_CUDA(cudaMemcpyAsync(hw.data(), W.w, sizeof(double) * ninst * kMaxSub, cudaMemcpyDeviceToHost, s));
-        FCI_CUDA(cudaMemcpyAsync(hrn.data(), W.rn2, sizeof(double) * ninst * kMaxRoots, cudaMemcpyDeviceToHost, s));
-        FCI_CUDA(cudaStreamSynchronize(s));
-        // per-instance decisions (convergence only where the Ritz data are exact)
-        bool any_ref = false;
-        for (int i = 0; i < ninst; ++i) {
-            refine[i] = 0;
-            if (!active[i]) continue;
-            double rmax = 0.0, demax = 0.0;
-            for (int k = 0; k < nroots; ++k) {
-                rmax = std::max(rmax, std::sqrt(hrn[(size_t)i * kMaxRoots + k]));
-                demax = std::max(demax, std::fabs(hw[(size_t)i * kMaxSub + k] - e_prev[(size_t)i * nroots + k]));
-            }
-            for (int k = 0; k < nroots; ++k) energies[(size_t)i * nroots + k] = hw[(size_t)i * kMaxSub + k];
-            const double r15 = r_hist[(size_t)i * 16 + (it % 16)];  // residual 16 iterations ago
-            r_hist[(size_t)i * 16 + (it % 16)] = rmax;
-            if (exact[i]) {
-                if (demax < tol && rmax < std::sqrt(tol)) {
-                    active[i] = 0;
-                    continue;
-                }
-                for (int k = 0; k < nroots; ++k) e_prev[(size_t)i * nroots + k] = hw[(size_t)i * kMaxSub + k];
-                r_ref[i] = rmax;
-                inner[i] = 0;
-            } else if (++inner[i] >= 60 || rmax < std::sqrt(tol) ||
-                       (inner[i] >= 15 && rmax > 0.5 * r15)) {
-                refine[i] = 1;
-                any_ref = true;
-            }
-        }
-        all_done = std::none_of(active.begin(), active.end(), [](int a) { return a != 0; });
-        if (all_done) break;
-        for (int i = 0; i < ninst; ++i) expand[i] = active[i] && !refine[i];
-        FCI_CUDA(upload(W.on, active));
-        FCI_CUDA(upload(W.on_ref, refine));
-        FCI_CUDA(upload(W.on_exp, expand));
-        if (any_ref) {
+        k_bdecide<<<gi, 128, 0, s>>>(ninst, nroots, tol, W.mixed ? 1 : 0, can_refine ? 1 : 0, W.w, W.rn2, W.on,
+                                     W.on_ref, W.on_exp, W.exact, W.inner, W.its, W.eprev, W.rhist, W.energy, W.ndone);
+        if (can_refine) {
             // refinement: delta = sigma64(x_k) - HX_k corrects S along v_k (rank 1)
             for (int k = 0; k < nroots && !rc; ++k) {
                 double *d = W.T + (size_t)k * ntot;  // refining instances add no correction this round
@@ -1249,77 +1284,131 @@ static int batch_davidson_run(fci_batch *b, int nroots, double tol, double *ener
                 if (rc) break;
                 k_bsub<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on_ref, d, W.HX + (size_t)k * ntot);
                 k_badd<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on_ref, W.HX + (size_t)k * ntot, d);
-                bdots(W, W.on_ref, W.Bv, m, d, W.g, kMaxSub, 1);
-                k_brank1<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on_ref, W.Sv, ntot, m, W.V, k, d);
-                k_brank1_proj<<<ninst, 256, 0, s>>>(W.on_ref, W.A, W.g, W.V, m, k);
+                bdots(W, W.on_ref, W.Bv, mi, d, W.g, kMaxSub, 1);
+                k_brank1<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on_ref, W.Sv, ntot, mi, W.V, k, d);
+                k_brank1_proj<<<ninst, 256, 0, s>>>(W.on_ref, W.A, W.g, W.V, mi, k);
             }
-            if (rc) break;
-            FCI_CUDA(cudaGetLastError());
-            b->stats[1] += nroots;
-            for (int i = 0; i < ninst; ++i)
-                if (refine[i]) exact[i] = 1;
+            *sig_launches += nroots;
+            k_bexact<<<gi, 128, 0, s>>>(ninst, W.on_ref, nullptr, 0, W.exact);
         }
-        if (m + nroots > maxsub) {
-            // thick restart: every active instance collapses onto its lowest `keep`
-            // Ritz vectors and their sigma
-            const int keep = std::min(keepn, m);
-            for (int k = nroots; k < keep; ++k) {
-                k_blincomb<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on, W.Bv, ntot, m, W.V + k,
-                                                          kMaxSub * kMaxSub, m, 1.0, 0.0, W.X + (size_t)k * ntot);
-                k_blincomb<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on, W.Sv, ntot, m, W.V + k,
-                                                          kMaxSub * kMaxSub, m, 1.0, 0.0, W.HX + (size_t)k * ntot);
+        if (rc) return mi;
+        if (mi + nroots > maxsub) {
+            // thick restart: every active instance collapses onto its lowest
+            // `keep` Ritz vectors and their sigma
+            const int kk = std::min(keep, mi);
+            for (int k = nroots; k < kk; ++k) {
+                k_blincomb<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on, W.Bv, ntot, mi, W.V + k, kMaxSub * kMaxSub,
+                                                          mi, 1.0, 0.0, W.X + (size_t)k * ntot);
+                k_blincomb<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on, W.Sv, ntot, mi, W.V + k, kMaxSub * kMaxSub,
+                                                          mi, 1.0, 0.0, W.HX + (size_t)k * ntot);
             }
-            for (int k = 0; k < keep; ++k) {
-                k_bcopy<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on, W.X + (size_t)k * ntot,
-                                                       W.Bv + (size_t)k * ntot, 0);
-                k_bcopy<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on, W.HX + (size_t)k * ntot,
-                                                       W.Sv + (size_t)k * ntot, 0);
+            for (int k = 0; k < kk; ++k) {
+                k_bcopy<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on, W.X + (size_t)k * ntot, W.Bv + (size_t)k * ntot, 0);
+                k_bcopy<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on, W.HX + (size_t)k * ntot, W.Sv + (size_t)k * ntot, 0);
             }
-            m = keep;
-            if (W.mixed && keep > nroots)
-                for (int i = 0; i < ninst; ++i) exact[i] = 0;  // the extra vectors carry FP32 sigma
-            FCI_CUDA(cudaMemsetAsync(W.A, 0, sizeof(double) * ninst * kMaxSub * kMaxSub, s));
-            for (int j = 0; j < m; ++j)
-                bdots(W, W.on, W.Bv, m, W.Sv + (size_t)j * ntot, W.A + j, kMaxSub * kMaxSub, kMaxSub);
+            mi = kk;
+            if (W.mixed && kk > nroots) k_bexact<<<gi, 128, 0, s>>>(ninst, nullptr, nullptr, 1, W.exact);  // FP32 sigma kept
+            cudaMemsetAsync(W.A, 0, sizeof(double) * ninst * kMaxSub * kMaxSub, s);
+            for (int j = 0; j < mi; ++j)
+                bdots(W, W.on, W.Bv, mi, W.Sv + (size_t)j * ntot, W.A + j, kMaxSub * kMaxSub, kMaxSub);
         }
         // expansion: one new vector per root and instance (padding where not expanding)
-        auto ge = W.g_expand.find(m);
-        if (ge == W.g_expand.end()) {
-            cudaGraph_t graph;
-            FCI_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-            for (int k = 0, mm = m; k < nroots; ++k, ++mm) {
-                double *bv = W.Bv + (size_t)mm * ntot, *sv = W.Sv + (size_t)mm * ntot;
-                k_bcopy<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on_exp, W.T + (size_t)k * ntot, bv, 1);
-                for (int pass = 0; pass < 2; ++pass) {
-                    bdots(W, W.on_exp, W.Bv, mm, bv, W.g, kMaxSub, 1);
-                    k_blincomb<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on_exp, W.Bv, ntot, mm, W.g, kMaxSub, 1,
-                                                              -1.0, 1.0, bv);
-                }
-                bdots(W, W.on_exp, bv, 1, bv, W.nrm2, 1, 1);
-                k_bnormalise<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on_exp, W.nrm2, bv);
-                cudaMemsetAsync(sv, 0, sizeof(double) * ntot, s);
-                bsigma(W, W.on_exp, bv, sv, W.ptrBS + (size_t)mm * 2 * ninst, W.mixed);
-                bdots(W, W.on_exp, W.Bv, mm + 1, sv, W.A + mm, kMaxSub * kMaxSub, kMaxSub);
-                bdots(W, W.on_exp, W.Sv, mm + 1, bv, W.A + (size_t)mm * kMaxSub, kMaxSub * kMaxSub, 1);
-                k_bpad<<<(ninst + 127) / 128, 128, 0, s>>>(W.on_exp, W.nrm2, W.A, mm, ninst);
+        for (int k = 0, mm = mi; k < nroots && !rc; ++k, ++mm) {
+            double *bv = W.Bv + (size_t)mm * ntot, *sv = W.Sv + (size_t)mm * ntot;
+            k_bcopy<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on_exp, W.T + (size_t)k * ntot, bv, 1);
+            for (int pass = 0; pass < 2; ++pass) {
+                bdots(W, W.on_exp, W.Bv, mm, bv, W.g, kMaxSub, 1);
+                k_blincomb<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on_exp, W.Bv, ntot, mm, W.g, kMaxSub, 1, -1.0, 1.0,
+                                                          bv);
             }
-            FCI_CUDA(cudaStreamEndCapture(s, &graph));
-            cudaGraphExec_t ex;
-            FCI_CUDA(cudaGraphInstantiate(&ex, graph, 0));
-            cudaGraphDestroy(graph);
-            ge = W.g_expand.emplace(m, ex).first;
+            bdots(W, W.on_exp, bv, 1, bv, W.nrm2, 1, 1);
+            k_bnormalise<<<b->nchunks, kBlock, 0, s>>>(b->d_chunks, W.on_exp, W.nrm2, bv);
+            cudaMemsetAsync(sv, 0, sizeof(double) * ntot, s);
+            rc = bsigma(W, W.on_exp, bv, sv, W.ptrBS + (size_t)mm * 2 * ninst, W.mixed);
+            bdots(W, W.on_exp, W.Bv, mm + 1, sv, W.A + mm, kMaxSub * kMaxSub, kMaxSub);
+            bdots(W, W.on_exp, W.Sv, mm + 1, bv, W.A + (size_t)mm * kMaxSub, kMaxSub * kMaxSub, 1);
+            k_bpad<<<(ninst + 127) / 128, 128, 0, s>>>(W.on_exp, W.nrm2, W.A, mm, ninst);
         }
-        FCI_CUDA(cudaGraphLaunch(ge->second, s));
+        *sig_launches += nroots;
+        if (W.mixed) k_bexact<<<gi, 128, 0, s>>>(ninst, nullptr, W.on_exp, 0, W.exact);
+        return mi + nroots;
+    };
+    // Refinements (mixed precision) are allowed on every kRefinePeriod-th
+    // iteration that is not a thick restart (a restart keeps vectors with FP32
+    // sigma, which would undo the refinement's exactness): `phase` counts the
+    // non-restart iterations modulo the period.  The iterations from subspace
+    // size m0 up to and including the next restart (at most 8, no more than
+    // `left`), with the refinement flag of each: their count, size and phase after.
+    auto chunk = [&](int m0, int ph0, int left, int *m_after, int *ph_after, std::vector<char> &refs) {
+        int mm = m0, ph = ph0, L = 0;
+        refs.clear();
+        while (L < 8 && L < left) {
+            ++L;
+            const bool restart = mm + nroots > maxsub;
+            refs.push_back(W.mixed && !restart && ph == 0 ? 1 : 0);
+            if (!restart) ph = (ph + 1) % kRefinePeriod;
+            mm = (restart ? std::min(keep, mm) : mm) + nroots;
+            if (restart) break;
+        }
+        *m_after = mm;
+        *ph_after = ph;
+        return L;
+    };
+    // Host loop: one graph launch per chunk of iterations, then one 4-byte
+    // read (the number of converged instances); nothing else returns to the host.
+    int it = 0, hdone = 0, phase = 1;  // the first refinement comes after kRefinePeriod - 1 FP32 iterations
+    bool all_done = false;
+    std::map<int, int> chunk_sig;
+    std::vector<char> refs;
+    while (it < b->opt.max_iter && !rc) {
+        int m_after = 0, ph_after = 0;
+        const int L = chunk(m, phase, b->opt.max_iter - it, &m_after, &ph_after, refs);
+        const int key = (m * 64 + L) * kRefinePeriod + phase;
+        auto g = W.g_chunk.find(key);
+        if (g == W.g_chunk.end()) {
+            cudaGraph_t graph;
+            int sl = 0;
+            FCI_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            int mm = m;
+            for (int j = 0; j < L && !rc; ++j) mm = iteration(mm, refs[j] != 0, &sl);
+            const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+            if (rc) {
+                if (ce == cudaSuccess) cudaGraphDestroy(graph);
+                break;
+            }
+            FCI_CUDA(ce);
+            cudaGraphExec_t ex;
+            const cudaError_t ie = cudaGraphInstantiate(&ex, graph, 0);
+            cudaGraphDestroy(graph);
+            FCI_CUDA(ie);
+            g = W.g_chunk.emplace(key, ex).first;
+            chunk_sig[key] = sl;
+        }
+        FCI_CUDA(cudaGraphLaunch(g->second, s));
+        b->stats[1] += chunk_sig[key];
         b->stats[2]++;
-        b->stats[1] += nroots;
-        m += nroots;
-        if (W.mixed)
-            for (int i = 0; i < ninst; ++i)
-                if (expand[i]) exact[i] = 0;
+        it += L;
+        m = m_after;
+        phase = ph_after;
+        FCI_CUDA(cudaMemcpyAsync(&hdone, W.ndone, sizeof(int), cudaMemcpyDeviceToHost, s));
+        FCI_CUDA(cudaStreamSynchronize(s));
+        b->stats[3]++;
+        if (hdone >= ninst) {
+            all_done = true;
+            break;
+        }
     }
-    b->stats[0] = it > b->opt.max_iter ? b->opt.max_iter : it;
-    cudaError_t e = cudaStreamSynchronize(s);
     if (rc) return rc;
+    {
+        std::vector<int> its(ninst);
+        std::vector<double> en((size_t)ninst * kMaxRoots);
+        FCI_CUDA(cudaMemcpy(its.data(), W.its, sizeof(int) * ninst, cudaMemcpyDeviceToHost));
+        FCI_CUDA(cudaMemcpy(en.data(), W.energy, sizeof(double) * en.size(), cudaMemcpyDeviceToHost));
+        b->stats[0] = *std::max_element(its.begin(), its.end());
+        for (int i = 0; i < ninst; ++i)
+            for (int k = 0; k < nroots; ++k) energies[(size_t)i * nroots + k] = en[(size_t)i * kMaxRoots + k];
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "batched Davidson");
     for (int i : b->hyb) {  // bounded waits of the tensor-core sigma_3
         int derr = 0;
@@ -1357,8 +1446,7 @@ extern "C" int fci_batch_davidson(fci_batch *b, int nroots, double tol, double *
         if (g) cudaGraphDestroy(g);
     }
     cudaStreamSynchronize(b->stream);
-    for (auto &kv : W.g_ritz) cudaGraphExecDestroy(kv.second);
-    for (auto &kv : W.g_expand) cudaGraphExecDestroy(kv.second);
+    for (auto &kv : W.g_chunk) cudaGraphExecDestroy(kv.second);
     for (auto &a : mine)
         if (a.first) cudaFree(a.first);
     return rc;

@@ -231,10 +231,11 @@ static unsigned grid_stride_blocks(int64_t n) {
 //     transpose back into the accumulator buffer;
 //  3. slice C; sigma_3 and sigma_2 add to the accumulator;
 //  4. convert the accumulator to FP64 into sig.
-// Profiling slots: slice, sigma1, sigma3, sigma2, convert.
+// Profiling slots: transpose and slice, sigma1, sigma3 (with the slicing of C),
+// sigma2, convert.
 int launch_sigma_f64_wide(fci_ctx *ctx, const double *C, double *sig, cudaStream_t s) {
     if (!sigma_wide_ok(ctx)) return fail(FCI_ERR_STATE, "wide FP64 sigma tables were not built for this context");
-    static const char *const names[5] = {"slice_c", "sigma1_wide", "sigma3_wide", "sigma2_wide", "convert"};
+    static const char *const names[5] = {"transpose_slice", "sigma1_wide", "sigma3_wide", "sigma2_wide", "convert"};
     const int rec = prof_begin(ctx, s, 5, names);
     const SpinTables &A = ctx->A, &B = ctx->B;
     const int64_t nsa = A.ns, nsb = B.ns, n = ctx->ndet;

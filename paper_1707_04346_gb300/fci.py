@@ -395,7 +395,8 @@ def fci_batch_stats(batch: FciBatch) -> dict:
     lib = load()
     return {"iterations": int(lib.fci_batch_stats(batch.handle, 0)),
             "sigma_launches": int(lib.fci_batch_stats(batch.handle, 1)),
-            "graph_launches": int(lib.fci_batch_stats(batch.handle, 2))}
+            "graph_launches": int(lib.fci_batch_stats(batch.handle, 2)),
+            "host_syncs": int(lib.fci_batch_stats(batch.handle, 3))}
 
 
 def fci_batch_free(batch: FciBatch):

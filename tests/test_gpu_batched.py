@@ -69,6 +69,8 @@ def test_batch_davidson_fp64_matches_lapack(pkg, oracle_mod):
         assert np.abs(e[i] - ref).max() < 1e-9, (i, e[i], ref)
     st = pkg.fci_batch_stats(batch)
     assert st["iterations"] > 0 and st["graph_launches"] > 0 and st["sigma_launches"] > 0
+    # device-driven iterations: one graph and one host synchronisation per chunk of up to 8
+    assert st["graph_launches"] == st["host_syncs"] and st["graph_launches"] <= st["iterations"] / 2 + 1
 
 
 def test_batch_davidson_mixed_matches_single_fp64(pkg):
