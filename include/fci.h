@@ -101,6 +101,13 @@ typedef struct fci_options {
                             0 = only when the FP64 basis does not fit in free device memory
                             (default; then at most 8 vectors, fewer if memory asks), 1 =
                             always (max_subspace vectors), 2 = never */
+    int spin_parity;     /* Davidson on the Ms = 0 combinations of one spin parity
+                            (n_alpha = n_beta): +1 = C^T = C (S even: singlets,
+                            quintets, ...), -1 = C^T = -C (S odd: triplets, ...), 0 = all
+                            states (default).  The guess and every correction are
+                            projected onto the parity, and sigma_1 = parity sigma_2^T is
+                            formed from sigma_2 by a transpose-add (Section 3.1's Ms = 0
+                            combinations); fci_sigma itself is unaffected */
 } fci_options;
 
 /* fci_options.f64_kernels: how the FCI_F64 sigma is computed.  All modes meet

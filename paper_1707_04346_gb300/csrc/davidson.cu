@@ -386,13 +386,21 @@ __device__ void block_min_vi(double &best, int64_t &bi, double *sb, int64_t *si)
     bi = si[0];
 }
 
+// par != 0 (spin parity, a square [ncols][ncols] vector) restricts the
+// candidates to one determinant per pair (I_a, I_b), (I_b, I_a): I_a >= I_b, and
+// I_a > I_b for par < 0 (the diagonal ones have no antisymmetric combination).
 __global__ void __launch_bounds__(256) k_argmin_excl_part(const double *__restrict__ d, int64_t n,
                                                           const int64_t *__restrict__ chosen, int nchosen,
-                                                          double *__restrict__ pv, int64_t *__restrict__ pi) {
+                                                          double *__restrict__ pv, int64_t *__restrict__ pi,
+                                                          int64_t ncols, int par) {
     double best = INFINITY;
     int64_t bi = INT64_MAX;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        if (par != 0) {
+            const int64_t r = i / ncols, c = i % ncols;
+            if (r < c || (par < 0 && r == c)) continue;
+        }
         bool skip = false;
         for (int c = 0; c < nchosen; ++c) skip |= (chosen[c] == i);
         if (skip) continue;
@@ -692,6 +700,7 @@ struct Work {
     int *keep = nullptr;
     int64_t *idx = nullptr;                 // [nroots]
     int64_t *pidx = nullptr;                // [kDotBlocks + 1] reduction scratch (indices)
+    int parity = 0;                         // fci_options.spin_parity (C^T = parity C), 0 = none
     int rc = FCI_OK;
     std::vector<void *> allocs;
     std::vector<size_t> sizes;
@@ -719,7 +728,7 @@ unsigned grid_for(int64_t n) {
 
 // W.idx[k] = index of the smallest diagonal entry not among W.idx[0..k)
 void argmin_excl(Work &W, const double *d, int k) {
-    k_argmin_excl_part<<<kDotBlocks, 256, 0, W.s>>>(d, W.n, W.idx, k, W.partial, W.pidx);
+    k_argmin_excl_part<<<kDotBlocks, 256, 0, W.s>>>(d, W.n, W.idx, k, W.partial, W.pidx, W.ctx->B.ns, W.parity);
     k_argmin_final<<<1, 256, 0, W.s>>>(W.partial, W.pidx, kDotBlocks, W.idx + k);
 }
 
@@ -758,12 +767,18 @@ int dots(Work &W, const double *X, int m, const double *y, double *out, int stri
     return FCI_OK;
 }
 
+// project y onto the spin parity (y <- (y + p y^T) / 2), if one is set
+int project_parity(Work &W, void *y, int elem) {
+    if (W.parity == 0) return FCI_OK;
+    return sym_pairs(y, W.ctx->A.ns, elem, W.parity, 1, W.s);
+}
+
 int sigma_of(Work &W, bool fp32, const double *x, double *hx) {
     fci_ctx *ctx = W.ctx;
     ctx->sigma_calls++;
-    if (!fp32) return launch_sigma(ctx, x, hx, FCI_F64, W.s);
+    if (!fp32) return launch_sigma(ctx, x, hx, FCI_F64, W.s, W.parity);
     k_cvt_d2f<<<grid_for(W.n), 256, 0, W.s>>>(x, W.c32, W.n);
-    int rc = launch_sigma(ctx, W.c32, W.s32, FCI_F32, W.s);
+    int rc = launch_sigma(ctx, W.c32, W.s32, FCI_F32, W.s, W.parity);
     if (rc) return rc;
     k_cvt_f2d<<<grid_for(W.n), 256, 0, W.s>>>(W.s32, hx, W.n);
     FCI_CUDA(cudaGetLastError());
@@ -874,6 +889,7 @@ static int run_davidson_f32basis(fci_ctx *ctx, int nroots, double tol, double *e
     W.n = ctx->ndet;
     W.nroots = nroots;
     W.maxsub = maxsub;
+    W.parity = ctx->opt.spin_parity;
     const int64_t n = W.n;
     cudaStream_t s = W.s;
     W.Bf = W.get<float>((size_t)maxsub * n);
@@ -897,11 +913,11 @@ static int run_davidson_f32basis(fci_ctx *ctx, int nroots, double tol, double *e
     ctx->sigma_calls = 0;
     auto sigma32 = [&](int i) {
         ctx->sigma_calls++;
-        return launch_sigma(ctx, W.Bf + (size_t)i * n, W.Sf + (size_t)i * n, FCI_F32, s);
+        return launch_sigma(ctx, W.Bf + (size_t)i * n, W.Sf + (size_t)i * n, FCI_F32, s, W.parity);
     };
     auto sigma64 = [&](int k) {
         ctx->sigma_calls++;
-        return launch_sigma(ctx, W.X + (size_t)k * n, W.HX + (size_t)k * n, FCI_F64, s);
+        return launch_sigma(ctx, W.X + (size_t)k * n, W.HX + (size_t)k * n, FCI_F64, s, W.parity);
     };
     auto project = [&](int m) -> int {  // A = B^T S (columns j < m)
         FCI_CUDA(cudaMemsetAsync(W.A, 0, sizeof(double) * kMaxSub * kMaxSub, s));
@@ -921,6 +937,7 @@ static int run_davidson_f32basis(fci_ctx *ctx, int nroots, double tol, double *e
             k_set_unit_f32<<<grid_for(n), 256, 0, s>>>(b, n, W.idx + k);
         }
         FCI_CUDA(cudaGetLastError());
+        if (int rc = project_parity(W, b, 4)) return rc;
         int kept = 0;
         if (int rc = orthonormalise_f32(W, W.Bf, m, b, &kept)) return rc;
         if (kept) ++m;
@@ -1026,6 +1043,7 @@ static int run_davidson_f32basis(fci_ctx *ctx, int nroots, double tol, double *e
             float *b = W.Bf + (size_t)m * n;
             k_precond_f32<<<grid_for(n), 256, 0, s>>>(W.X + (size_t)k * n, W.HX + (size_t)k * n, ctx->hdiag, W.w, k, b, n);
             FCI_CUDA(cudaGetLastError());
+            if (int rc = project_parity(W, b, 4)) return rc;
             int kept = 0;
             if (int rc = orthonormalise_f32(W, W.Bf, m, b, &kept)) return rc;
             if (!kept) continue;
@@ -1107,6 +1125,7 @@ int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *v
     if (maxsub < 2 * nroots) maxsub = 2 * nroots;
     if (maxsub > W.n) maxsub = (int)W.n;
     W.maxsub = maxsub;
+    W.parity = ctx->opt.spin_parity;
     const bool mixed = ctx->opt.precision == FCI_PREC_MIXED;
     W.Bv = W.get<double>((size_t)maxsub * W.n);
     W.Sv = W.get<double>((size_t)maxsub * W.n);
@@ -1149,6 +1168,7 @@ int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *v
             k_set_unit<<<grid_for(n), 256, 0, s>>>(b, n, W.idx + k);
             FCI_CUDA(cudaGetLastError());
         }
+        if (int rc = project_parity(W, b, 8)) return rc;
         int kept = 0;
         if (int rc = orthonormalise(W, W.Bv, m, b, &kept)) return rc;
         if (kept) ++m;
@@ -1283,6 +1303,7 @@ int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *v
         for (int k = 0; k < nr && m < maxsub; ++k) {
             double *b = W.Bv + (size_t)m * n;
             FCI_CUDA(cudaMemcpyAsync(b, W.T + (size_t)k * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+            if (int rc = project_parity(W, b, 8)) return rc;
             int kept = 0;
             if (int rc = orthonormalise(W, W.Bv, m, b, &kept)) return rc;
             if (!kept) continue;

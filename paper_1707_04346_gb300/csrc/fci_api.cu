@@ -154,6 +154,9 @@ int fci_init(fci_ctx **out, int norb, int nalpha, int nbeta, const double *h1, c
     if (!(o.max_device_bytes >= 0)) return fail(FCI_ERR_ARG, "max_device_bytes must be >= 0");
     if (o.f32_row_global != 0 && o.f32_row_global != 1) return fail(FCI_ERR_ARG, "f32_row_global must be 0 or 1");
     if (o.basis_f32 < 0 || o.basis_f32 > 2) return fail(FCI_ERR_ARG, "basis_f32 must be 0, 1 or 2");
+    if (o.spin_parity < -1 || o.spin_parity > 1) return fail(FCI_ERR_ARG, "spin_parity must be -1, 0 or 1");
+    if (o.spin_parity != 0 && nalpha != nbeta)
+        return fail(FCI_ERR_ARG, "spin_parity needs n_alpha = n_beta (Ms = 0)");
     if (o.f64_kernels < FCI_F64_AUTO || o.f64_kernels > FCI_F64_WIDE)
         return fail(FCI_ERR_ARG, "f64_kernels must be FCI_F64_AUTO, FCI_F64_FMA, FCI_F64_SLICED or FCI_F64_WIDE");
     if (int rc = check_integrals(norb, h1, eri, o.symmetry_tol)) return rc;

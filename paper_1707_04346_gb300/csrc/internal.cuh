@@ -152,7 +152,14 @@ bool tile_schedule_host(const uint32_t *tab, int64_t ns, int K, std::vector<uint
                         std::vector<int32_t> &off);
 
 // sigma.cu
-int launch_sigma(fci_ctx *ctx, const void *c, void *sigma, int dtype, cudaStream_t s);
+// parity != 0 (Davidson with fci_options.spin_parity, n_alpha = n_beta): c is
+// known to satisfy C^T = parity * C, so sigma_1 = parity * sigma_2^T is formed
+// from sigma_2 by one transpose-add instead of its own kernel
+int launch_sigma(fci_ctx *ctx, const void *c, void *sigma, int dtype, cudaStream_t s, int parity = 0);
+// y <- y + sgn * y^T (half = 0) or (y + sgn * y^T) / 2 (half = 1) in place for a
+// square n x n matrix of floats (elem 4), doubles (elem 8) or 64-bit integers
+// (elem -8; half must be 0)
+int sym_pairs(void *y, int64_t n, int elem, int sgn, int half, cudaStream_t s);
 bool f32_same_spin_tc(const fci_ctx *ctx);
 int alloc_sigma_workspace(fci_ctx *ctx);  // at fci_init: ws32 when the FP32 same-spin tensor-core path is used
 
@@ -182,7 +189,7 @@ int build_sliced_tables(fci_ctx *ctx, const double *h1_host, const double *eri_h
 void free_sliced_tables(fci_ctx *ctx);
 bool sigma3_sliced_ok(const fci_ctx *ctx);
 int launch_sigma3_sliced(fci_ctx *ctx, const double *C, double *sig, cudaStream_t s, int rec, int prof_slot,
-                         const int *active = nullptr);
+                         const int *active = nullptr, int add = 0);
 int prepare_sigma3_sliced(const fci_ctx *ctx);
 
 // sigma_wide.cu (FP64-accurate sigma for large spaces: all three terms on the
@@ -191,7 +198,7 @@ bool sigma_wide_fits(const fci_ctx *ctx);
 bool sigma_wide_ok(const fci_ctx *ctx);
 int build_wide_tables(fci_ctx *ctx, const double *h1_host, const double *eri_host);
 void free_wide_tables(fci_ctx *ctx);
-int launch_sigma_f64_wide(fci_ctx *ctx, const double *C, double *sig, cudaStream_t s);
+int launch_sigma_f64_wide(fci_ctx *ctx, const double *C, double *sig, cudaStream_t s, int parity = 0);
 
 // davidson.cu
 int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *vecs, const void *guess);

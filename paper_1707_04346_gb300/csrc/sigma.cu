@@ -371,6 +371,53 @@ __global__ void __launch_bounds__(512) k_sigma3_exact(const double *__restrict__
     for (int64_t j = threadIdx.x; j < nsb; j += blockDim.x) sig[ia * nsb + j] += acc[j];
 }
 
+// y <- y + sgn y^T (half = 0) or (y + sgn y^T) / 2 (half = 1), in place, for a
+// square n x n matrix: a block takes the 32 x 32 tile (bi, bj), bi <= bj, and
+// its mirror (bj, bi), reads both into shared memory and writes both (a
+// diagonal tile once).  With c^T = sgn c this forms sigma_1 = sgn sigma_2^T
+// from sigma_2 (Eq. 8 with the alpha and beta strings of one space), and it
+// projects a vector onto the Ms = 0 combinations of one spin parity.
+template <typename T>
+__global__ void k_sym_pairs(T *__restrict__ y, int64_t n, int sgn, int half) {
+    const int64_t bi = blockIdx.y, bj = blockIdx.x;
+    if (bi > bj) return;
+    __shared__ T a[32][33], b[32][33];
+    const int tx = threadIdx.x;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t i = bi * 32 + r, j = bj * 32 + tx, i2 = bj * 32 + r, j2 = bi * 32 + tx;
+        a[r][tx] = (i < n && j < n) ? y[i * n + j] : T(0);    // tile (bi, bj)
+        b[r][tx] = (i2 < n && j2 < n) ? y[i2 * n + j2] : T(0);  // tile (bj, bi)
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t i = bi * 32 + r, j = bj * 32 + tx;
+        T v = sgn > 0 ? T(a[r][tx] + b[tx][r]) : T(a[r][tx] - b[tx][r]);
+        if (half) v = v / T(2);
+        if (i < n && j < n) y[i * n + j] = v;
+        if (bi != bj) {
+            const int64_t i2 = bj * 32 + r, j2 = bi * 32 + tx;
+            T w = sgn > 0 ? T(b[r][tx] + a[tx][r]) : T(b[r][tx] - a[tx][r]);
+            if (half) w = w / T(2);
+            if (i2 < n && j2 < n) y[i2 * n + j2] = w;
+        }
+    }
+}
+
+int sym_pairs(void *y, int64_t n, int elem, int sgn, int half, cudaStream_t s) {
+    const dim3 grid(ceil_div(n, 32), ceil_div(n, 32)), block(32, 8);
+    if (grid.y > 65535) return fail(FCI_ERR_ARG, "spin parity: more than 2097120 strings");
+    if (elem == 8)
+        k_sym_pairs<double><<<grid, block, 0, s>>>((double *)y, n, sgn, half);
+    else if (elem == 4)
+        k_sym_pairs<float><<<grid, block, 0, s>>>((float *)y, n, sgn, half);
+    else if (elem == -8 && !half)
+        k_sym_pairs<long long><<<grid, block, 0, s>>>((long long *)y, n, sgn, 0);
+    else
+        return fail(FCI_ERR_ARG, "sym_pairs: bad element kind");
+    FCI_CUDA(cudaGetLastError());
+    return FCI_OK;
+}
+
 static size_t smem_limit() {
     static int lim = -1;
     if (lim < 0) {
@@ -402,10 +449,12 @@ int alloc_sigma_workspace(fci_ctx *ctx) {
 }
 
 template <typename T>
-static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s) {
-    if constexpr (sizeof(T) == 8)
-        if (sigma_wide_ok(ctx)) return launch_sigma_f64_wide(ctx, C, sig, s);
+static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s, int parity) {
     const SpinTables &A = ctx->A, &B = ctx->B;
+    // a vector of known spin parity (C^T = parity C, one string space): sigma_1 from sigma_2
+    if (A.ne != B.ne || A.ns != B.ns) parity = 0;
+    if constexpr (sizeof(T) == 8)
+        if (sigma_wide_ok(ctx)) return launch_sigma_f64_wide(ctx, C, sig, s, parity);
     const int64_t nsa = A.ns, nsb = B.ns;
     const size_t lim = smem_limit();
     // sigma_1 then sigma_2: R rows / columns per block, the largest R whose block fits
@@ -430,6 +479,42 @@ static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s) {
     // FP64 with the sliced tensor-core sigma_3: it runs first and overwrites sigma
     const bool sliced = sizeof(T) == 8 && A.nsingle > 0 && B.nsingle > 0 && ctx->opt.f64_kernels != FCI_F64_FMA &&
                         sigma3_sliced_ok(ctx);
+    if (parity != 0 && A.nsingle > 0) {
+        // sigma = sigma_2 + parity sigma_2^T + sigma_3: FP64 with the sliced sigma_3 and the
+        // double-float sigma_2, FP32 with the tensor-core kernels of large spaces
+        if constexpr (sizeof(T) == 8) {
+            if (sliced) {
+                static const char *const namesp[4] = {"sigma2_cols", "sigma1_sym", "slice_c", "sigma3_sliced"};
+                const int rec = prof_begin(ctx, s, 4, namesp);
+                FCI_CUDA(cudaMemsetAsync(sig, 0, sizeof(T) * (size_t)ctx->ndet, s));
+                const int R = pick_r(nsa);
+                if (!R) return fail(FCI_ERR_ARG, "alpha string count too large for the sigma_2 kernel");
+                void *k = R == 8 ? (void *)k_sigma2_cols_df<8> : R == 4 ? (void *)k_sigma2_cols_df<4>
+                          : R == 2 ? (void *)k_sigma2_cols_df<2> : (void *)k_sigma2_cols_df<1>;
+                FCI_CUDA(opt_in_max_smem(k, ctx->device));
+                int64_t nsb_ = nsb;
+                SpinTables At = A;
+                const int *no_gate = nullptr;
+                void *args[] = {(void *)&C, (void *)&sig, (void *)&At, (void *)&nsb_, (void *)&no_gate};
+                FCI_CUDA(cudaLaunchKernel(k, dim3(ceil_div(nsb, R)), dim3(512), args, (size_t)R * nsa * sizeof(T), s));
+                prof_mark(ctx, rec, 0, s);
+                if (int rc = sym_pairs(sig, nsa, 8, parity, 0, s)) return rc;
+                prof_mark(ctx, rec, 1, s);
+                return launch_sigma3_sliced(ctx, C, sig, s, rec, 2, nullptr, 1);
+            }
+        } else if (same_tc) {
+            static const char *const namesp[3] = {"sigma2_tc", "sigma1_sym", "sigma3_tc"};
+            const int rec = prof_begin(ctx, s, 3, namesp);
+            FCI_CUDA(cudaMemsetAsync(sig, 0, sizeof(float) * (size_t)ctx->ndet, s));
+            if (int rc = launch_same_spin_tc(ctx, (const float *)C, (float *)sig, A, B, s)) return rc;
+            prof_mark(ctx, rec, 0, s);
+            if (int rc = sym_pairs(sig, nsa, 4, parity, 0, s)) return rc;
+            prof_mark(ctx, rec, 1, s);
+            if (int rc = launch_sigma3_tc(ctx, (const float *)C, (float *)sig, ctx->opt.f32_splits, s)) return rc;
+            prof_mark(ctx, rec, 2, s);
+            return FCI_OK;
+        }
+    }
     const int rec = sliced ? prof_begin(ctx, s, 4, names4)
                     : same_tc ? prof_begin(ctx, s, 3, names3tc)
                     : fusedR ? prof_begin(ctx, s, 2, names2) : prof_begin(ctx, s, 3, names3);
@@ -604,9 +689,9 @@ int launch_sigma_f64_gated(fci_ctx *ctx, const double *C, double *sig, const int
     return FCI_OK;
 }
 
-int launch_sigma(fci_ctx *ctx, const void *c, void *sigma, int dtype, cudaStream_t s) {
-    if (dtype == FCI_F64) return sigma_impl<double>(ctx, (const double *)c, (double *)sigma, s);
-    if (dtype == FCI_F32) return sigma_impl<float>(ctx, (const float *)c, (float *)sigma, s);
+int launch_sigma(fci_ctx *ctx, const void *c, void *sigma, int dtype, cudaStream_t s, int parity) {
+    if (dtype == FCI_F64) return sigma_impl<double>(ctx, (const double *)c, (double *)sigma, s, parity);
+    if (dtype == FCI_F32) return sigma_impl<float>(ctx, (const float *)c, (float *)sigma, s, parity);
     return fail(FCI_ERR_ARG, "dtype must be FCI_F64 or FCI_F32");
 }
 

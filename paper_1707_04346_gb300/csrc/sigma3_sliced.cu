@@ -167,11 +167,11 @@ static void *sliced_kernel(int kpad) {
 }
 
 // Row exponents and digit slices of C (stream-ordered), then sigma_3 into sig,
-// which is overwritten.  prof_slot: profiling slot of the pre-pass (the kernel
+// which is overwritten (add = 0) or added to.  prof_slot: profiling slot of the pre-pass (the kernel
 // takes the next one).  active: null, or a device flag; the kernels return at
 // once when it is 0 (batched engine: one captured graph for any active set).
 int launch_sigma3_sliced(fci_ctx *ctx, const double *C, double *sig, cudaStream_t s, int rec, int prof_slot,
-                         const int *active) {
+                         const int *active, int add) {
     int kpad = 0, npad = 0, n0 = 0;
     uint32_t smem = 0;
     if (!sigma3_sliced_ok(ctx) || !sliced_shape(ctx, &kpad, &npad, &n0, &smem))
@@ -198,7 +198,7 @@ int launch_sigma3_sliced(fci_ctx *ctx, const double *C, double *sig, cudaStream_
     int npair = ctx->npair, eW = ctx->eW;
     void *args[] = {(void *)&c0,   (void *)&c4,    (void *)&sig,  (void *)&At, (void *)&Bt,         (void *)&xw,
                     (void *)&rexp, (void *)&npair, (void *)&npad, (void *)&n0, (void *)&eW, (void *)&ctx->d_err,
-                    (void *)&active};
+                    (void *)&active, (void *)&add};
     FCI_CUDA(cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(sl::kThreads), args, smem, s));
     prof_mark(ctx, rec, prof_slot + 1, s);
     return FCI_OK;

@@ -35,7 +35,7 @@
 //    not matter, so the result is bit-reproducible;
 //  * at the end of the row the integers are converted to FP64 (integer
 //    arithmetic only, round to nearest even) and written to sigma, which this
-//    kernel overwrites.
+//    kernel overwrites (or adds to, when add != 0).
 // Per product the representation and the products left out (s + t >= 6) are
 // below about 2^-46 of (largest gathered |C|) x (largest |(pq|rs)|).
 //
@@ -214,7 +214,7 @@ template <int KPAD>
 __global__ void __launch_bounds__(kThreads, 1)
     k_sigma3_sliced(const uint2 *__restrict__ cs0123, const uint32_t *__restrict__ cs45, double *__restrict__ sig,
                     SpinTables A, SpinTables B, const long long *__restrict__ XW, const int *__restrict__ rowexp,
-                    int npair, int npad, int n0, int eW, int *err, const int *__restrict__ active) {
+                    int npair, int npad, int n0, int eW, int *err, const int *__restrict__ active, int add) {
     if (active != nullptr && *active == 0) return;  // gated launch (batched engine): instance not active
     constexpr int NKS = KPAD / 16;
     constexpr int kgroups = KPAD / 8;
@@ -508,7 +508,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int e2 = emax - 1022 + eW - 48;
         double *out = sig + row * nsb;
         for (int64_t j = tid; j < nsb; j += kThreads) {
-            out[j] = emax == 0x7FF ? __longlong_as_double(0x7FF8000000000000ll) : scaled_i64((long long)sAcc[j], e2);
+            const double v = emax == 0x7FF ? __longlong_as_double(0x7FF8000000000000ll) : scaled_i64((long long)sAcc[j], e2);
+            out[j] = add ? out[j] + v : v;
             sAcc[j] = 0ull;
         }
         __syncthreads();

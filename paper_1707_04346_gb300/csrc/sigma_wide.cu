@@ -233,8 +233,34 @@ static unsigned grid_stride_blocks(int64_t n) {
 //  4. convert the accumulator to FP64 into sig.
 // Profiling slots: transpose and slice, sigma1, sigma3 (with the slicing of C),
 // sigma2, convert.
-int launch_sigma_f64_wide(fci_ctx *ctx, const double *C, double *sig, cudaStream_t s) {
+int launch_sigma_f64_wide(fci_ctx *ctx, const double *C, double *sig, cudaStream_t s, int parity) {
     if (!sigma_wide_ok(ctx)) return fail(FCI_ERR_STATE, "wide FP64 sigma tables were not built for this context");
+    if (parity != 0 && ctx->A.nsingle > 0) {
+        // C^T = parity C (one string space): sigma_2 into the accumulator, sigma_1 =
+        // parity sigma_2^T by one integer transpose-add, then sigma_3 adds
+        static const char *const namesp[5] = {"slice_c", "sigma2_wide", "sigma1_sym", "sigma3_wide", "convert"};
+        const int rec = prof_begin(ctx, s, 5, namesp);
+        const int64_t ns = ctx->A.ns, n = ctx->ndet;
+        unsigned long long *acc = ctx->ws32 ? reinterpret_cast<unsigned long long *>(ctx->ws32)
+                                            : reinterpret_cast<unsigned long long *>(ctx->wsacc);
+        FCI_CUDA(cudaMemsetAsync(ctx->d_eG, 0, sizeof(int), s));
+        k_global_exponent<<<grid_stride_blocks(n), 256, 0, s>>>(C, n, ctx->d_eG);
+        k_slice_global<<<ceil_div(n, 256), 256, 0, s>>>(C, n, ctx->d_eG, ctx->cs0123, ctx->cs45);
+        FCI_CUDA(cudaGetLastError());
+        FCI_CUDA(cudaMemsetAsync(acc, 0, sizeof(long long) * (size_t)n, s));
+        prof_mark(ctx, rec, 0, s);
+        if (int rc = launch_wide<1>(ctx, ctx->A, ns, acc, s)) return rc;
+        prof_mark(ctx, rec, 1, s);
+        if (int rc = sym_pairs(acc, ns, -8, parity, 0, s)) return rc;
+        prof_mark(ctx, rec, 2, s);
+        if (int rc = launch_wide<0>(ctx, ctx->A, ns, acc, s)) return rc;
+        prof_mark(ctx, rec, 3, s);
+        k_convert_acc<<<grid_stride_blocks(n), 256, 0, s>>>(reinterpret_cast<const long long *>(acc), sig, n,
+                                                             ctx->d_eG, ctx->eC);
+        FCI_CUDA(cudaGetLastError());
+        prof_mark(ctx, rec, 4, s);
+        return FCI_OK;
+    }
     static const char *const names[5] = {"transpose_slice", "sigma1_wide", "sigma3_wide", "sigma2_wide", "convert"};
     const int rec = prof_begin(ctx, s, 5, names);
     const SpinTables &A = ctx->A, &B = ctx->B;

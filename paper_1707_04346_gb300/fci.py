@@ -65,6 +65,7 @@ class fci_options(ctypes.Structure):
         ("max_device_bytes", ctypes.c_double),
         ("f32_row_global", ctypes.c_int),
         ("basis_f32", ctypes.c_int),
+        ("spin_parity", ctypes.c_int),
     ]
 
 
