@@ -39,6 +39,7 @@ import fci_inputs as fi  # noqa: E402
 WORKLOADS = {"cas14": (14, 7, 7, 100), "cas16": (16, 8, 8, 100), "cas12": (12, 6, 6, 100), "cas8": (8, 4, 4, 40),
              "cas18": (18, 9, 9, 100)}
 LARGE = {"cas18"}  # vectors too large for the host: trial vector regenerated on the device
+F64_KERNELS = {"auto": 0, "fma": 1, "sliced": 2, "wide": 3}  # fci_options.f64_kernels of the main context
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), nominal
 GB300_SMS = 152
 FP32_LANES_PER_SM = 128  # FP32 operations issued per SM per clock
@@ -50,6 +51,12 @@ FP32_LANES_PER_SM = 128  # FP32 operations issued per SM per clock
 NCU_TRAFFIC = {
     "sigma3_exact": ("paper_1707_04346_gb300/csrc/sigma.cu", "k_sigma3_exact(", "d3fba1cadf6cd31c", 610262016.0),
     "sigma3_tc": ("paper_1707_04346_gb300/csrc/sigma_tc_kernel.cuh", "k_sigma3_tc(", "878aabf229629b81", 124323328.0),
+    "sigma3_sliced": ("paper_1707_04346_gb300/csrc/sigma3_sliced_kernel.cuh", "k_sigma3_sliced(", "032cc9d38aaa6af8",
+                      975301888.0),
+    # the wide kernels at CAS(14,14) (bench.py --f64-kernels wide)
+    "sigma3_wide": ("paper_1707_04346_gb300/csrc/sigma_wide_kernel.cuh", "k_sigma_wide(", "3b63c3cbe309e741", 1016815808.0),
+    "sigma1_wide": ("paper_1707_04346_gb300/csrc/sigma_wide_kernel.cuh", "k_sigma_wide(", "3b63c3cbe309e741", 2433141328.0),
+    "sigma2_wide": ("paper_1707_04346_gb300/csrc/sigma_wide_kernel.cuh", "k_sigma_wide(", "3b63c3cbe309e741", 2452579616.0),
 }
 
 
@@ -570,7 +577,8 @@ def run_ours(args):
 
     norb, na, nb, rank_eri = WORKLOADS[args.workload]
     h1, eri = fi.make_integrals(norb, rank_eri)
-    ctx = pkg.fci_init(norb, na, nb, h1, eri)
+    ctx = pkg.fci_init(norb, na, nb, h1, eri, pkg.default_options(f64_kernels=F64_KERNELS[args.f64_kernels],
+                                                                  same_spin_tc=args.same_spin_tc))
     N = ctx.ndet
     nsa, nsb = ctx.nstr
     c_host = fi.make_vector(N)
@@ -719,6 +727,26 @@ def run_ours(args):
         }
         if ctxm is not None:
             pkg.fci_free(ctxm)
+        if na == nb and nr == 1 and not args.ref_from_mixed:
+            # the same solves on the singlet combinations (spin_parity = +1: the
+            # ground state here is a singlet), with sigma_1 formed from sigma_2
+            sp = {}
+            for label, prec in (("fp64", pkg.FCI_PREC_FP64), ("mixed", pkg.FCI_PREC_MIXED)):
+                cs = pkg.fci_init(norb, na, nb, h1, eri, pkg.default_options(precision=prec, spin_parity=1))
+                if label == "fp64":
+                    pkg.fci_profile_enable(cs, True)  # the solver's sigma calls (sigma_1 from sigma_2)
+                es = pkg.fci_davidson(cs, 1, 1e-10)
+                ls = pkg.fci_davidson_log(cs, 1)
+                sp[label] = {"E": float(es[0]), "abs_diff_vs_full_space_fp64": float(abs(es[0] - e_ref[0])),
+                             "time_to_1e-8_s": time_to_tol(ls, e_ref), "iterations": int(len(ls))}
+                if label == "fp64":
+                    names_s, prof_s = pkg.fci_profile_read(cs)
+                    km = prof_s[2:].mean(axis=0)
+                    sp[label]["sigma_ms"] = float(km.sum())
+                    sp[label]["sigma_kernels_ms"] = {n: float(km[i]) for i, n in enumerate(names_s)}
+                    pkg.fci_profile_enable(cs, False)
+                pkg.fci_free(cs)
+            result["davidson"]["singlet"] = sp
     if args.batched and rank == 0:
         result["batched"] = run_batched(pkg, args.batch_instances)
     if args.extra and args.workload == "cas14":
@@ -755,6 +783,10 @@ def main():
                     help="skip the CAS(16,16) and CAS(18,18) sigma legs")
     ap.add_argument("--roots", type=int, default=1, help="Davidson roots (CAS(16,16) configuration: 3)")
     ap.add_argument("--max-iter", type=int, default=600, help="Davidson iteration limit of the CAS(18,18) solve")
+    ap.add_argument("--f64-kernels", default="auto", choices=sorted(F64_KERNELS),
+                    help="FP64 sigma kernels of the timed context (profiling a kernel family on a small space)")
+    ap.add_argument("--same-spin-tc", type=int, default=0, choices=(0, 1),
+                    help="FP32 same-spin terms through intermediate strings on the tensor cores in the timed context")
     ap.add_argument("--ref-from-mixed", action="store_true",
                     help="FP64 reference energies from an FP64 solve started at the mixed solution")
     args = ap.parse_args()
