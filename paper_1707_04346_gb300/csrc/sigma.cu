@@ -156,6 +156,18 @@ __device__ __forceinline__ void df_mac(float vh, float vl, float2 c, float &sh, 
 }
 
 
+// Staging of R (4 or 8) double-float values per string for the double-float
+// kernels: one record of R float2 per string, whose 16-byte chunk k (values 2k
+// and 2k + 1) sits at chunk position k ^ (x mod R/2).  An ELL entry then reads
+// R/2 16-byte chunks of one record, and the lanes of a warp, which read the same
+// chunk of different records, spread over all banks; with R rows of pairs
+// staged one after the other each entry took R 8-byte loads that collided in
+// the banks about 2.5 times.
+template <int R>
+__device__ __forceinline__ float4 *stage_chunk(float4 *base, int64_t x, int k) {
+    return base + x * (R / 2) + (k ^ (int)(x & (R / 2 - 1)));
+}
+
 // sigma_1 in double-float: R rows of C staged as pairs; sigma overwritten or
 // (add != 0) added to.
 template <int R, int U = 8>
@@ -163,12 +175,23 @@ __global__ void __launch_bounds__(512, 1) k_sigma1_rows_df(const double *__restr
                                                            SpinTables B, int64_t nsa, int add,
                                                            const int *__restrict__ active) {
     if (active != nullptr && *active == 0) return;  // gated launch (batched engine)
-    extern __shared__ float2 rows2[];  // [R][nsb]
+    extern __shared__ float4 stage4[];  // R >= 4: [nsb] records of R pairs; else [R][nsb] pairs
+    float2 *rows2 = reinterpret_cast<float2 *>(stage4);
     const int64_t nsb = B.ns;
     const int64_t r0 = (int64_t)blockIdx.x * R;
-    for (int64_t t = threadIdx.x; t < (int64_t)R * nsb; t += blockDim.x) {
-        const int64_t r = t / nsb, j = t % nsb;
-        rows2[t] = (r0 + r < nsa) ? df_split(C[(r0 + r) * nsb + j]) : make_float2(0.f, 0.f);
+    if constexpr (R >= 4) {
+        for (int64_t j = threadIdx.x; j < nsb; j += blockDim.x)
+#pragma unroll
+            for (int k = 0; k < R / 2; ++k) {
+                const float2 a = (r0 + 2 * k < nsa) ? df_split(C[(r0 + 2 * k) * nsb + j]) : make_float2(0.f, 0.f);
+                const float2 b = (r0 + 2 * k + 1 < nsa) ? df_split(C[(r0 + 2 * k + 1) * nsb + j]) : make_float2(0.f, 0.f);
+                *stage_chunk<R>(stage4, j, k) = make_float4(a.x, a.y, b.x, b.y);
+            }
+    } else {
+        for (int64_t t = threadIdx.x; t < (int64_t)R * nsb; t += blockDim.x) {
+            const int64_t r = t / nsb, j = t % nsb;
+            rows2[t] = (r0 + r < nsa) ? df_split(C[(r0 + r) * nsb + j]) : make_float2(0.f, 0.f);
+        }
     }
     __syncthreads();
     for (int64_t ib = threadIdx.x; ib < nsb; ib += blockDim.x) {
@@ -187,9 +210,19 @@ __global__ void __launch_bounds__(512, 1) k_sigma1_rows_df(const double *__restr
                 vl[u] = ok ? B.gvall[idx] : 0.f;
             }
 #pragma unroll
-            for (int u = 0; u < U; ++u)
+            for (int u = 0; u < U; ++u) {
+                if constexpr (R >= 4) {
 #pragma unroll
-                for (int r = 0; r < R; ++r) df_mac(vh[u], vl[u], rows2[(int64_t)r * nsb + col[u]], sh[r], sl[r]);
+                    for (int k = 0; k < R / 2; ++k) {
+                        const float4 q = *stage_chunk<R>(stage4, col[u], k);
+                        df_mac(vh[u], vl[u], make_float2(q.x, q.y), sh[2 * k], sl[2 * k]);
+                        df_mac(vh[u], vl[u], make_float2(q.z, q.w), sh[2 * k + 1], sl[2 * k + 1]);
+                    }
+                } else {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) df_mac(vh[u], vl[u], rows2[(int64_t)r * nsb + col[u]], sh[r], sl[r]);
+                }
+            }
         }
 #pragma unroll
         for (int r = 0; r < R; ++r)
@@ -206,13 +239,23 @@ template <int R, int U = 8>
 __global__ void __launch_bounds__(512, 1) k_sigma2_cols_df(const double *__restrict__ C, double *__restrict__ sig,
                                                            SpinTables A, int64_t nsb, const int *__restrict__ active) {
     if (active != nullptr && *active == 0) return;
-    extern __shared__ float2 cols2[];  // [R][nsa]
+    extern __shared__ float4 stage4[];  // R >= 4: [nsa] records of R pairs; else [R][nsa] pairs
+    float2 *cols2 = reinterpret_cast<float2 *>(stage4);
     const int64_t nsa = A.ns;
     const int64_t c0 = (int64_t)blockIdx.x * R;
     for (int64_t ia = threadIdx.x; ia < nsa; ia += blockDim.x) {
+        if constexpr (R >= 4) {
 #pragma unroll
-        for (int r = 0; r < R; ++r)
-            cols2[(int64_t)r * nsa + ia] = (c0 + r < nsb) ? df_split(C[ia * nsb + c0 + r]) : make_float2(0.f, 0.f);
+            for (int k = 0; k < R / 2; ++k) {
+                const float2 a = (c0 + 2 * k < nsb) ? df_split(C[ia * nsb + c0 + 2 * k]) : make_float2(0.f, 0.f);
+                const float2 b = (c0 + 2 * k + 1 < nsb) ? df_split(C[ia * nsb + c0 + 2 * k + 1]) : make_float2(0.f, 0.f);
+                *stage_chunk<R>(stage4, ia, k) = make_float4(a.x, a.y, b.x, b.y);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                cols2[(int64_t)r * nsa + ia] = (c0 + r < nsb) ? df_split(C[ia * nsb + c0 + r]) : make_float2(0.f, 0.f);
+        }
     }
     __syncthreads();
     for (int64_t ia = threadIdx.x; ia < nsa; ia += blockDim.x) {
@@ -231,9 +274,19 @@ __global__ void __launch_bounds__(512, 1) k_sigma2_cols_df(const double *__restr
                 vl[u] = ok ? A.gvall[idx] : 0.f;
             }
 #pragma unroll
-            for (int u = 0; u < U; ++u)
+            for (int u = 0; u < U; ++u) {
+                if constexpr (R >= 4) {
 #pragma unroll
-                for (int r = 0; r < R; ++r) df_mac(vh[u], vl[u], cols2[(int64_t)r * nsa + col[u]], sh[r], sl[r]);
+                    for (int k = 0; k < R / 2; ++k) {
+                        const float4 q = *stage_chunk<R>(stage4, col[u], k);
+                        df_mac(vh[u], vl[u], make_float2(q.x, q.y), sh[2 * k], sl[2 * k]);
+                        df_mac(vh[u], vl[u], make_float2(q.z, q.w), sh[2 * k + 1], sl[2 * k + 1]);
+                    }
+                } else {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) df_mac(vh[u], vl[u], cols2[(int64_t)r * nsa + col[u]], sh[r], sl[r]);
+                }
+            }
         }
 #pragma unroll
         for (int r = 0; r < R; ++r)
