@@ -221,7 +221,9 @@ int fci_hdiag(fci_ctx *ctx, double *out, void *stream);
  *  guess     NULL (unit vectors on the lowest diagonal elements), or DEVICE
  *            FP64 [nroots][N] starting vectors
  * Uses the options given at fci_init (max_subspace, max_iter, precision,
- * basis_f32).  In FCI_PREC_MIXED with an FP32 basis (large spaces: the FP64
+ * basis_f32, spin_parity: with a parity the guess and every correction are
+ * projected onto it and the energies are those of that parity's states).
+ * In FCI_PREC_MIXED with an FP32 basis (large spaces: the FP64
  * basis of CAS(18,18) would need 300 GB) the device workspace is
  * 8 (2 m + 1) / 2 + 16 nroots bytes per determinant for m basis vectors.
  * Blocking; runs on the context's internal stream.
