@@ -271,6 +271,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tmem_st8(lb + acc_col(h, 0, n0, n1) + (uint32_t)(c * 8), kBias0);
                 tmem_st8(lb + acc_col(h, 1, n0, n1) + (uint32_t)(c * 8), kBias1);
                 tmem_st8(lb + acc_col(h, 2, n0, n1) + (uint32_t)(c * 8), kBias2);
+                tmem_st8(lb + acc_col(h, 3, n0, n1) + (uint32_t)(c * 8), 0u);
             }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
@@ -316,10 +317,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int sl = 0; sl < kSlices; ++sl) w[sl][i] = pack_bf16(f[0][sl], f[1][sl]);
             }
-            const uint32_t off = tc::kmajor_offset(q, kg, KPAD);
+            // half h keeps its six slices stacked along N: rows bh + sl nh + (q - q0h)
+            const int h = q < n0 ? 0 : 1;
+            const int nhh = h ? n1 : n0, rbase = h ? kSlices * n0 : 0, ql = q - (h ? n0 : 0);
 #pragma unroll
             for (int sl = 0; sl < kSlices; ++sl)
-                *reinterpret_cast<uint4 *>(sB + (uint32_t)sl * L.bytesB + off) = make_uint4(w[sl][0], w[sl][1], w[sl][2], w[sl][3]);
+                *reinterpret_cast<uint4 *>(sB + tc::kmajor_offset(rbase + sl * nhh + ql, kg, KPAD)) =
+                    make_uint4(w[sl][0], w[sl][1], w[sl][2], w[sl][3]);
         }
         tc::fence_async_smem();
         tc::fence_before();
@@ -423,10 +427,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                                            "=r"(r[lv][4]), "=r"(r[lv][5]), "=r"(r[lv][6]), "=r"(r[lv][7])
                                          : "r"(lane_base + acc_col(h, lv, n0, n1) + (uint32_t)(c * 8)));
                         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                        // the next tile accumulates levels 0-2 onto their biases again
+                        // the next tile accumulates levels 0-2 onto their biases and level 3 onto zero
                         tmem_st8(lane_base + acc_col(h, 0, n0, n1) + (uint32_t)(c * 8), kBias0);
                         tmem_st8(lane_base + acc_col(h, 1, n0, n1) + (uint32_t)(c * 8), kBias1);
                         tmem_st8(lane_base + acc_col(h, 2, n0, n1) + (uint32_t)(c * 8), kBias2);
+                        tmem_st8(lane_base + acc_col(h, 3, n0, n1) + (uint32_t)(c * 8), 0u);
                         if (c + 2 >= nchunks) {  // last chunk of this thread in the half: release it
                             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                             tc::fence_before();
@@ -448,37 +453,47 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         } else if (warp == 12 && lane == 0) {
             // ---- MMA issuer: descriptors of K-step 0, advanced by 256 bytes (16 in
-            // the address field) per K-step ----
+            // the address field) per K-step.  A half's six B slices are stacked
+            // along N and its four levels sit side by side in tensor memory, so
+            // A slice s times B slices 0..3-s is one MMA of N = (4 - s) n_h writing
+            // levels s..3, and the products of weight 4 and 5 are MMAs of N = n_h
+            // into level 3: 15 MMAs per K-step instead of 21 (each M = 128 MMA
+            // reads its 4 KB A slice from shared memory; fewer, wider MMAs read it
+            // fewer times).  Level 3 starts from zero (written by the epilogue). ----
             uint64_t ad[kSlices], bd0[kSlices], bd1[kSlices];
 #pragma unroll
             for (int sl = 0; sl < kSlices; ++sl) {
                 ad[sl] = tc::smem_desc(tc::smem_u32(sA + sl * L.bytesA), 128, sbo);
-                bd0[sl] = tc::smem_desc(tc::smem_u32(sB + sl * L.bytesB), 128, sbo);
-                bd1[sl] = tc::smem_desc(tc::smem_u32(sB + sl * L.bytesB) + (uint32_t)(n0 / 8) * sbo, 128, sbo);
+                bd0[sl] = tc::smem_desc(tc::smem_u32(sB) + (uint32_t)(sl * n0 / 8) * sbo, 128, sbo);
+                bd1[sl] = tc::smem_desc(tc::smem_u32(sB) + (uint32_t)((kSlices * n0 + sl * n1) / 8) * sbo, 128, sbo);
             }
-            const uint32_t id0 = tc::instr_desc(kM, n0), id1 = tc::instr_desc(kM, n1 > 0 ? n1 : 16);
+            uint32_t id0[4], id1[4];  // N = (k + 1) n_h
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                id0[k] = tc::instr_desc(kM, (k + 1) * n0);
+                id1[k] = tc::instr_desc(kM, n1 > 0 ? (k + 1) * n1 : 16);
+            }
             uint32_t col0[4], col1[4];
 #pragma unroll
             for (int lv = 0; lv < 4; ++lv) {
                 col0[lv] = tmem + acc_col(0, lv, n0, n1);
                 col1[lv] = tmem + acc_col(1, lv, n0, n1);
             }
-            auto issue_half = [&](const uint64_t(&bd)[kSlices], const uint32_t(&col)[4], uint32_t idesc, bool wait_a,
-                                  bool last, int64_t Tt) -> bool {
-                bool fresh3 = true;
+            auto issue_half = [&](const uint64_t(&bd)[kSlices], const uint32_t(&col)[4], const uint32_t(&idn)[4],
+                                  bool wait_a, bool last, int64_t Tt) -> bool {
 #pragma unroll
                 for (int ks = 0; ks < NKS; ++ks) {
                     if (wait_a && !tc::mbar_wait_bounded(a_full(ks), (uint32_t)(Tt & 1))) return false;
                     tc::fence_after();
 #pragma unroll
-                    for (int sa = 0; sa < kSlices; ++sa)
+                    for (int sa = 0; sa < kSlices; ++sa) {
+                        const uint64_t a = ad[sa] + (uint64_t)(ks * 16);
+                        const int st = sa < 4 ? 4 - sa : 0;  // stacked B slices 0..st-1 -> levels sa..3
+                        if (st > 0) tc::mma_bf16(col[sa], a, bd[0] + (uint64_t)(ks * 16), idn[st - 1], 1u);
 #pragma unroll
-                        for (int sb = 0; sa + sb < kSlices; ++sb) {
-                            const int lv = sa + sb < 3 ? sa + sb : 3;
-                            const uint32_t accum = (lv < 3 || !fresh3) ? 1u : 0u;
-                            if (lv == 3) fresh3 = false;
-                            tc::mma_bf16(col[lv], ad[sa] + (uint64_t)(ks * 16), bd[sb] + (uint64_t)(ks * 16), idesc, accum);
-                        }
+                        for (int t = st; sa + t < kSlices; ++t)  // weights 4, 5 -> level 3
+                            tc::mma_bf16(col[3], a, bd[t] + (uint64_t)(ks * 16), idn[0], 1u);
+                    }
                     if (last) tc::mma_commit(a_free(ks));
                 }
                 return true;
