@@ -12,7 +12,7 @@ What lives here:
   single-replacement lists (Eq. 7), the Hamiltonian of Eq. 6 built two
   independent ways (Slater-Condon rules, and Eq. 6 applied term by term to
   bitstrings), direct sigma = H c (Eq. 4/5), H diagonal, the spin-summed
-  one-particle density and the total spin <S^2> of an expansion.
+  one- and two-particle densities and the total spin <S^2> of an expansion.
 * ``oracle.davidson`` -- a plain NumPy Davidson eigensolver following the
   steps of Section 3.3 (reading of the unspecified parts in its docstring).
 
@@ -71,6 +71,8 @@ def _bind(lib):
     lib.oracle_hdiag.argtypes = [i32, i32, i32, dp, dp, dp]
     lib.oracle_rdm1.restype = i32
     lib.oracle_rdm1.argtypes = [i32, i32, i32, dp, dp]
+    lib.oracle_rdm2.restype = i32
+    lib.oracle_rdm2.argtypes = [i32, i32, i32, dp, dp]
     lib.oracle_s2.restype = ctypes.c_double
     lib.oracle_s2.argtypes = [i32, i32, i32, dp]
     lib.oracle_num_threads.restype = i32
@@ -199,6 +201,20 @@ def rdm1(norb: int, na: int, nb: int, c) -> np.ndarray:
     return g
 
 
+def rdm2(norb: int, na: int, nb: int, c) -> np.ndarray:
+    """Gamma_pqrs = <c| E_pq E_rs |c> (spin summed), shaped [norb]*4.
+
+    With gamma = rdm1(c), <c|H|c> = sum h_pq gamma_pq
+    + 1/2 sum (pq|rs) (Gamma_pqrs - delta_qr gamma_ps) (Eq. 6)."""
+    c = _f64(c)
+    if c.size != ndet(norb, na, nb):
+        raise ValueError("vector length does not match the space")
+    g = np.zeros((norb,) * 4)
+    if _load().oracle_rdm2(norb, na, nb, _ptr(c), _ptr(g)):
+        raise ValueError("bad space")
+    return g
+
+
 def s_squared(norb: int, na: int, nb: int, c) -> float:
     """<c|S^2|c> / <c|c>: total spin of an expansion in the (na, nb) sector
     (a diagnostic for the roots; Ms = 0 roots of random integrals can have any S)."""
@@ -215,5 +231,5 @@ from .davidson import davidson  # noqa: E402  (pure NumPy, no library import)
 
 __all__ = [
     "build", "binom", "strings", "single_table", "ndet", "hamiltonian", "sigma",
-    "sigma_rows", "sigma_rows_generated", "hdiag", "rdm1", "s_squared", "davidson", "num_threads",
+    "sigma_rows", "sigma_rows_generated", "hdiag", "rdm1", "rdm2", "s_squared", "davidson", "num_threads",
 ]

@@ -30,6 +30,7 @@
  *  oracle_sigma          the same for every I (OpenMP over I)
  *  oracle_hdiag          H_II
  *  oracle_rdm1           spin-summed one-particle density <c|E_pq|c>
+ *  oracle_rdm2           spin-summed two-particle density <c|E_pq E_rs|c>
  *  oracle_s2             <c|S^2|c> / <c|c> (total spin of an expansion)
  */
 #include <math.h>
@@ -450,6 +451,46 @@ int oracle_rdm1(int norb, int na, int nb, const double *c, double *gamma) {
                     int64_t I = det_index(&S, dI);
                     gamma[p * n + q] += ph * c[I] * c[J];
                 }
+    }
+    space_free(&S);
+    return 0;
+}
+
+/* Spin-summed two-particle density Gamma_pqrs = <c| E_pq E_rs |c>, the
+ * density of the two-electron term of Eq. 6, with which
+ *   <c|H|c> = sum h_pq gamma_pq + 1/2 sum (pq|rs) (Gamma_pqrs - delta_qr gamma_ps).
+ * Straight from the definition: E_rs (both spins) takes J to K, E_pq (both
+ * spins) takes K to I, and c_I * phase * c_J lands in Gamma[p][q][r][s].
+ * OpenMP over p; each thread owns the slab Gamma[p][.][.][.]. */
+int oracle_rdm2(int norb, int na, int nb, const double *c, double *gamma2) {
+    space_t S;
+    if (space_init(&S, norb, na, nb)) return -1;
+    const int n = norb;
+    const int64_t N = S.nsa * S.nsb;
+    const int64_t n2 = (int64_t)n * n;
+    memset(gamma2, 0, sizeof(double) * n2 * n2);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int p = 0; p < n; ++p) {
+        double *slab = gamma2 + p * n2 * n;
+        for (int64_t J = 0; J < N; ++J) {
+            if (c[J] == 0.0) continue;
+            det_t dJ = make_det(n, S.la[J / S.nsb], S.lb[J % S.nsb]);
+            for (int r = 0; r < n; ++r)
+                for (int s = 0; s < n; ++s)
+                    for (int t = 0; t < 2; ++t) {
+                        det_t dK;
+                        int ph1 = op_excite(dJ, r + t * n, s + t * n, &dK);
+                        if (!ph1) continue;
+                        for (int q = 0; q < n; ++q)
+                            for (int u = 0; u < 2; ++u) {
+                                det_t dI;
+                                int ph2 = op_excite(dK, p + u * n, q + u * n, &dI);
+                                if (!ph2) continue;
+                                int64_t I = det_index(&S, dI);
+                                slab[(q * n + r) * n + s] += (double)(ph1 * ph2) * c[I] * c[J];
+                            }
+                    }
+        }
     }
     space_free(&S);
     return 0;

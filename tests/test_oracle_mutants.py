@@ -7,7 +7,7 @@ planted in a temporary copy of ``oracle/csrc/oracle.c`` or
 built and exercised in a child process (so a mutant that crashes cannot take
 the test run down), against the pins of ``test_oracle_strings.py``,
 ``test_oracle_hamiltonian.py``, ``test_oracle_davidson_rdm.py`` and
-``test_oracle_spin.py``.  A mutant
+``test_oracle_spin.py`` and ``test_oracle_rdm2.py``.  A mutant
 counts as caught when at least one pin fails (or a signal kills the child).  The
 unmodified copy, built the same way, must pass every pin, so the harness itself
 is checked too.
@@ -89,6 +89,16 @@ C_MUTANTS = [
     # 1-RDM: ket coefficient used twice
     ("rdm1_wrong_coefficient", "c",
      "gamma[p * n + q] += ph * c[I] * c[J];", "gamma[p * n + q] += ph * c[J] * c[J];"),
+    # 2-RDM: the second operator acts on alpha electrons only
+    ("rdm2_one_spin", "c",
+     "for (int u = 0; u < 2; ++u) {", "for (int u = 0; u < 1; ++u) {"),
+    # 2-RDM: phase of the first replacement dropped
+    ("rdm2_phase_dropped", "c", "(double)(ph1 * ph2) * c[I] * c[J]", "(double)ph2 * c[I] * c[J]"),
+    # 2-RDM: second and third indices swapped on store
+    ("rdm2_index_swapped", "c", "slab[(q * n + r) * n + s]", "slab[(r * n + q) * n + s]"),
+    # 2-RDM: operators applied in the other order (Gamma_rspq)
+    ("rdm2_operator_order", "c",
+     "int ph1 = op_excite(dJ, r + t * n, s + t * n, &dK);", "int ph1 = op_excite(dJ, s + t * n, r + t * n, &dK);"),
     # single-replacement list: sign not stored
     ("table_sign_dropped", "c", "sg[at] = (int8_t)s;", "sg[at] = (int8_t)1;"),
     # single-replacement list: operator indices swapped (a+_l a_k)
@@ -126,6 +136,7 @@ def _pins():
     sys.path.insert(0, HERE)
     import test_oracle_davidson_rdm as td
     import test_oracle_hamiltonian as th
+    import test_oracle_rdm2 as tr2
     import test_oracle_spin as tsp
     import test_oracle_strings as ts
 
@@ -152,6 +163,10 @@ def _pins():
         ("davidson_collapse", td.test_davidson_collapse_path),
         ("rdm1_hellmann_feynman", lambda o: td.test_rdm1_hellmann_feynman(o, 4, 2, 2)),
         ("rdm1_e_pq", td.test_rdm1_equals_expectation_of_e_pq),
+        ("rdm2_energy", lambda o: tr2.test_energy_of_any_vector(o, 5, 3, 2)),
+        ("rdm2_e_matrices", tr2.test_equals_product_of_explicit_e_matrices),
+        ("rdm2_single_det", lambda o: tr2.test_single_determinant_closed_form(o, 4, 2, 2, 0b0011, 0b0101)),
+        ("rdm2_commutator", lambda o: tr2.test_commutator_and_traces(o, 5, 2, 3)),
         ("s2_closed_shell", lambda o: tsp.test_closed_shell_is_singlet(o, 4, 2, 0b0110)),
         ("s2_high_spin", lambda o: tsp.test_high_spin_determinant(o, 4, 3, 1, 0b0111, 0b0010)),
         ("s2_open_shell", tsp.test_two_electron_open_shell),
