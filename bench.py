@@ -569,6 +569,56 @@ def run_large(args):
     return 0
 
 
+def density_leg(pkg, norb, na, nb, h1, eri, c_dev, sigma_ms, peaks):
+    """The density step after the Davidson iterations (Table 2's "1e/2e
+    Density Matrices"): gamma (fci_rdm1) and Gamma with gamma (fci_rdm2) of one
+    vector, blocking calls timed whole (median of three), and the kernels of a
+    one-chunk fci_rdm2 from the library's CUDA-event profile."""
+    import time
+
+    ctx = pkg.fci_init(norb, na, nb, h1, eri)
+    t1, t2 = [], []
+    for _ in range(3):
+        t = time.perf_counter()
+        pkg.fci_rdm1(ctx, c_dev)
+        t1.append(time.perf_counter() - t)
+        t = time.perf_counter()
+        pkg.fci_rdm2(ctx, c_dev)
+        t2.append(time.perf_counter() - t)
+    pkg.fci_free(ctx)
+    n = norb
+    R = n * n + 1
+    Rd = (R + 7) // 8 * 8
+    nks = (c_dev.numel() + 15) // 16
+    ctx1 = pkg.fci_init(norb, na, nb, h1, eri, pkg.default_options(rdm2_chunk_bytes=float(6 * Rd * 32 * nks + 1)))
+    pkg.fci_profile_enable(ctx1, True)
+    for _ in range(3):
+        pkg.fci_rdm2(ctx1, c_dev)
+    names, prof = pkg.fci_profile_read(ctx1)
+    pkg.fci_profile_enable(ctx1, False)
+    pkg.fci_free(ctx1)
+    km = np.median(prof[-2:], axis=0)  # ms per kernel
+    nrb, ncb = (Rd + 127) // 128, (Rd + 47) // 48
+    ntile = sum(ncb - (-(-(rb * 128 - 47) // 48) if rb * 128 > 47 else 0) for rb in range(nrb))
+    executed = 2.0 * 128 * 48 * 16 * 21 * ntile * nks  # MMA FLOP: 21 digit products per tile and K-step
+    useful = float(R) * R * 16 * nks  # one triangle of the FP64 Gram matrix, 2 FLOP per product
+    itc = list(names).index("rdm2_tc")
+    tc_s = km[itc] / 1e3
+    peak = peaks.get("bf16_tflops")
+    return {
+        "workload": f"CAS({na + nb}e,{norb}o), N = {c_dev.numel()}",
+        "rdm1_ms": 1e3 * float(np.median(t1)), "rdm2_ms": 1e3 * float(np.median(t2)),
+        "rdm2_over_sigma": float(np.median(t2)) * 1e3 / sigma_ms,
+        "rdm2_one_chunk_kernels_ms": {nm: float(km[i]) for i, nm in enumerate(names)},
+        "rdm2_tc_roofline": {"bound": "tensor", "achieved": executed / tc_s / 1e12, "peak": peak,
+                             "unit": "TFLOP/s", "frac": (executed / tc_s / 1e12 / peak) if peak else None,
+                             "executed_flop": executed, "fp64_equivalent_tflops": useful / tc_s / 1e12,
+                             "note": "executed bf16 MMA FLOP (6 digits, 21 products, 128 x 48 tiles) per launch / "
+                                     "CUDA-event time; peak = measured burst bf16"},
+        "timing": "whole blocking calls (allocation, statistics round trip, host copies included), median of 3",
+    }
+
+
 def run_ours(args):
     import torch
 
@@ -765,6 +815,10 @@ def run_ours(args):
                                         args.cpu_seconds / 3 if (args.cpu_baseline and world == 1) else 0)
         legs["cas18_sigma"] = sigma_leg(pkg, "cas18", 2, 2, stream, world,
                                         args.cpu_seconds / 3 if (args.cpu_baseline and world == 1) else 0)
+        if rank == 0:
+            cd = torch.from_numpy(c_host / np.linalg.norm(c_host)).to(dev)
+            legs["densities"] = density_leg(pkg, norb, na, nb, h1, eri, cd, t / args.steps * 1e3, peaks)
+            del cd
         if rank == 0:
             result.update(legs)
     if args.cpu_baseline and rank == 0 and world == 1:

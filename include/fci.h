@@ -108,6 +108,10 @@ typedef struct fci_options {
                             projected onto the parity, and sigma_1 = parity sigma_2^T is
                             formed from sigma_2 by a transpose-add (Section 3.1's Ms = 0
                             combinations); fci_sigma itself is unaffected */
+    double rdm2_chunk_bytes; /* fci_rdm2: device memory for the digit planes of one chunk of
+                            determinants (about 192 (norb^2 + 1) bytes per 16 determinants
+                            per chunk); 0 = 1 GiB (default).  (Resource control; no
+                            counterpart in the paper.) */
 } fci_options;
 
 /* fci_options.f64_kernels: how the FCI_F64 sigma is computed.  All modes meet
@@ -254,6 +258,30 @@ int fci_davidson_log(fci_ctx *ctx, double *out, int cap, int *count);
  *  gamma  HOST array norb x norb, row-major, filled on return (blocking)
  */
 int fci_rdm1(fci_ctx *ctx, const void *c, int dtype, double *gamma);
+
+/*
+ * Spin-summed two-particle density Gamma_pqrs = <c| E_pq E_rs |c> (the
+ * density of the two-electron term of Eq. 6; E_pq of Eq. 7), the second half
+ * of the density step after the Davidson iterations (Section 4, Table 2's
+ * "1e/2e Density Matrices").  With gamma = fci_rdm1's density,
+ *   <c|H|c> = sum h_pq gamma_pq + 1/2 sum (pq|rs) (Gamma_pqrs - delta_qr gamma_ps).
+ * Gamma_pqrs = sum_K <K|E_qp|c> <K|E_rs|c> over the determinants K, computed
+ * as one Gram matrix on the tensor cores with FP64 accuracy (c in 45-bit fixed
+ * point relative to its largest element, six 8-bit digits, exact 64-bit
+ * integer accumulation): about 1e-14 of ||c||^2, bit-reproducible.  c need
+ * not be normalised (both densities scale with ||c||^2).
+ *
+ *  c       device vector (dtype FCI_F64 or FCI_F32) of N elements; the call
+ *          first waits for all work on the device
+ *  gamma1  HOST array norb x norb (gamma_pq, from the same pass), or NULL
+ *  gamma2  HOST array norb^4, row-major [p][q][r][s], filled on return
+ * Allocates its scratch (the digit planes of one chunk of determinants, see
+ * fci_options.rdm2_chunk_bytes, and (norb^2 + 1)^2 64-bit integers) per call.
+ * A non-finite c gives NaN densities.  Blocking.  FCI_ERR_TIMEOUT when a
+ * bounded wait inside the tensor-core kernel gave up, FCI_ERR_RANGE if an
+ * exact accumulator left its range (neither is expected).
+ */
+int fci_rdm2(fci_ctx *ctx, const void *c, int dtype, double *gamma1, double *gamma2);
 
 /*
  * fci_rdm1_noalloc -- the density of fci_rdm1, computed without allocating

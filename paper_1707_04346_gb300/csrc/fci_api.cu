@@ -157,6 +157,7 @@ int fci_init(fci_ctx **out, int norb, int nalpha, int nbeta, const double *h1, c
     if (o.spin_parity < -1 || o.spin_parity > 1) return fail(FCI_ERR_ARG, "spin_parity must be -1, 0 or 1");
     if (o.spin_parity != 0 && nalpha != nbeta)
         return fail(FCI_ERR_ARG, "spin_parity needs n_alpha = n_beta (Ms = 0)");
+    if (!(o.rdm2_chunk_bytes >= 0)) return fail(FCI_ERR_ARG, "rdm2_chunk_bytes must be >= 0");
     if (o.f64_kernels < FCI_F64_AUTO || o.f64_kernels > FCI_F64_WIDE)
         return fail(FCI_ERR_ARG, "f64_kernels must be FCI_F64_AUTO, FCI_F64_FMA, FCI_F64_SLICED or FCI_F64_WIDE");
     if (int rc = check_integrals(norb, h1, eri, o.symmetry_tol)) return rc;
@@ -254,6 +255,18 @@ int fci_rdm1(fci_ctx *ctx, const void *c, int dtype, double *gamma) {
     FCI_CUDA(cudaDeviceSynchronize());  // c may still be in flight on the caller's streams
     try {
         return run_rdm1(ctx, c, dtype, gamma);
+    } catch (const std::bad_alloc &) {
+        return fail(FCI_ERR_OOM, "host allocation failed");
+    }
+}
+
+int fci_rdm2(fci_ctx *ctx, const void *c, int dtype, double *gamma1, double *gamma2) {
+    if (!ctx || !c || !gamma2) return fail(FCI_ERR_ARG, "NULL argument");
+    if (dtype != FCI_F64 && dtype != FCI_F32) return fail(FCI_ERR_ARG, "dtype must be FCI_F64 or FCI_F32");
+    FCI_CUDA(cudaSetDevice(ctx->device));
+    FCI_CUDA(cudaDeviceSynchronize());  // c may still be in flight on the caller's streams
+    try {
+        return run_rdm2(ctx, c, dtype, gamma1, gamma2);
     } catch (const std::bad_alloc &) {
         return fail(FCI_ERR_OOM, "host allocation failed");
     }

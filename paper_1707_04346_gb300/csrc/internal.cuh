@@ -205,6 +205,8 @@ int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *v
 
 // rdm.cu
 int run_rdm1(fci_ctx *ctx, const void *c, int dtype, double *gamma);
+// rdm2.cu
+int run_rdm2(fci_ctx *ctx, const void *c, int dtype, double *gamma1, double *gamma2);
 
 inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 

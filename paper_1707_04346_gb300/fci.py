@@ -27,7 +27,7 @@ FCI_Q_DEVICE_BYTES, FCI_Q_ITERATIONS, FCI_Q_SIGMA_CALLS, FCI_Q_DEVICE_ERROR = 7,
 
 EXPORTED = [
     "fci_default_options", "fci_init", "fci_free", "fci_sigma", "fci_hdiag", "fci_davidson",
-    "fci_davidson_log", "fci_rdm1", "fci_get_strings", "fci_get_single_table", "fci_query",
+    "fci_davidson_log", "fci_rdm1", "fci_rdm2", "fci_get_strings", "fci_get_single_table", "fci_query",
     "fci_last_error", "fci_profile_enable", "fci_profile_read", "fci_profile_kernel_name",
     "fci_rdm1_noalloc", "fci_batch_init", "fci_batch_davidson", "fci_batch_sigma", "fci_batch_offset",
     "fci_batch_tuning", "fci_batch_stats", "fci_batch_free", "fci_tile_schedule", "fci_check_wait_timeout",
@@ -66,6 +66,7 @@ class fci_options(ctypes.Structure):
         ("f32_row_global", ctypes.c_int),
         ("basis_f32", ctypes.c_int),
         ("spin_parity", ctypes.c_int),
+        ("rdm2_chunk_bytes", ctypes.c_double),
     ]
 
 
@@ -99,6 +100,8 @@ def load(path: str = LIB_PATH):
         lib.fci_davidson_log.argtypes = [vp, vp, i32, ctypes.POINTER(i32)]
         lib.fci_rdm1.restype = i32
         lib.fci_rdm1.argtypes = [vp, vp, i32, vp]
+        lib.fci_rdm2.restype = i32
+        lib.fci_rdm2.argtypes = [vp, vp, i32, vp, vp]
         lib.fci_get_strings.restype = i32
         lib.fci_get_strings.argtypes = [vp, i32, vp]
         lib.fci_get_single_table.restype = i32
@@ -266,6 +269,17 @@ def fci_rdm1(ctx: FciContext, c) -> np.ndarray:
     code = _dtype_code(c)
     _check(load().fci_rdm1(ctx.handle, _dev_ptr(c, code), code, _np_ptr(g)))
     return g
+
+
+def fci_rdm2(ctx: FciContext, c):
+    """(gamma [n][n], Gamma [n][n][n][n]): Gamma_pqrs = <c|E_pq E_rs|c> and
+    gamma_pq = <c|E_pq|c> from one tensor-core pass (see include/fci.h)."""
+    n = ctx.norb
+    g1 = np.zeros((n, n))
+    g2 = np.zeros((n, n, n, n))
+    code = _dtype_code(c)
+    _check(load().fci_rdm2(ctx.handle, _dev_ptr(c, code), code, _np_ptr(g1), _np_ptr(g2)))
+    return g1, g2
 
 
 def fci_rdm1_noalloc(ctx: FciContext, c, stream=None) -> np.ndarray:
