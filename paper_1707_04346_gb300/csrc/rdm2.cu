@@ -35,8 +35,10 @@
 //    2^22 units for 64 determinants), weights 4-5 in FP32; every 64
 //    determinants the epilogue turns the five words into one 64-bit integer
 //    and sums them in registers, and at the end of a work item adds them to
-//    the integer G with red.global.add.u64 (exact and order-free, so the
-//    result is bit-reproducible).  Only tiles that hold some G[a][b] with
+//    the integer G with red.global.add.u64 (exact and order-free).  The
+//    64-determinant groups are fixed (K-steps 4j .. 4j + 3) and each is
+//    accumulated in one order, so the result is the same bits on every run and
+//    for every chunking.  Only tiles that hold some G[a][b] with
 //    a <= b are computed (G is symmetric);
 //  * k_rdm2_finish scales the integers to FP64 and permutes G into gamma and
 //    Gamma.
@@ -516,8 +518,11 @@ int rdm2_impl(fci_ctx *ctx, const T *C, double *g1_host, double *g2_host) {
     cudaStream_t s = ctx->stream;
     const size_t step_bytes = (size_t)6 * Rd * 32;
     size_t budget = ctx->opt.rdm2_chunk_bytes > 0 ? (size_t)ctx->opt.rdm2_chunk_bytes : ((size_t)1 << 30);
+    // whole flush groups per chunk: every 64-determinant group K-steps [4j, 4j + 4)
+    // is accumulated in the same order whatever the chunking, so the result is
+    // the same bits for every chunk size
     int64_t chunk = (int64_t)(budget / step_bytes);
-    if (chunk < 1) chunk = 1;
+    if (chunk < nks) chunk = std::max<int64_t>(kKTile, chunk / kKTile * kKTile);
     if (chunk > nks) chunk = nks;
     const size_t gbytes = sizeof(long long) * (size_t)Rd * Rd;
     const size_t obytes = sizeof(double) * (size_t)(n4 + n2);
