@@ -31,12 +31,14 @@
 //    sit side by side in tensor memory, so that A digit s times B digits
 //    0..4-s is one MMA writing weights s..4 and B digit 5-s one more into the
 //    last accumulator (11 MMAs per K-step for the 21 digit products of weight
-//    <= 5).  Weights 0-3 accumulate exactly on biases (their sums stay below
-//    2^22 units for 64 determinants), weights 4-5 in FP32; every 64
+//    <= 5).  Weights 0-3 accumulate exact integers (at most 3 2^22 units
+//    for 256 determinants, FP32 holds them up to 2^24; the first MMA of each
+//    group of 256 overwrites the accumulators, so they need no resetting),
+//    weights 4-5 in FP32; every 256
 //    determinants the epilogue turns the five words into one 64-bit integer
 //    and sums them in registers, and at the end of a work item adds them to
 //    the integer G with red.global.add.u64 (exact and order-free).  The
-//    64-determinant groups are fixed (K-steps 4j .. 4j + 3) and each is
+//    256-determinant groups are fixed (K-steps 16j .. 16j + 15) and each is
 //    accumulated in one order, so the result is the same bits on every run and
 //    for every chunking.  Only tiles that hold some G[a][b] with
 //    a <= b are computed (G is symmetric);
@@ -57,11 +59,13 @@ namespace r2 {
 using sl::kSlices;
 using tc::kM;
 
-constexpr int kThreads = 320;        // warp 0 copies, warp 1 issues the MMAs, warps 2-9 epilogue
-constexpr int kEpiThreads = 256;
+constexpr int kThreads = 448;        // warp 0 copies, warp 1 issues the MMAs, warps 2-13 epilogue
+constexpr int kEpiThreads = 384;
+constexpr int kEpiPerQuarter = 3;    // epilogue warps per tensor-memory lane quarter
 constexpr int kBN = 48;              // B rows per tile (the MMA's N per digit)
-constexpr int kStages = 5;           // K-steps of operands in flight
-constexpr int kKTile = 4;            // K-steps (64 determinants) per accumulator flush
+constexpr int kStages = 6;           // K-steps of operands in flight
+constexpr int kKTile = 16;           // K-steps (256 determinants) per accumulator flush
+constexpr int kKRange = 16;          // K-steps per work item (all tiles of one range meet in L2)
 constexpr uint32_t kBytesA = 6 * 4096;       // six planes of 128 rows x 16
 constexpr uint32_t kBytesB = 6 * kBN * 32;   // six planes of 48 rows x 16
 constexpr uint32_t kStageBytes = kBytesA + kBytesB;
@@ -145,27 +149,38 @@ __device__ __forceinline__ void entry_orbitals(uint32_t x, uint32_t t, uint32_t 
 }
 
 // One block per K-step of 16 determinants: the integers X_D of rows 0..Rd-1
-// in shared memory, then their six digit planes into dg (K-step ks - ks0 of
+// in shared memory (determinant-major with an odd stride, so that the 16
+// determinants of one entry and the consecutive rows of the digit pass hit
+// distinct banks), then their six digit planes into dg (K-step ks - ks0 of
 // the chunk), plane t at byte (ks*6 + t) * Rd * 32, row r, determinant kk of
 // the K-step at (r/8) 256 + (kk/8) 128 + (r%8) 16 + (kk%8) 2.
 template <typename T>
 __global__ void __launch_bounds__(256) k_rdm2_digits(const T *__restrict__ c, SpinTables A, SpinTables B, int n,
                                                      int Rd, int emax, int64_t ks0, int64_t N,
                                                      uint4 *__restrict__ dg) {
-    extern __shared__ __align__(16) long long X[];  // [Rd][16]
+    extern __shared__ __align__(16) long long X[];  // [16][Rd + 1]
+    __shared__ int64_t s_ka[16];
+    __shared__ int s_kb[16];
+    const int Rs = Rd + 1;
     const int64_t ks = ks0 + blockIdx.x;
     const int64_t nsb = B.ns;
     const int crow = n * n;
-    for (int i = threadIdx.x; i < Rd * 16; i += blockDim.x) X[i] = 0;
+    if (threadIdx.x < 16) {
+        const int64_t K = ks * 16 + threadIdx.x;
+        const int64_t ka = K / nsb;
+        s_ka[threadIdx.x] = K < N ? ka : -1;
+        s_kb[threadIdx.x] = (int)(K - ka * nsb);
+    }
+    for (int i = threadIdx.x; i < Rs * 16; i += blockDim.x) X[i] = 0;
     __syncthreads();
     // alpha entries (and the row of c): stored
     for (int it = threadIdx.x; it < (A.nsingle + 1) * 16; it += blockDim.x) {
         const int e = it >> 4, kk = it & 15;
-        const int64_t K = ks * 16 + kk;
-        if (K >= N) continue;
-        const int64_t ka = K / nsb, kb = K - ka * nsb;
+        const int64_t ka = s_ka[kk];
+        if (ka < 0) continue;
+        const int64_t kb = s_kb[kk];
         if (e == A.nsingle) {
-            X[crow * 16 + kk] = fixed45(c[K], emax);
+            X[kk * Rs + crow] = fixed45(c[ka * nsb + kb], emax);
             continue;
         }
         const uint32_t ent = A.tab[(int64_t)e * A.ns + ka];
@@ -173,21 +188,21 @@ __global__ void __launch_bounds__(256) k_rdm2_digits(const T *__restrict__ c, Sp
         int l, k;
         entry_orbitals(A.str[ka], A.str[tg], ent_pair(ent), l, k);
         const long long v = fixed45(c[(int64_t)tg * nsb + kb], emax);
-        X[(l * n + k) * 16 + kk] = ent_negative(ent) ? -v : v;
+        X[kk * Rs + l * n + k] = ent_negative(ent) ? -v : v;
     }
     __syncthreads();
     // beta entries: added
     for (int it = threadIdx.x; it < B.nsingle * 16; it += blockDim.x) {
         const int e = it >> 4, kk = it & 15;
-        const int64_t K = ks * 16 + kk;
-        if (K >= N) continue;
-        const int64_t ka = K / nsb, kb = K - ka * nsb;
+        const int64_t ka = s_ka[kk];
+        if (ka < 0) continue;
+        const int kb = s_kb[kk];
         const uint32_t ent = B.tab[(int64_t)e * B.ns + kb];
         const uint32_t tg = ent_target(ent);
         int l, k;
         entry_orbitals(B.str[kb], B.str[tg], ent_pair(ent), l, k);
         const long long v = fixed45(c[ka * nsb + tg], emax);
-        X[(l * n + k) * 16 + kk] += ent_negative(ent) ? -v : v;
+        X[kk * Rs + l * n + k] += ent_negative(ent) ? -v : v;
     }
     __syncthreads();
     // digits: thread item it = (r/8) 16 + g 8 + r%8 owns 16 bytes at it*16 of each plane
@@ -198,8 +213,8 @@ __global__ void __launch_bounds__(256) k_rdm2_digits(const T *__restrict__ c, Sp
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             float f0[kSlices], f1[kSlices];
-            sl::digits6(X[r * 16 + g * 8 + 2 * i], f0);
-            sl::digits6(X[r * 16 + g * 8 + 2 * i + 1], f1);
+            sl::digits6(X[(g * 8 + 2 * i) * Rs + r], f0);
+            sl::digits6(X[(g * 8 + 2 * i + 1) * Rs + r], f1);
 #pragma unroll
             for (int s = 0; s < kSlices; ++s) w[s][i] = sl::pack_bf16(f0[s], f1[s]);
         }
@@ -213,18 +228,31 @@ __device__ __forceinline__ long long shl_round(long long x, int k) {
     return k >= 0 ? (long long)((unsigned long long)x << k) : (x + (1ll << (-k - 1))) >> -k;
 }
 
-// round(2^f (acc0 + ... + acc4)) of one element from its raw words (weights
-// 0-3 biased): 2^8 (acc0 + acc1) and 2^24 (acc2 + acc3) are exact integers;
-// acc4 is split into round(2^18 acc4), round(2^36 rest) and the remainder
-// (|.| <= 2^-37), each exact, so that every piece fits the FP32 magic-number
-// rounding.  16 <= f <= 52.
-__device__ __forceinline__ long long levels_to_int_f(uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3, uint32_t r4,
-                                                     int f, float two_f) {
+// The integer x = v 2^k of an FP32 value holding an exact integer in units
+// 2^-k, |x| <= 2^24: split as round(x 2^-12) 2^12 + rest by FP32 magic-number
+// rounding (both parts exact), without conversion instructions.
+__device__ __forceinline__ int exact_int24(float v, float two_k) {
     constexpr float M = 12582912.0f;  // 1.5 2^23
     constexpr int MB = 0x4B400000;
-    const int hi = (int)(r0 * 256u + r1 - (sl::kBias0 * 256u + sl::kBias1));
-    const int mid = (int)(r2 * 256u + r3 - (sl::kBias2 * 256u + wd::kBias3));
-    const float a4 = __uint_as_float(r4);
+    const float x = v * two_k;                     // exact (power of two)
+    const float t = fmaf(x, 0x1p-12f, M);
+    const int h = __float_as_int(t) - MB;          // round(x 2^-12), |.| <= 2^12
+    const float rest = fmaf(-(t - M), 4096.f, x);  // x - h 2^12, exact, |.| <= 2^11
+    return h * 4096 + (__float_as_int(rest + M) - MB);
+}
+
+// round(2^f (acc0 + ... + acc4)) of one element from its five accumulator
+// words: weights 0-3 hold exact integers in units 2^-8L (|.| <= 2^24 units);
+// 2^24 (acc0 + ... + acc3) = 2^16 (2^8 (acc0 + acc1)) + 2^24 (acc2 + acc3) is
+// then an exact integer.  acc4 is split into round(2^18 acc4), round(2^36 rest)
+// and the remainder (|.| <= 2^-37), each exact and each within the FP32
+// magic-number rounding.  16 <= f <= 52.
+__device__ __forceinline__ long long levels_to_int_f(float v0, float v1, float v2, float v3, float a4, int f,
+                                                     float two_f) {
+    constexpr float M = 12582912.0f;  // 1.5 2^23
+    constexpr int MB = 0x4B400000;
+    const long long hi = (long long)exact_int24(v0, 1.f) * 256 + exact_int24(v1, 256.f);
+    const long long mid = (long long)exact_int24(v2, 65536.f) * 256 + exact_int24(v3, 16777216.f);
     const float t1 = fmaf(a4, 262144.f, M);
     const int h1 = __float_as_int(t1) - MB;
     const float q1 = fmaf(-(t1 - M), 0x1p-18f, a4);  // a4 - h1 2^-18, exact
@@ -232,7 +260,9 @@ __device__ __forceinline__ long long levels_to_int_f(uint32_t r0, uint32_t r1, u
     const int h2 = __float_as_int(t2) - MB;
     const float q2 = fmaf(-(t2 - M), 0x1p-36f, q1);  // q1 - h2 2^-36, exact
     const int h3 = __float_as_int(fmaf(q2, two_f, M)) - MB;
-    return shl_round(hi, f - 8) + shl_round(mid, f - 24) + shl_round(h1, f - 18) + shl_round(h2, f - 36) + h3;
+    const long long lead = (hi << 16) + mid;         // 2^24 (acc0 + ... + acc3)
+    const int low = h1 * 262144 + h2;                // 2^36 (acc4 - remainder), |.| < 2^28
+    return shl_round(lead, f - 24) + shl_round(low, f - 36) + h3;
 }
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
@@ -263,10 +293,31 @@ struct TcArgs {
     const unsigned char *dg;  // digit planes of the chunk
     int64_t nks;              // K-steps in the chunk
     int Rd, R, nrb, ncb, ntile;
-    int klen;                 // K-steps per work item
     int f;                    // integer unit 2^-f of the accumulator scale
     unsigned long long *G;    // [Rd][Rd] integers, G[b * Rd + a] for a <= b
     int *err;
+};
+
+// Work of CTA b: with at least ntile CTAs (a multiple of ntile), CTA b keeps
+// tile b % ntile for the whole launch and takes the K-ranges g, g + ng, ...
+// (g = b / ntile, ng = grid / ntile), so that its sums stay in registers and
+// the ntile CTAs of a group read each K-range at about the same time; with
+// fewer CTAs than tiles, CTA b takes tiles b, b + grid, ... over every K-range.
+struct Work {
+    int t0, tstep, g, ng;
+    __device__ Work(int ntile) {
+        if ((int)gridDim.x >= ntile) {
+            t0 = blockIdx.x % ntile;
+            tstep = ntile;
+            g = blockIdx.x / ntile;
+            ng = gridDim.x / ntile;
+        } else {
+            t0 = blockIdx.x;
+            tstep = gridDim.x;
+            g = 0;
+            ng = 1;
+        }
+    }
 };
 
 __global__ void __launch_bounds__(kThreads, 1) k_rdm2_tc(TcArgs P) {
@@ -282,8 +333,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_rdm2_tc(TcArgs P) {
     auto acc_empty = [&](int b) { return bar0 + 8u * (uint32_t)(2 * kStages + 2 + b); };
     const uint32_t drain = bar0 + 8u * (uint32_t)(2 * kStages + 4);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t nkr = (P.nks + P.klen - 1) / P.klen;
-    const int64_t nitems = nkr * P.ntile;
+    const int64_t nkr = (P.nks + kKRange - 1) / kKRange;
+    const Work W(P.ntile);
 
     // zero the operand stages once: rows past the end of a partial tile then
     // hold finite digits (their lanes and columns are not read back)
@@ -311,12 +362,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_rdm2_tc(TcArgs P) {
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = *tslot;
-    if (warp >= 2) {  // starting words of both accumulator buffers
-        const uint32_t lb = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-        for (int b = 0; b < 2; ++b)
-            for (int c = (warp - 2) >> 2; c < kBN / 8; c += 2) wd::init_chunk(lb, b, kBN, c);
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-    }
     tc::fence_async_smem();  // the zeroed stages, before the bulk copies and MMAs read or write them
     tc::fence_before();
     __syncthreads();
@@ -326,26 +371,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_rdm2_tc(TcArgs P) {
     if (warp == 0 && lane == 0) {
         // ---- copies: the A and B planes of one K-step per stage ----
         int64_t &G = G_copied;
-        for (int64_t item = blockIdx.x; item < nitems && !*s_fail; item += gridDim.x) {
+        for (int t = W.t0; t < P.ntile && !*s_fail; t += W.tstep) {
             int rb, cb;
-            tile_blocks((int)(item % P.ntile), P.nrb, P.ncb, rb, cb);
-            const int64_t k0 = (item / P.ntile) * P.klen, k1 = min(P.nks, k0 + P.klen);
+            tile_blocks(t, P.nrb, P.ncb, rb, cb);
             const uint32_t ba = (uint32_t)min(128, P.Rd - rb * 128) * 32u;
             const uint32_t bb = (uint32_t)min(kBN, P.Rd - cb * kBN) * 32u;
-            for (int64_t ks = k0; ks < k1; ++ks, ++G) {
-                const int st = (int)(G % kStages);
-                if (G >= kStages && !tc::mbar_wait_bounded(freeb(st), (uint32_t)((G / kStages - 1) & 1))) {
-                    *s_fail = 1;
-                    break;
-                }
-                mbar_expect_tx(full(st), 6u * (ba + bb));
-                const unsigned char *src = P.dg + (size_t)ks * 6 * P.Rd * 32;
-                const uint32_t dst = sbase + (uint32_t)st * kStageBytes;
+            for (int64_t kr = W.g; kr < nkr && !*s_fail; kr += W.ng) {
+                const int64_t k1 = min(P.nks, (kr + 1) * kKRange);
+                for (int64_t ks = kr * kKRange; ks < k1; ++ks, ++G) {
+                    const int st = (int)(G % kStages);
+                    if (G >= kStages && !tc::mbar_wait_bounded(freeb(st), (uint32_t)((G / kStages - 1) & 1))) {
+                        *s_fail = 1;
+                        break;
+                    }
+                    mbar_expect_tx(full(st), 6u * (ba + bb));
+                    const unsigned char *src = P.dg + (size_t)ks * 6 * P.Rd * 32;
+                    const uint32_t dst = sbase + (uint32_t)st * kStageBytes;
 #pragma unroll
-                for (int t = 0; t < 6; ++t) {
-                    bulk_g2s(dst + (uint32_t)t * 4096u, src + ((size_t)t * P.Rd + rb * 128) * 32, ba, full(st));
-                    bulk_g2s(dst + kBytesA + (uint32_t)t * kBN * 32u, src + ((size_t)t * P.Rd + cb * kBN) * 32, bb,
-                             full(st));
+                    for (int p = 0; p < 6; ++p) {
+                        bulk_g2s(dst + (uint32_t)p * 4096u, src + ((size_t)p * P.Rd + rb * 128) * 32, ba, full(st));
+                        bulk_g2s(dst + kBytesA + (uint32_t)p * kBN * 32u, src + ((size_t)p * P.Rd + cb * kBN) * 32, bb,
+                                 full(st));
+                    }
                 }
             }
         }
@@ -363,104 +410,114 @@ __global__ void __launch_bounds__(kThreads, 1) k_rdm2_tc(TcArgs P) {
         for (int k = 0; k < 5; ++k) idn[k] = tc::instr_desc(kM, (k + 1) * kBN);
         int64_t G = 0, Tt = 0;
         bool ok = true;
-        for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-            const int64_t k0 = (item / P.ntile) * P.klen, k1 = min(P.nks, k0 + P.klen);
-            for (int64_t kt = k0; kt < k1 && ok; kt += kKTile, ++Tt) {
-                const int b = (int)(Tt & 1);
-                if (Tt >= 2 && !tc::mbar_wait_bounded(acc_empty(b), (uint32_t)(((Tt - 2) >> 1) & 1))) {
-                    ok = false;
-                    break;
-                }
-                tc::fence_after();
-                const int64_t ke = min(k1, kt + kKTile);
-                for (int64_t ks = kt; ks < ke; ++ks, ++G) {
-                    const int st = (int)(G % kStages);
-                    if (!tc::mbar_wait_bounded(full(st), (uint32_t)((G / kStages) & 1))) {
+        for (int t = W.t0; t < P.ntile && ok; t += W.tstep)
+            for (int64_t kr = W.g; kr < nkr && ok; kr += W.ng) {
+                const int64_t k1 = min(P.nks, (kr + 1) * kKRange);
+                for (int64_t kt = kr * kKRange; kt < k1 && ok; kt += kKTile, ++Tt) {
+                    const int b = (int)(Tt & 1);
+                    if (Tt >= 2 && !tc::mbar_wait_bounded(acc_empty(b), (uint32_t)(((Tt - 2) >> 1) & 1))) {
                         ok = false;
                         break;
                     }
                     tc::fence_after();
-                    const uint64_t so = (uint64_t)((st * kStageBytes) >> 4);
+                    const int64_t ke = min(k1, kt + kKTile);
+                    for (int64_t ks = kt; ks < ke; ++ks, ++G) {
+                        const int st = (int)(G % kStages);
+                        if (!tc::mbar_wait_bounded(full(st), (uint32_t)((G / kStages) & 1))) {
+                            ok = false;
+                            break;
+                        }
+                        tc::fence_after();
+                        const uint64_t so = (uint64_t)((st * kStageBytes) >> 4);
 #pragma unroll
-                    for (int sa = 0; sa < kSlices; ++sa) {
-                        if (sa < 5) tc::mma_bf16(tmem + wd::acc_col(b, sa, kBN), ad[sa] + so, bd[0] + so, idn[4 - sa], 1u);
-                        tc::mma_bf16(tmem + wd::acc_col(b, 4, kBN), ad[sa] + so, bd[5 - sa] + so, idn[0], 1u);
+                        for (int sa = 0; sa < kSlices; ++sa) {
+                            // the first MMA of a flush group writes every accumulator
+                            // column (weights 0..4), so it overwrites instead of adding
+                            if (sa < 5)
+                                tc::mma_bf16(tmem + wd::acc_col(b, sa, kBN), ad[sa] + so, bd[0] + so, idn[4 - sa],
+                                             (sa == 0 && ks == kt) ? 0u : 1u);
+                            tc::mma_bf16(tmem + wd::acc_col(b, 4, kBN), ad[sa] + so, bd[5 - sa] + so, idn[0], 1u);
+                        }
+                        tc::mma_commit(freeb(st));
                     }
-                    tc::mma_commit(freeb(st));
+                    if (!ok) break;
+                    tc::mma_commit(acc_full(b));
                 }
-                if (!ok) break;
-                tc::mma_commit(acc_full(b));
             }
-        }
         if (!ok) *s_fail = 1;
     } else if (warp >= 2) {
-        // ---- epilogue (the lane quarter of a warp is warp % 4): lane m of the
-        // tile, 8-column chunks grp, grp + 2, grp + 4 ----
-        const int quarter = warp & 3, grp = (warp - 2) >> 2;
+        // ---- epilogue: three warps per lane quarter (warp % 4); lane m of the
+        // tile, columns 16 sub .. 16 sub + 15 read as two groups of 8 ----
+        const int quarter = warp & 3, sub = (warp - 2) >> 2;
         const int m = quarter * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
         const float two_f = __int_as_float((127 + P.f) << 23);
-        uint32_t range_bad = 0;
+        bool range_bad = false;
         int64_t Tt = 0;
         bool ok = true;
-        for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+        for (int t = W.t0; t < P.ntile && ok; t += W.tstep) {
             int rb, cb;
-            tile_blocks((int)(item % P.ntile), P.nrb, P.ncb, rb, cb);
-            const int64_t k0 = (item / P.ntile) * P.klen, k1 = min(P.nks, k0 + P.klen);
+            tile_blocks(t, P.nrb, P.ncb, rb, cb);
             const int row = rb * 128 + m;
-            long long acc[3][8];
+            long long acc[2][8];
+            uint32_t live = 0;  // bit 8 h + j: element (row, column 16 sub + 8 h + j) is read back
 #pragma unroll
-            for (int ci = 0; ci < 3; ++ci)
+            for (int h = 0; h < 2; ++h)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[ci][j] = 0;
-            for (int64_t kt = k0; kt < k1; kt += kKTile, ++Tt) {
-                const int b = (int)(Tt & 1);
-                if (!tc::mbar_wait_bounded(acc_full(b), (uint32_t)((Tt >> 1) & 1))) {
-                    ok = false;
-                    break;
+                for (int j = 0; j < 8; ++j) {
+                    acc[h][j] = 0;
+                    const int col = cb * kBN + 16 * sub + 8 * h + j;
+                    if (row < P.R && col < P.R && col >= row) live |= 1u << (8 * h + j);
                 }
-                tc::fence_after();
-#pragma unroll
-                for (int ci = 0; ci < 3; ++ci) {
-                    const int c = grp + 2 * ci;
-                    uint32_t r[wd::kLevels][8];
-#pragma unroll
-                    for (int lv = 0; lv < wd::kLevels; ++lv)
-                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                                     : "=r"(r[lv][0]), "=r"(r[lv][1]), "=r"(r[lv][2]), "=r"(r[lv][3]),
-                                       "=r"(r[lv][4]), "=r"(r[lv][5]), "=r"(r[lv][6]), "=r"(r[lv][7])
-                                     : "r"(lane_base + wd::acc_col(b, lv, kBN) + (uint32_t)(c * 8)));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    wd::init_chunk(lane_base, b, kBN, c);
-                    if (ci == 2) {
-                        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-                        tc::fence_before();
-                        tc::mbar_arrive(acc_empty(b));
+            for (int64_t kr = W.g; kr < nkr && ok; kr += W.ng) {
+                const int64_t k1 = min(P.nks, (kr + 1) * kKRange);
+                for (int64_t kt = kr * kKRange; kt < k1; kt += kKTile, ++Tt) {
+                    const int b = (int)(Tt & 1);
+                    if (!tc::mbar_wait_bounded(acc_full(b), (uint32_t)((Tt >> 1) & 1))) {
+                        ok = false;
+                        break;
                     }
+                    tc::fence_after();
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int col = cb * kBN + c * 8 + j;
-                        if (row < P.R && col < P.R && col >= row) {
-                            range_bad |= (r[3][j] >> 23) ^ (wd::kBias3 >> 23);
-                            acc[ci][j] += levels_to_int_f(r[0][j], r[1][j], r[2][j], r[3][j], r[4][j], P.f, two_f);
+                    for (int h = 0; h < 2; ++h) {
+                        uint32_t r[wd::kLevels][8];
+#pragma unroll
+                        for (int lv = 0; lv < wd::kLevels; ++lv)
+                            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                         : "=r"(r[lv][0]), "=r"(r[lv][1]), "=r"(r[lv][2]), "=r"(r[lv][3]),
+                                           "=r"(r[lv][4]), "=r"(r[lv][5]), "=r"(r[lv][6]), "=r"(r[lv][7])
+                                         : "r"(lane_base + wd::acc_col(b, lv, kBN) + (uint32_t)(16 * sub + 8 * h)));
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        if (h == 1) {  // the buffer is read: the next flush group may overwrite it
+                            tc::fence_before();
+                            tc::mbar_arrive(acc_empty(b));
                         }
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            if (live >> (8 * h + j) & 1u) {
+                                const float v2 = __uint_as_float(r[2][j]), v3 = __uint_as_float(r[3][j]);
+                                range_bad |= !(fabsf(v2) <= 256.f) || !(fabsf(v3) <= 1.f);  // |.| <= 2^24 units
+                                acc[h][j] += levels_to_int_f(__uint_as_float(r[0][j]), __uint_as_float(r[1][j]), v2, v3,
+                                                             __uint_as_float(r[4][j]), P.f, two_f);
+                            }
                     }
                 }
             }
             if (!ok) break;
 #pragma unroll
-            for (int ci = 0; ci < 3; ++ci)
+            for (int h = 0; h < 2; ++h)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int col = cb * kBN + (grp + 2 * ci) * 8 + j;
-                    if (row < P.R && col < P.R && col >= row)
-                        atomicAdd(P.G + (size_t)col * P.Rd + row, (unsigned long long)acc[ci][j]);
-                }
+                for (int j = 0; j < 8; ++j)
+                    if (live >> (8 * h + j) & 1u) {
+                        const int col = cb * kBN + 16 * sub + 8 * h + j;
+                        atomicAdd(P.G + (size_t)col * P.Rd + row, (unsigned long long)acc[h][j]);
+                    }
         }
         if (!ok) *s_fail = 1;
         if (range_bad) atomicOr(P.err, 2);
     }
-    // ---- exit: wait for every MMA this CTA issued, then free tensor memory ----
+    // ---- exit: wait for every MMA this CTA issued and every copy it started,
+    // then free tensor memory ----
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
@@ -468,7 +525,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rdm2_tc(TcArgs P) {
         tc::mma_commit(drain);
         if (!tc::mbar_wait_bounded(drain, 0u)) *s_fail = 1;
     }
-    if (warp == 0 && lane == 0) {  // every bulk copy issued has landed (at once unless a wait gave up)
+    if (warp == 0 && lane == 0) {  // at once unless a wait gave up
         for (int st = 0; st < kStages; ++st) {
             const int64_t fills = G_copied / kStages + (st < G_copied % kStages ? 1 : 0);
             if (fills > 0 && !tc::mbar_wait_bounded(full(st), (uint32_t)((fills - 1) & 1))) *s_fail = 1;
@@ -518,7 +575,7 @@ int rdm2_impl(fci_ctx *ctx, const T *C, double *g1_host, double *g2_host) {
     cudaStream_t s = ctx->stream;
     const size_t step_bytes = (size_t)6 * Rd * 32;
     size_t budget = ctx->opt.rdm2_chunk_bytes > 0 ? (size_t)ctx->opt.rdm2_chunk_bytes : ((size_t)1 << 30);
-    // whole flush groups per chunk: every 64-determinant group K-steps [4j, 4j + 4)
+    // whole flush groups per chunk: every 256-determinant group K-steps [16j, 16j + 16)
     // is accumulated in the same order whatever the chunking, so the result is
     // the same bits for every chunk size
     int64_t chunk = (int64_t)(budget / step_bytes);
@@ -585,7 +642,7 @@ int rdm2_impl(fci_ctx *ctx, const T *C, double *g1_host, double *g2_host) {
         FCI_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
         for (int64_t k0 = 0; k0 < nks && e == cudaSuccess; k0 += chunk) {
             const int64_t kn = std::min<int64_t>(chunk, nks - k0);
-            k_rdm2_digits<T><<<(unsigned)kn, 256, (size_t)Rd * 16 * sizeof(long long), s>>>(
+            k_rdm2_digits<T><<<(unsigned)kn, 256, (size_t)(Rd + 1) * 16 * sizeof(long long), s>>>(
                 C, ctx->A, ctx->B, n, Rd, emax, k0, N, reinterpret_cast<uint4 *>(dg));
             e = cudaGetLastError();
             if (e != cudaSuccess) break;
@@ -598,15 +655,13 @@ int rdm2_impl(fci_ctx *ctx, const T *C, double *g1_host, double *g2_host) {
             P.nrb = nrb;
             P.ncb = ncb;
             P.ntile = ntile;
-            // about six work items per CTA, whole 64-determinant flushes
-            int64_t kl = (kn * ntile + 6 * (int64_t)nsm - 1) / (6 * (int64_t)nsm);
-            kl = (kl + kKTile - 1) / kKTile * kKTile;
-            P.klen = (int)std::max<int64_t>(kKTile, std::min<int64_t>(kl, 1 << 20));
             P.f = f;
             P.G = reinterpret_cast<unsigned long long *>(G);
             P.err = d_err;
-            const int64_t items = ((kn + P.klen - 1) / P.klen) * ntile;
-            const unsigned grid = (unsigned)std::min<int64_t>(items, nsm);
+            // a multiple of ntile CTAs (one tile each) when the tiles fit the
+            // SMs, no more groups than K-ranges
+            const int64_t nkr = (kn + kKRange - 1) / kKRange;
+            const unsigned grid = ntile <= nsm ? (unsigned)(ntile * std::min<int64_t>(nsm / ntile, nkr)) : (unsigned)nsm;
             k_rdm2_tc<<<grid, kThreads, kSmem, s>>>(P);
             e = cudaGetLastError();
             prof_mark(ctx, rec, 2, s);
