@@ -22,6 +22,8 @@
 //    X = round(c 2^(45 - eD)); D's values are exact integer sums of these
 //    (|X_D| < 2^46, top digit in [-64, 64]), cut into six balanced 8-bit
 //    digits that bf16 holds exactly;
+//  * k_rdm2_fixed writes c's fixed-point integers once and k_rdm2_rows the D
+//    row (l n + k) of every replacement-list entry;
 //  * k_rdm2_digits writes, per K-step of 16 determinants, the six digit planes
 //    of the R rows in the tensor cores' K-major no-swizzle layout (8 x 8 core
 //    matrices of 128 bytes, 8-row groups 256 bytes apart), so that one bulk
@@ -61,7 +63,6 @@ using tc::kM;
 
 constexpr int kThreads = 448;        // warp 0 copies, warp 1 issues the MMAs, warps 2-13 epilogue
 constexpr int kEpiThreads = 384;
-constexpr int kEpiPerQuarter = 3;    // epilogue warps per tensor-memory lane quarter
 constexpr int kBN = 48;              // B rows per tile (the MMA's N per digit)
 constexpr int kStages = 6;           // K-steps of operands in flight
 constexpr int kKTile = 16;           // K-steps (256 determinants) per accumulator flush
@@ -148,16 +149,34 @@ __device__ __forceinline__ void entry_orbitals(uint32_t x, uint32_t t, uint32_t 
     }
 }
 
+// c in fixed point, once per call: Xc[i] = round(c_i 2^(45 - eD)).
+template <typename T>
+__global__ void k_rdm2_fixed(const T *__restrict__ c, int64_t n, int emax, long long *__restrict__ Xc) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) Xc[i] = fixed45(c[i], emax);
+}
+
+// rows[e * ns + x] = l n + k for the entry a+_k a_l |x> = sign |target> of
+// string x (the row of D that the entry feeds), entry-major like SpinTables::tab.
+__global__ void k_rdm2_rows(SpinTables S, int n, uint16_t *__restrict__ rows) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= S.ns * (int64_t)S.nsingle) return;
+    const uint32_t ent = S.tab[t];
+    int l, k;
+    entry_orbitals(S.str[t % S.ns], S.str[ent_target(ent)], ent_pair(ent), l, k);
+    rows[t] = (uint16_t)(l * n + k);
+}
+
 // One block per K-step of 16 determinants: the integers X_D of rows 0..Rd-1
 // in shared memory (determinant-major with an odd stride, so that the 16
 // determinants of one entry and the consecutive rows of the digit pass hit
 // distinct banks), then their six digit planes into dg (K-step ks - ks0 of
 // the chunk), plane t at byte (ks*6 + t) * Rd * 32, row r, determinant kk of
 // the K-step at (r/8) 256 + (kk/8) 128 + (r%8) 16 + (kk%8) 2.
-template <typename T>
-__global__ void __launch_bounds__(256) k_rdm2_digits(const T *__restrict__ c, SpinTables A, SpinTables B, int n,
-                                                     int Rd, int emax, int64_t ks0, int64_t N,
-                                                     uint4 *__restrict__ dg) {
+__global__ void __launch_bounds__(256) k_rdm2_digits(const long long *__restrict__ Xc, SpinTables A, SpinTables B,
+                                                     const uint16_t *__restrict__ rows_a,
+                                                     const uint16_t *__restrict__ rows_b, int n, int Rd, int64_t ks0,
+                                                     int64_t N, uint4 *__restrict__ dg) {
     extern __shared__ __align__(16) long long X[];  // [16][Rd + 1]
     __shared__ int64_t s_ka[16];
     __shared__ int s_kb[16];
@@ -180,15 +199,13 @@ __global__ void __launch_bounds__(256) k_rdm2_digits(const T *__restrict__ c, Sp
         if (ka < 0) continue;
         const int64_t kb = s_kb[kk];
         if (e == A.nsingle) {
-            X[kk * Rs + crow] = fixed45(c[ka * nsb + kb], emax);
+            X[kk * Rs + crow] = Xc[ka * nsb + kb];
             continue;
         }
-        const uint32_t ent = A.tab[(int64_t)e * A.ns + ka];
-        const uint32_t tg = ent_target(ent);
-        int l, k;
-        entry_orbitals(A.str[ka], A.str[tg], ent_pair(ent), l, k);
-        const long long v = fixed45(c[(int64_t)tg * nsb + kb], emax);
-        X[kk * Rs + l * n + k] = ent_negative(ent) ? -v : v;
+        const int64_t at = (int64_t)e * A.ns + ka;
+        const uint32_t ent = A.tab[at];
+        const long long v = Xc[(int64_t)ent_target(ent) * nsb + kb];
+        X[kk * Rs + rows_a[at]] = ent_negative(ent) ? -v : v;
     }
     __syncthreads();
     // beta entries: added
@@ -196,13 +213,10 @@ __global__ void __launch_bounds__(256) k_rdm2_digits(const T *__restrict__ c, Sp
         const int e = it >> 4, kk = it & 15;
         const int64_t ka = s_ka[kk];
         if (ka < 0) continue;
-        const int kb = s_kb[kk];
-        const uint32_t ent = B.tab[(int64_t)e * B.ns + kb];
-        const uint32_t tg = ent_target(ent);
-        int l, k;
-        entry_orbitals(B.str[kb], B.str[tg], ent_pair(ent), l, k);
-        const long long v = fixed45(c[ka * nsb + tg], emax);
-        X[kk * Rs + l * n + k] += ent_negative(ent) ? -v : v;
+        const int64_t at = (int64_t)e * B.ns + s_kb[kk];
+        const uint32_t ent = B.tab[at];
+        const long long v = Xc[ka * nsb + ent_target(ent)];
+        X[kk * Rs + rows_b[at]] += ent_negative(ent) ? -v : v;
     }
     __syncthreads();
     // digits: thread item it = (r/8) 16 + g 8 + r%8 owns 16 bytes at it*16 of each plane
@@ -563,6 +577,8 @@ __global__ void k_rdm2_finish(const long long *__restrict__ G, int Rd, int n, in
         g1[i - n4] = v;
 }
 
+inline unsigned grid_blocks(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16); }
+
 template <typename T>
 int rdm2_impl(fci_ctx *ctx, const T *C, double *g1_host, double *g2_host) {
     const int n = ctx->norb;
@@ -584,16 +600,22 @@ int rdm2_impl(fci_ctx *ctx, const T *C, double *g1_host, double *g2_host) {
     const size_t gbytes = sizeof(long long) * (size_t)Rd * Rd;
     const size_t obytes = sizeof(double) * (size_t)(n4 + n2);
     const size_t sbytes = sizeof(int) * 2 + sizeof(double) * kStatBlocks;
+    const size_t xbytes = sizeof(long long) * (size_t)N;
+    const size_t rbytes = sizeof(uint16_t) * ((size_t)ctx->A.ns * ctx->A.nsingle + (size_t)ctx->B.ns * ctx->B.nsingle + 8);
     int rc = FCI_OK;
     unsigned char *dg = (unsigned char *)dalloc(ctx, step_bytes * (size_t)chunk, &rc);
     long long *G = rc ? nullptr : (long long *)dalloc(ctx, gbytes, &rc);
     double *out = rc ? nullptr : (double *)dalloc(ctx, obytes, &rc);
     unsigned char *stat = rc ? nullptr : (unsigned char *)dalloc(ctx, sbytes, &rc);
+    long long *Xc = rc ? nullptr : (long long *)dalloc(ctx, xbytes, &rc);
+    uint16_t *rows = rc ? nullptr : (uint16_t *)dalloc(ctx, rbytes, &rc);
     auto release = [&]() {
         dfree(ctx, dg, step_bytes * (size_t)chunk);
         dfree(ctx, G, gbytes);
         dfree(ctx, out, obytes);
         dfree(ctx, stat, sbytes);
+        dfree(ctx, Xc, xbytes);
+        dfree(ctx, rows, rbytes);
     };
     if (rc) {
         release();
@@ -604,8 +626,8 @@ int rdm2_impl(fci_ctx *ctx, const T *C, double *g1_host, double *g2_host) {
     std::vector<double> part(kStatBlocks);
     int emax = 0, herr = 0;
     // per-kernel timing (fci_profile_*) when the call runs as one chunk
-    static const char *const names[4] = {"rdm2_stats", "rdm2_digits", "rdm2_tc", "rdm2_finish"};
-    const int rec = chunk >= nks ? prof_begin(ctx, s, 4, names) : -1;
+    static const char *const names[5] = {"rdm2_stats", "rdm2_prep", "rdm2_digits", "rdm2_tc", "rdm2_finish"};
+    const int rec = chunk >= nks ? prof_begin(ctx, s, 5, names) : -1;
     cudaError_t e = cudaMemsetAsync(stat, 0, sbytes, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(G, 0, gbytes, s);
     if (e == cudaSuccess) {
@@ -636,17 +658,24 @@ int rdm2_impl(fci_ctx *ctx, const T *C, double *g1_host, double *g2_host) {
         // the FP32 sums of c^2 may sit slightly below the exact norm: one bit of margin
         f -= 1;
         e2 += 1;
-        FCI_CUDA(opt_in_max_smem((const void *)k_rdm2_digits<T>, ctx->device));
+        FCI_CUDA(opt_in_max_smem((const void *)k_rdm2_digits, ctx->device));
+        const SpinTables &SA = ctx->A, &SB = ctx->B;
+        uint16_t *rows_a = rows, *rows_b = rows + (size_t)SA.ns * SA.nsingle;
+        k_rdm2_fixed<T><<<grid_blocks(N), 256, 0, s>>>(C, N, emax, Xc);
+        if (SA.nsingle) k_rdm2_rows<<<ceil_div(SA.ns * (int64_t)SA.nsingle, 256), 256, 0, s>>>(SA, n, rows_a);
+        if (SB.nsingle) k_rdm2_rows<<<ceil_div(SB.ns * (int64_t)SB.nsingle, 256), 256, 0, s>>>(SB, n, rows_b);
+        FCI_CUDA(cudaGetLastError());
+        prof_mark(ctx, rec, 1, s);
         FCI_CUDA(cudaFuncSetAttribute((const void *)k_rdm2_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));
         int nsm = 0;
         FCI_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
         for (int64_t k0 = 0; k0 < nks && e == cudaSuccess; k0 += chunk) {
             const int64_t kn = std::min<int64_t>(chunk, nks - k0);
-            k_rdm2_digits<T><<<(unsigned)kn, 256, (size_t)(Rd + 1) * 16 * sizeof(long long), s>>>(
-                C, ctx->A, ctx->B, n, Rd, emax, k0, N, reinterpret_cast<uint4 *>(dg));
+            k_rdm2_digits<<<(unsigned)kn, 256, (size_t)(Rd + 1) * 16 * sizeof(long long), s>>>(
+                Xc, SA, SB, rows_a, rows_b, n, Rd, k0, N, reinterpret_cast<uint4 *>(dg));
             e = cudaGetLastError();
             if (e != cudaSuccess) break;
-            prof_mark(ctx, rec, 1, s);
+            prof_mark(ctx, rec, 2, s);
             TcArgs P;
             P.dg = dg;
             P.nks = kn;
@@ -664,17 +693,18 @@ int rdm2_impl(fci_ctx *ctx, const T *C, double *g1_host, double *g2_host) {
             const unsigned grid = ntile <= nsm ? (unsigned)(ntile * std::min<int64_t>(nsm / ntile, nkr)) : (unsigned)nsm;
             k_rdm2_tc<<<grid, kThreads, kSmem, s>>>(P);
             e = cudaGetLastError();
-            prof_mark(ctx, rec, 2, s);
+            prof_mark(ctx, rec, 3, s);
         }
     }
     if (nonfinite || emax == 0 || !(norm2 > 0.0)) {  // nothing to contract: empty timing slots
         prof_mark(ctx, rec, 1, s);
         prof_mark(ctx, rec, 2, s);
+        prof_mark(ctx, rec, 3, s);
     }
     if (e == cudaSuccess) {
         k_rdm2_finish<<<ceil_div(n4 + n2, 256), 256, 0, s>>>(G, Rd, n, e2, nonfinite, out, out + n4);
         e = cudaGetLastError();
-        prof_mark(ctx, rec, 3, s);
+        prof_mark(ctx, rec, 4, s);
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(g2_host, out, sizeof(double) * n4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && g1_host) e = cudaMemcpyAsync(g1_host, out + n4, sizeof(double) * n2, cudaMemcpyDeviceToHost, s);
