@@ -78,7 +78,7 @@ typedef struct fci_options {
     int max_iter;        /* Davidson iteration limit (default 300) */
     int precision;       /* FCI_PREC_FP64 (default) or FCI_PREC_MIXED */
     double mixed_switch; /* MIXED: residual reduction between FP64 refinements (default 1e-2) */
-    double symmetry_tol; /* tolerance of the h1/eri symmetry check (default 1e-10) */
+    double symmetry_tol; /* absolute tolerance of the h1/eri symmetry check (default 1e-12) */
     int f32_splits;      /* FCI_F32 sigma_3 on the tensor cores: FP32 operands split into 2
                             (split-BF16x3, ~1e-5 relative) or 3 (split-BF16x6, ~FP32) bf16
                             slices; default 3 */
@@ -178,6 +178,21 @@ int fci_init(fci_ctx **ctx, int norb, int nalpha, int nbeta, const double *h1, c
 /* Release every device buffer of the context.  NULL is accepted.  (Resource
  * management; no counterpart in the paper.) */
 int fci_free(fci_ctx *ctx);
+
+/*
+ * The short form fci_init(norb, nalpha, nbeta, h1, eri): one context held by
+ * the library, built with the default options (fci_default_options) on the
+ * current device.  fci_init_default builds it, first freeing any earlier
+ * default context; fci_default_context returns it (NULL when none), for use
+ * with every other call; fci_free_default frees it (also when none exists).
+ * Arguments and errors as fci_init; on an error no default context remains.
+ * The three calls are serialised by a lock; calls that use the default
+ * context while another thread replaces or frees it are the caller's race.
+ * (Interface convenience; no counterpart in the paper.)
+ */
+int fci_init_default(int norb, int nalpha, int nbeta, const double *h1, const double *eri);
+fci_ctx *fci_default_context(void);
+int fci_free_default(void);
 
 /*
  * sigma = H c (Eq. 4-5), computed as sigma_1 + sigma_2 + sigma_3 (Eq. 8):

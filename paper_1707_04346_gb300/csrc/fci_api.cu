@@ -5,6 +5,8 @@
 #include <cstring>
 #include <new>
 
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace fci {
@@ -121,7 +123,7 @@ void fci_default_options(fci_options *opt) {
     opt->max_iter = 300;
     opt->precision = FCI_PREC_FP64;
     opt->mixed_switch = 1e-2;
-    opt->symmetry_tol = 1e-10;
+    opt->symmetry_tol = 1e-12;
     opt->f32_splits = 3;
     opt->same_spin_tc = 0;
     opt->f64_kernels = FCI_F64_AUTO;
@@ -202,6 +204,30 @@ int fci_free(fci_ctx *ctx) {
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return FCI_OK;
+}
+
+namespace {
+std::mutex g_default_mu;
+fci_ctx *g_default_ctx = nullptr;
+}  // namespace
+
+int fci_init_default(int norb, int nalpha, int nbeta, const double *h1, const double *eri) {
+    std::lock_guard<std::mutex> lock(g_default_mu);
+    fci_free(g_default_ctx);
+    g_default_ctx = nullptr;
+    return fci_init(&g_default_ctx, norb, nalpha, nbeta, h1, eri, nullptr);
+}
+
+fci_ctx *fci_default_context(void) {
+    std::lock_guard<std::mutex> lock(g_default_mu);
+    return g_default_ctx;
+}
+
+int fci_free_default(void) {
+    std::lock_guard<std::mutex> lock(g_default_mu);
+    const int rc = fci_free(g_default_ctx);
+    g_default_ctx = nullptr;
+    return rc;
 }
 
 int fci_sigma(fci_ctx *ctx, const void *c, void *sigma, int dtype, void *stream) {

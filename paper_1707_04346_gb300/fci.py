@@ -26,7 +26,7 @@ FCI_Q_NSINGLE_ALPHA, FCI_Q_NSINGLE_BETA, FCI_Q_NPAIR = 4, 5, 6
 FCI_Q_DEVICE_BYTES, FCI_Q_ITERATIONS, FCI_Q_SIGMA_CALLS, FCI_Q_DEVICE_ERROR = 7, 8, 9, 10
 
 EXPORTED = [
-    "fci_default_options", "fci_init", "fci_free", "fci_sigma", "fci_hdiag", "fci_davidson",
+    "fci_default_options", "fci_init", "fci_free", "fci_init_default", "fci_default_context", "fci_free_default", "fci_sigma", "fci_hdiag", "fci_davidson",
     "fci_davidson_log", "fci_rdm1", "fci_rdm2", "fci_get_strings", "fci_get_single_table", "fci_query",
     "fci_last_error", "fci_profile_enable", "fci_profile_read", "fci_profile_kernel_name",
     "fci_rdm1_noalloc", "fci_batch_init", "fci_batch_davidson", "fci_batch_sigma", "fci_batch_offset",
@@ -90,6 +90,12 @@ def load(path: str = LIB_PATH):
         lib.fci_init.argtypes = [ctypes.POINTER(vp), i32, i32, i32, vp, vp, ctypes.POINTER(fci_options)]
         lib.fci_free.restype = i32
         lib.fci_free.argtypes = [vp]
+        lib.fci_init_default.restype = i32
+        lib.fci_init_default.argtypes = [i32, i32, i32, vp, vp]
+        lib.fci_default_context.restype = vp
+        lib.fci_default_context.argtypes = []
+        lib.fci_free_default.restype = i32
+        lib.fci_free_default.argtypes = []
         lib.fci_sigma.restype = i32
         lib.fci_sigma.argtypes = [vp, vp, vp, i32, vp]
         lib.fci_hdiag.restype = i32
@@ -190,11 +196,13 @@ def default_options(**kw) -> fci_options:
 
 
 class FciContext:
-    """Owns a ``fci_ctx*``; freed by :func:`fci_free` or garbage collection."""
+    """Owns a ``fci_ctx*``; freed by :func:`fci_free` or garbage collection
+    (a view of the library's default context, ``owned=False``, frees nothing)."""
 
-    def __init__(self, handle: ctypes.c_void_p, norb: int, nalpha: int, nbeta: int):
+    def __init__(self, handle: ctypes.c_void_p, norb: int, nalpha: int, nbeta: int, owned: bool = True):
         self.handle = handle
         self.norb, self.nalpha, self.nbeta = norb, nalpha, nbeta
+        self.owned = owned
 
     @property
     def ndet(self) -> int:
@@ -224,9 +232,25 @@ def fci_init(norb: int, nalpha: int, nbeta: int, h1, eri, options: fci_options |
 
 
 def fci_free(ctx: FciContext):
-    if ctx.handle:
+    if ctx.handle and getattr(ctx, "owned", True):
         load().fci_free(ctx.handle)
-        ctx.handle = None
+    ctx.handle = None
+
+
+def fci_init_default(norb: int, nalpha: int, nbeta: int, h1, eri) -> FciContext:
+    """The short form fci_init(norb, nalpha, nbeta, h1, eri): (re)builds the
+    library's default context with default options and returns a view of it."""
+    lib = load()
+    h1 = np.ascontiguousarray(h1, dtype=np.float64)
+    eri = np.ascontiguousarray(eri, dtype=np.float64)
+    if h1.size != norb * norb or eri.size != norb ** 4:
+        raise ValueError("h1 must have norb^2 and eri norb^4 elements")
+    _check(lib.fci_init_default(norb, nalpha, nbeta, _np_ptr(h1), _np_ptr(eri)))
+    return FciContext(ctypes.c_void_p(lib.fci_default_context()), norb, nalpha, nbeta, owned=False)
+
+
+def fci_free_default():
+    _check(load().fci_free_default())
 
 
 def fci_sigma(ctx: FciContext, c, sigma, stream=None):

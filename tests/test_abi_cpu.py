@@ -52,7 +52,7 @@ def test_default_options(lib):
     o = fci.default_options()
     assert o.struct_size == ctypes.sizeof(fci.fci_options)
     assert o.max_subspace == 24 and o.max_iter == 300 and o.precision == fci.FCI_PREC_FP64
-    assert o.device == -1 and o.symmetry_tol == 1e-10 and o.f32_splits == 3
+    assert o.device == -1 and o.symmetry_tol == 1e-12 and o.f32_splits == 3
 
 
 def _init(lib, norb, na, nb, h1, eri, opt=None):
@@ -97,6 +97,10 @@ def test_bad_arguments_are_rejected_before_any_cuda_call(lib):
     assert lib.fci_sigma(None, None, None, 0, None) == fci.FCI_ERR_ARG
     assert lib.fci_query(None, 1) == -1
     assert lib.fci_rdm2(None, None, 0, None, None) == fci.FCI_ERR_ARG
+    # the short form: argument errors leave no default context behind
+    assert lib.fci_init_default(0, 0, 0, None, None) == fci.FCI_ERR_ARG
+    assert lib.fci_default_context() is None
+    assert lib.fci_free_default() == fci.FCI_OK
     assert lib.fci_free(None) == fci.FCI_OK
 
 

@@ -133,3 +133,22 @@ def test_mixed_davidson_fp64_tail(pkg):
     assert (log[:, 1] == 1).sum() > 0 and log[-1, 1] == 0  # FP32 phase first, exact at the end
     pkg.fci_free(ctx)
     pkg.fci_free(ref_ctx)
+
+
+def test_default_context_short_form(pkg, oracle_mod):
+    """fci_init(norb, nalpha, nbeta, h1, eri) over the library's default context:
+    the same sigma as an explicit context, replaced by a second init, freed."""
+    h1, eri = fi.make_integrals(6, 20)
+    ctx = pkg.fci_init_default(6, 3, 2, h1, eri)
+    c = fi.make_vector(ctx.ndet)
+    cd = torch.from_numpy(c).to(DEV)
+    s = torch.empty_like(cd)
+    pkg.fci_sigma(ctx, cd, s)
+    torch.cuda.synchronize()
+    assert np.abs(s.cpu().numpy() - oracle_mod.sigma(6, 3, 2, h1, eri, c)).max() <= 1e-12 * np.abs(s.cpu().numpy()).max()
+    ctx2 = pkg.fci_init_default(5, 2, 2, *fi.make_integrals(5, 20))  # replaces the first
+    assert ctx2.ndet == 100
+    del ctx  # a view: dropping it frees nothing
+    assert ctx2.ndet == 100
+    pkg.fci_free_default()
+    pkg.fci_free_default()  # nothing left: still fine
