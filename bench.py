@@ -598,9 +598,10 @@ def density_leg(pkg, norb, na, nb, h1, eri, c_dev, sigma_ms, peaks):
     pkg.fci_profile_enable(ctx1, False)
     pkg.fci_free(ctx1)
     km = np.median(prof[-2:], axis=0)  # ms per kernel
-    nrb, ncb = (Rd + 127) // 128, (Rd + 47) // 48
-    ntile = sum(ncb - (-(-(rb * 128 - 47) // 48) if rb * 128 > 47 else 0) for rb in range(nrb))
-    executed = 2.0 * 128 * 48 * 16 * 21 * ntile * nks  # MMA FLOP: 21 digit products per tile and K-step
+    bn = 48  # B rows per tile of the Gram kernel
+    nrb, ncb = (Rd + 127) // 128, (Rd + bn - 1) // bn
+    ntile = sum(ncb - (-(-(rb * 128 - (bn - 1)) // bn) if rb * 128 > bn - 1 else 0) for rb in range(nrb))
+    executed = 2.0 * 128 * bn * 16 * 21 * ntile * nks  # MMA FLOP: 21 digit products per tile and K-step
     useful = float(R) * R * 16 * nks  # one triangle of the FP64 Gram matrix, 2 FLOP per product
     itc = list(names).index("rdm2_tc")
     tc_s = km[itc] / 1e3
