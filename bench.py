@@ -51,13 +51,20 @@ FP32_LANES_PER_SM = 128  # FP32 operations issued per SM per clock
 NCU_TRAFFIC = {
     "sigma3_exact": ("paper_1707_04346_gb300/csrc/sigma.cu", "k_sigma3_exact(", "d3fba1cadf6cd31c", 610262016.0),
     "sigma3_tc": ("paper_1707_04346_gb300/csrc/sigma_tc_kernel.cuh", "k_sigma3_tc(", "878aabf229629b81", 124323328.0),
-    "sigma3_sliced": ("paper_1707_04346_gb300/csrc/sigma3_sliced_kernel.cuh", "k_sigma3_sliced(", "032cc9d38aaa6af8",
-                      975301888.0),
+    "sigma3_sliced": ("paper_1707_04346_gb300/csrc/sigma3_sliced_kernel.cuh", "k_sigma3_sliced(", "2f62dcb8acf96f61",
+                      978847232.0),
     # the wide kernels at CAS(14,14) (bench.py --f64-kernels wide)
     "sigma3_wide": ("paper_1707_04346_gb300/csrc/sigma_wide_kernel.cuh", "k_sigma_wide(", "3b63c3cbe309e741", 1016815808.0),
     "sigma1_wide": ("paper_1707_04346_gb300/csrc/sigma_wide_kernel.cuh", "k_sigma_wide(", "3b63c3cbe309e741", 2433141328.0),
     "sigma2_wide": ("paper_1707_04346_gb300/csrc/sigma_wide_kernel.cuh", "k_sigma_wide(", "3b63c3cbe309e741", 2452579616.0),
 }
+
+
+# The 2-RDM's Gram kernel, captured on CAS(12e,12o) (the CAS(14,14) launch holds 28 GB of digit
+# planes, above the capture size rule): DRAM bytes per byte of digit planes read once, scaled to
+# the workload's planes while the kernel's source is unchanged.
+RDM2_TC_TRAFFIC = ("paper_1707_04346_gb300/csrc/rdm2.cu", "k_rdm2_tc(", "dbb9c2a6acd29160",
+                   (2413767000.0 + 3238656.0) / (53361 * 6 * 152 * 32))
 
 
 def kernel_digest(path: str, marker: str) -> str:
@@ -606,6 +613,12 @@ def density_leg(pkg, norb, na, nb, h1, eri, c_dev, sigma_ms, peaks):
     itc = list(names).index("rdm2_tc")
     tc_s = km[itc] / 1e3
     peak = peaks.get("bf16_tflops")
+    planes = 6.0 * Rd * 32 * nks  # digit-plane bytes, read once
+    path, marker, digest, ratio = RDM2_TC_TRAFFIC
+    try:
+        traffic = planes * ratio if kernel_digest(path, marker) == digest else None
+    except (OSError, ValueError):
+        traffic = None
     return {
         "workload": f"CAS({na + nb}e,{norb}o), N = {c_dev.numel()}",
         "rdm1_ms": 1e3 * float(np.median(t1)), "rdm2_ms": 1e3 * float(np.median(t2)),
@@ -614,10 +627,41 @@ def density_leg(pkg, norb, na, nb, h1, eri, c_dev, sigma_ms, peaks):
         "rdm2_tc_roofline": {"bound": "tensor", "achieved": executed / tc_s / 1e12, "peak": peak,
                              "unit": "TFLOP/s", "frac": (executed / tc_s / 1e12 / peak) if peak else None,
                              "executed_flop": executed, "fp64_equivalent_tflops": useful / tc_s / 1e12,
+                             "traffic": traffic, "digit_plane_bytes": planes,
+                             "traffic_note": "DRAM bytes per digit-plane byte of a CAS(12e,12o) ncu capture "
+                                             "(profiles/rdm2_tc_cas12.md), scaled to this workload's planes",
                              "note": "executed bf16 MMA FLOP (6 digits, 21 products, 128 x 48 tiles) per launch / "
                                      "CUDA-event time; peak = measured burst bf16"},
         "timing": "whole blocking calls (allocation, statistics round trip, host copies included), median of 3",
     }
+
+
+def run_densities(args):
+    """Only the density step on the chosen workload (profiling the 2-RDM kernels):
+    one JSON line with the density leg and the FP64 sigma time it is compared with."""
+    import torch
+
+    import paper_1707_04346_gb300 as pkg
+
+    norb, na, nb, rank_eri = WORKLOADS[args.workload]
+    h1, eri = fi.make_integrals(norb, rank_eri)
+    ctx = pkg.fci_init(norb, na, nb, h1, eri)
+    c = fi.make_vector(ctx.ndet)
+    cd = torch.from_numpy(c / np.linalg.norm(c)).cuda()
+    sd = torch.empty_like(cd)
+    for _ in range(args.warmup):
+        pkg.fci_sigma(ctx, cd, sd)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        pkg.fci_sigma(ctx, cd, sd)
+    e1.record()
+    torch.cuda.synchronize()
+    sigma_ms = e0.elapsed_time(e1) / args.steps
+    pkg.fci_free(ctx)
+    print(json.dumps({"workload": workload_desc(args.workload), "sigma_ms": sigma_ms,
+                      "densities": density_leg(pkg, norb, na, nb, h1, eri, cd, sigma_ms, load_peaks())}))
+    return 0
 
 
 def run_ours(args):
@@ -853,6 +897,8 @@ def main():
                     help="CAS(18,18) solve on the Ms = 0 combinations of one spin parity (1: singlets)")
     ap.add_argument("--same-spin-tc", type=int, default=0, choices=(0, 1),
                     help="FP32 same-spin terms through intermediate strings on the tensor cores in the timed context")
+    ap.add_argument("--densities-only", action="store_true",
+                    help="run only the density step (fci_rdm1, fci_rdm2) on the workload and print its leg")
     ap.add_argument("--ref-from-mixed", action="store_true",
                     help="FP64 reference energies from an FP64 solve started at the mixed solution")
     args = ap.parse_args()
@@ -860,6 +906,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.densities_only and args.workload not in LARGE:
+        return run_densities(args)
     if args.workload in LARGE:
         return run_large(args)
     return run_ours(args)
