@@ -237,9 +237,16 @@ __global__ void __launch_bounds__(256) k_rdm2_digits(const long long *__restrict
     }
 }
 
-// x 2^k for k >= 0, else x / 2^-k rounded to nearest (ties up)
+// x 2^k for k >= 0, else x / 2^-k rounded to nearest, ties to even: the
+// rounding is applied once per flush, hundreds of thousands of times per
+// element, so it must not lean either way
 __device__ __forceinline__ long long shl_round(long long x, int k) {
-    return k >= 0 ? (long long)((unsigned long long)x << k) : (x + (1ll << (-k - 1))) >> -k;
+    if (k >= 0) return (long long)((unsigned long long)x << k);
+    const int r = -k;
+    const long long q = x >> r;                      // floor
+    const long long rem = x - (long long)((unsigned long long)q << r);  // in [0, 2^r)
+    const long long half = 1ll << (r - 1);
+    return q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
 }
 
 // The integer x = v 2^k of an FP32 value holding an exact integer in units

@@ -172,3 +172,32 @@ def test_rdm2_cas14_energy_traces_commutator(pkg):
     assert np.abs(lhs - rhs).max() <= 1e-12
     assert np.array_equal(g2, g2.transpose(3, 2, 1, 0))  # read from one integer per pair
     pkg.fci_free(ctx)
+
+
+def test_rdm2_cas16_energy_and_traces(pkg):
+    """CAS(16e,16o), 165.6 million determinants: 257 rows of D (three 128-row
+    tiles, 11 Gram tiles), digit planes in about 490 chunks of 1 GiB; the
+    energy from the densities equals c^T sigma (FP64 sigma of the large-space
+    kernels), gamma matches fci_rdm1 and the partial traces give N gamma."""
+    from fci_inputs import gpu
+
+    norb, ne = 16, 8
+    h1, eri = fi.make_integrals(norb, 100)
+    ctx = pkg.fci_init(norb, ne, ne, h1, eri)
+    c = torch.empty(ctx.ndet, dtype=torch.float64, device=DEV)
+    gpu.fill_pm1(c)
+    c /= torch.linalg.vector_norm(c)
+    s = torch.empty_like(c)
+    pkg.fci_sigma(ctx, c, s)
+    e_sigma = float(torch.dot(c, s))
+    del s
+    g1, g2 = pkg.fci_rdm2(ctx, c)
+    e_dens = float(np.sum(h1 * g1) + 0.5 * (np.einsum("pqrs,pqrs->", eri, g2) - np.einsum("pqqs,ps->", eri, g1)))
+    assert abs(e_dens - e_sigma) <= 1e-11 * max(1.0, abs(e_sigma))
+    assert np.abs(g1 - pkg.fci_rdm1(ctx, c)).max() <= 1e-12
+    assert np.abs(np.einsum("pqrr->pq", g2) - 2 * ne * g1).max() <= 1e-11
+    d = np.eye(norb)
+    lhs = g2 - g2.transpose(2, 3, 0, 1)
+    rhs = np.einsum("qr,ps->pqrs", d, g1) - np.einsum("ps,rq->pqrs", d, g1)
+    assert np.abs(lhs - rhs).max() <= 1e-12
+    pkg.fci_free(ctx)
