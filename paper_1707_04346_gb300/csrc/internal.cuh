@@ -114,6 +114,14 @@ struct fci_ctx {
     int sh1 = 0;
     int *d_eG = nullptr;            // device: largest biased exponent of C
     long long *wsacc = nullptr;     // [ndet] when ws32 is absent
+    // FP64 same-spin terms as dense sliced products (sigma_ss.cu): digit planes
+    // of each spin's same-spin Hamiltonian G_s with per-row exponents (the
+    // beta ones alias the alpha ones when both spins share one string space),
+    // and the per-call planes of C by rows and by columns with their exponents
+    unsigned char *ssG_a = nullptr, *ssG_b = nullptr;
+    int *ssE_a = nullptr, *ssE_b = nullptr;
+    unsigned char *ssCr = nullptr, *ssCc = nullptr;
+    int *ssEr = nullptr, *ssEc = nullptr;
     double *hdiag = nullptr;        // [ndet]
     int *d_err = nullptr;           // device error word (bounded waits that gave up)
     size_t bytes = 0;
@@ -199,6 +207,13 @@ bool sigma_wide_ok(const fci_ctx *ctx);
 int build_wide_tables(fci_ctx *ctx, const double *h1_host, const double *eri_host);
 void free_wide_tables(fci_ctx *ctx);
 int launch_sigma_f64_wide(fci_ctx *ctx, const double *C, double *sig, cudaStream_t s, int parity = 0);
+
+// sigma_ss.cu (FP64 sigma_1 / sigma_2 as dense sliced tensor-core products)
+bool sigma_ss_ok(const fci_ctx *ctx);
+int build_ss_tables(fci_ctx *ctx);
+void free_ss_tables(fci_ctx *ctx);
+// sigma += sigma_1 (which & 1) then sigma_2 (which & 2); profiling slots slot, slot + 1
+int launch_sigma_ss(fci_ctx *ctx, const double *C, double *sig, int which, cudaStream_t s, int rec, int slot);
 
 // davidson.cu
 int run_davidson(fci_ctx *ctx, int nroots, double tol, double *energies, void *vecs, const void *guess);

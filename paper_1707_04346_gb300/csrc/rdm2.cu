@@ -50,7 +50,7 @@
 // 2^60 units), so G is resolved to about 2^-59 ||c||^2.  Left out are the
 // digit products of weight >= 6 (below 2^-46 of the leading product, zero
 // mean) and c's fixed-point rounding (2^-46 of max |c|).
-#include "sigma_wide_kernel.cuh"
+#include "sliced_mma.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -60,6 +60,9 @@ namespace r2 {
 
 using sl::kSlices;
 using tc::kM;
+using sm::bulk_g2s;
+using sm::levels_to_int_f;
+using sm::mbar_expect_tx;
 
 constexpr int kThreads = 448;        // warp 0 copies, warp 1 issues the MMAs, warps 2-13 epilogue
 constexpr int kEpiThreads = 384;
@@ -235,64 +238,6 @@ __global__ void __launch_bounds__(256) k_rdm2_digits(const long long *__restrict
 #pragma unroll
         for (int s = 0; s < kSlices; ++s) base[(int64_t)s * Rd * 2 + it] = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
     }
-}
-
-// x 2^k for k >= 0, else x / 2^-k rounded to nearest, ties to even: the
-// rounding is applied once per flush, hundreds of thousands of times per
-// element, so it must not lean either way
-__device__ __forceinline__ long long shl_round(long long x, int k) {
-    if (k >= 0) return (long long)((unsigned long long)x << k);
-    const int r = -k;
-    const long long q = x >> r;                      // floor
-    const long long rem = x - (long long)((unsigned long long)q << r);  // in [0, 2^r)
-    const long long half = 1ll << (r - 1);
-    return q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
-}
-
-// The integer x = v 2^k of an FP32 value holding an exact integer in units
-// 2^-k, |x| <= 2^24: split as round(x 2^-12) 2^12 + rest by FP32 magic-number
-// rounding (both parts exact), without conversion instructions.
-__device__ __forceinline__ int exact_int24(float v, float two_k) {
-    constexpr float M = 12582912.0f;  // 1.5 2^23
-    constexpr int MB = 0x4B400000;
-    const float x = v * two_k;                     // exact (power of two)
-    const float t = fmaf(x, 0x1p-12f, M);
-    const int h = __float_as_int(t) - MB;          // round(x 2^-12), |.| <= 2^12
-    const float rest = fmaf(-(t - M), 4096.f, x);  // x - h 2^12, exact, |.| <= 2^11
-    return h * 4096 + (__float_as_int(rest + M) - MB);
-}
-
-// round(2^f (acc0 + ... + acc4)) of one element from its five accumulator
-// words: weights 0-3 hold exact integers in units 2^-8L (|.| <= 2^24 units);
-// 2^24 (acc0 + ... + acc3) = 2^16 (2^8 (acc0 + acc1)) + 2^24 (acc2 + acc3) is
-// then an exact integer.  acc4 is split into round(2^18 acc4), round(2^36 rest)
-// and the remainder (|.| <= 2^-37), each exact and each within the FP32
-// magic-number rounding.  16 <= f <= 52.
-__device__ __forceinline__ long long levels_to_int_f(float v0, float v1, float v2, float v3, float a4, int f,
-                                                     float two_f) {
-    constexpr float M = 12582912.0f;  // 1.5 2^23
-    constexpr int MB = 0x4B400000;
-    const long long hi = (long long)exact_int24(v0, 1.f) * 256 + exact_int24(v1, 256.f);
-    const long long mid = (long long)exact_int24(v2, 65536.f) * 256 + exact_int24(v3, 16777216.f);
-    const float t1 = fmaf(a4, 262144.f, M);
-    const int h1 = __float_as_int(t1) - MB;
-    const float q1 = fmaf(-(t1 - M), 0x1p-18f, a4);  // a4 - h1 2^-18, exact
-    const float t2 = fmaf(q1, 0x1p36f, M);
-    const int h2 = __float_as_int(t2) - MB;
-    const float q2 = fmaf(-(t2 - M), 0x1p-36f, q1);  // q1 - h2 2^-36, exact
-    const int h3 = __float_as_int(fmaf(q2, two_f, M)) - MB;
-    const long long lead = (hi << 16) + mid;         // 2^24 (acc0 + ... + acc3)
-    const int low = h1 * 262144 + h2;                // 2^36 (acc4 - remainder), |.| < 2^28
-    return shl_round(lead, f - 24) + shl_round(low, f - 36) + h3;
-}
-
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(mbar)
-                 : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
 }
 
 // Row block rb (128 rows) and column block cb (48 rows) of tile `tile` among

@@ -555,6 +555,15 @@ static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s, int pari
         // sigma = sigma_2 + parity sigma_2^T + sigma_3: FP64 with the sliced sigma_3 and the
         // double-float sigma_2, FP32 with the tensor-core kernels of large spaces
         if constexpr (sizeof(T) == 8) {
+            if (sliced && sigma_ss_ok(ctx)) {  // sigma_2 as a dense sliced product
+                static const char *const namesp[4] = {"sigma2_ss", "sigma1_sym", "slice_c", "sigma3_sliced"};
+                const int rec = prof_begin(ctx, s, 4, namesp);
+                FCI_CUDA(cudaMemsetAsync(sig, 0, sizeof(T) * (size_t)ctx->ndet, s));
+                if (int rc = launch_sigma_ss(ctx, (const double *)C, (double *)sig, 2, s, rec, 0)) return rc;
+                if (int rc = sym_pairs(sig, nsa, 8, parity, 0, s)) return rc;
+                prof_mark(ctx, rec, 1, s);
+                return launch_sigma3_sliced(ctx, C, sig, s, rec, 2, nullptr, 1);
+            }
             if (sliced) {
                 static const char *const namesp[4] = {"sigma2_cols", "sigma1_sym", "slice_c", "sigma3_sliced"};
                 const int rec = prof_begin(ctx, s, 4, namesp);
@@ -587,15 +596,20 @@ static int sigma_impl(fci_ctx *ctx, const T *C, T *sig, cudaStream_t s, int pari
             return FCI_OK;
         }
     }
-    const int rec = sliced ? prof_begin(ctx, s, 4, names4)
+    static const char *const names4ss[4] = {"slice_c", "sigma3_sliced", "sigma1_ss", "sigma2_ss"};
+    const bool ss = sliced && sigma_ss_ok(ctx);
+    const int rec = ss ? prof_begin(ctx, s, 4, names4ss)
+                    : sliced ? prof_begin(ctx, s, 4, names4)
                     : same_tc ? prof_begin(ctx, s, 3, names3tc)
                     : fusedR ? prof_begin(ctx, s, 2, names2) : prof_begin(ctx, s, 3, names3);
     const int slot3 = (fusedR && !same_tc) ? 1 : 2;
     int slot = 0;  // next profiling slot of the staged same-spin kernels
     int add1 = 0;  // sigma_1 adds to what sigma_3 wrote
     if (sliced) {
-        if constexpr (sizeof(T) == 8)
+        if constexpr (sizeof(T) == 8) {
             if (int rc = launch_sigma3_sliced(ctx, C, sig, s, rec, 0)) return rc;
+            if (ss) return launch_sigma_ss(ctx, (const double *)C, (double *)sig, 3, s, rec, 2);
+        }
         slot = 2;
         add1 = 1;
     }
