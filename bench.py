@@ -210,6 +210,14 @@ def kernel_work(name, norb, na, nb, N, sa, sb, nsa, nsb, peaks, f32_splits=3):
     if name in ("sigma1_rows", "sigma2_cols"):  # FP64 path: double-float, 12 FP32 operations per term
         return ("alu", 12.0 * nsame * N, "Tops/s", fp32_pipe, fp32src,
                 f"FP32 operations: 12 per term x {nsame} terms per determinant")
+    if name in ("sigma1_ss", "sigma2_ss"):  # FP64 same-spin terms as dense sliced products
+        # one GEMM of (strings of the summed spin) x (other spin) x (summed spin), 21 digit
+        # products, tiles of 128 x 48 rows (the plane rows padded to 384) and the FP64 diagonal
+        ns_sum = nsb if name == "sigma1_ss" else nsa
+        mt, nt = -(-nsb // 128), -(-nsa // 48)  # output tiles: beta strings x alpha strings
+        f = 21 * 2.0 * 128 * 48 * (-(-ns_sum // 16) * 16) * mt * nt
+        return ("tensor", f, "TFLOP/s", *bf16,
+                f"bf16 MMA FLOP: 21 digit products x 2 x 128 x 48 x {-(-ns_sum // 16) * 16} x {mt * nt} tiles")
     if name == "sigma12_f32":  # FP32 sigma_1 + sigma_2: one FMA per term
         return ("alu", 2.0 * nsame * N, "Tops/s", fp32_pipe, fp32src,
                 f"FP32 FMAs: {nsame} terms per determinant, two spins")

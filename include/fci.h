@@ -108,10 +108,12 @@ typedef struct fci_options {
                             projected onto the parity, and sigma_1 = parity sigma_2^T is
                             formed from sigma_2 by a transpose-add (Section 3.1's Ms = 0
                             combinations); fci_sigma itself is unaffected */
-    int f64_same_spin;   /* FCI_F64 sigma_1 and sigma_2 where the sliced sigma_3 runs:
+    int f64_same_spin;   /* FCI_F64 sigma_1 and sigma_2 with the tensor-core sigma_3:
                             FCI_SS_AUTO (default) as dense sliced products on the tensor cores
                             (below) when both string spaces hold at most 16384 strings,
-                            FCI_SS_DOUBLE_FLOAT the double-float kernels */
+                            FCI_SS_FAMILY the same-spin kernels of the f64_kernels family
+                            (double-float next to the per-row sigma_3, intermediate strings
+                            next to the wide kernels) */
     double rdm2_chunk_bytes; /* fci_rdm2: device memory for the digit planes of one chunk of
                             determinants (about 192 (norb^2 + 1) bytes per 16 determinants
                             per chunk); 0 = 1 GiB (default).  (Resource control; no
@@ -123,11 +125,11 @@ typedef struct fci_options {
  * of Eq. 6 between the strings of one spin, zeros included) on the bf16
  * tensor cores: every row of G_s and every row or column of C in 46-bit fixed
  * point relative to its own largest power of two, six 8-bit digits, exact
- * 64-bit integer sums.  Costs 12 bytes per element of each G_s (141 MB at
- * CAS(14,14)) at fci_init and the same for two copies of C.  The results are
- * bit-reproducible. */
+ * 64-bit integer sums; the diagonal of G_s in FP64.  Costs 12 bytes per
+ * element of each G_s (141 MB at CAS(14,14), 2 GB at CAS(16,16)) at fci_init
+ * and the same for two copies of C.  The results are bit-reproducible. */
 #define FCI_SS_AUTO 0
-#define FCI_SS_DOUBLE_FLOAT 1
+#define FCI_SS_FAMILY 1
 
 /* fci_options.f64_kernels: how the FCI_F64 sigma is computed.  All modes meet
  * the FP64 accuracy of Eq. 4-8's direct sum (the tests hold each to the same

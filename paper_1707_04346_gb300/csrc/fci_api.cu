@@ -160,8 +160,8 @@ int fci_init(fci_ctx **out, int norb, int nalpha, int nbeta, const double *h1, c
     if (o.spin_parity != 0 && nalpha != nbeta)
         return fail(FCI_ERR_ARG, "spin_parity needs n_alpha = n_beta (Ms = 0)");
     if (!(o.rdm2_chunk_bytes >= 0)) return fail(FCI_ERR_ARG, "rdm2_chunk_bytes must be >= 0");
-    if (o.f64_same_spin != FCI_SS_AUTO && o.f64_same_spin != FCI_SS_DOUBLE_FLOAT)
-        return fail(FCI_ERR_ARG, "f64_same_spin must be FCI_SS_AUTO or FCI_SS_DOUBLE_FLOAT");
+    if (o.f64_same_spin != FCI_SS_AUTO && o.f64_same_spin != FCI_SS_FAMILY)
+        return fail(FCI_ERR_ARG, "f64_same_spin must be FCI_SS_AUTO or FCI_SS_FAMILY");
     if (o.f64_kernels < FCI_F64_AUTO || o.f64_kernels > FCI_F64_WIDE)
         return fail(FCI_ERR_ARG, "f64_kernels must be FCI_F64_AUTO, FCI_F64_FMA, FCI_F64_SLICED or FCI_F64_WIDE");
     if (int rc = check_integrals(norb, h1, eri, o.symmetry_tol)) return rc;

@@ -401,7 +401,7 @@ bool sigma_ss_ok(const fci_ctx *ctx) { return ctx->ssG_a != nullptr; }
 
 int build_ss_tables(fci_ctx *ctx) {
     const SpinTables &A = ctx->A, &B = ctx->B;
-    if (ctx->opt.f64_same_spin == FCI_SS_DOUBLE_FLOAT) return FCI_OK;
+    if (ctx->opt.f64_same_spin == FCI_SS_FAMILY) return FCI_OK;
     if (A.nsingle == 0 || B.nsingle == 0 || A.ns > 16384 || B.ns > 16384) return FCI_OK;
     int rc = FCI_OK;
     cudaStream_t s = ctx->stream;

@@ -53,12 +53,14 @@ __global__ void k_transpose_u64(const unsigned long long *__restrict__ in, unsig
 
 // sigma[i] = acc[i] 2^(e2) as FP64 with e2 = *eG - 1022 + eC - 49 (NaN
 // everywhere when C held a non-finite value).  acc and sigma may alias.
-__global__ void k_convert_acc(const long long *acc, double *sig, int64_t n, const int *__restrict__ eG, int eC) {
+__global__ void k_convert_acc(const long long *acc, double *sig, int64_t n, const int *__restrict__ eG, int eC,
+                              int add = 0) {
     const int e = *eG;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const long long v = acc[i];
-        sig[i] = e == 0x7FF ? __longlong_as_double(0x7FF8000000000000ll) : sl::scaled_i64(v, e - 1022 + eC - 49);
+        const double x = e == 0x7FF ? __longlong_as_double(0x7FF8000000000000ll) : sl::scaled_i64(v, e - 1022 + eC - 49);
+        sig[i] = add ? sig[i] + x : x;
     }
 }
 
@@ -235,6 +237,40 @@ static unsigned grid_stride_blocks(int64_t n) {
 // sigma2, convert.
 int launch_sigma_f64_wide(fci_ctx *ctx, const double *C, double *sig, cudaStream_t s, int parity) {
     if (!sigma_wide_ok(ctx)) return fail(FCI_ERR_STATE, "wide FP64 sigma tables were not built for this context");
+    if (sigma_ss_ok(ctx)) {
+        // sigma_3 through the wide kernel; sigma_1 and sigma_2 as dense sliced products
+        const int64_t n = ctx->ndet;
+        unsigned long long *acc = ctx->ws32 ? reinterpret_cast<unsigned long long *>(ctx->ws32)
+                                            : reinterpret_cast<unsigned long long *>(ctx->wsacc);
+        auto sigma3 = [&](int rec, int slot, int add) -> int {
+            FCI_CUDA(cudaMemsetAsync(ctx->d_eG, 0, sizeof(int), s));
+            k_global_exponent<<<grid_stride_blocks(n), 256, 0, s>>>(C, n, ctx->d_eG);
+            k_slice_global<<<ceil_div(n, 256), 256, 0, s>>>(C, n, ctx->d_eG, ctx->cs0123, ctx->cs45);
+            FCI_CUDA(cudaGetLastError());
+            FCI_CUDA(cudaMemsetAsync(acc, 0, sizeof(long long) * (size_t)n, s));
+            prof_mark(ctx, rec, slot, s);
+            if (int rc = launch_wide<0>(ctx, ctx->A, ctx->B.ns, acc, s)) return rc;
+            prof_mark(ctx, rec, slot + 1, s);
+            k_convert_acc<<<grid_stride_blocks(n), 256, 0, s>>>(reinterpret_cast<const long long *>(acc), sig, n,
+                                                                 ctx->d_eG, ctx->eC, add);
+            FCI_CUDA(cudaGetLastError());
+            prof_mark(ctx, rec, slot + 2, s);
+            return FCI_OK;
+        };
+        if (parity != 0) {  // sigma_2, sigma_1 = parity sigma_2^T, then sigma_3 added
+            static const char *const namesp[5] = {"sigma2_ss", "sigma1_sym", "slice_c", "sigma3_wide", "convert"};
+            const int rec = prof_begin(ctx, s, 5, namesp);
+            FCI_CUDA(cudaMemsetAsync(sig, 0, sizeof(double) * (size_t)n, s));
+            if (int rc = launch_sigma_ss(ctx, C, sig, 2, s, rec, 0)) return rc;
+            if (int rc = sym_pairs(sig, ctx->A.ns, 8, parity, 0, s)) return rc;
+            prof_mark(ctx, rec, 1, s);
+            return sigma3(rec, 2, 1);
+        }
+        static const char *const names[5] = {"slice_c", "sigma3_wide", "convert", "sigma1_ss", "sigma2_ss"};
+        const int rec = prof_begin(ctx, s, 5, names);
+        if (int rc = sigma3(rec, 0, 0)) return rc;
+        return launch_sigma_ss(ctx, C, sig, 3, s, rec, 3);
+    }
     if (parity != 0 && ctx->A.nsingle > 0) {
         // C^T = parity C (one string space): sigma_2 into the accumulator, sigma_1 =
         // parity sigma_2^T by one integer transpose-add, then sigma_3 adds

@@ -418,7 +418,7 @@ int build_tables(fci_ctx *ctx, const double *h1_host, const double *eri_host) {
     }
     ctx->ndet = ctx->A.ns * ctx->B.ns;
     if ((rc = build_sliced_tables(ctx, h1_host, eri_host))) return rc;
-    if (sigma3_sliced_ok(ctx) && (rc = build_ss_tables(ctx))) return rc;
+    if ((sigma3_sliced_ok(ctx) || sigma_wide_ok(ctx)) && (rc = build_ss_tables(ctx))) return rc;
     if ((rc = alloc_sigma_workspace(ctx))) return rc;
     ctx->hdiag = (double *)dalloc(ctx, sizeof(double) * ctx->ndet, &rc);
     ctx->d_err = (int *)dalloc(ctx, sizeof(int), &rc);

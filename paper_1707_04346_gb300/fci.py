@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "libfci_gb300.so")
 FCI_F64, FCI_F32 = 0, 1
 FCI_PREC_FP64, FCI_PREC_MIXED = 0, 1
 FCI_F64_AUTO, FCI_F64_FMA, FCI_F64_SLICED, FCI_F64_WIDE = 0, 1, 2, 3
-FCI_SS_AUTO, FCI_SS_DOUBLE_FLOAT = 0, 1
+FCI_SS_AUTO, FCI_SS_FAMILY = 0, 1
 FCI_Q_NDET, FCI_Q_NSTR_ALPHA, FCI_Q_NSTR_BETA = 1, 2, 3
 FCI_Q_NSINGLE_ALPHA, FCI_Q_NSINGLE_BETA, FCI_Q_NPAIR = 4, 5, 6
 FCI_Q_DEVICE_BYTES, FCI_Q_ITERATIONS, FCI_Q_SIGMA_CALLS, FCI_Q_DEVICE_ERROR = 7, 8, 9, 10

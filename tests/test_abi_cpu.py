@@ -128,7 +128,8 @@ def test_option_validation_on_host(lib):
     h1, eri = fi.make_integrals(4, 10)
     for field, bad in (("f32_splits", 4), ("precision", 7), ("max_subspace", 1), ("max_iter", 0),
                        ("same_spin_tc", 2), ("f64_kernels", 4), ("basis_f32", 3), ("spin_parity", 2),
-                       ("spin_parity", -2), ("f32_row_global", 2), ("rdm2_chunk_bytes", -1.0)):
+                       ("spin_parity", -2), ("f32_row_global", 2), ("rdm2_chunk_bytes", -1.0),
+                       ("f64_same_spin", 2), ("f64_same_spin", -1)):
         o = fci.default_options()
         setattr(o, field, bad)
         assert _init(lib, 4, 2, 2, h1, eri, o)[0] == fci.FCI_ERR_ARG, field
@@ -146,7 +147,7 @@ def test_default_options_match_header(lib):
     assert o.struct_size == ctypes.sizeof(fci.fci_options)
     assert (o.max_subspace, o.max_iter, o.f32_splits, o.same_spin_tc) == (24, 300, 3, 0)
     assert (o.f64_kernels, o.basis_f32, o.spin_parity, o.f32_row_global) == (0, 0, 0, 0)
-    assert o.rdm2_chunk_bytes == 0.0
+    assert o.rdm2_chunk_bytes == 0.0 and o.f64_same_spin == 0
 
 
 def test_batch_rejects_bad_instances_on_host(lib):

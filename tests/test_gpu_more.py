@@ -75,13 +75,14 @@ def test_davidson_not_converged_reports_energies(pkg):
     pkg.fci_free(ctx)
 
 
-@pytest.mark.parametrize("mode,expect", [
-    (0, ["slice_c", "sigma3_sliced", "sigma1_rows", "sigma2_cols"]),  # FCI_F64_AUTO
-    (1, ["sigma1_rows", "sigma2_cols", "sigma3_exact"]),  # FCI_F64_FMA
+@pytest.mark.parametrize("mode,ss,expect", [
+    (0, 0, ["slice_c", "sigma3_sliced", "sigma1_ss", "sigma2_ss"]),  # FCI_F64_AUTO
+    (0, 1, ["slice_c", "sigma3_sliced", "sigma1_rows", "sigma2_cols"]),  # FCI_SS_FAMILY: double-float
+    (1, 0, ["sigma1_rows", "sigma2_cols", "sigma3_exact"]),  # FCI_F64_FMA
 ])
-def test_profile_api(pkg, mode, expect):
+def test_profile_api(pkg, mode, ss, expect):
     h1, eri = fi.make_integrals(10, 60)
-    ctx = pkg.fci_init(10, 5, 5, h1, eri, pkg.default_options(f64_kernels=mode))
+    ctx = pkg.fci_init(10, 5, 5, h1, eri, pkg.default_options(f64_kernels=mode, f64_same_spin=ss))
     c = torch.from_numpy(fi.make_vector(ctx.ndet)).to(DEV)
     s = torch.empty_like(c)
     pkg.fci_profile_enable(ctx, True)

@@ -1,8 +1,10 @@
 """GPU parity of the FP64 sigma kernels against the CPU oracle, in both
 kernel families (fci_options.f64_kernels):
 * FCI_F64_SLICED: sigma_3 from six 8-bit slices of C and of the integrals on
-  the bf16 tensor cores (an integer scatter), sigma_1 and sigma_2 in
-  double-float FP32 arithmetic;
+  the bf16 tensor cores (an integer scatter), sigma_1 and sigma_2 as dense
+  sliced products with the same-spin Hamiltonians on the tensor cores (or, with
+  fci_options.f64_same_spin = FCI_SS_FAMILY, in double-float FP32
+  arithmetic);
 * FCI_F64_FMA: FP64 fused multiply-adds throughout.
 Both are held to the same bars:
 * per element on small spaces: |d sigma_I| <= 1e-12 * sum_J |H_IJ||c_J|;
@@ -140,3 +142,27 @@ def test_sliced_refused_where_it_does_not_fit(pkg):
         with pytest.raises(pkg.FciError) as ei:
             pkg.fci_init(19, 1, 10, h1, eri, pkg.default_options(f64_kernels=mode))
         assert ei.value.code == pkg.fci.FCI_ERR_ARG
+
+
+@pytest.mark.parametrize("norb,na,nb", [(6, 3, 3), (7, 3, 4), (9, 4, 5), (8, 5, 3), (10, 1, 9)])
+def test_same_spin_dense_and_double_float(pkg, oracle_mod, norb, na, nb):
+    """sigma_1 and sigma_2 both ways (dense sliced products on the tensor cores,
+    the default; double-float kernels): each per element within the FP64 bar of
+    H c, the dense result bit-identical on a repeat, and the profile names show
+    which kernels ran."""
+    h1, eri = fi.make_integrals(norb, 40)
+    H = oracle_mod.hamiltonian(norb, na, nb, h1, eri)
+    c = fi.make_vector(H.shape[0])
+    ref = H @ c
+    bound = 1e-12 * (np.abs(H) @ np.abs(c)) + 1e-300
+    got = {}
+    for ss in (pkg.fci.FCI_SS_AUTO, pkg.fci.FCI_SS_FAMILY):
+        ctx = pkg.fci_init(norb, na, nb, h1, eri, pkg.default_options(f64_same_spin=ss))
+        pkg.fci_profile_enable(ctx, True)
+        got[ss] = sigma(pkg, ctx, c)
+        names, _ = pkg.fci_profile_read(ctx)
+        assert ("sigma1_ss" in names and "sigma2_ss" in names) == (ss == pkg.fci.FCI_SS_AUTO), names
+        assert np.all(np.abs(got[ss] - ref) <= bound), float(np.max(np.abs(got[ss] - ref) / bound))
+        if ss == pkg.fci.FCI_SS_AUTO:
+            assert np.array_equal(sigma(pkg, ctx, c), got[ss])
+        pkg.fci_free(ctx)

@@ -39,6 +39,7 @@ CASES = [  # (label, options)
     ("fp64", dict()),
     ("mixed", dict(precision=1)),
     ("fp64_wide", dict(f64_kernels=3)),
+    ("fp64_wide_family", dict(f64_kernels=3, f64_same_spin=1)),
     ("mixed_tc_same_spin", dict(precision=1, same_spin_tc=1)),
     ("mixed_f32basis", dict(precision=1, basis_f32=1, max_subspace=8)),
 ]

@@ -34,7 +34,8 @@ def pkg():
 
 def ctx_for(pkg, norb, na, nb, mode, rank=40, seed=1707):
     h1, eri = fi.make_integrals(norb, rank, seed)
-    return pkg.fci_init(norb, na, nb, h1, eri, pkg.default_options(f64_kernels=mode)), h1, eri
+    # the wide family's own same-spin kernels (intermediate strings), not the dense products
+    return pkg.fci_init(norb, na, nb, h1, eri, pkg.default_options(f64_kernels=mode, f64_same_spin=1)), h1, eri
 
 
 def sigma(pkg, ctx, c):
@@ -95,7 +96,7 @@ def test_wide_large_one_body(pkg, oracle_mod):
     norb, na, nb = 8, 4, 4
     h1, eri = fi.make_integrals(norb, 40, 1707)
     h1 = 40.0 * h1
-    ctx = pkg.fci_init(norb, na, nb, h1, eri, pkg.default_options(f64_kernels=WIDE))
+    ctx = pkg.fci_init(norb, na, nb, h1, eri, pkg.default_options(f64_kernels=WIDE, f64_same_spin=1))
     H = oracle_mod.hamiltonian(norb, na, nb, h1, eri)
     c = fi.make_vector(ctx.ndet)
     got = sigma(pkg, ctx, c)
@@ -151,7 +152,8 @@ def test_wide_cas14_sampled_rows(pkg, oracle_mod):
 
 def test_auto_cas16_takes_wide_path(pkg, oracle_mod):
     """CAS(16,16) under the default options: the per-row kernel does not fit,
-    so the FP64 sigma runs the wide kernels (profiled names), on sampled rows
+    so the FP64 sigma runs the wide sigma_3 and the dense same-spin products
+    (profiled names), on sampled rows
     against the oracle, with the trial vector filled on the device."""
     from fci_inputs import gpu
 
@@ -166,7 +168,7 @@ def test_auto_cas16_takes_wide_path(pkg, oracle_mod):
     pkg.fci_sigma(ctx, c, s)
     torch.cuda.synchronize()
     names, _ = pkg.fci_profile_read(ctx)
-    assert "sigma3_wide" in names and "sigma1_wide" in names and "sigma2_wide" in names
+    assert "sigma3_wide" in names and "sigma1_ss" in names and "sigma2_ss" in names
     rows = np.unique(np.concatenate([[0, 1, 12870, N // 2, N - 1],
                                      np.random.default_rng(16).integers(0, N, 195)]))
     got = s[torch.from_numpy(rows).to(DEV)].cpu().numpy()
