@@ -53,6 +53,8 @@ NCU_TRAFFIC = {
     "sigma3_tc": ("paper_1707_04346_gb300/csrc/sigma_tc_kernel.cuh", "k_sigma3_tc(", "878aabf229629b81", 124323328.0),
     "sigma3_sliced": ("paper_1707_04346_gb300/csrc/sigma3_sliced_kernel.cuh", "k_sigma3_sliced(", "2f62dcb8acf96f61",
                       978847232.0),
+    # sigma_1 as a dense sliced product (k_ss_tc; sigma_2 runs the same kernel with the operands swapped)
+    "sigma1_ss": ("paper_1707_04346_gb300/csrc/sigma_ss.cu", "k_ss_tc(", "9c370e9bb4171175", 2206744880.0),
     # the wide kernels at CAS(14,14) (bench.py --f64-kernels wide)
     "sigma3_wide": ("paper_1707_04346_gb300/csrc/sigma_wide_kernel.cuh", "k_sigma_wide(", "3b63c3cbe309e741", 1016815808.0),
     "sigma1_wide": ("paper_1707_04346_gb300/csrc/sigma_wide_kernel.cuh", "k_sigma_wide(", "3b63c3cbe309e741", 2433141328.0),
