@@ -136,13 +136,17 @@ typedef struct fci_options {
  * 1e-12 bars).
  *  FCI_F64_FMA     FP64 fused multiply-adds throughout (GB300's FP64 pipe).
  *  FCI_F64_AUTO    sigma_3 on the bf16 tensor cores from 8-bit slices where the
- *                  space fits the per-row sliced kernel (CAS(14,14)), with
- *                  sigma_1 and sigma_2 in double-float FP32 arithmetic (each
- *                  FP64 value as two FP32 parts, 48 significant bits;
+ *                  space fits the per-row sliced kernel (CAS(14,14)), else,
+ *                  when both spins have electrons, through the wide kernels
+ *                  (CAS(16,16), CAS(18,18)); sigma_1 and sigma_2 next to either
+ *                  as dense sliced products on the tensor cores where each
+ *                  string space holds at most 16384 strings (fci_options.
+ *                  f64_same_spin), else with the family's own kernels:
+ *                  double-float FP32 arithmetic next to the per-row sigma_3
+ *                  (each FP64 value as two FP32 parts, 48 significant bits;
  *                  error-free products and sums to within a few units of
- *                  2^-48); where it does not fit and both spins have
- *                  electrons, all three terms on the tensor cores through the
- *                  wide kernels (CAS(16,16), CAS(18,18)); else FP64 FMAs.
+ *                  2^-48), intermediate strings next to the wide sigma_3;
+ *                  where neither tensor-core sigma_3 applies, FP64 FMAs.
  *  FCI_F64_SLICED  as AUTO, but fci_init fails with FCI_ERR_ARG where neither
  *                  tensor-core FP64 path fits.
  *  FCI_F64_WIDE    the wide kernels on every space they cover (FCI_ERR_ARG
