@@ -221,7 +221,10 @@ int fci_free_default(void);
  *
  *  c, sigma  device vectors of N = N_alpha * N_beta elements of type dtype
  *            (FCI_F64 or FCI_F32); must not overlap.  sigma is overwritten.
- *  dtype     FCI_F64: FP64 arithmetic throughout.  FCI_F32: FP32 vectors;
+ *  dtype     FCI_F64: FP64 vectors and FP64 accuracy (fci_options.f64_kernels
+ *            and f64_same_spin say which kernels: tensor-core contractions of
+ *            8-bit digit slices with exact integer sums, double-float FP32
+ *            arithmetic, or FP64 FMAs).  FCI_F32: FP32 vectors;
  *            sigma_1/sigma_2 in FP32, sigma_3 on the tensor cores with bf16
  *            slices of the FP32 operands and FP32 accumulation (see
  *            fci_options.f32_splits); the low-precision phase of the mixed
@@ -231,13 +234,16 @@ int fci_free_default(void);
  *            E_ij E_kl); their adds are atomic, so FP32 results may differ in
  *            the last bits between calls.  FCI_F32 needs the replacement lists
  *            of both spins to have at most 96 entries (norb 18 at half
- *            filling) and at most 65408 strings per spin; FCI_F64 needs one
- *            beta row of C and sigma (2 N_beta doubles) in shared memory
- *            (N_beta <= about 14000, CAS(16,16)).
+ *            filling) and at most 65408 strings per spin; FCI_F64 covers
+ *            every space with at most 96 replacements per string and 255
+ *            orbital pairs on the tensor cores (CAS(18,18) included), beyond
+ *            that the FMA kernels, which need one beta row of C and sigma
+ *            (2 N_beta doubles) in shared memory.
  *  stream    cudaStream_t or NULL.  Asynchronous; allocates nothing (the
- *            workspaces of the large-space FP32 path, 8N bytes, and of the
- *            sliced FP64 sigma_3, 12N bytes, are made at fci_init), so it can
- *            be captured in a CUDA graph.  The context's workspaces are shared
+ *            workspaces of the large-space FP32 path, 8N bytes, of the sliced
+ *            FP64 sigma_3, 12N bytes, and of the dense same-spin products,
+ *            24N bytes, are made at fci_init), so it can be captured in a
+ *            CUDA graph.  The context's workspaces are shared
  *            by its calls: fci_sigma calls on one context must not overlap in
  *            time (issue them on one stream, or order the streams).
  * Errors: FCI_ERR_ARG (including the size limits above, reported on the host
