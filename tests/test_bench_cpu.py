@@ -47,3 +47,26 @@ def test_committed_traffic_entries_name_existing_kernels():
     for name, (path, marker, digest, nbytes) in bench.NCU_TRAFFIC.items():
         assert os.path.exists(os.path.join(bench.ROOT, path)), name
         assert len(digest) == 16 and nbytes > 0
+
+
+def test_every_profiled_kernel_of_the_default_pipelines_has_a_roofline():
+    """The profile slot names that fci_sigma's FP64 and FP32 pipelines record (the
+    names are string literals in the library's sources) all have an algorithmic
+    work entry, so the bench's roofline table covers each of them; the launch
+    counts per FP64 pipeline are at least one per slot."""
+    import re
+
+    peaks = {"bf16_tflops": 1937.6, "hbm_gbs": 6779.0}
+    src = ""
+    for f in ("sigma.cu", "sigma_wide.cu", "sigma3_sliced.cu"):
+        src += open(os.path.join(bench.ROOT, "paper_1707_04346_gb300", "csrc", f)).read()
+    names = set(re.findall(r'"(sigma[0-9a-z_]+|slice_c|transpose_slice|convert)"', src))
+    assert {"sigma1_ss", "sigma2_ss", "sigma3_sliced", "sigma3_wide", "slice_c"} <= names
+    uncovered = {"sigma1_sym"}  # the parity transpose-add: a copy, no algorithmic work entry
+    for n in sorted(names - uncovered):
+        w = bench.kernel_work(n, 14, 7, 7, 3432 * 3432, 56, 56, 3432, 3432, peaks)
+        assert w is not None, n
+        bound, amount, unit, peak, _, _ = w
+        assert bound in ("tensor", "hbm", "alu") and amount > 0 and peak > 0, n
+    for slots, launches in bench.LAUNCHES_PER_SIGMA.items():
+        assert launches >= len(slots)
